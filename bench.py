@@ -1,0 +1,392 @@
+#!/usr/bin/env python
+"""Benchmark of the contraction hot path on synthetic circuits (one JSON line on rank 0).
+
+Workloads (seeded; see paper_2108_06831_gb300/circuits.py):
+  state24   (default) 24-qubit 1D brickwork, depth 20 (U3 on every qubit + alternating CZ),
+            full 2^24 complex64 state per step; metric amplitudes/s
+  state10   10-qubit brickwork, depth 8, a batch of 512 circuits' worth of parameter sets
+  grad20    20-qubit hardware-efficient ansatz (400 parameters), TFIM energy forward plus
+            adjoint gradient over a batch of 64 parameter sets; metric grads/s
+
+Timing: W warm-up steps, then exactly K steps, each bracketed by CUDA events on the
+launching stream, with a write of a buffer larger than L2 between steps (untimed); the
+value is the units of all ranks over the maximum per-rank time.  Multi-GPU runs are
+independent replicas (the path has no exchange step).
+
+--impl reference times the FP64 oracle (the CPU program the parity tests use) on bounded
+samples of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "amplitudes/s, grads/s & % roofline; split-prec+batched vs plain FP32 at ≤1e-5 err"
+FP32_ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x (FMA = 2 flops) x max SM clock
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="state24", choices=["state24", "state10", "grad20"])
+    ap.add_argument("--tile", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ----------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- oracle (CPU) timing
+
+ORACLE_SNIPPET = r"""
+import json, sys, time
+sys.path.insert(0, {root!r})
+import numpy as np
+from paper_2108_06831_gb300 import circuits as C
+from oracle.statevector import basis_state, apply_matrix, gate_matrix
+from oracle import observables as OB
+kind = {kind!r}
+if kind == "state":
+    c, p = C.brickwork({n}, {depth}, {seed}, parameterized=True)
+    psi = basis_state(c.n_qubits, 0)
+    t0 = time.perf_counter()
+    done = 0
+    for g in c.gates:
+        psi = apply_matrix(psi, c.n_qubits, gate_matrix(c, g, p), g.qubits)
+        done += 1
+        if time.perf_counter() - t0 > {budget}:
+            break
+    dt = time.perf_counter() - t0
+    per_circuit = dt * len(c.gates) / done
+    print(json.dumps(dict(value=(1 << c.n_qubits) / per_circuit, gates=done, total_gates=len(c.gates), seconds=dt)))
+else:
+    c = C.hea({n}, 10)
+    H = C.tfim({n})
+    params = C.hea_params(c.n_params, 1, 4000)[0]
+    t0 = time.perf_counter()
+    e = OB.expectation(c, H, params)
+    dt = time.perf_counter() - t0
+    # parameter shift: 2 expectation evaluations per parameter
+    per_param = 2 * dt
+    print(json.dumps(dict(value=1.0 / per_param, seconds=dt, evals=1)))
+"""
+
+
+def run_oracle_sample(kind: str, n: int, depth: int, seed: int, budget: float):
+    code = ORACLE_SNIPPET.format(root=ROOT, kind=kind, n=n, depth=depth, seed=seed, budget=budget)
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1", CUDA_VISIBLE_DEVICES="")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=600)
+    if r.returncode != 0:
+        return None, r.stderr[-400:]
+    return json.loads(r.stdout.strip().splitlines()[-1]), None
+
+
+# ----------------------------------------------------------------------------- workloads
+
+WORKLOADS = {
+    "state24": dict(kind="state", n=24, depth=20, seed=1001, batch=1),
+    "state10": dict(kind="state", n=10, depth=8, seed=1000, batch=512),
+    "grad20": dict(kind="grad", n=20, depth=10, seed=4000, batch=64),
+}
+
+
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    wl = WORKLOADS[args.workload]
+    vals = []
+    info = None
+    for _ in range(args.warmup):
+        run_oracle_sample(wl["kind"], wl["n"], wl["depth"], wl["seed"], 2.0)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        info, err = run_oracle_sample(wl["kind"], wl["n"], wl["depth"], wl["seed"], 8.0)
+        if info is None:
+            print(json.dumps({"impl": "reference", "unavailable": f"oracle sample failed: {err}"}))
+            return 0
+        vals.append(info["value"])
+    wall = time.perf_counter() - t0
+    unit = "amplitudes/s" if wl["kind"] == "state" else "grads/s"
+    v = statistics.median(vals)
+    sample = (f"oracle state-vector FP64 on the first {info.get('gates')} of {info.get('total_gates')} gates, "
+              f"scaled to the whole circuit" if wl["kind"] == "state" else
+              "oracle: one FP64 expectation of one parameter set; parameter shift = 2 per gradient entry")
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": unit, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * wall / max(args.steps, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, **{k: wl[k] for k in ("n", "depth", "batch")}},
+            "cpu_baseline": {"value": v, "unit": unit, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return reference_arm(args)
+    wl = WORKLOADS[args.workload]
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    # the CPU baseline runs first, in a fresh process, before this process touches the GPU
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        info, err = run_oracle_sample(wl["kind"], wl["n"], wl["depth"], wl["seed"], 12.0)
+        unit = "amplitudes/s" if wl["kind"] == "state" else "grads/s"
+        if info is not None:
+            sample = (f"FP64 state-vector oracle, first {info['gates']} of {info['total_gates']} gates of the same "
+                      f"circuit ({info['seconds']:.1f} s, 1 thread), scaled to the whole circuit"
+                      if wl["kind"] == "state" else
+                      f"FP64 oracle expectation of one parameter set ({info['seconds']:.1f} s, 1 thread); a "
+                      f"parameter-shift gradient entry costs two")
+            cpu = {"value": info["value"], "unit": unit, "cores": 1, "kind": "oracle", "sample": sample}
+        else:
+            cpu = {"value": None, "unit": unit, "cores": 1, "kind": "oracle", "sample": f"failed: {err}"}
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    from paper_2108_06831_gb300 import circuits as C
+    from paper_2108_06831_gb300 import tn
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # 256 MiB > L2
+
+    hbm_peak, peak_kind = load_peaks()
+    if wl["kind"] == "state":
+        circ_p, params0 = C.brickwork(wl["n"], wl["depth"], wl["seed"], parameterized=True)
+        circ_f, _ = C.brickwork(wl["n"], wl["depth"], wl["seed"])
+        batch = wl["batch"]
+        params = np.tile(params0, (batch, 1))
+        ctr = tn.Contractor(circ_p, batch=batch, tile_qubits=args.tile, device=dev)
+        p_dev = torch.as_tensor(params, device=dev)
+        out = torch.empty((batch, 1 << wl["n"]), dtype=torch.complex64, device=dev)
+        units_per_step = batch * (1 << wl["n"])
+        unit = "amplitudes/s"
+
+        def step():
+            tn.contract_state(ctr.plan, p_dev, out, ctr.workspace)
+        launches_per_step = 1 + ctr.plan.stats()["n_passes"]
+        fixed = tn.Contractor(circ_f, batch=batch, tile_qubits=args.tile, device=dev)
+        fst = fixed.plan.stats()
+
+        def kernel_only():
+            tn.contract_state(fixed.plan, None, out, fixed.workspace)
+        kernel_launches = fst["n_passes"]
+        alg_bytes = fst["hbm_bytes"] * batch
+        alg_flops = fst["flops"] * batch
+    else:
+        circ = C.hea(wl["n"], wl["depth"])
+        batch = wl["batch"]
+        params = C.hea_params(circ.n_params, batch, wl["seed"])
+        ctr = tn.Contractor(circ, target=tn.TARGET_EXPECTATION, batch=batch, tile_qubits=args.tile, device=dev)
+        obs = tn.Observable(C.tfim(wl["n"]))
+        p_dev = torch.as_tensor(params, device=dev)
+        e_out = torch.empty(batch, dtype=torch.float64, device=dev)
+        g_out = torch.empty((batch, circ.n_params), dtype=torch.float64, device=dev)
+        units_per_step = batch * circ.n_params
+        unit = "grads/s"
+
+        def step():
+            tn.expectation(ctr.plan, obs, p_dev, e_out, ctr.workspace)
+            tn.expectation_backward(ctr.plan, obs, p_dev, None, g_out, ctr.workspace)
+        st = ctr.plan.stats()
+        launches_per_step = None
+        kernel_only = None
+
+    def timed(fn, k):
+        times = []
+        for _ in range(k):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            times.append((a, b))
+        torch.cuda.synchronize()
+        return [a.elapsed_time(b) for a, b in times]
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        ms = timed(step, args.steps)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    total_ms = sum(ms)
+    t_max = total_ms
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    value = units_per_step * args.steps * world / (t_max / 1000.0)
+    assert tn.sync_status() == tn.OK
+
+    line = {"metric": METRIC, "value": value, "unit": unit, "n_gpus": world, "steps": args.steps,
+            "warmup": max(args.warmup, 3), "ms_per_step": t_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "c64 (f32)", "data": "synthetic",
+            "config": {"workload": args.workload, "n_qubits": wl["n"], "depth": wl["depth"], "batch": batch,
+                       "tile_qubits": ctr.plan.stats()["tile_qubits"],
+                       "l2": "256 MiB buffer written between timed steps (untimed)",
+                       "parallelism": f"replicas x{world}"},
+            "clocks": clk.summary()}
+    if launches_per_step is not None:
+        line["gpu_launches"] = launches_per_step * args.steps
+
+    # roofline of the dominant kernel (fused gate-apply): the fixed-angle plan launches only it
+    if kernel_only is not None:
+        for _ in range(3):
+            kernel_only()
+        kms = timed(kernel_only, args.steps)
+        avg_launch_ms = statistics.mean(kms) / kernel_launches
+        bytes_per_launch = alg_bytes / kernel_launches
+        flops_per_launch = alg_flops / kernel_launches
+        gbs = bytes_per_launch / (avg_launch_ms / 1000) / 1e9
+        tfl = flops_per_launch / (avg_launch_ms / 1000) / 1e12
+        hbm_frac = gbs / hbm_peak
+        alu_frac = tfl / FP32_ALU_PEAK_TFLOPS
+        if alu_frac >= hbm_frac:
+            line["roofline"] = {"bound": "alu", "achieved": tfl, "peak": FP32_ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
+                                "frac": alu_frac, "traffic": None,
+                                "kernel": "k_fwd_pass<4> (fused gate-apply)",
+                                "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 x 2070 MHz",
+                                "also": {"hbm_gbs": gbs, "hbm_frac": hbm_frac, "hbm_peak": hbm_peak,
+                                         "hbm_peak_source": peak_kind}}
+        else:
+            line["roofline"] = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": hbm_frac,
+                                "traffic": None, "kernel": "k_fwd_pass<4> (fused gate-apply)",
+                                "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})",
+                                "also": {"tflops": tfl, "alu_frac": alu_frac}}
+        line["roofline"]["launches_per_step"] = kernel_launches
+        line["roofline"]["avg_launch_ms"] = avg_launch_ms
+
+    # end to end through the public API with host buffers
+    if not args.no_e2e and wl["kind"] == "state":
+        h_params = torch.as_tensor(params).pin_memory()
+        h_out = torch.empty((batch, 1 << wl["n"]), dtype=torch.complex64).pin_memory()
+
+        def e2e_step():
+            p_dev.copy_(h_params, non_blocking=True)
+            tn.contract_state(ctr.plan, p_dev, out, ctr.workspace)
+            h_out.copy_(out, non_blocking=True)
+        for _ in range(3):
+            e2e_step()
+        ems = timed(e2e_step, args.steps)
+        line["e2e"] = {"value": units_per_step * args.steps / (sum(ems) / 1000), "unit": unit,
+                       "h2d_bytes_per_step": int(h_params.numel() * 8),
+                       "d2h_bytes_per_step": int(h_out.numel() * 8)}
+    elif not args.no_e2e:
+        h_params = torch.as_tensor(params).pin_memory()
+        h_g = torch.empty_like(g_out, device="cpu").pin_memory()
+        h_e = torch.empty_like(e_out, device="cpu").pin_memory()
+
+        def e2e_step():
+            p_dev.copy_(h_params, non_blocking=True)
+            step()
+            h_e.copy_(e_out, non_blocking=True)
+            h_g.copy_(g_out, non_blocking=True)
+        for _ in range(3):
+            e2e_step()
+        ems = timed(e2e_step, args.steps)
+        line["e2e"] = {"value": units_per_step * args.steps / (sum(ems) / 1000), "unit": unit,
+                       "h2d_bytes_per_step": int(h_params.numel() * 8),
+                       "d2h_bytes_per_step": int((h_g.numel() + h_e.numel()) * 8)}
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,246 @@
+/*
+ * tn.h - C ABI of libtnq: GB300 (sm_103a) contraction of quantum-circuit tensor networks.
+ *
+ * The problem follows "Tensor Networks for Simulating Quantum Circuits on FPGAs"
+ * (arXiv 2108.06831):
+ *   - a register of N qubits evolves by gates applied in sequence, each a unitary
+ *     acting as psi' = U psi, multi-qubit operators being Kronecker products (Sec. 2.1);
+ *   - the circuit is a tensor network whose open legs are the state's indices
+ *     (Sec. 2.2.2, Eq. 2.3); closing those legs with a final basis state gives one
+ *     amplitude (Sec. 2.2.3);
+ *   - contracting a pair of tensors is a sum over their shared indices, i.e. a
+ *     (batched) matrix product once the legs are grouped (Sec. 2.2.1, Eq. 2.2), and
+ *     the contraction order is a free choice planned ahead (Sec. 2.2.3, Sec. 3).
+ *
+ * Conventions used by every entry point:
+ *   - qubit q of an N-qubit register is bit (N-1-q) of a basis index (most significant
+ *     first: |00>,|01>,|10>,|11> are |0>..|3>, Sec. 2.1); bitstrings are uint64 with the
+ *     same mapping (N <= 63);
+ *   - states and amplitudes are complex64, interleaved (re, im) float pairs; a batch of B
+ *     states is B consecutive vectors of 2^N entries;
+ *   - a two-qubit gate on (a, b) has a 4x4 matrix indexed 2*bit(a) + bit(b);
+ *   - parameters are float64, laid out [batch][n_params]; gradients likewise.
+ *
+ * Ownership and errors:
+ *   - the caller owns every device buffer and the stream; the library owns the opaque
+ *     handles (circuit, plan, observable) and their device-side tables, which it
+ *     allocates when a plan or observable is built and frees in tn_free_*;
+ *   - calls that take a stream only enqueue work on it (asynchronous); none allocates
+ *     device memory; none throws across the ABI;
+ *   - argument checks return a status at once and leave the stream untouched; the text
+ *     of the last error on the calling thread is in tn_last_error();
+ *   - a device-side failure (a bounded wait that ran out, a non-finite result) is
+ *     recorded in a per-device status word and reported by tn_sync_status().
+ */
+#ifndef TNQ_TN_H
+#define TNQ_TN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* A CUDA stream (cudaStream_t); NULL means the legacy default stream. */
+typedef struct CUstream_st *tn_stream_t;
+
+typedef enum {
+  TN_OK = 0,
+  TN_ERR_INVALID_ARG = 1, /* a pointer, size, qubit index or option is out of range */
+  TN_ERR_UNSUPPORTED = 2, /* valid request this build does not implement (message says which) */
+  TN_ERR_OOM = 3,         /* a plan/observable table could not be allocated */
+  TN_ERR_CUDA = 4,        /* a CUDA runtime call failed (message holds cudaGetErrorString) */
+  TN_ERR_TIMEOUT = 5,     /* a device-side bounded wait ran out (from tn_sync_status) */
+  TN_ERR_NUMERIC = 6      /* a device-side non-finite value was detected (from tn_sync_status) */
+} tn_status;
+
+/* Gate kinds.  Matrices (Sec. 2.1 leaves them implicit; these are the textbook ones):
+ * H = [[1,1],[1,-1]]/sqrt2; X, Y, Z Pauli; S = diag(1,i); SDG = S^dagger; T = diag(1,e^{i pi/4});
+ * TDG = T^dagger; SX = RX(pi/2); SY = RY(pi/2); SW = exp(-i pi/4 (X+Y)/sqrt2);
+ * RX/RY/RZ(t) = exp(-i t P/2); U3(t,p,l) = [[cos t/2, -e^{il} sin t/2], [e^{ip} sin t/2, e^{i(p+l)} cos t/2]];
+ * CZ = diag(1,1,1,-1); CNOT(control = q[0], target = q[1]); CP(p) = diag(1,1,1,e^{ip}); SWAP;
+ * MAT1 / MAT2: a caller-supplied 2x2 / 4x4 matrix (row-major complex128, copied at build time). */
+typedef enum {
+  TN_GATE_H = 0, TN_GATE_X = 1, TN_GATE_Y = 2, TN_GATE_Z = 3,
+  TN_GATE_S = 4, TN_GATE_SDG = 5, TN_GATE_T = 6, TN_GATE_TDG = 7,
+  TN_GATE_SX = 8, TN_GATE_SY = 9, TN_GATE_SW = 10,
+  TN_GATE_RX = 11, TN_GATE_RY = 12, TN_GATE_RZ = 13, TN_GATE_U3 = 14,
+  TN_GATE_CZ = 15, TN_GATE_CNOT = 16, TN_GATE_CP = 17, TN_GATE_SWAP = 18,
+  TN_GATE_MAT1 = 19, TN_GATE_MAT2 = 20,
+  TN_GATE_KIND_COUNT = 21
+} tn_gate_kind;
+
+/* One gate of a circuit (host memory, read during tn_build_from_circuit only).
+ *   kind       tn_gate_kind
+ *   q          qubit indices; q[1] ignored for one-qubit kinds
+ *   param_idx  -1: angles are taken from angle[]; >= 0: the gate reads its angles
+ *              from params[param_idx .. param_idx + arity - 1] at contraction time
+ *              (arity 3 for U3, 1 for RX/RY/RZ/CP; invalid for fixed kinds)
+ *   angle      fixed angles (U3: theta, phi, lambda)
+ *   mat        MAT1/MAT2 only: row-major complex128 (re, im pairs), 2x2 or 4x4 */
+typedef struct {
+  int32_t kind;
+  int32_t q[2];
+  int32_t param_idx;
+  double angle[3];
+  const double *mat;
+} tn_gate;
+
+typedef struct tn_circuit tn_circuit;       /* opaque, library-owned, host only */
+typedef struct tn_plan tn_plan;             /* opaque, library-owned, holds device tables */
+typedef struct tn_observable tn_observable; /* opaque, library-owned, holds device tables */
+
+typedef enum { TN_TARGET_STATE = 0, TN_TARGET_AMPLITUDES = 1, TN_TARGET_EXPECTATION = 2 } tn_target;
+
+/* Arithmetic of dense pairwise merges (batched complex GEMM):
+ *   FP32        CUDA-core FFMA, FP32 accumulate (the plain reference);
+ *   3XTF32      tcgen05 kind::tf32, a = hi + lo split, hi*hi + hi*lo + lo*hi, FP32 accumulate in TMEM;
+ *   SPLIT_BF16  tcgen05 kind::f16 (bf16), a = a0 + a1 + a2 split, the 6 products with i + j <= 2,
+ *               FP32 accumulate in TMEM. */
+typedef enum { TN_PREC_FP32 = 0, TN_PREC_3XTF32 = 1, TN_PREC_SPLIT_BF16 = 2 } tn_precision;
+
+#define TN_PLAN_HOST_ONLY 1 /* plan without touching the GPU: only tn_plan_get_stats may use it */
+
+typedef struct {
+  int32_t target;                /* tn_target: what the plan will be used for */
+  int32_t precision;             /* tn_precision of dense merges */
+  int32_t batch;                 /* parameter sets (states) per call, >= 1 */
+  int32_t tile_qubits;           /* 0 = automatic; qubits held on chip per tile of the fused gate-apply kernel */
+  int32_t max_intermediate_log2; /* 0 = 28; largest intermediate tensor (complex64 entries) a plan may create */
+  int32_t flags;                 /* TN_PLAN_* bits */
+  uint64_t seed;                 /* planner tie-break seed */
+  int64_t reserved[6];           /* must be zero */
+} tn_plan_opts;
+
+/* Plan summary (for measurement and tests). */
+typedef struct {
+  int32_t n_qubits;
+  int32_t n_params;
+  int64_t n_gates;
+  int32_t n_passes;     /* launches of the fused gate-apply kernel per contraction */
+  int32_t n_phases;     /* register remappings summed over passes */
+  int64_t n_ops;        /* register-level gate operations over all phases */
+  int32_t tile_qubits;  /* qubits per on-chip tile */
+  int32_t reg_qubits;   /* qubits held in registers per thread during a phase */
+  double hbm_bytes;     /* algorithmic HBM bytes of one tn_contract_state call (per batch element) */
+  double flops;         /* algorithmic FP32 flops of one tn_contract_state call (per batch element) */
+  int32_t n_bwd_passes; /* passes of the adjoint sweep */
+  int32_t reserved[7];
+} tn_plan_stats;
+
+/* Pauli sum H = sum_t coef[t] * P_t (host memory, read during tn_build_observable only).
+ *   paulis[t * n_qubits + q] in {0 = I, 1 = X, 2 = Y, 3 = Z} is the factor on qubit q. */
+typedef struct {
+  int32_t n_terms;
+  const double *coef;
+  const uint8_t *paulis;
+} tn_pauli_sum;
+
+/* ---------------------------------------------------------------------------------------
+ * Network construction and planning (host; not hot).
+ * ------------------------------------------------------------------------------------- */
+
+/* Build the network of an n_qubits circuit (Sec. 2.2.2: gate tensors joined to the
+ * register's input legs |init_basis>).  gates[0..n_gates) in time order, host memory.
+ * Returns TN_ERR_INVALID_ARG for n_qubits outside [1, 34], a bad kind or qubit, equal
+ * qubits of a two-qubit gate, a parameter index on a fixed kind, init_basis >= 2^n. */
+tn_status tn_build_from_circuit(int32_t n_qubits, const tn_gate *gates, int64_t n_gates,
+                                uint64_t init_basis, tn_circuit **out);
+/* Number of float64 parameters per batch element the circuit reads (max param_idx + arity). */
+tn_status tn_circuit_num_params(const tn_circuit *c, int32_t *n_params);
+void tn_free_circuit(tn_circuit *c);
+
+/* Plan the contraction (Sec. 2.2.3 / Sec. 3: the order is chosen ahead of evaluation):
+ * groups the gates into passes of the fused gate-apply kernel, and within a pass into
+ * register phases, honouring every gate's dependencies; also plans the adjoint sweep.
+ * Allocates and uploads the plan's device tables on the current CUDA device unless
+ * opts->flags has TN_PLAN_HOST_ONLY.  opts may be NULL (defaults). */
+tn_status tn_plan_contraction(const tn_circuit *c, const tn_plan_opts *opts, tn_plan **out);
+/* Device workspace (bytes) that every contraction call of this plan needs. */
+tn_status tn_plan_workspace_bytes(const tn_plan *p, size_t *bytes);
+tn_status tn_plan_get_stats(const tn_plan *p, tn_plan_stats *stats);
+void tn_free_plan(tn_plan *p);
+
+/* Prepare a Pauli-sum observable on n_qubits (uploads its reduction tables). */
+tn_status tn_build_observable(int32_t n_qubits, const tn_pauli_sum *H, tn_observable **out);
+void tn_free_observable(tn_observable *o);
+
+/* ---------------------------------------------------------------------------------------
+ * Contraction (device; asynchronous on stream s).
+ * ------------------------------------------------------------------------------------- */
+
+/* Full state: state_dev[b] = U_G(theta_b) ... U_1(theta_b) |init_basis>, b < batch
+ * (Sec. 2.2.2, Eq. 2.3: every output leg left open).
+ *   params_dev     float64 [batch][n_params] device, or NULL when n_params == 0
+ *   state_dev      complex64 [batch][2^N] device, written (no input contents needed)
+ *   workspace_dev  >= tn_plan_workspace_bytes device bytes, or NULL when that is 0 */
+tn_status tn_contract_state(const tn_plan *p, const double *params_dev, void *state_dev,
+                            void *workspace_dev, tn_stream_t s);
+
+/* Single amplitudes <x_i| C |init_basis> (Sec. 2.2.3: output legs closed by basis states).
+ *   bitstrings_dev uint64 [n_bitstrings] device (bit N-1-q = qubit q), each < 2^N
+ *   amps_dev       complex64 [batch][n_bitstrings] device, written
+ * The batch of parameter sets and the batch of bitstrings are independent. */
+tn_status tn_contract_amplitudes(const tn_plan *p, const double *params_dev,
+                                 const uint64_t *bitstrings_dev, int64_t n_bitstrings,
+                                 void *amps_dev, void *workspace_dev, tn_stream_t s);
+
+/* Expectation values out_dev[b] = <psi_b| H |psi_b> (float64 [batch], device), where
+ * psi_b is the contracted state; the final reduction accumulates in FP64. */
+tn_status tn_expectation(const tn_plan *p, const tn_observable *H, const double *params_dev,
+                         double *out_dev, void *workspace_dev, tn_stream_t s);
+
+/* Adjoint gradient: grad_params_dev[b][k] = grad_out_dev[b] * d<H>_b / d theta_{b,k}
+ * (float64, device; overwritten).  Recomputes the forward state, forms lambda = H psi and
+ * sweeps the gates in reverse (psi <- U^dagger psi, g += 2 Re <lambda| dU |psi>,
+ * lambda <- U^dagger lambda).  grad_out_dev may be NULL (treated as all ones). */
+tn_status tn_expectation_backward(const tn_plan *p, const tn_observable *H, const double *params_dev,
+                                  const double *grad_out_dev, double *grad_params_dev,
+                                  void *workspace_dev, tn_stream_t s);
+
+/* ---------------------------------------------------------------------------------------
+ * Kernels exposed on their own (composable; used for measurement).
+ * ------------------------------------------------------------------------------------- */
+
+/* <psi_b| H |psi_b> for given states (complex64 [batch][2^N] device) into out_dev
+ * (float64 [batch] device).  Partial sums go to workspace_dev, which must hold
+ * tn_state_expectation_workspace_bytes(...) bytes. */
+tn_status tn_state_expectation_workspace_bytes(const tn_observable *H, int32_t batch, size_t *bytes);
+tn_status tn_state_expectation(const tn_observable *H, int32_t batch, const void *state_dev,
+                               double *out_dev, void *workspace_dev, size_t workspace_bytes,
+                               tn_stream_t s);
+
+/* Index permutation over binary legs (Sec. 3: operands regrouped into matrices before a
+ * merge): for a tensor of n_legs legs of size 2 (leg 0 most significant), out has legs
+ * ordered perm[0..n_legs): out leg j is in leg perm[j].  complex64, batch independent
+ * tensors back to back; in_dev and out_dev must not overlap; 1 <= n_legs <= 34. */
+tn_status tn_permute(int32_t n_legs, const int32_t *perm, int64_t batch, const void *in_dev,
+                     void *out_dev, tn_stream_t s);
+
+/* Batched complex GEMM (Sec. 2.2.1, Eq. 2.2: a pairwise merge as a sum over shared indices):
+ *   C[b][m][n] = sum_k A[b][m][k] * B[b][n][k]   (both operands K-contiguous)
+ * complex64 interleaved, row-major; precision is a tn_precision.  workspace_dev must hold
+ * tn_cgemm_workspace_bytes(...) bytes (split operand copies; may be 0). */
+tn_status tn_cgemm_workspace_bytes(int32_t precision, int64_t batch, int64_t M, int64_t N, int64_t K,
+                                   size_t *bytes);
+tn_status tn_cgemm_batched(int32_t precision, int64_t batch, int64_t M, int64_t N, int64_t K,
+                           const void *A_dev, const void *B_dev, void *C_dev, void *workspace_dev,
+                           size_t workspace_bytes, tn_stream_t s);
+
+/* ---------------------------------------------------------------------------------------
+ * Status.
+ * ------------------------------------------------------------------------------------- */
+
+/* Synchronise stream s, then read and clear this device's status word: TN_OK, or the
+ * first device-side failure recorded since the last call (TN_ERR_TIMEOUT / TN_ERR_NUMERIC),
+ * or TN_ERR_CUDA if the synchronisation itself failed. */
+tn_status tn_sync_status(tn_stream_t s);
+/* Message of the last failed call on this thread ("" if none).  Valid until the next call. */
+const char *tn_last_error(void);
+const char *tn_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TNQ_TN_H */

@@ -1,0 +1,254 @@
+// FP64 reductions over the contracted state: Pauli-sum expectation values and H psi.
+//
+// Closing the state's open legs against an operator (Sec. 2.2.3 closes them with a basis
+// state; an observable closes them with <psi| P) is a reduction over all 2^N entries:
+//   <psi|P|psi> = sum_x i^ny (-1)^popc(x & zm) conj(psi[x ^ xm]) psi[x]
+// for P with X/Y factors on the bits xm and Z/Y factors on zm.  Terms are grouped into
+// tile passes whose tiles contain every flip bit of their terms, so each pass reads the
+// state once (coalesced, staged in shared memory) and evaluates all of its terms from
+// the tile.  Per-amplitude sums are FP32, per-thread and per-CTA sums FP64, and the
+// per-CTA partials are summed in a fixed order (deterministic result).
+#include "apply_common.cuh"
+#include "kernels.h"
+
+namespace tnq {
+
+constexpr int kRedThreads = 256;
+constexpr int kRedMaxCTAs = 512;  // per pass and batch element
+
+namespace {
+
+__device__ __forceinline__ float2 times_i_pow(float2 z, int ny) {
+  switch (ny & 3) {
+    case 0: return z;
+    case 1: return make_float2(-z.y, z.x);
+    case 2: return make_float2(-z.x, -z.y);
+    default: return make_float2(z.y, -z.x);
+  }
+}
+
+struct TileCtx {
+  int T, L, tile, lowmask;
+  long long *run_off;
+};
+
+__device__ void setup_tile(const RedPass &rp, long long *run_off, TileCtx &c) {
+  c.T = rp.T;
+  c.L = c.T < kLowBits ? c.T : kLowBits;
+  c.tile = 1 << c.T;
+  c.lowmask = (1 << c.L) - 1;
+  c.run_off = run_off;
+  for (int r = threadIdx.x; r < (1 << (c.T - c.L)); r += blockDim.x) {
+    long long off = 0;
+    for (int j = 0; j < c.T - c.L; ++j)
+      if ((r >> j) & 1) off |= 1ll << rp.tile_pos[c.L + j];
+    run_off[r] = off;
+  }
+}
+
+__device__ __forceinline__ unsigned long long tile_base(const RedPass &rp, long long t) {
+  unsigned long long base = 0;
+  for (int j = 0; j < rp.n_outer; ++j) base |= (unsigned long long)((t >> j) & 1) << rp.outer_pos[j];
+  return base;
+}
+
+__device__ __forceinline__ void load_tile(float2 *sm, const float2 *st, unsigned long long base, const TileCtx &c) {
+  for (int k = threadIdx.x; k < (c.tile >> 1); k += blockDim.x) {
+    const int i = k << 1;
+    const long long g = (long long)base + c.run_off[i >> c.L] + (i & c.lowmask);
+    const float4 v = *reinterpret_cast<const float4 *>(st + g);
+    sm[swz(i)] = make_float2(v.x, v.y);
+    sm[swz(i + 1)] = make_float2(v.z, v.w);
+  }
+}
+
+__device__ __forceinline__ double block_sum(double v, double *scratch) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, off);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) scratch[warp] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += scratch[w];
+  __syncthreads();
+  return s;
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(kRedThreads) k_expect_pass(const RedPass *__restrict__ passes, int pass_idx,
+                                                             int n_passes, const DevTerm *__restrict__ terms,
+                                                             const float2 *__restrict__ state, int N,
+                                                             double *__restrict__ part) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ RedPass rp;
+  __shared__ double scratch[kRedThreads / 32];
+  for (int i = threadIdx.x; i < (int)(sizeof(RedPass) / 4); i += blockDim.x)
+    reinterpret_cast<int *>(&rp)[i] = reinterpret_cast<const int *>(passes + pass_idx)[i];
+  __syncthreads();
+  TileCtx c;
+  float2 *sm = reinterpret_cast<float2 *>(smem_raw);
+  setup_tile(rp, reinterpret_cast<long long *>(smem_raw + ((size_t)sizeof(float2) << rp.T)), c);
+  __syncthreads();
+  const int b = blockIdx.y;
+  const float2 *st = state + ((long long)b << N);
+  const long long n_tiles = 1ll << rp.n_outer;
+  double acc = 0.0;
+  for (long long t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+    const unsigned long long base = tile_base(rp, t);
+    load_tile(sm, st, base, c);
+    __syncthreads();
+    float tacc = 0.f;
+    for (int i = threadIdx.x; i < c.tile; i += blockDim.x) {
+      const unsigned long long x = base + (unsigned long long)c.run_off[i >> c.L] + (unsigned long long)(i & c.lowmask);
+      const float2 v = sm[swz(i)];
+      const float nrm = fmaf(v.x, v.x, v.y * v.y);
+      float s = 0.f;
+      for (int k = rp.term_begin; k < rp.term_end; ++k) {
+        const DevTerm &tm = terms[k];
+        const float cf = (float)tm.coef;
+        const float sgn = (__popcll(x & tm.zm) & 1) ? -cf : cf;
+        if (tm.xl == 0) {
+          s = fmaf(sgn, nrm, s);  // diagonal term (ny is even and i^ny = +-1)
+          continue;
+        }
+        const float2 w = sm[swz(i ^ tm.xl)];
+        // z = conj(w) * v
+        const float2 z = make_float2(fmaf(w.x, v.x, w.y * v.y), fmaf(w.x, v.y, -w.y * v.x));
+        s = fmaf(sgn, times_i_pow(z, tm.ny).x, s);
+      }
+      tacc += s;
+    }
+    acc += (double)tacc;
+    __syncthreads();
+  }
+  const double tot = block_sum(acc, scratch);
+  if (threadIdx.x == 0) part[((long long)b * n_passes + pass_idx) * kRedMaxCTAs + blockIdx.x] = tot;
+}
+
+// out[b] = sum over passes and CTAs of the partials (fixed order).
+__global__ void k_expect_final(const double *__restrict__ part, int n_passes, int gx, double *__restrict__ out) {
+  __shared__ double scratch[kRedThreads / 32];
+  const int b = blockIdx.x;
+  double v = 0.0;
+  for (int k = threadIdx.x; k < n_passes * gx; k += blockDim.x) {
+    const int p = k / gx, x = k % gx;
+    v += part[((long long)b * n_passes + p) * kRedMaxCTAs + x];
+  }
+  const double tot = block_sum(v, scratch);
+  if (threadIdx.x == 0) out[b] = tot;
+}
+
+// lam (+)= (sum of the pass's terms) psi, lam[x] = sum_t c_t i^ny (-1)^popc((x^xm)&zm) psi[x^xm].
+__global__ void __launch_bounds__(kRedThreads) k_hamiltonian_pass(const RedPass *__restrict__ passes, int pass_idx,
+                                                                  const DevTerm *__restrict__ terms,
+                                                                  const float2 *__restrict__ psi,
+                                                                  float2 *__restrict__ lam, int N, int accumulate) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ RedPass rp;
+  for (int i = threadIdx.x; i < (int)(sizeof(RedPass) / 4); i += blockDim.x)
+    reinterpret_cast<int *>(&rp)[i] = reinterpret_cast<const int *>(passes + pass_idx)[i];
+  __syncthreads();
+  TileCtx c;
+  float2 *sm = reinterpret_cast<float2 *>(smem_raw);
+  setup_tile(rp, reinterpret_cast<long long *>(smem_raw + ((size_t)sizeof(float2) << rp.T)), c);
+  __syncthreads();
+  const int b = blockIdx.y;
+  const float2 *st = psi + ((long long)b << N);
+  float2 *lt = lam + ((long long)b << N);
+  const long long n_tiles = 1ll << rp.n_outer;
+  for (long long t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+    const unsigned long long base = tile_base(rp, t);
+    load_tile(sm, st, base, c);
+    __syncthreads();
+    for (int i = threadIdx.x; i < c.tile; i += blockDim.x) {
+      const unsigned long long x = base + (unsigned long long)c.run_off[i >> c.L] + (unsigned long long)(i & c.lowmask);
+      float2 s = accumulate ? lt[x] : make_float2(0.f, 0.f);
+      for (int k = rp.term_begin; k < rp.term_end; ++k) {
+        const DevTerm &tm = terms[k];
+        const float cf = (float)tm.coef;
+        const float sgn = (__popcll((x ^ tm.xm) & tm.zm) & 1) ? -cf : cf;
+        const float2 w = times_i_pow(sm[swz(i ^ tm.xl)], tm.ny);
+        s.x = fmaf(sgn, w.x, s.x);
+        s.y = fmaf(sgn, w.y, s.y);
+      }
+      lt[x] = s;
+    }
+    __syncthreads();
+  }
+}
+
+namespace {
+size_t red_smem(int T) {
+  const int L = T < kLowBits ? T : kLowBits;
+  return ((size_t)1 << T) * sizeof(float2) + ((size_t)1 << (T - L)) * sizeof(long long);
+}
+int red_grid_x(const tn_observable *o, int pass, int batch, const void *fn) {
+  const RedPass &rp = o->passes[pass];
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kRedThreads, red_smem(rp.T)) != cudaSuccess ||
+      per_sm < 1)
+    per_sm = 1;
+  long long gx = ((long long)num_sms() * per_sm + batch - 1) / batch;
+  const long long n_tiles = 1ll << rp.n_outer;
+  if (gx > n_tiles) gx = n_tiles;
+  if (gx > kRedMaxCTAs) gx = kRedMaxCTAs;
+  if (gx < 1) gx = 1;
+  return (int)gx;
+}
+cudaError_t ensure_smem(const void *fn, size_t smem) {
+  if (smem <= 48 * 1024) return cudaSuccess;
+  return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+}  // namespace
+
+size_t observable_partials(const tn_observable *o, int batch) {
+  return (size_t)batch * o->passes.size() * kRedMaxCTAs;
+}
+
+cudaError_t launch_expectation(const tn_observable *o, int batch, const float2 *state, double *part, double *out,
+                               cudaStream_t s) {
+  const int np = (int)o->passes.size();
+  if (np == 0) return cudaMemsetAsync(out, 0, sizeof(double) * batch, s);
+  int gx_max = 1;
+  for (int p = 0; p < np; ++p) {
+    const size_t smem = red_smem(o->passes[p].T);
+    cudaError_t e = ensure_smem((const void *)k_expect_pass, smem);
+    if (e != cudaSuccess) return e;
+    const int gx = red_grid_x(o, p, batch, (const void *)k_expect_pass);
+    gx_max = gx > gx_max ? gx : gx_max;
+  }
+  // passes with a smaller grid leave zero partials below gx_max (the final sum reads gx_max per pass)
+  cudaError_t e = cudaMemsetAsync(part, 0, observable_partials(o, batch) * sizeof(double), s);
+  if (e != cudaSuccess) return e;
+  for (int p = 0; p < np; ++p) {
+    const int gx = red_grid_x(o, p, batch, (const void *)k_expect_pass);
+    dim3 grid((unsigned)gx, (unsigned)batch);
+    k_expect_pass<<<grid, kRedThreads, red_smem(o->passes[p].T), s>>>(o->d_passes, p, np, o->d_terms, state, o->n,
+                                                                     part);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  k_expect_final<<<batch, kRedThreads, 0, s>>>(part, np, gx_max, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_apply_hamiltonian(const tn_observable *o, int batch, const float2 *psi, float2 *lam,
+                                     cudaStream_t s) {
+  const int np = (int)o->passes.size();
+  if (np == 0) return cudaMemsetAsync(lam, 0, (sizeof(float2) << o->n) * batch, s);
+  for (int p = 0; p < np; ++p) {
+    const size_t smem = red_smem(o->passes[p].T);
+    cudaError_t e = ensure_smem((const void *)k_hamiltonian_pass, smem);
+    if (e != cudaSuccess) return e;
+    const int gx = red_grid_x(o, p, batch, (const void *)k_hamiltonian_pass);
+    dim3 grid((unsigned)gx, (unsigned)batch);
+    k_hamiltonian_pass<<<grid, kRedThreads, smem, s>>>(o->d_passes, p, o->d_terms, psi, lam, o->n, p > 0 ? 1 : 0);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+}  // namespace tnq

@@ -1,0 +1,48 @@
+// Launchers of libtnq's CUDA kernels (host declarations).
+#pragma once
+
+#include "tnq_internal.h"
+
+namespace tnq {
+
+int num_sms();  // SM count of the current device (cached per device)
+
+// Matrix tables: write the complex64 entries of every slot for each batch element.
+cudaError_t launch_materialize(const MatSlot *d_slots, int n_slots, const double *params, int n_params,
+                               int batch, long long mstride, float2 *out, cudaStream_t s);
+
+// Kernel (a): all forward passes of a plan (state <- U_G .. U_1 |init>).
+cudaError_t launch_forward(const tn_plan *p, const float2 *mats, long long mstride, float2 *state, cudaStream_t s);
+
+// Adjoint sweep: psi, lambda swept back through the gates; grad[b][k] accumulated (FP64).
+cudaError_t launch_backward(const tn_plan *p, const float2 *mats, long long mstride, float2 *psi, float2 *lam,
+                            double *grad, cudaStream_t s);
+
+// Pauli-sum reductions (tile passes).  part holds n_partials doubles per batch element.
+size_t observable_partials(const tn_observable *o, int batch);
+cudaError_t launch_expectation(const tn_observable *o, int batch, const float2 *state, double *part,
+                               double *out, cudaStream_t s);
+// lam = H psi (complex64).
+cudaError_t launch_apply_hamiltonian(const tn_observable *o, int batch, const float2 *psi, float2 *lam,
+                                     cudaStream_t s);
+// amps[b][i] = state[b][x_i]
+cudaError_t launch_gather(const float2 *state, int N, int batch, const uint64_t *xs, long long nx, float2 *amps,
+                          cudaStream_t s);
+// grad[b][k] *= gout[b] (gout may be NULL -> no-op), zero-fill helper
+cudaError_t launch_scale_grad(double *grad, const double *gout, int batch, int P, cudaStream_t s);
+cudaError_t launch_zero(void *p, size_t bytes, cudaStream_t s);
+
+// Kernel (b): permutation of binary legs.
+cudaError_t launch_permute(int n_legs, const int32_t *perm, long long batch, const float2 *in, float2 *out,
+                           cudaStream_t s);
+
+// Kernel (c): batched complex GEMM C[b] = A[b] * B[b]^T (K-contiguous operands).
+size_t cgemm_workspace(int precision, long long batch, long long M, long long N, long long K);
+cudaError_t launch_cgemm(int precision, long long batch, long long M, long long N, long long K, const float2 *A,
+                         const float2 *B, float2 *C, void *ws, size_t ws_bytes, cudaStream_t s);
+
+// Device status word (timeouts, non-finite values).
+void *status_word_ptr();
+cudaError_t read_and_clear_status(int *value, cudaStream_t s);
+
+}  // namespace tnq

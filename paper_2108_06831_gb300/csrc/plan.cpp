@@ -1,0 +1,337 @@
+// Host planner of libtnq: orders and groups the circuit's gate contractions.
+//
+// The paper treats the contraction order as a hyperparameter chosen before evaluation
+// (Sec. 2.2.3) and deploys only the order it selected (Sec. 3).  On one GPU the costly
+// contractions are the rank-growing ones, a small gate tensor merged into the large
+// state tensor (Sec. 2.2.1: tensor product followed by a contraction over the shared
+// index).  Each of them streams the whole state once, so the plan fuses as many of them
+// as dependencies allow into one pass over HBM:
+//
+//   pass   = one launch; a tile of 2^T amplitudes (T "tile bits", always including the
+//            kLowBits lowest bits so loads are 128-byte runs) is staged in shared memory;
+//   phase  = inside a pass, K tile bits are mapped to registers (2^K amplitudes per
+//            thread); every op of the phase touches only registers;
+//   op     = one gate.  A gate needs its non-diagonal qubits among the register bits;
+//            diagonal factors (Z/S/T/RZ, CZ, CP) and CNOT controls read any bit.
+//
+// A gate can join a phase only when every earlier gate sharing a qubit with it has
+// already been applied (a qubit touched by a deferred gate is "blocked" for the rest of
+// the scan).  Passes and phases are built greedily in time order.
+#include <algorithm>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "tnq_internal.h"
+
+namespace tnq {
+namespace {
+
+struct GateCls {
+  int type;        // OpType
+  int qa, qb;      // qubits (qb = -1 for one-qubit ops)
+  bool need_a, need_b;
+  int shape;       // MatShape of its entries (-1: none)
+};
+
+bool mat1_is_diagonal(const TnGate &g) {
+  return g.mat[2] == 0 && g.mat[3] == 0 && g.mat[4] == 0 && g.mat[5] == 0;
+}
+
+GateCls classify(const TnGate &g) {
+  GateCls c{};
+  c.qa = g.q[0];
+  c.qb = -1;
+  switch (g.kind) {
+    case TN_GATE_Z: case TN_GATE_S: case TN_GATE_SDG: case TN_GATE_T: case TN_GATE_TDG: case TN_GATE_RZ:
+      c.type = OP_D1; c.shape = SHAPE_DIAG2; break;
+    case TN_GATE_MAT1:
+      if (mat1_is_diagonal(g)) { c.type = OP_D1; c.shape = SHAPE_DIAG2; }
+      else { c.type = OP_G1; c.need_a = true; c.shape = SHAPE_M2; }
+      break;
+    case TN_GATE_CZ: c.type = OP_CZ; c.qb = g.q[1]; c.shape = -1; break;
+    case TN_GATE_CP: c.type = OP_DP; c.qb = g.q[1]; c.shape = SHAPE_PHASE; break;
+    case TN_GATE_CNOT: c.type = OP_C1; c.qb = g.q[1]; c.need_b = true; c.shape = SHAPE_M2; break;
+    case TN_GATE_SWAP: case TN_GATE_MAT2:
+      c.type = OP_G2; c.qb = g.q[1]; c.need_a = c.need_b = true; c.shape = SHAPE_M4; break;
+    default:  // H X Y SX SY SW RX RY U3
+      c.type = OP_G1; c.need_a = true; c.shape = SHAPE_M2; break;
+  }
+  return c;
+}
+
+// Algorithmic real flops per amplitude of one op (complex multiply = 6, add = 2).
+double op_flops(int type) {
+  switch (type) {
+    case OP_G1: return 14.0;
+    case OP_G2: return 30.0;
+    case OP_C1: return 7.0;
+    case OP_D1: return 6.0;
+    case OP_DP: return 1.5;
+    default: return 0.0;
+  }
+}
+
+int shape_entries(int shape) {
+  switch (shape) {
+    case SHAPE_M2: return 4;
+    case SHAPE_M4: return 16;
+    case SHAPE_DIAG2: return 2;
+    case SHAPE_PHASE: return 1;
+  }
+  return 0;
+}
+
+struct Planner {
+  int N, T, K;
+  std::vector<GateCls> cls;
+  std::vector<int> order;  // gate indices in application order
+  std::vector<char> done;
+
+  int bit_of(int q) const { return N - 1 - q; }
+
+  // needed register/tile bits of gate g (as global bit positions)
+  int needs(int g, int out[2]) const {
+    int k = 0;
+    if (cls[g].need_a) out[k++] = bit_of(cls[g].qa);
+    if (cls[g].need_b) out[k++] = bit_of(cls[g].qb);
+    return k;
+  }
+  void qubits(int g, int out[2], int &k) const {
+    k = 0;
+    out[k++] = cls[g].qa;
+    if (cls[g].qb >= 0) out[k++] = cls[g].qb;
+  }
+};
+
+uint64_t bitmask(int b) { return 1ull << b; }
+
+}  // namespace
+
+tn_status build_pass_plan(const tn_circuit &c, int T, int K, bool adjoint, std::vector<MatSlot> &slots,
+                          PassPlan &out, std::string &err) {
+  Planner P;
+  P.N = c.n;
+  P.T = T;
+  P.K = K;
+  const int G = (int)c.gates.size();
+  P.cls.resize(G);
+  for (int i = 0; i < G; ++i) P.cls[i] = classify(c.gates[i]);
+  P.order.resize(G);
+  for (int i = 0; i < G; ++i) P.order[i] = adjoint ? G - 1 - i : i;
+  P.done.assign(G, 0);
+
+  out = PassPlan();
+  const int N = c.n;
+  std::vector<int> pending = P.order;
+  int first_pass = 1;
+  // per-gate matrix slot offsets (allocated lazily, once per gate and form)
+  auto add_slot = [&](int gi, int form, int shape) -> int {
+    MatSlot s;
+    std::memset(&s, 0, sizeof(s));
+    const TnGate &g = c.gates[gi];
+    s.kind = g.kind;
+    s.form = form;
+    s.shape = shape;
+    s.param_idx = g.param_idx;
+    for (int a = 0; a < 3; ++a) s.angle[a] = g.angle[a];
+    for (int a = 0; a < 32; ++a) s.fixed[a] = g.mat[a];
+    int off = 0;
+    if (!slots.empty()) {
+      const MatSlot &l = slots.back();
+      off = l.offset + ((shape_entries(l.shape) + 1) & ~1);  // 16-byte aligned entries
+    }
+    s.offset = off;
+    slots.push_back(s);
+    return off;
+  };
+
+  while (!pending.empty() || (first_pass && !adjoint)) {
+    // ---- 1. tile bits
+    uint64_t S = 0;
+    int nS = 0;
+    if (N <= T) {
+      S = (N == 64) ? ~0ull : ((1ull << N) - 1);
+      nS = N;
+    } else {
+      for (int b = 0; b < kLowBits; ++b) S |= bitmask(b);
+      nS = kLowBits;
+      uint64_t blockedq = 0;  // bitmask over qubits
+      std::vector<int> wish;  // bits wanted by deferred gates, for filling
+      for (int g : pending) {
+        int qs[2], nq;
+        P.qubits(g, qs, nq);
+        bool blk = false;
+        for (int i = 0; i < nq; ++i) blk |= (blockedq >> qs[i]) & 1;
+        int nb[2];
+        int nn = P.needs(g, nb);
+        if (!blk) {
+          int add = 0;
+          for (int i = 0; i < nn; ++i) add += ((S >> nb[i]) & 1) ? 0 : 1;
+          if (nS + add <= T) {
+            for (int i = 0; i < nn; ++i) if (!((S >> nb[i]) & 1)) { S |= bitmask(nb[i]); ++nS; }
+            continue;
+          }
+        }
+        for (int i = 0; i < nn; ++i) wish.push_back(nb[i]);
+        for (int i = 0; i < nq; ++i) blockedq |= 1ull << qs[i];
+      }
+      for (int b : wish) {
+        if (nS >= T) break;
+        if (!((S >> b) & 1)) { S |= bitmask(b); ++nS; }
+      }
+      for (int b = kLowBits; b < N && nS < T; ++b)
+        if (!((S >> b) & 1)) { S |= bitmask(b); ++nS; }
+    }
+    PassDesc pd;
+    std::memset(&pd, 0, sizeof(pd));
+    pd.T = nS;
+    pd.K = std::min(K, nS);
+    pd.init_mode = (!adjoint && first_pass) ? 1 : 0;
+    int tl = 0, ol = 0;
+    int glob2tile[64];
+    for (int b = 0; b < 64; ++b) glob2tile[b] = -1;
+    for (int b = 0; b < N; ++b) {
+      if ((S >> b) & 1) { glob2tile[b] = tl; pd.tile_pos[tl++] = (uint8_t)b; }
+      else pd.outer_pos[ol++] = (uint8_t)b;
+    }
+    pd.n_outer = ol;
+    pd.phase_begin = (int)out.phases.size();
+    pd.grad_begin = (int)out.grads.size();
+    const int Kp = pd.K;
+    int grad_slots = 0;
+
+    // ---- 2. phases
+    for (;;) {
+      if (pending.empty()) break;
+      // choose register bits R (global positions) among S
+      uint64_t R = 0;
+      int nR = 0;
+      uint64_t blockedq = 0;
+      for (int g : pending) {
+        int qs[2], nq;
+        P.qubits(g, qs, nq);
+        bool blk = false;
+        for (int i = 0; i < nq; ++i) blk |= (blockedq >> qs[i]) & 1;
+        int nb[2];
+        int nn = P.needs(g, nb);
+        bool ok = !blk;
+        for (int i = 0; i < nn && ok; ++i) ok = (S >> nb[i]) & 1;
+        if (ok) {
+          int add = 0;
+          for (int i = 0; i < nn; ++i) add += ((R >> nb[i]) & 1) ? 0 : 1;
+          if (nR + add <= Kp) {
+            for (int i = 0; i < nn; ++i) if (!((R >> nb[i]) & 1)) { R |= bitmask(nb[i]); ++nR; }
+            continue;
+          }
+        }
+        for (int i = 0; i < nq; ++i) blockedq |= 1ull << qs[i];
+      }
+      for (int b = N - 1; b >= 0 && nR < Kp; --b)  // fill from the high tile bits
+        if (((S >> b) & 1) && !((R >> b) & 1)) { R |= bitmask(b); ++nR; }
+
+      // emit ops
+      PhaseDesc ph;
+      std::memset(&ph, 0, sizeof(ph));
+      ph.op_begin = (int)out.ops.size();
+      int regpos_of_bit[64];
+      for (int b = 0; b < 64; ++b) regpos_of_bit[b] = -1;
+      {
+        int r = 0;
+        for (int b = 0; b < N; ++b)
+          if ((R >> b) & 1) { ph.reg_pos[r] = (uint8_t)glob2tile[b]; regpos_of_bit[b] = r; ++r; }
+      }
+      // thread-index bits: non-register tile positions; lanes first, chosen so that the
+      // residues (position mod 4) of the first five cover 0..3 when possible
+      {
+        std::vector<int> rest;
+        for (int l = 0; l < nS; ++l) {
+          int b = pd.tile_pos[l];
+          if (!((R >> b) & 1)) rest.push_back(l);
+        }
+        std::vector<int> lanes, others;
+        std::vector<char> used(rest.size(), 0);
+        for (int res = 0; res < 4 && (int)lanes.size() < 5; ++res)
+          for (size_t i = 0; i < rest.size(); ++i)
+            if (!used[i] && (rest[i] & 3) == res) { lanes.push_back(rest[i]); used[i] = 1; break; }
+        for (size_t i = 0; i < rest.size() && lanes.size() < 5; ++i)
+          if (!used[i]) { lanes.push_back(rest[i]); used[i] = 1; }
+        for (size_t i = 0; i < rest.size(); ++i) if (!used[i]) others.push_back(rest[i]);
+        int t = 0;
+        for (int l : lanes) ph.thr_pos[t++] = (uint8_t)l;
+        for (int l : others) ph.thr_pos[t++] = (uint8_t)l;
+      }
+      auto src_of = [&](int q, uint8_t &kind, uint8_t &pos) {
+        int b = P.bit_of(q);
+        if (regpos_of_bit[b] >= 0) { kind = SRC_REG; pos = (uint8_t)regpos_of_bit[b]; }
+        else if (glob2tile[b] >= 0) { kind = SRC_TILE; pos = (uint8_t)glob2tile[b]; }
+        else { kind = SRC_GLOB; pos = (uint8_t)b; }
+      };
+      int emitted = 0;
+      blockedq = 0;
+      std::vector<int> rest_pending;
+      rest_pending.reserve(pending.size());
+      for (int g : pending) {
+        int qs[2], nq;
+        P.qubits(g, qs, nq);
+        bool blk = false;
+        for (int i = 0; i < nq; ++i) blk |= (blockedq >> qs[i]) & 1;
+        int nb[2];
+        int nn = P.needs(g, nb);
+        bool ok = !blk;
+        for (int i = 0; i < nn && ok; ++i) ok = (R >> nb[i]) & 1;
+        // a pass accumulates at most kMaxGradSlots parameter derivatives per tile
+        if (ok && adjoint && c.gates[g].param_idx >= 0 &&
+            grad_slots + gate_arity(c.gates[g].kind) > kMaxGradSlots)
+          ok = false;
+        if (!ok) {
+          for (int i = 0; i < nq; ++i) blockedq |= 1ull << qs[i];
+          rest_pending.push_back(g);
+          continue;
+        }
+        const GateCls &gc = P.cls[g];
+        OpDesc op;
+        std::memset(&op, 0, sizeof(op));
+        op.type = (uint8_t)gc.type;
+        src_of(gc.qa, op.a_kind, op.a_pos);
+        if (gc.qb >= 0) src_of(gc.qb, op.b_kind, op.b_pos);
+        op.mat = gc.shape >= 0 ? add_slot(g, adjoint ? FORM_ADJ : FORM_U, gc.shape) : 0;
+        op.aux = -1;
+        const TnGate &tg = c.gates[g];
+        if (adjoint && tg.param_idx >= 0) {
+          int ar = gate_arity(tg.kind);
+          op.has_grad = 1;
+          op.n_grad = (uint8_t)ar;
+          op.aux = (int)out.grads.size();
+          for (int a = 0; a < ar; ++a) {
+            GradRec gr;
+            gr.mat = add_slot(g, FORM_D0 + a, gc.shape);
+            gr.param = tg.param_idx + a;
+            gr.slot = grad_slots++;
+            gr.pad = 0;
+            out.grads.push_back(gr);
+          }
+        }
+        out.ops.push_back(op);
+        out.flops += op_flops(gc.type) * (double)(1ull << N);
+        ++emitted;
+      }
+      if (emitted == 0) break;
+      ph.op_end = (int)out.ops.size();
+      out.phases.push_back(ph);
+      pending.swap(rest_pending);
+    }
+    pd.phase_end = (int)out.phases.size();
+    pd.grad_slots = grad_slots;
+    out.max_grad_slots = std::max(out.max_grad_slots, grad_slots);
+    if (pd.phase_end == pd.phase_begin && !pd.init_mode) {
+      err = "planner made no progress (internal error)";
+      return TN_ERR_UNSUPPORTED;
+    }
+    out.passes.push_back(pd);
+    first_pass = 0;
+  }
+  return TN_OK;
+}
+
+}  // namespace tnq

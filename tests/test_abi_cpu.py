@@ -1,0 +1,74 @@
+"""Host-side checks of the C ABI that need no GPU: the library loads, exports every symbol
+include/tn.h declares, validates arguments and plans (host-only) without touching a device."""
+import os
+import re
+
+import pytest
+
+from paper_2108_06831_gb300 import circuits as C
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _tn():
+    from paper_2108_06831_gb300 import _build
+    if not os.path.exists(os.path.join(ROOT, "paper_2108_06831_gb300", "libtnq.so")):
+        _build.build()
+    from paper_2108_06831_gb300 import tn
+    return tn
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "tn.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(tn_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_exports_every_declared_symbol():
+    tn = _tn()
+    names = declared_functions()
+    assert len(names) >= 20
+    for name in names:
+        assert hasattr(tn._lib, name), name
+    assert set(names) <= set(tn.EXPORTED)
+
+
+def test_version_and_errors():
+    tn = _tn()
+    assert "sm_103a" in tn.version()
+    with pytest.raises(tn.TnError) as e:
+        tn.CircuitHandle(C.Circuit(0, []))
+    assert "n_qubits" in str(e.value)
+    with pytest.raises(tn.TnError):
+        tn.CircuitHandle(C.Circuit(4, [C.Gate("RX", (0,), (), -5)]))
+    with pytest.raises(tn.TnError):
+        tn.CircuitHandle(C.Circuit(4, [C.Gate("H", (0,), (), 0)]))
+
+
+def test_host_only_plans():
+    tn = _tn()
+    c, _ = C.brickwork(24, 20, 1001)
+    ch = tn.CircuitHandle(c)
+    for T in (8, 10, 12, 13):
+        s = tn.Plan(ch, tile_qubits=T, host_only=True).stats()
+        assert s["n_ops"] == len(c.gates)
+        assert s["tile_qubits"] == T and s["reg_qubits"] == 4
+        assert s["n_passes"] >= 2
+        # every gate is applied once: flops = sum over gates of per-amplitude cost * 2^N
+        n_u3 = sum(1 for g in c.gates if g.kind == "U3")
+        assert s["flops"] == pytest.approx(14.0 * n_u3 * (1 << 24))
+    small = tn.Plan(tn.CircuitHandle(C.brickwork(10, 8, 1000)[0]), host_only=True).stats()
+    assert small["n_passes"] == 1 and small["tile_qubits"] == 10
+
+
+def test_plan_option_validation():
+    tn = _tn()
+    ch = tn.CircuitHandle(C.ghz(5))
+    with pytest.raises(tn.TnError):
+        tn.Plan(ch, tile_qubits=3, host_only=True)
+    with pytest.raises(tn.TnError):
+        tn.Plan(ch, tile_qubits=20, host_only=True)
+    with pytest.raises(tn.TnError):
+        tn.Plan(ch, batch=-1, host_only=True)
+    p = tn.Plan(ch, target=tn.TARGET_EXPECTATION, batch=4, host_only=True)
+    assert p.workspace_bytes >= 2 * 4 * 8 * 32

@@ -1,0 +1,139 @@
+"""Parity of the CUDA contraction path with the FP64 oracle (GPU).
+
+Bar (complex64 states and amplitude vectors): relative L2 error <= 1e-5 against the
+oracle's complex128 result; expectations |E - E_ref| <= 1e-4 max(1, |E_ref|).
+"""
+import numpy as np
+import pytest
+
+from paper_2108_06831_gb300 import circuits as C
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+STATE_TOL = 1e-5
+
+
+def _tn():
+    from paper_2108_06831_gb300 import tn
+    return tn
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+def gpu_state(circ, params=None, batch=1, tile=0):
+    tn = _tn()
+    ctr = tn.Contractor(circ, target=tn.TARGET_STATE, batch=batch, tile_qubits=tile)
+    p = None if params is None else torch.as_tensor(np.asarray(params, dtype=np.float64).reshape(batch, -1),
+                                                    device="cuda").contiguous()
+    out = ctr.state(p)
+    torch.cuda.synchronize()
+    assert tn.sync_status() == tn.OK
+    return out.cpu().numpy()
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 6, 8, 9, 11, 12])
+def test_random_circuits_small(n):
+    from oracle.statevector import simulate_state
+    for seed in range(3):
+        c = C.random_circuit(n, 12 * n + 5, 100 * n + seed)
+        c.init_basis = (seed * 7919) % (1 << n)
+        ref = simulate_state(c)
+        got = gpu_state(c)[0]
+        assert rel_l2(got, ref) <= STATE_TOL, (n, seed)
+
+
+@pytest.mark.parametrize("n,tile", [(13, 5), (14, 6), (15, 8), (16, 10), (17, 12), (18, 13), (16, 7)])
+def test_random_circuits_multipass(n, tile):
+    """Several tiles and passes; tile sizes from the smallest allowed upwards."""
+    from oracle.statevector import simulate_state
+    c = C.random_circuit(n, 10 * n, 7 * n + tile)
+    c.init_basis = (n * 104729) % (1 << n)
+    ref = simulate_state(c)
+    got = gpu_state(c, tile=tile)[0]
+    assert rel_l2(got, ref) <= STATE_TOL
+
+
+def test_cfg1_brickwork_10q_depth8():
+    from oracle.statevector import simulate_state
+    c, _ = C.brickwork(10, 8, 1000)
+    ref = simulate_state(c)
+    got = gpu_state(c)[0]
+    assert rel_l2(got, ref) <= STATE_TOL
+
+
+@pytest.mark.parametrize("maker", [
+    lambda: C.brickwork(16, 12, 5)[0],
+    lambda: C.qft(16, 12345),
+    lambda: C.paper_fig31(16, 6, 3),
+    lambda: C.grid(4, 4, 10, 8),
+    lambda: C.ghz(14),
+])
+def test_workload_families(maker):
+    from oracle.statevector import simulate_state
+    c = maker()
+    ref = simulate_state(c)
+    for tile in (0, 9):
+        got = gpu_state(c, tile=tile)[0]
+        assert rel_l2(got, ref) <= STATE_TOL
+
+
+def test_parameterized_batch():
+    """Per-batch parameters: every batch element matches the oracle with its own angles."""
+    from oracle.statevector import simulate_state
+    c, p0 = C.brickwork(12, 6, 77, parameterized=True)
+    rng = np.random.default_rng(5)
+    params = np.stack([p0] + [rng.uniform(0, 2 * np.pi, size=p0.shape) for _ in range(4)])
+    got = gpu_state(c, params, batch=5)
+    for b in range(5):
+        assert rel_l2(got[b], simulate_state(c, params[b])) <= STATE_TOL
+
+
+def test_cfg2_full_size_sampled():
+    """24-qubit brickwork, depth 20, in the bench's launch configuration: sampled amplitudes
+    against the oracle's network contraction, plus the norm."""
+    from oracle.tn import contract_amplitude
+    c, _ = C.brickwork(24, 20, 1001)
+    got = gpu_state(c)[0]
+    assert abs(np.linalg.norm(got.astype(np.complex128)) - 1.0) < 1e-5
+    xs = C.random_bitstrings(24, 10, 4242)
+    ref = np.array([contract_amplitude(c, int(x)) for x in xs])
+    assert rel_l2(got[xs.astype(np.int64)], ref) <= STATE_TOL
+
+
+def test_amplitudes_gather():
+    from oracle.statevector import simulate_state
+    tn = _tn()
+    c = C.grid(4, 4, 8, 11)
+    ref = simulate_state(c)
+    ctr = tn.Contractor(c, target=tn.TARGET_AMPLITUDES)
+    xs = C.random_bitstrings(16, 300, 9)
+    got = ctr.amplitudes(torch.as_tensor(xs.astype(np.int64), device="cuda")).cpu().numpy()[0]
+    assert rel_l2(got, ref[xs.astype(np.int64)]) <= STATE_TOL
+    # empty batch of bitstrings is a no-op
+    ctr.amplitudes(torch.empty(0, dtype=torch.int64, device="cuda"))
+    torch.cuda.synchronize()
+
+
+def test_empty_circuit_and_basis():
+    c = C.Circuit(7, [], init_basis=93)
+    got = gpu_state(c)[0]
+    ref = np.zeros(128, dtype=np.complex128)
+    ref[93] = 1
+    assert np.abs(got - ref).max() == 0
+
+
+def test_invalid_arguments_rejected():
+    tn = _tn()
+    with pytest.raises(tn.TnError):
+        tn.CircuitHandle(C.Circuit(3, [C.Gate("H", (3,))]))
+    with pytest.raises(tn.TnError):
+        tn.CircuitHandle(C.Circuit(3, [C.Gate("CZ", (1, 1))]))
+    with pytest.raises(tn.TnError):
+        tn.CircuitHandle(C.Circuit(3, [], init_basis=8))
+    ctr = tn.Contractor(C.brickwork(6, 2, 1, parameterized=True)[0])
+    with pytest.raises(tn.TnError):
+        ctr.state(None)  # parameterised circuit without parameters
