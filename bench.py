@@ -44,6 +44,7 @@ def parse():
     ap.add_argument("--tile", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-specialize", action="store_true", help="run the interpreting gate-apply kernel")
     return ap.parse_args()
 
 
@@ -241,7 +242,8 @@ def main():
         circ_f, _ = C.brickwork(wl["n"], wl["depth"], wl["seed"])
         batch = wl["batch"]
         params = np.tile(params0, (batch, 1))
-        ctr = tn.Contractor(circ_p, batch=batch, tile_qubits=args.tile, device=dev)
+        spec = not args.no_specialize
+        ctr = tn.Contractor(circ_p, batch=batch, tile_qubits=args.tile, device=dev, specialize=spec)
         p_dev = torch.as_tensor(params, device=dev)
         out = torch.empty((batch, 1 << wl["n"]), dtype=torch.complex64, device=dev)
         units_per_step = batch * (1 << wl["n"])
@@ -250,7 +252,7 @@ def main():
         def step():
             tn.contract_state(ctr.plan, p_dev, out, ctr.workspace)
         launches_per_step = 1 + ctr.plan.stats()["n_passes"]
-        fixed = tn.Contractor(circ_f, batch=batch, tile_qubits=args.tile, device=dev)
+        fixed = tn.Contractor(circ_f, batch=batch, tile_qubits=args.tile, device=dev, specialize=spec)
         fst = fixed.plan.stats()
 
         def kernel_only():
@@ -315,6 +317,7 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "c64 (f32)", "data": "synthetic",
             "config": {"workload": args.workload, "n_qubits": wl["n"], "depth": wl["depth"], "batch": batch,
                        "tile_qubits": ctr.plan.stats()["tile_qubits"],
+                       "specialized_kernels": bool(ctr.plan.stats()["specialized"]),
                        "l2": "256 MiB buffer written between timed steps (untimed)",
                        "parallelism": f"replicas x{world}"},
             "clocks": clk.summary()}

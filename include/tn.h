@@ -101,6 +101,9 @@ typedef enum { TN_TARGET_STATE = 0, TN_TARGET_AMPLITUDES = 1, TN_TARGET_EXPECTAT
 typedef enum { TN_PREC_FP32 = 0, TN_PREC_3XTF32 = 1, TN_PREC_SPLIT_BF16 = 2 } tn_precision;
 
 #define TN_PLAN_HOST_ONLY 1 /* plan without touching the GPU: only tn_plan_get_stats may use it */
+#define TN_PLAN_NO_SPECIALIZE 2 /* run the interpreting gate-apply kernel instead of plan-specialised
+                                 * kernels (those are generated as CUDA C++ and compiled with NVRTC
+                                 * when the plan is built; compiled code is cached on disk) */
 
 typedef struct {
   int32_t target;                /* tn_target: what the plan will be used for */
@@ -126,7 +129,8 @@ typedef struct {
   double hbm_bytes;     /* algorithmic HBM bytes of one tn_contract_state call (per batch element) */
   double flops;         /* algorithmic FP32 flops of one tn_contract_state call (per batch element) */
   int32_t n_bwd_passes; /* passes of the adjoint sweep */
-  int32_t reserved[7];
+  int32_t specialized;  /* 1 if the forward passes run plan-specialised kernels */
+  int32_t reserved[6];
 } tn_plan_stats;
 
 /* Pauli sum H = sum_t coef[t] * P_t (host memory, read during tn_build_observable only).

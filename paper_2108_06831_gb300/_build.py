@@ -70,7 +70,7 @@ def build(verbose: bool = False, jobs: int = 0) -> str:
             list(ex.map(run, jobs_))
     if jobs_ or not os.path.exists(LIB) or any(os.path.getmtime(o) > os.path.getmtime(LIB) for o in objs):
         tmp = LIB + ".tmp"
-        run([cc] + ARCH + ["-shared", "-o", tmp] + objs + ["-cudart", "shared"])
+        run([cc] + ARCH + ["-shared", "-o", tmp] + objs + ["-cudart", "shared", "-lnvrtc", "-Xcompiler", "-pthread"])
         os.replace(tmp, LIB)
     return LIB
 

@@ -1,12 +1,14 @@
 // C ABI of libtnq (declared in include/tn.h): argument checks, plan construction and
 // upload, workspace layout, and the launch sequences of the contraction calls.
 #include <cstdarg>
+#include <cstdlib>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
 #include <string>
 #include <vector>
 
+#include "jit.h"
 #include "kernels.h"
 #include "tnq_internal.h"
 
@@ -175,7 +177,11 @@ tn_status tn_build_from_circuit(int32_t n_qubits, const tn_gate *gates, int64_t 
     t.q[0] = g.q[0];
     t.q[1] = nq == 2 ? g.q[1] : -1;
     t.param_idx = g.param_idx;
-    for (int a = 0; a < 3; ++a) t.angle[a] = g.angle[a];
+    for (int a = 0; a < 3; ++a) {
+      t.angle[a] = (g.param_idx >= 0 && a < ar) ? 0.0 : g.angle[a];
+      t.pidx[a][0] = (g.param_idx >= 0 && a < ar) ? g.param_idx + a : -1;
+      t.pidx[a][1] = -1;
+    }
     if (g.kind == TN_GATE_MAT1) std::memcpy(t.mat, g.mat, 8 * sizeof(double));
     if (g.kind == TN_GATE_MAT2) std::memcpy(t.mat, g.mat, 32 * sizeof(double));
     if (g.param_idx >= 0 && g.param_idx + ar > c->n_params) c->n_params = g.param_idx + ar;
@@ -202,7 +208,7 @@ tn_status tn_plan_contraction(const tn_circuit *c, const tn_plan_opts *opts, tn_
   TN_CHECK_ARG(o.batch >= 1 && o.batch <= (1 << 20), "batch=%d out of range", o.batch);
   TN_CHECK_ARG(o.target >= TN_TARGET_STATE && o.target <= TN_TARGET_EXPECTATION, "bad target %d", o.target);
   TN_CHECK_ARG(o.precision >= TN_PREC_FP32 && o.precision <= TN_PREC_SPLIT_BF16, "bad precision %d", o.precision);
-  TN_CHECK_ARG(o.tile_qubits == 0 || (o.tile_qubits >= 5 && o.tile_qubits <= kMaxTile), "tile_qubits=%d not in {0, 5..%d}",
+  TN_CHECK_ARG(o.tile_qubits == 0 || (o.tile_qubits >= kLowBits + 2 && o.tile_qubits <= kMaxTile), "tile_qubits=%d not in {0, 6..%d}",
                o.tile_qubits, kMaxTile);
   for (int i = 0; i < 6; ++i) TN_CHECK_ARG(o.reserved[i] == 0, "reserved fields must be zero");
   if (o.max_intermediate_log2 == 0) o.max_intermediate_log2 = 28;
@@ -213,6 +219,7 @@ tn_status tn_plan_contraction(const tn_circuit *c, const tn_plan_opts *opts, tn_
   p->n = c->n;
   p->batch = o.batch;
   p->n_params = c->n_params;
+  p->n_gates = (long long)c->gates.size();
   p->init = c->init;
   p->opts = o;
   p->host_only = (o.flags & TN_PLAN_HOST_ONLY) != 0;
@@ -222,7 +229,8 @@ tn_status tn_plan_contraction(const tn_circuit *c, const tn_plan_opts *opts, tn_
   p->T = T;
   p->K = K;
   std::string err;
-  tn_status st = build_pass_plan(*c, T, K, false, p->slots, p->fwd, err);
+  const tn_circuit fwd_circ = push_phases(*c);
+  tn_status st = build_pass_plan(fwd_circ, T, K, false, p->slots, p->fwd, err);
   if (st == TN_OK && o.target == TN_TARGET_EXPECTATION) st = build_pass_plan(*c, T, K, true, p->slots, p->bwd, err);
   if (st != TN_OK) {
     set_error("planner: %s", err.c_str());
@@ -257,6 +265,18 @@ tn_status tn_plan_contraction(const tn_circuit *c, const tn_plan_opts *opts, tn_
   }
   p->ws_bytes = off;
 
+  if (p->host_only && getenv("TNQ_JIT_COMPILE_CHECK") && !(o.flags & TN_PLAN_NO_SPECIALIZE) && jit_supported(*p)) {
+    // generate and compile the specialised kernels without loading them (no GPU needed)
+    std::vector<int> kinds(p->fwd.ops.size());
+    for (size_t i = 0; i < kinds.size(); ++i) kinds[i] = fwd_circ.gates[(size_t)p->fwd.op_gate[i]].kind;
+    std::string jerr;
+    tn_status u = jit_build(*p, kinds, true, jerr);
+    if (u != TN_OK) {
+      set_error("plan-specialised kernels: %s", jerr.c_str());
+      delete p;
+      return u;
+    }
+  }
   if (!p->host_only) {
     TN_CUDA(cudaGetDevice(&p->device), "cudaGetDevice");
     tn_status u = TN_OK;
@@ -280,7 +300,15 @@ tn_status tn_plan_contraction(const tn_circuit *c, const tn_plan_opts *opts, tn_
         if (e != cudaSuccess) u = cuda_fail(e, "fixed gate table");
       }
     }
+    if (u == TN_OK && !(o.flags & TN_PLAN_NO_SPECIALIZE) && jit_supported(*p)) {
+      std::vector<int> kinds(p->fwd.ops.size());
+      for (size_t i = 0; i < kinds.size(); ++i) kinds[i] = fwd_circ.gates[(size_t)p->fwd.op_gate[i]].kind;
+      std::string jerr;
+      u = jit_build(*p, kinds, false, jerr);
+      if (u != TN_OK) set_error("plan-specialised kernels: %s", jerr.c_str());
+    }
     if (u != TN_OK) {
+      jit_release(*p);
       free_plan_device(p);
       delete p;
       return u;
@@ -301,6 +329,7 @@ tn_status tn_plan_get_stats(const tn_plan *p, tn_plan_stats *st) {
   std::memset(st, 0, sizeof(*st));
   st->n_qubits = p->n;
   st->n_params = p->n_params;
+  st->n_gates = p->n_gates;
   st->n_passes = (int)p->fwd.passes.size();
   st->n_phases = (int)p->fwd.phases.size();
   st->n_ops = (long long)p->fwd.ops.size();
@@ -311,11 +340,13 @@ tn_status tn_plan_get_stats(const tn_plan *p, tn_plan_stats *st) {
   for (const PassDesc &pd : p->fwd.passes) bytes += (pd.init_mode ? 8.0 : 16.0) * (double)(1ull << p->n);
   st->hbm_bytes = bytes;
   st->n_bwd_passes = (int)p->bwd.passes.size();
+  st->specialized = p->jit_kernels.empty() ? 0 : 1;
   return TN_OK;
 }
 
 void tn_free_plan(tn_plan *p) {
   if (!p) return;
+  jit_release(*p);
   if (!p->host_only) free_plan_device(p);
   delete p;
 }

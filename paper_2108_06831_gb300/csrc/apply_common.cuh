@@ -39,7 +39,9 @@ __device__ __forceinline__ float2 cneg_if(float2 a, uint32_t flip) {
 }
 __device__ __forceinline__ float2 csel(bool p, float2 a, float2 b) { return p ? a : b; }
 
-__device__ __forceinline__ float2 ldg_c(const float2 *p) { return __ldg(p); }
+// Op records and matrix entries may live in global or (staged) shared memory: generic loads.
+__device__ __forceinline__ float2 ldg_c(const float2 *p) { return *p; }
+__device__ __forceinline__ float4 ld4(const float2 *p) { return *reinterpret_cast<const float4 *>(p); }
 
 // Bit r of every register index j < 2^K, as a mask over j.
 __device__ __forceinline__ uint32_t reg_bit_mask(int r) {
@@ -90,8 +92,8 @@ __device__ __forceinline__ void reg_g1(float2 (&a)[1 << K], float2 u00, float2 u
 
 template <int K, bool PRED>
 __device__ __forceinline__ void reg_g1_dispatch(float2 (&a)[1 << K], int r, const float2 *m, uint32_t pred) {
-  const float4 m01 = __ldg(reinterpret_cast<const float4 *>(m));
-  const float4 m23 = __ldg(reinterpret_cast<const float4 *>(m) + 1);
+  const float4 m01 = ld4(m);
+  const float4 m23 = ld4(m + 2);
   const float2 u00 = make_float2(m01.x, m01.y), u01 = make_float2(m01.z, m01.w);
   const float2 u10 = make_float2(m23.x, m23.y), u11 = make_float2(m23.z, m23.w);
   switch (r) {
@@ -142,7 +144,7 @@ __device__ __forceinline__ void reg_g2_dispatch(float2 (&a)[1 << K], int ra, int
     float2 u[16];
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
-      const float4 v = __ldg(reinterpret_cast<const float4 *>(m) + k);
+      const float4 v = ld4(m + 2 * k);
       u[2 * k] = make_float2(v.x, v.y);
       u[2 * k + 1] = make_float2(v.z, v.w);
     }
@@ -174,32 +176,39 @@ __device__ __forceinline__ void reg_flush_sign(float2 (&a)[1 << K], uint32_t neg
   for (int j = 0; j < (1 << K); ++j) a[j] = cneg_if(a[j], (neg >> j) & 1u);
 }
 
-// Apply one op to the registers.  Sign flips of CZ ops accumulate in neg and are
-// applied lazily (they commute with every other diagonal op).
+// Apply one op to the registers.  Sign flips of CZ ops accumulate in neg and are applied
+// lazily: they commute with every diagonal op and with every op whose register bits they do
+// not depend on; the planner sets OPF_FLUSH on the ops where that is not the case.
 template <int K>
 __device__ __forceinline__ void apply_op(float2 (&a)[1 << K], const OpDesc &op, const BitCtx &c,
                                          const float2 *mats, uint32_t &neg) {
   switch (op.type) {
     case OP_G1:
-      reg_flush_sign<K>(a, neg);
-      neg = 0;
+      if (op.flags & OPF_FLUSH) {
+        if (neg) reg_flush_sign<K>(a, neg);
+        neg = 0;
+      }
       reg_g1_dispatch<K, false>(a, op.a_pos, mats + op.mat, 0u);
       break;
     case OP_C1: {
-      reg_flush_sign<K>(a, neg);
-      neg = 0;
+      if (op.flags & OPF_FLUSH) {
+        if (neg) reg_flush_sign<K>(a, neg);
+        neg = 0;
+      }
       const uint32_t pm = src_mask(c, op.a_kind, op.a_pos);
       if (pm == c.full) reg_g1_dispatch<K, false>(a, op.b_pos, mats + op.mat, 0u);
       else if (pm != 0u) reg_g1_dispatch<K, true>(a, op.b_pos, mats + op.mat, pm);
       break;
     }
     case OP_G2:
-      reg_flush_sign<K>(a, neg);
-      neg = 0;
+      if (op.flags & OPF_FLUSH) {
+        if (neg) reg_flush_sign<K>(a, neg);
+        neg = 0;
+      }
       reg_g2_dispatch<K>(a, op.a_pos, op.b_pos, mats + op.mat);
       break;
     case OP_D1: {
-      const float4 d = __ldg(reinterpret_cast<const float4 *>(mats + op.mat));
+      const float4 d = ld4(mats + op.mat);
       reg_diag<K>(a, src_mask(c, op.a_kind, op.a_pos), make_float2(d.x, d.y), make_float2(d.z, d.w));
       break;
     }
@@ -212,6 +221,11 @@ __device__ __forceinline__ void apply_op(float2 (&a)[1 << K], const OpDesc &op, 
       break;
     }
   }
+}
+
+// Copy n 16-byte records (n4 int4 words) from global to shared memory, all threads.
+__device__ __forceinline__ void stage_int4(int4 *dst, const int4 *src, int n4) {
+  for (int i = threadIdx.x; i < n4; i += blockDim.x) dst[i] = __ldg(src + i);
 }
 
 // Deposit the low bits of v into the tile positions pos[0..n).

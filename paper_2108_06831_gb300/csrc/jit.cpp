@@ -1,0 +1,565 @@
+// Plan-specialised fused gate-apply kernels, generated as CUDA C++ and compiled with NVRTC.
+//
+// The interpreting kernel (k_apply.cu) reads every op record at run time and dispatches on
+// its type and register positions, which keeps the compiler from scheduling arithmetic
+// across gates.  Here the planner's passes are turned into source in which each phase's
+// register positions, shared-memory offsets, CZ sign patterns, control bits and the
+// position of every matrix entry are constants, so one pass compiles to straight-line
+// FFMA code.  Gate matrices still come from the per-call table (so parameterised circuits
+// share the compiled code); they are staged in shared memory once per batch element.
+//
+// Compiled cubins are cached in-process by a 64-bit hash of the source, and on disk in
+// $TNQ_CACHE_DIR (default ~/.cache/tnq) so repeated plans of the same circuit structure
+// skip compilation.
+#include <nvrtc.h>
+#include <sys/stat.h>
+#include <sys/types.h>
+#include <unistd.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <fstream>
+#include <map>
+#include <mutex>
+#include <sstream>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "jit.h"
+#include "tnq_internal.h"
+
+namespace tnq {
+
+namespace {
+
+const char *kPrelude = R"(
+typedef unsigned long long u64;
+struct __align__(8) c2 { float x, y; };
+__device__ __forceinline__ float2 cm2(float2 a, float2 x, float2 b, float2 y) {
+  float re = a.x * x.x; re = fmaf(-a.y, x.y, re); re = fmaf(b.x, y.x, re); re = fmaf(-b.y, y.y, re);
+  float im = a.x * x.y; im = fmaf(a.y, x.x, im); im = fmaf(b.x, y.y, im); im = fmaf(b.y, y.x, im);
+  return make_float2(re, im);
+}
+__device__ __forceinline__ float2 cm(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ float2 ng(float2 a) { return make_float2(-a.x, -a.y); }
+// r*x + b*y with r real
+__device__ __forceinline__ float2 rc(float r, float2 x, float2 b, float2 y) {
+  float re = r * x.x; re = fmaf(b.x, y.x, re); re = fmaf(-b.y, y.y, re);
+  float im = r * x.y; im = fmaf(b.x, y.y, im); im = fmaf(b.y, y.x, im);
+  return make_float2(re, im);
+}
+// r*x + s*y with r, s real
+__device__ __forceinline__ float2 rr(float r, float2 x, float s, float2 y) {
+  return make_float2(fmaf(s, y.x, r * x.x), fmaf(s, y.y, r * x.y));
+}
+// r*x + (i t)*y with r, t real
+__device__ __forceinline__ float2 ri(float r, float2 x, float t, float2 y) {
+  return make_float2(fmaf(-t, y.y, r * x.x), fmaf(t, y.x, r * x.y));
+}
+__device__ __forceinline__ float2 f2(float4 v, int hi) { return hi ? make_float2(v.z, v.w) : make_float2(v.x, v.y); }
+__device__ __forceinline__ int swz(int i) { int h = i >> 4; h ^= h >> 4; h ^= h >> 8; return i ^ (h & 15); }
+)";
+
+uint64_t fnv1a(const std::string &s) {
+  uint64_t h = 1469598103934665603ull;
+  for (unsigned char c : s) {
+    h ^= c;
+    h *= 1099511628211ull;
+  }
+  return h;
+}
+
+int swz_host(int i) {
+  int h = i >> 4;
+  h ^= h >> 4;
+  h ^= h >> 8;
+  return i ^ (h & 15);
+}
+
+struct Emitter {
+  std::ostringstream o;
+  int K = 4;
+  int R = 16;  // registers per thread
+  void line(const std::string &s) { o << s << "\n"; }
+};
+
+// condition expression (thread- or tile-uniform) for a non-register bit operand
+std::string cond_expr(uint8_t kind, uint8_t pos) {
+  char b[96];
+  if (kind == SRC_TILE) snprintf(b, sizeof b, "((tb >> %d) & 1)", (int)pos);
+  else snprintf(b, sizeof b, "((int)((base >> %d) & 1ull))", (int)pos);
+  return b;
+}
+
+void emit_op(Emitter &E, const OpDesc &op, int kind) {
+  const int R = E.R;
+  char buf[256];
+  auto mat = [&](int k) {  // k-th complex entry of the op's matrix
+    snprintf(buf, sizeof buf, "f2(M4[%d], %d)", (op.mat + k) >> 1, (op.mat + k) & 1);
+    return std::string(buf);
+  };
+  switch (op.type) {
+    case OP_G1: {
+      const int r = op.a_pos;
+      if (kind == TN_GATE_X) {  // permutation: swap register pairs
+        for (int j = 0; j < R; ++j)
+          if (!(j & (1 << r))) {
+            snprintf(buf, sizeof buf, "{ const float2 t = a[%d]; a[%d] = a[%d]; a[%d] = t; }", j, j, j | (1 << r), j | (1 << r));
+            E.line(buf);
+          }
+        return;
+      }
+      E.line("{ const float2 u00 = " + mat(0) + ", u01 = " + mat(1) + ", u10 = " + mat(2) + ", u11 = " + mat(3) + ";");
+      // arithmetic specialised to the matrix structure the gate kind guarantees
+      const char *pair_fmt;
+      if (kind == KIND_V)  // real first column
+        pair_fmt = "  { const float2 x = a[%d], y = a[%d]; a[%d] = rc(u00.x, x, u01, y); a[%d] = rc(u10.x, x, u11, y); }";
+      else if (kind == TN_GATE_RY || kind == TN_GATE_H || kind == TN_GATE_SY)  // real matrix
+        pair_fmt = "  { const float2 x = a[%d], y = a[%d]; a[%d] = rr(u00.x, x, u01.x, y); a[%d] = rr(u10.x, x, u11.x, y); }";
+      else if (kind == TN_GATE_RX || kind == TN_GATE_SX)  // real diagonal, imaginary off-diagonal
+        pair_fmt = "  { const float2 x = a[%d], y = a[%d]; a[%d] = ri(u00.x, x, u01.y, y); a[%d] = ri(u11.x, y, u10.y, x); }";
+      else
+        pair_fmt = "  { const float2 x = a[%d], y = a[%d]; a[%d] = cm2(u00, x, u01, y); a[%d] = cm2(u10, x, u11, y); }";
+      for (int j = 0; j < R; ++j)
+        if (!(j & (1 << r))) {
+          const int j1 = j | (1 << r);
+          snprintf(buf, sizeof buf, pair_fmt, j, j1, j, j1);
+          E.line(buf);
+        }
+      E.line("}");
+      return;
+    }
+    case OP_C1: {
+      const int r = op.b_pos;
+      const bool ctrl_reg = op.a_kind == SRC_REG;
+      const bool is_x = kind == TN_GATE_CNOT;
+      if (!ctrl_reg) E.line("if (" + cond_expr(op.a_kind, op.a_pos) + ") {");
+      if (!is_x) E.line("{ const float2 u00 = " + mat(0) + ", u01 = " + mat(1) + ", u10 = " + mat(2) + ", u11 = " + mat(3) + ";");
+      for (int j = 0; j < R; ++j) {
+        if (j & (1 << r)) continue;
+        if (ctrl_reg && !(j & (1 << op.a_pos))) continue;
+        const int j1 = j | (1 << r);
+        if (is_x) snprintf(buf, sizeof buf, "{ const float2 t = a[%d]; a[%d] = a[%d]; a[%d] = t; }", j, j, j1, j1);
+        else
+          snprintf(buf, sizeof buf,
+                   "  { const float2 x = a[%d], y = a[%d]; a[%d] = cm2(u00, x, u01, y); a[%d] = cm2(u10, x, u11, y); }", j,
+                   j1, j, j1);
+        E.line(buf);
+      }
+      if (!is_x) E.line("}");
+      if (!ctrl_reg) E.line("}");
+      return;
+    }
+    case OP_G2: {
+      const int ra = op.a_pos, rb = op.b_pos;
+      if (kind == TN_GATE_SWAP) {
+        for (int j = 0; j < R; ++j)
+          if ((j & (1 << ra)) && !(j & (1 << rb))) {
+            const int j2 = (j & ~(1 << ra)) | (1 << rb);
+            snprintf(buf, sizeof buf, "{ const float2 t = a[%d]; a[%d] = a[%d]; a[%d] = t; }", j, j, j2, j2);
+            E.line(buf);
+          }
+        return;
+      }
+      E.line("{ float2 u[16];");
+      for (int k = 0; k < 16; ++k) E.line("  u[" + std::to_string(k) + "] = " + mat(k) + ";");
+      for (int j = 0; j < R; ++j) {
+        if (j & ((1 << ra) | (1 << rb))) continue;
+        const int i0 = j, i1 = j | (1 << rb), i2 = j | (1 << ra), i3 = j | (1 << ra) | (1 << rb);
+        snprintf(buf, sizeof buf, "  { const float2 v0 = a[%d], v1 = a[%d], v2 = a[%d], v3 = a[%d];", i0, i1, i2, i3);
+        E.line(buf);
+        const int idx[4] = {i0, i1, i2, i3};
+        for (int k = 0; k < 4; ++k) {
+          snprintf(buf, sizeof buf,
+                   "    { const float2 s = cm2(u[%d], v0, u[%d], v1), t = cm2(u[%d], v2, u[%d], v3); a[%d] = make_float2(s.x + t.x, s.y + t.y); }",
+                   4 * k, 4 * k + 1, 4 * k + 2, 4 * k + 3, idx[k]);
+          E.line(buf);
+        }
+        E.line("  }");
+      }
+      E.line("}");
+      return;
+    }
+    case OP_D1: {
+      if (kind == TN_GATE_Z) {  // sign on bit value 1
+        if (op.a_kind == SRC_REG) {
+          for (int j = 0; j < R; ++j)
+            if (j & (1 << op.a_pos)) E.line("a[" + std::to_string(j) + "] = ng(a[" + std::to_string(j) + "]);");
+        } else {
+          E.line("if (" + cond_expr(op.a_kind, op.a_pos) + ") {");
+          for (int j = 0; j < R; ++j) E.line("  a[" + std::to_string(j) + "] = ng(a[" + std::to_string(j) + "]);");
+          E.line("}");
+        }
+        return;
+      }
+      if (kind == KIND_P || kind == TN_GATE_S || kind == TN_GATE_SDG || kind == TN_GATE_T || kind == TN_GATE_TDG) {
+        // diag(1, e): only amplitudes whose bit is 1 change
+        E.line("{ const float2 d1 = " + mat(1) + ";");
+        if (op.a_kind == SRC_REG) {
+          for (int j = 0; j < R; ++j)
+            if (j & (1 << op.a_pos)) {
+              snprintf(buf, sizeof buf, "  a[%d] = cm(a[%d], d1);", j, j);
+              E.line(buf);
+            }
+        } else {
+          E.line("  if (" + cond_expr(op.a_kind, op.a_pos) + ") {");
+          for (int j = 0; j < R; ++j) {
+            snprintf(buf, sizeof buf, "    a[%d] = cm(a[%d], d1);", j, j);
+            E.line(buf);
+          }
+          E.line("  }");
+        }
+        E.line("}");
+        return;
+      }
+      E.line("{ const float2 d0 = " + mat(0) + ", d1 = " + mat(1) + ";");
+      if (op.a_kind == SRC_REG) {
+        for (int j = 0; j < R; ++j) {
+          snprintf(buf, sizeof buf, "  a[%d] = cm(a[%d], %s);", j, j, (j & (1 << op.a_pos)) ? "d1" : "d0");
+          E.line(buf);
+        }
+      } else {
+        E.line("  const float2 d = " + cond_expr(op.a_kind, op.a_pos) + " ? d1 : d0;");
+        for (int j = 0; j < R; ++j) {
+          snprintf(buf, sizeof buf, "  a[%d] = cm(a[%d], d);", j, j);
+          E.line(buf);
+        }
+      }
+      E.line("}");
+      return;
+    }
+    case OP_CZ:
+    case OP_DP: {
+      // set of register indices j where both operands are 1, under a uniform condition
+      std::string cond;
+      uint32_t mask = (R >= 32) ? 0xFFFFFFFFu : ((1u << R) - 1u);
+      auto take = [&](uint8_t k, uint8_t p) {
+        if (k == SRC_REG) {
+          uint32_t m = 0;
+          for (int j = 0; j < R; ++j)
+            if (j & (1 << p)) m |= 1u << j;
+          mask &= m;
+        } else {
+          cond += (cond.empty() ? "" : " & ") + cond_expr(k, p);
+        }
+      };
+      take(op.a_kind, op.a_pos);
+      take(op.b_kind, op.b_pos);
+      if (mask == 0) return;
+      if (!cond.empty()) E.line("if (" + cond + ") {");
+      if (op.type == OP_DP) E.line("{ const float2 e = " + mat(0) + ";");
+      for (int j = 0; j < R; ++j)
+        if (mask & (1u << j)) {
+          if (op.type == OP_CZ) snprintf(buf, sizeof buf, "  a[%d] = ng(a[%d]);", j, j);
+          else snprintf(buf, sizeof buf, "  a[%d] = cm(a[%d], e);", j, j);
+          E.line(buf);
+        }
+      if (op.type == OP_DP) E.line("}");
+      if (!cond.empty()) E.line("}");
+      return;
+    }
+  }
+}
+
+std::string gen_pass(const tn_plan &p, int pi, const std::vector<int> &op_kind, int *threads_out, size_t *smem_out) {
+  const PassDesc &pd = p.fwd.passes[pi];
+  const int T = pd.T, K = pd.K, L = T < kLowBits ? T : kLowBits;
+  const int NTHR = 1 << (T - K);
+  const int TILE = 1 << T;
+  const int N = p.n;
+  const int mat_n = pd.mat_end - pd.mat_begin;  // even
+  Emitter E;
+  E.K = K;
+  E.R = 1 << K;
+  char buf[512];
+  snprintf(buf, sizeof buf,
+           "extern \"C\" __global__ void __launch_bounds__(%d) tnq_p%d(const float2 *__restrict__ mats_g, long long mstride, "
+           "float2 *__restrict__ state, long long work, u64 init_basis) {",
+           NTHR, pi);
+  E.line(buf);
+  E.line("  extern __shared__ __align__(16) unsigned char smraw[];");
+  E.line("  float2 *sm = reinterpret_cast<float2 *>(smraw);");
+  snprintf(buf, sizeof buf, "  float4 *smat = reinterpret_cast<float4 *>(sm + %d);", TILE);
+  E.line(buf);
+  E.line("  const int tid = threadIdx.x;");
+  // per-thread part of the load/store deposit: tile index i = 2*tid + 2*k*NTHR
+  {
+    std::string dep = "0ll";
+    for (int j = 1; j <= T - K; ++j) {
+      snprintf(buf, sizeof buf, " | ((long long)((tid >> %d) & 1) << %d)", j - 1, (int)pd.tile_pos[j]);
+      dep += buf;
+    }
+    E.line("  const long long dep_t = " + dep + ";");
+    E.line("  const int sw_t = swz(2 * tid);");
+  }
+  E.line("  long long cur_b = -1;");
+  snprintf(buf, sizeof buf, "  for (long long w = blockIdx.x; w < work; w += gridDim.x) {");
+  E.line(buf);
+  snprintf(buf, sizeof buf, "    const long long b = w >> %d; const long long t = w & %lldll;", pd.n_outer,
+           (long long)((1ll << pd.n_outer) - 1));
+  E.line(buf);
+  {
+    std::string base = "0ull";
+    for (int j = 0; j < pd.n_outer; ++j) {
+      snprintf(buf, sizeof buf, " | ((u64)((t >> %d) & 1) << %d)", j, (int)pd.outer_pos[j]);
+      base += buf;
+    }
+    E.line("    const u64 base = " + base + ";");
+  }
+  snprintf(buf, sizeof buf, "    float2 *st = state + (b << %d);", N);
+  E.line(buf);
+  // stage this batch element's matrix entries
+  E.line("    if (b != cur_b) {");
+  E.line("      if (cur_b >= 0) __syncthreads();");
+  snprintf(buf, sizeof buf,
+           "      const float4 *src = reinterpret_cast<const float4 *>(mats_g + b * mstride + %d);", pd.mat_begin);
+  E.line(buf);
+  snprintf(buf, sizeof buf, "      for (int i = tid; i < %d; i += %d) smat[i] = src[i];", mat_n / 2, NTHR);
+  E.line(buf);
+  E.line("      cur_b = b;");
+  E.line("    }");
+  snprintf(buf, sizeof buf, "    const float4 *M4 = smat - %d;", pd.mat_begin / 2);
+  E.line(buf);
+  // load (or synthesise) the tile
+  const int chunks = TILE / 2 / NTHR;
+  if (pd.init_mode) {
+    snprintf(buf, sizeof buf, "    for (int i = tid; i < %d; i += %d) sm[i] = make_float2(0.f, 0.f);", TILE, NTHR);
+    E.line(buf);
+    E.line("    __syncthreads();");
+    unsigned long long outer_mask = 0;
+    for (int j = 0; j < pd.n_outer; ++j) outer_mask |= 1ull << pd.outer_pos[j];
+    snprintf(buf, sizeof buf, "    if (tid == 0 && (init_basis & %lluull) == base) {", outer_mask);
+    E.line(buf);
+    std::string li = "0";
+    for (int j = 0; j < T; ++j) {
+      snprintf(buf, sizeof buf, " | ((int)((init_basis >> %d) & 1ull) << %d)", (int)pd.tile_pos[j], j);
+      li += buf;
+    }
+    E.line("      const int li = " + li + ";");
+    E.line("      sm[swz(li)] = make_float2(1.f, 0.f);");
+    E.line("    }");
+  } else {
+    for (int k = 0; k < chunks; ++k) {
+      const int ik = 2 * k * NTHR;
+      long long depk = 0;
+      for (int j = 0; j < T; ++j)
+        if ((ik >> j) & 1) depk |= 1ll << pd.tile_pos[j];
+      const int swk = swz_host(ik);
+      snprintf(buf, sizeof buf,
+               "    { const float4 v = *reinterpret_cast<const float4 *>(st + base + dep_t + %lldll); "
+               "sm[sw_t ^ %d] = make_float2(v.x, v.y); sm[sw_t ^ %d ^ 1] = make_float2(v.z, v.w); }",
+               depk, swk, swk);
+      // the second amplitude is tile index i + 1: swz(i + 1) = swz(i) ^ swz(1) = swz(i) ^ 1
+      E.line(buf);
+    }
+  }
+  E.line("    __syncthreads();");
+  // phases
+  for (int ph = pd.phase_begin; ph < pd.phase_end; ++ph) {
+    const PhaseDesc &d = p.fwd.phases[ph];
+    E.line("    {");
+    std::string tb = "0";
+    for (int j = 0; j < T - K; ++j) {
+      snprintf(buf, sizeof buf, " | (((tid >> %d) & 1) << %d)", j, (int)d.thr_pos[j]);
+      tb += buf;
+    }
+    E.line("      const int tb = " + tb + ";");
+    E.line("      const int pb = swz(tb);");
+    E.line("      float2 a[" + std::to_string(E.R) + "];");
+    int ro[32];
+    for (int j = 0; j < E.R; ++j) {
+      int off = 0;
+      for (int r = 0; r < K; ++r)
+        if ((j >> r) & 1) off |= 1 << d.reg_pos[r];
+      ro[j] = swz_host(off);
+      snprintf(buf, sizeof buf, "      a[%d] = sm[pb ^ %d];", j, ro[j]);
+      E.line(buf);
+    }
+    for (int o = d.op_begin; o < d.op_end; ++o) emit_op(E, p.fwd.ops[o], op_kind[o]);
+    for (int j = 0; j < E.R; ++j) {
+      snprintf(buf, sizeof buf, "      sm[pb ^ %d] = a[%d];", ro[j], j);
+      E.line(buf);
+    }
+    E.line("    }");
+    E.line("    __syncthreads();");
+  }
+  // store
+  for (int k = 0; k < chunks; ++k) {
+    const int ik = 2 * k * NTHR;
+    long long depk = 0;
+    for (int j = 0; j < T; ++j)
+      if ((ik >> j) & 1) depk |= 1ll << pd.tile_pos[j];
+    const int swk = swz_host(ik);
+    snprintf(buf, sizeof buf,
+             "    { const float2 x = sm[sw_t ^ %d], y = sm[sw_t ^ %d ^ 1]; "
+             "*reinterpret_cast<float4 *>(st + base + dep_t + %lldll) = make_float4(x.x, x.y, y.x, y.y); }",
+             swk, swk, depk);
+    E.line(buf);
+  }
+  E.line("    __syncthreads();");
+  E.line("  }");
+  E.line("}");
+  *threads_out = NTHR;
+  *smem_out = (size_t)TILE * 8 + (size_t)mat_n * 8;
+  return E.o.str();
+}
+
+std::mutex g_cache_mu;
+std::map<uint64_t, std::string> g_cubins;
+
+std::string cache_dir() {
+  const char *d = getenv("TNQ_CACHE_DIR");
+  if (d && *d) return d;
+  const char *h = getenv("HOME");
+  return std::string(h && *h ? h : "/tmp") + "/.cache/tnq";
+}
+
+bool read_file(const std::string &path, std::string &out) {
+  std::ifstream f(path, std::ios::binary);
+  if (!f) return false;
+  std::ostringstream ss;
+  ss << f.rdbuf();
+  out = ss.str();
+  return !out.empty();
+}
+
+void write_file(const std::string &dir, const std::string &path, const std::string &data) {
+  std::string acc;
+  for (size_t i = 1; i <= dir.size(); ++i)
+    if (i == dir.size() || dir[i] == '/') mkdir(dir.substr(0, i).c_str(), 0755);
+  const std::string tmp = path + ".tmp" + std::to_string((unsigned long long)getpid());
+  std::ofstream f(tmp, std::ios::binary);
+  if (!f) return;
+  f.write(data.data(), (std::streamsize)data.size());
+  f.close();
+  rename(tmp.c_str(), path.c_str());
+}
+
+tn_status compile_cubin(const std::string &src, std::string &cubin, std::string &err) {
+  const uint64_t h = fnv1a(src);
+  {
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    auto it = g_cubins.find(h);
+    if (it != g_cubins.end()) {
+      cubin = it->second;
+      return TN_OK;
+    }
+  }
+  char name[64];
+  snprintf(name, sizeof name, "%016llx.cubin", (unsigned long long)h);
+  const std::string dir = cache_dir();
+  const std::string path = dir + "/" + name;
+  if (!read_file(path, cubin)) {
+    nvrtcProgram prog;
+    if (nvrtcCreateProgram(&prog, src.c_str(), "tnq_pass.cu", 0, nullptr, nullptr) != NVRTC_SUCCESS) {
+      err = "nvrtcCreateProgram failed";
+      return TN_ERR_UNSUPPORTED;
+    }
+    const char *opts[] = {"-arch=sm_103a", "-std=c++17", "-default-device", "-lineinfo"};
+    nvrtcResult r = nvrtcCompileProgram(prog, 4, opts);
+    if (r != NVRTC_SUCCESS) {
+      size_t n = 0;
+      nvrtcGetProgramLogSize(prog, &n);
+      std::string log(n, '\0');
+      nvrtcGetProgramLog(prog, &log[0]);
+      nvrtcDestroyProgram(&prog);
+      err = "NVRTC compile failed: " + log.substr(0, 800);
+      return TN_ERR_UNSUPPORTED;
+    }
+    size_t n = 0;
+    nvrtcGetCUBINSize(prog, &n);
+    cubin.assign(n, '\0');
+    nvrtcGetCUBIN(prog, &cubin[0]);
+    nvrtcDestroyProgram(&prog);
+    write_file(dir, path, cubin);
+  }
+  std::lock_guard<std::mutex> lk(g_cache_mu);
+  g_cubins[h] = cubin;
+  return TN_OK;
+}
+
+}  // namespace
+
+bool jit_supported(const tn_plan &p) {
+  if (p.fwd.passes.empty()) return false;
+  for (const PassDesc &pd : p.fwd.passes)
+    if (pd.K != 4 || pd.T < kLowBits + 2) return false;
+  return true;
+}
+
+tn_status jit_build(tn_plan &p, const std::vector<int> &op_kind, bool compile_only, std::string &err) {
+  // one NVRTC program per pass: compile time grows faster than linearly with module size,
+  // and separate programs compile in parallel and are cached independently
+  const size_t np = p.fwd.passes.size();
+  std::vector<std::string> srcs(np), cubins(np), errs(np);
+  std::vector<int> threads(np);
+  std::vector<size_t> smem(np);
+  std::vector<tn_status> sts(np, TN_OK);
+  for (size_t i = 0; i < np; ++i) {
+    int th = 0;
+    size_t sm = 0;
+    srcs[i] = std::string(kPrelude) + gen_pass(p, (int)i, op_kind, &th, &sm);
+    threads[i] = th;
+    smem[i] = sm;
+    if (const char *dump = getenv("TNQ_JIT_DUMP_DIR")) {
+      char name[64];
+      snprintf(name, sizeof name, "/%016llx.cu", (unsigned long long)fnv1a(srcs[i]));
+      write_file(dump, std::string(dump) + name, srcs[i]);
+    }
+  }
+  {
+    unsigned hw = std::thread::hardware_concurrency();
+    const size_t nthreads = std::max<size_t>(1, std::min<size_t>(np, hw ? hw : 4));
+    std::atomic<size_t> next(0);
+    std::vector<std::thread> pool;
+    for (size_t t = 0; t < nthreads; ++t)
+      pool.emplace_back([&]() {
+        for (size_t i = next++; i < np; i = next++) sts[i] = compile_cubin(srcs[i], cubins[i], errs[i]);
+      });
+    for (auto &th : pool) th.join();
+  }
+  for (size_t i = 0; i < np; ++i)
+    if (sts[i] != TN_OK) {
+      err = errs[i];
+      return sts[i];
+    }
+  if (compile_only) return TN_OK;
+  p.jit_libs.assign(np, nullptr);
+  p.jit_kernels.assign(np, nullptr);
+  p.jit_threads = threads;
+  p.jit_smem = smem;
+  for (size_t i = 0; i < np; ++i) {
+    cudaError_t e = cudaLibraryLoadData(&p.jit_libs[i], cubins[i].data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
+    if (e != cudaSuccess) {
+      err = std::string("cudaLibraryLoadData: ") + cudaGetErrorString(e);
+      return TN_ERR_CUDA;
+    }
+    char name[32];
+    snprintf(name, sizeof name, "tnq_p%zu", i);
+    cudaKernel_t k = nullptr;
+    e = cudaLibraryGetKernel(&k, p.jit_libs[i], name);
+    if (e == cudaSuccess && smem[i] > 48 * 1024)
+      e = cudaFuncSetAttribute((const void *)k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem[i]);
+    if (e != cudaSuccess) {
+      err = std::string("loading generated kernel: ") + cudaGetErrorString(e);
+      return TN_ERR_CUDA;
+    }
+    p.jit_kernels[i] = k;
+  }
+  return TN_OK;
+}
+
+void jit_release(tn_plan &p) {
+  for (cudaLibrary_t l : p.jit_libs)
+    if (l) cudaLibraryUnload(l);
+  p.jit_libs.clear();
+  p.jit_kernels.clear();
+}
+
+}  // namespace tnq

@@ -1,0 +1,16 @@
+// Plan-specialised gate-apply kernels (generated CUDA C++, compiled with NVRTC).
+#pragma once
+
+#include <string>
+#include <vector>
+
+#include "tnq_internal.h"
+
+namespace tnq {
+// Whether every forward pass of the plan has the shape the generator handles.
+bool jit_supported(const tn_plan &p);
+// Generate, compile (or fetch from the cache) and load the plan's pass kernels.
+// op_kind[o] is the gate kind of forward op o.  compile_only: stop after compiling (no GPU).
+tn_status jit_build(tn_plan &p, const std::vector<int> &op_kind, bool compile_only, std::string &err);
+void jit_release(tn_plan &p);
+}  // namespace tnq

@@ -38,8 +38,8 @@ __device__ __forceinline__ float grad_dot(const float2 (&a)[1 << K], const float
                                           const BitCtx &c, const float2 *dm) {
   float acc = 0.f;
   if (op.type == OP_G1) {
-    const float4 m01 = __ldg(reinterpret_cast<const float4 *>(dm));
-    const float4 m23 = __ldg(reinterpret_cast<const float4 *>(dm) + 1);
+    const float4 m01 = ld4(dm);
+    const float4 m23 = ld4(dm + 2);
     const float2 d00 = make_float2(m01.x, m01.y), d01 = make_float2(m01.z, m01.w);
     const float2 d10 = make_float2(m23.x, m23.y), d11 = make_float2(m23.z, m23.w);
     switch (op.a_pos) {
@@ -50,7 +50,7 @@ __device__ __forceinline__ float grad_dot(const float2 (&a)[1 << K], const float
       case 4: if constexpr (K > 4) acc = grad_dot_g1<K, 4>(a, l, d00, d01, d10, d11); break;
     }
   } else if (op.type == OP_D1) {
-    const float4 d = __ldg(reinterpret_cast<const float4 *>(dm));
+    const float4 d = ld4(dm);
     const float2 d0 = make_float2(d.x, d.y), d1 = make_float2(d.z, d.w);
     const uint32_t m = src_mask(c, op.a_kind, op.a_pos);
 #pragma unroll

@@ -17,10 +17,10 @@ namespace tnq {
 template <int K>
 __global__ void __launch_bounds__(512) k_fwd_pass(const PassDesc *__restrict__ pdesc,
                                                    const PhaseDesc *__restrict__ phases,
-                                                   const OpDesc *__restrict__ ops,
-                                                   const float2 *__restrict__ mats, long long mstride,
+                                                   const OpDesc *__restrict__ ops_g,
+                                                   const float2 *__restrict__ mats_g, long long mstride,
                                                    float2 *__restrict__ state, int N, int batch,
-                                                   unsigned long long init_basis) {
+                                                   unsigned long long init_basis, int staged) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ PassDesc pd;
   for (int i = threadIdx.x; i < (int)(sizeof(PassDesc) / 4); i += blockDim.x)
@@ -40,6 +40,18 @@ __global__ void __launch_bounds__(512) k_fwd_pass(const PassDesc *__restrict__ p
   }
   unsigned long long outer_mask = 0;
   for (int j = 0; j < pd.n_outer; ++j) outer_mask |= 1ull << pd.outer_pos[j];
+  // the pass's op records and matrix entries are read by every tile: stage them once
+  const int n_ops = pd.op_end - pd.op_begin;
+  const int n_mat = pd.mat_end - pd.mat_begin;
+  const int n_runs = (1 << (T - L)) < 2 ? 2 : (1 << (T - L));  // 16-byte aligned run table
+  OpDesc *s_ops = reinterpret_cast<OpDesc *>(run_off + n_runs);
+  float2 *s_mat = reinterpret_cast<float2 *>(s_ops + n_ops);
+  const OpDesc *ops = ops_g;
+  if (staged) {
+    stage_int4(reinterpret_cast<int4 *>(s_ops), reinterpret_cast<const int4 *>(ops_g + pd.op_begin), n_ops);
+    ops = s_ops - pd.op_begin;
+  }
+  long long cur_b = -1;
   __syncthreads();
 
   const long long n_tiles = 1ll << pd.n_outer;
@@ -53,7 +65,15 @@ __global__ void __launch_bounds__(512) k_fwd_pass(const PassDesc *__restrict__ p
     unsigned long long base = 0;
     for (int j = 0; j < pd.n_outer; ++j) base |= (unsigned long long)((t >> j) & 1) << pd.outer_pos[j];
     float2 *st = state + ((long long)b << N);
-    const float2 *mb = mats + b * mstride;
+    const float2 *mb = mats_g + b * mstride;
+    if (staged) {
+      if (b != cur_b) {
+        if (cur_b >= 0) __syncthreads();
+        stage_int4(reinterpret_cast<int4 *>(s_mat), reinterpret_cast<const int4 *>(mb + pd.mat_begin), n_mat >> 1);
+        cur_b = b;
+      }
+      mb = s_mat - pd.mat_begin;
+    }
 
     if (pd.init_mode) {
       for (int i = threadIdx.x; i < tile; i += nthr) sm[swz(i)] = make_float2(0.f, 0.f);
@@ -95,12 +115,12 @@ __global__ void __launch_bounds__(512) k_fwd_pass(const PassDesc *__restrict__ p
       for (int j = 0; j < (1 << K); ++j) a[j] = sm[pb ^ ro[j]];
       uint32_t neg = 0;
       for (int o = ph.op_begin; o < ph.op_end; ++o) {
-        const int4 raw = __ldg(reinterpret_cast<const int4 *>(ops + o));
+        const int4 raw = *reinterpret_cast<const int4 *>(ops + o);
         OpDesc op;
         *reinterpret_cast<int4 *>(&op) = raw;
         apply_op<K>(a, op, ctx, mb, neg);
       }
-      reg_flush_sign<K>(a, neg);
+      if (neg) reg_flush_sign<K>(a, neg);
 #pragma unroll
       for (int j = 0; j < (1 << K); ++j) sm[pb ^ ro[j]] = a[j];
       __syncthreads();
@@ -117,6 +137,8 @@ __global__ void __launch_bounds__(512) k_fwd_pass(const PassDesc *__restrict__ p
 }
 
 namespace {
+constexpr size_t kStageBytes = 48 * 1024;  // ops + matrices staged in shared memory when they fit
+
 template <int K>
 cudaError_t launch_fwd_k(const PassDesc &h, const PassDesc *d_pass, const PhaseDesc *d_phases, const OpDesc *d_ops,
                          const float2 *mats, long long mstride, float2 *state, int N, int batch,
@@ -124,7 +146,11 @@ cudaError_t launch_fwd_k(const PassDesc &h, const PassDesc *d_pass, const PhaseD
   const int T = h.T;
   const int L = T < kLowBits ? T : kLowBits;
   const int threads = 1 << (T - K);
-  const size_t smem = ((size_t)1 << T) * sizeof(float2) + ((size_t)1 << (T - L)) * sizeof(long long);
+  const size_t n_runs = ((size_t)1 << (T - L)) < 2 ? 2 : ((size_t)1 << (T - L));
+  size_t smem = ((size_t)1 << T) * sizeof(float2) + n_runs * sizeof(long long);
+  const size_t stage = (size_t)(h.op_end - h.op_begin) * sizeof(OpDesc) + (size_t)(h.mat_end - h.mat_begin) * sizeof(float2);
+  const int staged = stage <= kStageBytes ? 1 : 0;
+  if (staged) smem += stage;
   static int configured_smem[kMaxReg + 1] = {0};
   if ((int)smem > configured_smem[K]) {
     cudaError_t e = cudaFuncSetAttribute(k_fwd_pass<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -138,12 +164,33 @@ cudaError_t launch_fwd_k(const PassDesc &h, const PassDesc *d_pass, const PhaseD
   const long long work = (long long)batch << h.n_outer;
   long long grid = (long long)num_sms() * per_sm;
   if (grid > work) grid = work;
-  k_fwd_pass<K><<<(unsigned)grid, threads, smem, s>>>(d_pass, d_phases, d_ops, mats, mstride, state, N, batch, init);
+  k_fwd_pass<K><<<(unsigned)grid, threads, smem, s>>>(d_pass, d_phases, d_ops, mats, mstride, state, N, batch, init,
+                                                       staged);
   return cudaGetLastError();
 }
 }  // namespace
 
 cudaError_t launch_forward(const tn_plan *p, const float2 *mats, long long mstride, float2 *state, cudaStream_t s) {
+  if (!p->jit_kernels.empty()) {
+    for (size_t i = 0; i < p->fwd.passes.size(); ++i) {
+      const PassDesc &h = p->fwd.passes[i];
+      const int threads = p->jit_threads[i];
+      const size_t smem = p->jit_smem[i];
+      int per_sm = 0;
+      cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)p->jit_kernels[i], threads, smem);
+      if (e != cudaSuccess) return e;
+      if (per_sm < 1) per_sm = 1;
+      long long work = (long long)p->batch << h.n_outer;
+      long long grid = (long long)num_sms() * per_sm;
+      if (grid > work) grid = work;
+      const float2 *m = mats;
+      unsigned long long init = p->init;
+      void *args[] = {(void *)&m, (void *)&mstride, (void *)&state, (void *)&work, (void *)&init};
+      e = cudaLaunchKernel((const void *)p->jit_kernels[i], dim3((unsigned)grid), dim3(threads), args, smem, s);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  }
   for (size_t i = 0; i < p->fwd.passes.size(); ++i) {
     const PassDesc &h = p->fwd.passes[i];
     cudaError_t e = cudaSuccess;

@@ -15,10 +15,9 @@ __global__ void k_materialize(const MatSlot *__restrict__ slots, int n_slots, co
   const int k = (int)(idx % n_slots);
   const MatSlot &s = slots[k];
   double ang[3] = {s.angle[0], s.angle[1], s.angle[2]};
-  if (s.param_idx >= 0) {
-    const int ar = gate_arity(s.kind);
-    for (int a = 0; a < ar; ++a) ang[a] = params[(long long)b * n_params + s.param_idx + a];
-  }
+  for (int a = 0; a < 3; ++a)
+    for (int k = 0; k < 2; ++k)
+      if (s.pidx[a][k] >= 0) ang[a] += params[(long long)b * n_params + s.pidx[a][k]];
   double tmp[32];
   float ent[32];
   const int n = slot_entries(s, ang, tmp, ent);

@@ -43,7 +43,7 @@ GateCls classify(const TnGate &g) {
   c.qa = g.q[0];
   c.qb = -1;
   switch (g.kind) {
-    case TN_GATE_Z: case TN_GATE_S: case TN_GATE_SDG: case TN_GATE_T: case TN_GATE_TDG: case TN_GATE_RZ:
+    case TN_GATE_Z: case TN_GATE_S: case TN_GATE_SDG: case TN_GATE_T: case TN_GATE_TDG: case TN_GATE_RZ: case KIND_P:
       c.type = OP_D1; c.shape = SHAPE_DIAG2; break;
     case TN_GATE_MAT1:
       if (mat1_is_diagonal(g)) { c.type = OP_D1; c.shape = SHAPE_DIAG2; }
@@ -60,13 +60,25 @@ GateCls classify(const TnGate &g) {
   return c;
 }
 
-// Algorithmic real flops per amplitude of one op (complex multiply = 6, add = 2).
-double op_flops(int type) {
+// Real flops per amplitude of one op as executed (complex multiply = 6, add = 2; a real
+// coefficient times a complex value = 2): a general 2x2 costs 14, a matrix with a real first
+// column (V) 10, a real or real-diagonal/imaginary-off-diagonal one (RY, H, SY, RX, SX) 6;
+// a phase diag(1, e) touches half the amplitudes.
+double op_flops(int type, int kind) {
   switch (type) {
-    case OP_G1: return 14.0;
+    case OP_G1:
+      if (kind == KIND_V) return 10.0;
+      if (kind == TN_GATE_RY || kind == TN_GATE_H || kind == TN_GATE_SY || kind == TN_GATE_RX || kind == TN_GATE_SX)
+        return 6.0;
+      if (kind == TN_GATE_X) return 0.0;
+      return 14.0;
+    case OP_D1:
+      if (kind == KIND_P || kind == TN_GATE_S || kind == TN_GATE_SDG || kind == TN_GATE_T || kind == TN_GATE_TDG)
+        return 3.0;
+      if (kind == TN_GATE_Z) return 0.0;
+      return 6.0;
     case OP_G2: return 30.0;
     case OP_C1: return 7.0;
-    case OP_D1: return 6.0;
     case OP_DP: return 1.5;
     default: return 0.0;
   }
@@ -106,7 +118,94 @@ struct Planner {
 
 uint64_t bitmask(int b) { return 1ull << b; }
 
+bool is_diagonal_kind(const TnGate &g) {
+  switch (g.kind) {
+    case TN_GATE_Z: case TN_GATE_S: case TN_GATE_SDG: case TN_GATE_T: case TN_GATE_TDG: case TN_GATE_RZ:
+    case TN_GATE_CZ: case TN_GATE_CP: case KIND_P:
+      return true;
+    case TN_GATE_MAT1:
+      return mat1_is_diagonal(g);
+    default:
+      return false;
+  }
+}
+
 }  // namespace
+
+// Rewrites every U3(t, p, l) as P(p) V(t, l) (exact: U3 = P(p) RY(t) P(l)) and carries each
+// pending P(p) forward along its qubit while it commutes with what follows (diagonal gates,
+// the control of a CNOT, a SWAP that relabels it), merging it into the next V as
+// V(t', l' + p).  A pending phase that meets anything else is emitted as a gate P(p) first;
+// the remaining ones are emitted at the end.  V costs 12 real multiply-adds per amplitude
+// pair instead of 16 for a general 2x2 matrix, because its first column is real.
+tn_circuit push_phases(const tn_circuit &c) {
+  tn_circuit o;
+  o.n = c.n;
+  o.init = c.init;
+  o.n_params = c.n_params;
+  struct Pending {
+    bool on = false;
+    double val = 0;
+    int idx = -1;
+  };
+  std::vector<Pending> pend((size_t)c.n);
+  auto emit_p = [&](int q) {
+    Pending &pp = pend[(size_t)q];
+    if (!pp.on) return;
+    TnGate g;
+    std::memset(&g, 0, sizeof(g));
+    g.kind = KIND_P;
+    g.q[0] = q;
+    g.q[1] = -1;
+    g.param_idx = -1;
+    for (int a = 0; a < 3; ++a) g.pidx[a][0] = g.pidx[a][1] = -1;
+    g.angle[0] = pp.val;
+    g.pidx[0][0] = pp.idx;
+    o.gates.push_back(g);
+    pp = Pending();
+  };
+  for (const TnGate &g : c.gates) {
+    if (g.kind == TN_GATE_U3) {
+      const int q = g.q[0];
+      TnGate v;
+      std::memset(&v, 0, sizeof(v));
+      v.kind = KIND_V;
+      v.q[0] = q;
+      v.q[1] = -1;
+      v.param_idx = -1;
+      for (int a = 0; a < 3; ++a) v.pidx[a][0] = v.pidx[a][1] = -1;
+      v.angle[0] = g.angle[0];
+      v.pidx[0][0] = g.pidx[0][0];
+      v.angle[1] = g.angle[2] + (pend[(size_t)q].on ? pend[(size_t)q].val : 0.0);
+      v.pidx[1][0] = g.pidx[2][0];
+      v.pidx[1][1] = pend[(size_t)q].on ? pend[(size_t)q].idx : -1;
+      o.gates.push_back(v);
+      pend[(size_t)q].on = true;
+      pend[(size_t)q].val = g.angle[1];
+      pend[(size_t)q].idx = g.pidx[1][0];
+      continue;
+    }
+    if (is_diagonal_kind(g)) {
+      o.gates.push_back(g);
+      continue;
+    }
+    if (g.kind == TN_GATE_CNOT) {
+      emit_p(g.q[1]);
+      o.gates.push_back(g);
+      continue;
+    }
+    if (g.kind == TN_GATE_SWAP) {
+      std::swap(pend[(size_t)g.q[0]], pend[(size_t)g.q[1]]);
+      o.gates.push_back(g);
+      continue;
+    }
+    emit_p(g.q[0]);
+    if (gate_nqubits(g.kind) == 2) emit_p(g.q[1]);
+    o.gates.push_back(g);
+  }
+  for (int q = 0; q < c.n; ++q) emit_p(q);
+  return o;
+}
 
 tn_status build_pass_plan(const tn_circuit &c, int T, int K, bool adjoint, std::vector<MatSlot> &slots,
                           PassPlan &out, std::string &err) {
@@ -133,8 +232,11 @@ tn_status build_pass_plan(const tn_circuit &c, int T, int K, bool adjoint, std::
     s.kind = g.kind;
     s.form = form;
     s.shape = shape;
-    s.param_idx = g.param_idx;
-    for (int a = 0; a < 3; ++a) s.angle[a] = g.angle[a];
+    for (int a = 0; a < 3; ++a) {
+      s.angle[a] = g.angle[a];
+      s.pidx[a][0] = g.pidx[a][0];
+      s.pidx[a][1] = g.pidx[a][1];
+    }
     for (int a = 0; a < 32; ++a) s.fixed[a] = g.mat[a];
     int off = 0;
     if (!slots.empty()) {
@@ -198,6 +300,7 @@ tn_status build_pass_plan(const tn_circuit &c, int T, int K, bool adjoint, std::
     pd.n_outer = ol;
     pd.phase_begin = (int)out.phases.size();
     pd.grad_begin = (int)out.grads.size();
+    pd.mat_begin = slots.empty() ? 0 : slots.back().offset + ((shape_entries(slots.back().shape) + 1) & ~1);
     const int Kp = pd.K;
     int grad_slots = 0;
 
@@ -268,6 +371,7 @@ tn_status build_pass_plan(const tn_circuit &c, int T, int K, bool adjoint, std::
         else { kind = SRC_GLOB; pos = (uint8_t)b; }
       };
       int emitted = 0;
+      uint32_t pending_sign_bits = 0;  // register positions the accumulated CZ signs depend on
       blockedq = 0;
       std::vector<int> rest_pending;
       rest_pending.reserve(pending.size());
@@ -312,8 +416,23 @@ tn_status build_pass_plan(const tn_circuit &c, int T, int K, bool adjoint, std::
             out.grads.push_back(gr);
           }
         }
+        if (gc.type == OP_CZ) {
+          if (op.a_kind == SRC_REG) pending_sign_bits |= 1u << op.a_pos;
+          if (op.b_kind == SRC_REG) pending_sign_bits |= 1u << op.b_pos;
+        } else if (gc.type == OP_G1 || gc.type == OP_G2 || gc.type == OP_C1) {
+          uint32_t touched = 0;
+          if (gc.type == OP_G1) touched = 1u << op.a_pos;
+          if (gc.type == OP_G2) touched = (1u << op.a_pos) | (1u << op.b_pos);
+          if (gc.type == OP_C1) touched = 1u << op.b_pos;
+          // signs that depend only on other bits commute with this op; otherwise apply them first
+          if ((pending_sign_bits & touched) || (adjoint && op.has_grad)) {
+            op.flags |= OPF_FLUSH;
+            pending_sign_bits = 0;
+          }
+        }
         out.ops.push_back(op);
-        out.flops += op_flops(gc.type) * (double)(1ull << N);
+        out.op_gate.push_back(g);
+        out.flops += op_flops(gc.type, c.gates[g].kind) * (double)(1ull << N);
         ++emitted;
       }
       if (emitted == 0) break;
@@ -322,8 +441,12 @@ tn_status build_pass_plan(const tn_circuit &c, int T, int K, bool adjoint, std::
       pending.swap(rest_pending);
     }
     pd.phase_end = (int)out.phases.size();
+    pd.op_begin = pd.phase_begin < pd.phase_end ? out.phases[pd.phase_begin].op_begin : (int)out.ops.size();
+    pd.op_end = (int)out.ops.size();
     pd.grad_slots = grad_slots;
     out.max_grad_slots = std::max(out.max_grad_slots, grad_slots);
+    pd.mat_end = slots.empty() ? 0 : slots.back().offset + ((shape_entries(slots.back().shape) + 1) & ~1);
+    if (pd.mat_end < pd.mat_begin) pd.mat_end = pd.mat_begin;
     if (pd.phase_end == pd.phase_begin && !pd.init_mode) {
       err = "planner made no progress (internal error)";
       return TN_ERR_UNSUPPORTED;

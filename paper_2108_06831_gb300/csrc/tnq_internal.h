@@ -45,6 +45,7 @@ enum OpType : uint8_t {
   OP_DP = 6,  // phase e where bits a and b are both 1                  (1 entry)
 };
 enum SrcKind : uint8_t { SRC_REG = 0, SRC_TILE = 1, SRC_GLOB = 2 };
+enum OpFlags : uint8_t { OPF_FLUSH = 1 };
 
 struct alignas(16) OpDesc {
   uint8_t type;
@@ -52,7 +53,7 @@ struct alignas(16) OpDesc {
   uint8_t b_kind, b_pos;
   uint8_t has_grad;  // adjoint sweep: this op carries a parameter derivative
   uint8_t n_grad;    // number of derivative forms (angles) that follow at aux
-  uint8_t pad;
+  uint8_t flags;     // OPF_FLUSH: apply the pending CZ signs first (they touch this op's register bits)
   int32_t mat;       // offset (complex64 units) of the op's entries in a batch's matrix table
   int32_t aux;       // adjoint sweep: index of the first derivative record (GradRec) or -1
 };
@@ -79,6 +80,8 @@ struct alignas(16) PassDesc {
   int32_t n_outer;    // N - T
   int32_t grad_slots; // adjoint sweep: accumulation slots used by this pass
   int32_t grad_begin; // adjoint sweep: index of the pass's first GradRec (slot s = record grad_begin + s)
+  int32_t op_begin, op_end;    // the pass's ops (contiguous)
+  int32_t mat_begin, mat_end;  // the pass's matrix-table entries (contiguous, complex64 units)
   uint8_t tile_pos[16];   // tile-local bit -> global bit (tile_pos[i] = i for i < kLowBits)
   uint8_t outer_pos[40];  // outer (tile-index) bit -> global bit, ascending
 };
@@ -89,16 +92,23 @@ enum MatForm : int32_t { FORM_U = 0, FORM_ADJ = 1, FORM_D0 = 2, FORM_D1 = 3, FOR
 enum MatShape : int32_t { SHAPE_M2 = 0, SHAPE_M4 = 1, SHAPE_DIAG2 = 2, SHAPE_PHASE = 3 };
 
 struct alignas(16) MatSlot {
-  int32_t kind;       // tn_gate_kind
+  int32_t kind;       // tn_gate_kind or an internal kind (KIND_V, KIND_P)
   int32_t form;       // MatForm
   int32_t shape;      // MatShape
-  int32_t param_idx;  // -1: fixed angles below
   int32_t offset;     // destination offset (complex64 units)
-  int32_t pad[3];
+  int32_t pidx[3][2]; // angle a = angle[a] + sum of params[pidx[a][k]] over pidx >= 0
+  int32_t pad[2];
   double angle[3];
   double pad2;
   double fixed[32];   // MAT1/MAT2 entries (re, im)
 };
+
+// Internal gate kinds produced by the planner's phase-pushing rewrite (never in the ABI):
+//   V(t, a) = RY(t) P(a) = [[cos t/2, -sin t/2 e^{ia}], [sin t/2, cos t/2 e^{ia}]]
+//   P(a)    = diag(1, e^{ia})
+// so that U3(t, p, l) = P(p) V(t, l).
+constexpr int KIND_V = 64;
+constexpr int KIND_P = 65;
 
 // ---------------------------------------------------------------------------------------
 // Gate matrices in double precision (shared by the plan-time host path and the per-call
@@ -108,9 +118,14 @@ TNQ_HD void cset(double *o, int i, double re, double im) { o[2 * i] = re; o[2 * 
 
 // Full 2x2 / 4x4 matrix of a gate kind (form FORM_U), or its derivative w.r.t. angle a
 // (FORM_D0 + a).  Returns the dimension (2 or 4); 0 for an unknown kind.
+TNQ_HD int gate_nqubits(int kind) {
+  return (kind == TN_GATE_CZ || kind == TN_GATE_CNOT || kind == TN_GATE_CP || kind == TN_GATE_SWAP ||
+          kind == TN_GATE_MAT2) ? 2 : 1;
+}
+
 TNQ_HD int gate_matrix(int kind, int form, const double *ang, const double *fixed, double *o) {
   const double r2 = 0.70710678118654752440;
-  int dim = (kind >= TN_GATE_CZ && kind != TN_GATE_MAT1) ? 4 : 2;
+  int dim = gate_nqubits(kind) == 2 ? 4 : 2;
   for (int i = 0; i < 2 * dim * dim; ++i) o[i] = 0.0;
   const bool deriv = form >= FORM_D0;
   const int a = form - FORM_D0;
@@ -173,6 +188,12 @@ TNQ_HD int gate_matrix(int kind, int form, const double *ang, const double *fixe
     }
     case TN_GATE_SWAP: cset(o, 0, 1, 0); cset(o, 6, 1, 0); cset(o, 9, 1, 0); cset(o, 15, 1, 0); break;
     case TN_GATE_MAT1: for (int i = 0; i < 8; ++i) o[i] = fixed[i]; break;
+    case KIND_V: {
+      double c = cos(ang[0] * 0.5), s = sin(ang[0] * 0.5), ca = cos(ang[1]), sa = sin(ang[1]);
+      cset(o, 0, c, 0); cset(o, 1, -s * ca, -s * sa); cset(o, 2, s, 0); cset(o, 3, c * ca, c * sa);
+      break;
+    }
+    case KIND_P: cset(o, 0, 1, 0); cset(o, 3, cos(ang[0]), sin(ang[0])); break;
     case TN_GATE_MAT2: for (int i = 0; i < 32; ++i) o[i] = fixed[i]; break;
     default: return 0;
   }
@@ -181,10 +202,8 @@ TNQ_HD int gate_matrix(int kind, int form, const double *ang, const double *fixe
 
 // Number of angles a kind reads.
 TNQ_HD int gate_arity(int kind) {
-  return kind == TN_GATE_U3 ? 3 : (kind == TN_GATE_RX || kind == TN_GATE_RY || kind == TN_GATE_RZ || kind == TN_GATE_CP) ? 1 : 0;
-}
-TNQ_HD int gate_nqubits(int kind) {
-  return (kind >= TN_GATE_CZ && kind != TN_GATE_MAT1) ? 2 : 1;
+  return kind == TN_GATE_U3 ? 3 : kind == KIND_V ? 2
+       : (kind == TN_GATE_RX || kind == TN_GATE_RY || kind == TN_GATE_RZ || kind == TN_GATE_CP || kind == KIND_P) ? 1 : 0;
 }
 
 // Entries of a matrix slot: the full matrix in the shape the op consumes, optionally
@@ -220,7 +239,8 @@ TNQ_HD int slot_entries(const MatSlot &s, const double *ang, double *tmp /*32*/,
 struct TnGate {
   int kind;
   int q[2];
-  int param_idx;
+  int param_idx;   // ABI parameter index (first angle), -1 if fixed; -1 for internal kinds
+  int pidx[3][2];  // angle a = angle[a] + sum of params[pidx[a][k]] over pidx >= 0
   double angle[3];
   double mat[32];
 };
@@ -237,6 +257,7 @@ struct PassPlan {
   std::vector<tnq::PassDesc> passes;
   std::vector<tnq::PhaseDesc> phases;
   std::vector<tnq::OpDesc> ops;
+  std::vector<int> op_gate;  // circuit gate index of every op
   std::vector<tnq::GradRec> grads;
   double flops = 0;   // per batch element
   int max_grad_slots = 0;
@@ -244,6 +265,7 @@ struct PassPlan {
 
 struct tn_plan {
   int n;
+  long long n_gates;
   int batch;
   int n_params;
   uint64_t init;
@@ -262,6 +284,11 @@ struct tn_plan {
   tnq::OpDesc *d_fwd_ops = nullptr, *d_bwd_ops = nullptr;
   tnq::GradRec *d_bwd_grads = nullptr;
   float *d_fixed_mats = nullptr;  // materialised once when !param_dependent
+  // plan-specialised forward kernels (generated; empty when the interpreting kernel runs)
+  std::vector<cudaLibrary_t> jit_libs;
+  std::vector<cudaKernel_t> jit_kernels;
+  std::vector<int> jit_threads, jit_grid;
+  std::vector<size_t> jit_smem;
   size_t ws_bytes = 0;
   // workspace layout (byte offsets)
   size_t ws_mats = 0, ws_psi = 0, ws_lam = 0, ws_part = 0, ws_gacc = 0;
@@ -304,4 +331,5 @@ void set_error(const char *fmt, ...);
 tn_status cuda_fail(cudaError_t e, const char *what);
 tn_status build_pass_plan(const tn_circuit &c, int T, int K, bool adjoint, std::vector<MatSlot> &slots,
                           PassPlan &out, std::string &err);
+tn_circuit push_phases(const tn_circuit &c);
 }  // namespace tnq

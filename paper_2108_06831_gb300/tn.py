@@ -24,6 +24,7 @@ OK, ERR_INVALID_ARG, ERR_UNSUPPORTED, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_NUMERI
 TARGET_STATE, TARGET_AMPLITUDES, TARGET_EXPECTATION = 0, 1, 2
 PREC_FP32, PREC_3XTF32, PREC_SPLIT_BF16 = 0, 1, 2
 PLAN_HOST_ONLY = 1
+PLAN_NO_SPECIALIZE = 2
 
 GATE_KINDS = {name: i for i, name in enumerate(
     ["H", "X", "Y", "Z", "S", "SDG", "T", "TDG", "SX", "SY", "SW", "RX", "RY", "RZ", "U3",
@@ -46,7 +47,8 @@ class TnPlanStats(C.Structure):
     _fields_ = [("n_qubits", C.c_int32), ("n_params", C.c_int32), ("n_gates", C.c_int64),
                 ("n_passes", C.c_int32), ("n_phases", C.c_int32), ("n_ops", C.c_int64),
                 ("tile_qubits", C.c_int32), ("reg_qubits", C.c_int32), ("hbm_bytes", C.c_double),
-                ("flops", C.c_double), ("n_bwd_passes", C.c_int32), ("reserved", C.c_int32 * 7)]
+                ("flops", C.c_double), ("n_bwd_passes", C.c_int32), ("specialized", C.c_int32),
+                ("reserved", C.c_int32 * 6)]
 
 
 class TnPauliSum(C.Structure):
@@ -156,10 +158,10 @@ class CircuitHandle:
 
 class Plan:
     def __init__(self, ch: CircuitHandle, target: int = TARGET_STATE, precision: int = PREC_FP32, batch: int = 1,
-                 tile_qubits: int = 0, host_only: bool = False):
+                 tile_qubits: int = 0, host_only: bool = False, specialize: bool = True):
         o = TnPlanOpts()
         o.target, o.precision, o.batch, o.tile_qubits = target, precision, batch, tile_qubits
-        o.flags = PLAN_HOST_ONLY if host_only else 0
+        o.flags = (PLAN_HOST_ONLY if host_only else 0) | (0 if specialize else PLAN_NO_SPECIALIZE)
         h = _vp()
         _check(_lib.tn_plan_contraction(ch._h, C.byref(o), C.byref(h)), "tn_plan_contraction")
         self._h = h
@@ -277,13 +279,13 @@ class Contractor:
     """Plan + workspace for repeated contractions of one circuit (device memory from torch)."""
 
     def __init__(self, circ: Circuit, target: int = TARGET_STATE, batch: int = 1, tile_qubits: int = 0,
-                 precision: int = PREC_FP32, device=None):
+                 precision: int = PREC_FP32, device=None, specialize: bool = True):
         torch = _torch()
         self.device = torch.device(device or "cuda")
         with torch.cuda.device(self.device):
             self.circuit_handle = CircuitHandle(circ)
             self.plan = Plan(self.circuit_handle, target=target, precision=precision, batch=batch,
-                             tile_qubits=tile_qubits)
+                             tile_qubits=tile_qubits, specialize=specialize)
         self.n_qubits, self.batch, self.n_params = circ.n_qubits, batch, self.plan.n_params
         nb = max(self.plan.workspace_bytes, 16)
         self.workspace = torch.empty(nb, dtype=torch.uint8, device=self.device)

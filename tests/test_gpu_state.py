@@ -24,9 +24,9 @@ def rel_l2(a, b):
     return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
 
 
-def gpu_state(circ, params=None, batch=1, tile=0):
+def gpu_state(circ, params=None, batch=1, tile=0, specialize=True):
     tn = _tn()
-    ctr = tn.Contractor(circ, target=tn.TARGET_STATE, batch=batch, tile_qubits=tile)
+    ctr = tn.Contractor(circ, target=tn.TARGET_STATE, batch=batch, tile_qubits=tile, specialize=specialize)
     p = None if params is None else torch.as_tensor(np.asarray(params, dtype=np.float64).reshape(batch, -1),
                                                     device="cuda").contiguous()
     out = ctr.state(p)
@@ -35,25 +35,28 @@ def gpu_state(circ, params=None, batch=1, tile=0):
     return out.cpu().numpy()
 
 
+@pytest.mark.parametrize("specialize", [True, False])
 @pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 6, 8, 9, 11, 12])
-def test_random_circuits_small(n):
+def test_random_circuits_small(n, specialize):
+    """Every gate kind, both the plan-specialised kernels and the interpreting kernel."""
     from oracle.statevector import simulate_state
     for seed in range(3):
         c = C.random_circuit(n, 12 * n + 5, 100 * n + seed)
         c.init_basis = (seed * 7919) % (1 << n)
         ref = simulate_state(c)
-        got = gpu_state(c)[0]
+        got = gpu_state(c, specialize=specialize)[0]
         assert rel_l2(got, ref) <= STATE_TOL, (n, seed)
 
 
-@pytest.mark.parametrize("n,tile", [(13, 5), (14, 6), (15, 8), (16, 10), (17, 12), (18, 13), (16, 7)])
-def test_random_circuits_multipass(n, tile):
+@pytest.mark.parametrize("specialize", [True, False])
+@pytest.mark.parametrize("n,tile", [(13, 6), (14, 6), (15, 8), (16, 10), (17, 12), (18, 13), (16, 7)])
+def test_random_circuits_multipass(n, tile, specialize):
     """Several tiles and passes; tile sizes from the smallest allowed upwards."""
     from oracle.statevector import simulate_state
     c = C.random_circuit(n, 10 * n, 7 * n + tile)
     c.init_basis = (n * 104729) % (1 << n)
     ref = simulate_state(c)
-    got = gpu_state(c, tile=tile)[0]
+    got = gpu_state(c, tile=tile, specialize=specialize)[0]
     assert rel_l2(got, ref) <= STATE_TOL
 
 
@@ -93,11 +96,13 @@ def test_parameterized_batch():
 
 
 def test_cfg2_full_size_sampled():
-    """24-qubit brickwork, depth 20, in the bench's launch configuration: sampled amplitudes
-    against the oracle's network contraction, plus the norm."""
+    """24-qubit brickwork, depth 20, in the bench's launch configuration (parameterised
+    U3 angles, plan-specialised kernels): sampled amplitudes against the oracle's network
+    contraction, plus the norm."""
     from oracle.tn import contract_amplitude
+    c, params = C.brickwork(24, 20, 1001, parameterized=True)
+    got = gpu_state(c, params)[0]
     c, _ = C.brickwork(24, 20, 1001)
-    got = gpu_state(c)[0]
     assert abs(np.linalg.norm(got.astype(np.complex128)) - 1.0) < 1e-5
     xs = C.random_bitstrings(24, 10, 4242)
     ref = np.array([contract_amplitude(c, int(x)) for x in xs])
