@@ -215,6 +215,21 @@ tn_status tn_state_expectation(const tn_observable *H, int32_t batch, const void
                                double *out_dev, void *workspace_dev, size_t workspace_bytes,
                                tn_stream_t s);
 
+/* The reduction of tn_state_expectation for callers that cannot provide a workspace (the
+ * paper has no counterpart; this is a deployment variant).  Such callers either have all of
+ * their device memory owned by another allocator with a fixed budget, or run where a
+ * cudaMalloc would implicitly synchronise the device.  The partial sums go to a 1 MiB array
+ * compiled into the library (held on every GPU that loads it until the process exits):
+ *   - requests needing more than 131072 partial sums (batch x reduction passes x 512) fail
+ *     with TN_ERR_INVALID_ARG, and nothing is enqueued;
+ *   - all calls on a device share the array; each clears the slots it uses, but calls that
+ *     overlap on the GPU (unordered streams) race on it;
+ *   - the first call on a device looks up the array's address (cudaGetSymbolAddress) with
+ *     that device current; make that first call before any stream capture begins.
+ * Allocates no device memory.  Other arguments and results as tn_state_expectation. */
+tn_status tn_state_expectation_noalloc(const tn_observable *H, int32_t batch, const void *state_dev,
+                                       double *out_dev, tn_stream_t s);
+
 /* Index permutation over binary legs (Sec. 3: operands regrouped into matrices before a
  * merge): for a tensor of n_legs legs of size 2 (leg 0 most significant), out has legs
  * ordered perm[0..n_legs): out leg j is in leg perm[j].  complex64, batch independent

@@ -72,6 +72,7 @@ _sigs = {
     "tn_expectation_backward": [_vp, _vp, _vp, _vp, _vp, _vp, _vp],
     "tn_state_expectation_workspace_bytes": [_vp, C.c_int32, C.POINTER(C.c_size_t)],
     "tn_state_expectation": [_vp, C.c_int32, _vp, _vp, _vp, C.c_size_t, _vp],
+    "tn_state_expectation_noalloc": [_vp, C.c_int32, _vp, _vp, _vp],
     "tn_permute": [C.c_int32, C.POINTER(C.c_int32), C.c_int64, _vp, _vp, _vp],
     "tn_cgemm_workspace_bytes": [C.c_int32, C.c_int64, C.c_int64, C.c_int64, C.c_int64, C.POINTER(C.c_size_t)],
     "tn_cgemm_batched": [C.c_int32, C.c_int64, C.c_int64, C.c_int64, C.c_int64, _vp, _vp, _vp, _vp, C.c_size_t, _vp],
@@ -245,6 +246,12 @@ def state_expectation_workspace_bytes(obs: Observable, batch: int) -> int:
 def state_expectation(obs: Observable, batch: int, state, out, workspace, workspace_bytes: int, stream=None) -> None:
     _check(_lib.tn_state_expectation(obs._h, batch, _ptr(state), _ptr(out), _ptr(workspace), workspace_bytes,
                                      _stream(stream)), "tn_state_expectation")
+
+
+def state_expectation_noalloc(obs: Observable, batch: int, state, out, stream=None) -> None:
+    """tn_state_expectation without a workspace (scratch compiled into the library)."""
+    _check(_lib.tn_state_expectation_noalloc(obs._h, batch, _ptr(state), _ptr(out), _stream(stream)),
+           "tn_state_expectation_noalloc")
 
 
 def permute(n_legs: int, perm: Sequence[int], batch: int, inp, out, stream=None) -> None:
