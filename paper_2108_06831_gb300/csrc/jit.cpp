@@ -284,8 +284,11 @@ std::string gen_pass(const tn_plan &p, int pi, const std::vector<int> &op_kind, 
            NTHR, pi);
   E.line(buf);
   E.line("  extern __shared__ __align__(16) unsigned char smraw[];");
-  E.line("  float2 *sm = reinterpret_cast<float2 *>(smraw);");
-  snprintf(buf, sizeof buf, "  float4 *smat = reinterpret_cast<float4 *>(sm + %d);", TILE);
+  const int nbuf = pd.init_mode ? 1 : 2;  // loaded passes double-buffer their tiles
+  E.line("  float2 *const sm0 = reinterpret_cast<float2 *>(smraw);");
+  snprintf(buf, sizeof buf, "  float2 *const sm1 = sm0 + %d;", (nbuf - 1) * TILE);
+  E.line(buf);
+  snprintf(buf, sizeof buf, "  float4 *smat = reinterpret_cast<float4 *>(sm0 + %d);", nbuf * TILE);
   E.line(buf);
   E.line("  const int tid = threadIdx.x;");
   // per-thread part of the load/store deposit: tile index i = 2*tid + 2*k*NTHR
@@ -299,35 +302,74 @@ std::string gen_pass(const tn_plan &p, int pi, const std::vector<int> &op_kind, 
     E.line("  const int sw_t = swz(2 * tid);");
   }
   E.line("  long long cur_b = -1;");
+  const int chunks = TILE / 2 / NTHR;
+  auto emit_base = [&](const char *tv, const char *bv) {
+    std::string base = "0ull";
+    for (int j = 0; j < pd.n_outer; ++j) {
+      snprintf(buf, sizeof buf, " | ((u64)((%s >> %d) & 1) << %d)", tv, j, (int)pd.outer_pos[j]);
+      base += buf;
+    }
+    return std::string("const u64 ") + bv + " = " + base + ";";
+  };
+  if (!pd.init_mode) {
+    // asynchronous copy of one tile into a buffer (8-byte cp.async keeps the element swizzle)
+    E.line("  auto issue = [&](long long w2, float2 *dst) {");
+    snprintf(buf, sizeof buf, "    const long long b2 = w2 >> %d; const long long t2 = w2 & %lldll;", pd.n_outer,
+             (long long)((1ll << pd.n_outer) - 1));
+    E.line(buf);
+    E.line("    " + emit_base("t2", "base2"));
+    snprintf(buf, sizeof buf, "    const float2 *src = state + (b2 << %d) + base2 + dep_t;", N);
+    E.line(buf);
+    E.line("    const unsigned d0 = (unsigned)__cvta_generic_to_shared(dst);");
+    for (int k = 0; k < chunks; ++k) {
+      const int ik = 2 * k * NTHR;
+      long long depk = 0;
+      for (int j = 0; j < T; ++j)
+        if ((ik >> j) & 1) depk |= 1ll << pd.tile_pos[j];
+      const int swk = swz_host(ik);
+      snprintf(buf, sizeof buf,
+               "    asm volatile(\"cp.async.ca.shared.global [%%0], [%%1], 8;\" :: \"r\"(d0 + 8u * (unsigned)(sw_t ^ %d)), \"l\"(src + %lldll));",
+               swk, depk);
+      E.line(buf);
+      snprintf(buf, sizeof buf,
+               "    asm volatile(\"cp.async.ca.shared.global [%%0], [%%1], 8;\" :: \"r\"(d0 + 8u * (unsigned)(sw_t ^ %d ^ 1)), \"l\"(src + %lldll + 1));",
+               swk, depk);
+      E.line(buf);
+    }
+    E.line("  };");
+    E.line("  if (blockIdx.x < work) issue(blockIdx.x, sm0);");
+    E.line("  asm volatile(\"cp.async.commit_group;\" ::: \"memory\");");
+  }
+  E.line("  int cur = 0;");
   snprintf(buf, sizeof buf, "  for (long long w = blockIdx.x; w < work; w += gridDim.x) {");
   E.line(buf);
+  E.line("    float2 *const sm = cur ? sm1 : sm0;");
   snprintf(buf, sizeof buf, "    const long long b = w >> %d; const long long t = w & %lldll;", pd.n_outer,
            (long long)((1ll << pd.n_outer) - 1));
   E.line(buf);
-  {
-    std::string base = "0ull";
-    for (int j = 0; j < pd.n_outer; ++j) {
-      snprintf(buf, sizeof buf, " | ((u64)((t >> %d) & 1) << %d)", j, (int)pd.outer_pos[j]);
-      base += buf;
-    }
-    E.line("    const u64 base = " + base + ";");
+  E.line("    " + emit_base("t", "base"));
+  if (!pd.init_mode) {
+    // prefetch the next tile into the other buffer, then wait for this one
+    E.line("    if (w + gridDim.x < work) issue(w + gridDim.x, cur ? sm0 : sm1);");
+    E.line("    asm volatile(\"cp.async.commit_group;\" ::: \"memory\");");
+    E.line("    asm volatile(\"cp.async.wait_group 1;\" ::: \"memory\");");
+    E.line("    __syncthreads();");
   }
   snprintf(buf, sizeof buf, "    float2 *st = state + (b << %d);", N);
   E.line(buf);
   // stage this batch element's matrix entries
   E.line("    if (b != cur_b) {");
-  E.line("      if (cur_b >= 0) __syncthreads();");
   snprintf(buf, sizeof buf,
            "      const float4 *src = reinterpret_cast<const float4 *>(mats_g + b * mstride + %d);", pd.mat_begin);
   E.line(buf);
   snprintf(buf, sizeof buf, "      for (int i = tid; i < %d; i += %d) smat[i] = src[i];", mat_n / 2, NTHR);
   E.line(buf);
   E.line("      cur_b = b;");
+  E.line("      __syncthreads();");
   E.line("    }");
   snprintf(buf, sizeof buf, "    const float4 *M4 = smat - %d;", pd.mat_begin / 2);
   E.line(buf);
-  // load (or synthesise) the tile
-  const int chunks = TILE / 2 / NTHR;
+  // synthesise the first pass's tile (loaded passes were filled by cp.async above)
   if (pd.init_mode) {
     snprintf(buf, sizeof buf, "    for (int i = tid; i < %d; i += %d) sm[i] = make_float2(0.f, 0.f);", TILE, NTHR);
     E.line(buf);
@@ -344,22 +386,8 @@ std::string gen_pass(const tn_plan &p, int pi, const std::vector<int> &op_kind, 
     E.line("      const int li = " + li + ";");
     E.line("      sm[swz(li)] = make_float2(1.f, 0.f);");
     E.line("    }");
-  } else {
-    for (int k = 0; k < chunks; ++k) {
-      const int ik = 2 * k * NTHR;
-      long long depk = 0;
-      for (int j = 0; j < T; ++j)
-        if ((ik >> j) & 1) depk |= 1ll << pd.tile_pos[j];
-      const int swk = swz_host(ik);
-      snprintf(buf, sizeof buf,
-               "    { const float4 v = *reinterpret_cast<const float4 *>(st + base + dep_t + %lldll); "
-               "sm[sw_t ^ %d] = make_float2(v.x, v.y); sm[sw_t ^ %d ^ 1] = make_float2(v.z, v.w); }",
-               depk, swk, swk);
-      // the second amplitude is tile index i + 1: swz(i + 1) = swz(i) ^ swz(1) = swz(i) ^ 1
-      E.line(buf);
-    }
+    E.line("    __syncthreads();");
   }
-  E.line("    __syncthreads();");
   // phases
   for (int ph = pd.phase_begin; ph < pd.phase_end; ++ph) {
     const PhaseDesc &d = p.fwd.phases[ph];
@@ -403,10 +431,12 @@ std::string gen_pass(const tn_plan &p, int pi, const std::vector<int> &op_kind, 
     E.line(buf);
   }
   E.line("    __syncthreads();");
+  E.line("    cur ^= 1;");
   E.line("  }");
+  if (!pd.init_mode) E.line("  asm volatile(\"cp.async.wait_group 0;\" ::: \"memory\");");
   E.line("}");
   *threads_out = NTHR;
-  *smem_out = (size_t)TILE * 8 + (size_t)mat_n * 8;
+  *smem_out = (size_t)nbuf * TILE * 8 + (size_t)mat_n * 8;
   return E.o.str();
 }
 
