@@ -1,4 +1,28 @@
 // Kernel (c), tensor-core forms: batched complex GEMM on tcgen05 with TMEM accumulators.
+//
+// A pairwise merge of two tensors is the product of Eq. 2.2, C[m][n] = sum_k A[m][k] B[n][k]
+// once the legs are grouped (both operands with the contracted index contiguous).  The
+// complex product is computed as one real GEMM: A (complex M x K, interleaved) is already
+// the real M x 2K matrix [re im re im ...], and B is replaced by its 2x2 real embedding
+// B2 (2N x 2K) with rows 2n = (Br, -Bi) and 2n+1 = (Bi, Br) per k, so that the real
+// product A B2^T, read as interleaved pairs, is exactly Cr = ArBr - AiBi, Ci = ArBi + AiBr.
+//
+// FP32 accuracy on low-precision tensor cores comes from splitting the operands:
+//   3XTF32:     x = hi + lo, hi = x rounded to TF32, lo = x - hi (exact);
+//               C = hi*hi + hi*lo + lo*hi (kind::tf32, three MMAs per K slice);
+//   SPLIT_BF16: x = x0 + x1 + x2 with x0 = bf16(x), x1 = bf16(x - x0), x2 = bf16(x - x0 - x1);
+//               C = x0y0 + x0y1 + x1y0 + x0y2 + x1y1 + x2y0 (kind::f16 with bf16 operands).
+// The split and the embedding are written once per call into the workspace by small
+// prep kernels; the GEMM kernel streams the parts with TMA (128-byte swizzle) through a
+// multi-stage mbarrier pipeline, a single thread issues tcgen05.mma into a 128 x BN FP32
+// accumulator in tensor memory, and all four warps drain it with tcgen05.ld.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include <cstring>
+#include <mutex>
+
 #include "kernels.h"
 
 namespace tnq {
@@ -6,16 +30,404 @@ namespace tnq {
 cudaError_t launch_cgemm_fp32(long long batch, long long M, long long N, long long K, const float2 *A, const float2 *B,
                               float2 *C, cudaStream_t s);
 
+namespace {
+
+constexpr int BM = 128;          // rows of A per CTA (MMA M)
+constexpr int BN = 128;          // real columns of C per CTA (MMA N) = 64 complex columns
+constexpr int KBYTES = 128;      // bytes of K per stage and operand row (one 128-byte swizzle span)
+constexpr int kThreads = 128;
+constexpr unsigned long long kWaitNs = 2000000000ull;  // bound of every mbarrier wait
+
+enum : int { PREC_TF32 = 1, PREC_BF16 = 2 };
+
+template <int PREC>
+struct Cfg;
+template <>
+struct Cfg<PREC_TF32> {
+  static constexpr int kElem = 4, kParts = 2, kProducts = 3, kStages = 3, kMmaK = 8, kFmt = 2;
+  __device__ static int pa(int p) { return p == 2 ? 1 : 0; }  // (hi,hi), (hi,lo), (lo,hi)
+  __device__ static int pb(int p) { return p == 1 ? 1 : 0; }
+};
+template <>
+struct Cfg<PREC_BF16> {
+  static constexpr int kElem = 2, kParts = 3, kProducts = 6, kStages = 2, kMmaK = 16, kFmt = 1;
+  // (0,0) (0,1) (1,0) (0,2) (1,1) (2,0)
+  __device__ static int pa(int p) { return p == 2 ? 1 : p == 4 ? 1 : p == 5 ? 2 : 0; }
+  __device__ static int pb(int p) { return p == 1 ? 1 : p == 3 ? 2 : p == 4 ? 1 : 0; }
+};
+
+constexpr int kTileA = BM * KBYTES;  // bytes of one A part per stage
+constexpr int kTileB = BN * KBYTES;
+
+__device__ __forceinline__ uint32_t saddr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *b, int n) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(b)), "r"(n));
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(saddr(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t *b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(saddr(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ unsigned long long now_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+// Bounded wait (about two seconds of wall time): false, and the device status word set, if
+// the phase never completed.
+__device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity, int *status) {
+  if (mbar_try(b, parity)) return true;
+  const unsigned long long t0 = now_ns();
+  for (;;) {
+    for (int i = 0; i < 256; ++i)
+      if (mbar_try(b, parity)) return true;
+    if (now_ns() - t0 > kWaitNs) break;
+  }
+  if (status) atomicCAS(status, 0, (int)TN_ERR_TIMEOUT);
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, uint64_t *bar, int c0, int c1, int c2) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];" ::
+          "r"(saddr(dst)),
+      "l"(map), "r"(saddr(bar)), "r"(c0), "r"(c1), "r"(c2)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor (K-major operand, 128-byte swizzle, 8-row groups 1024 B apart).
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr & 0x3FFFF) >> 4);       // start address
+  d |= (uint64_t)1 << 16;                        // leading byte offset (unused with this swizzle)
+  d |= (uint64_t)(1024 >> 4) << 32;              // stride byte offset: next 8-row group
+  d |= (uint64_t)1 << 46;                        // descriptor version
+  d |= (uint64_t)2 << 61;                        // 128-byte swizzle
+  return d;
+}
+
+template <int PREC>
+__device__ __forceinline__ constexpr uint32_t instr_desc() {
+  return (1u << 4)                                   // D: F32
+         | ((uint32_t)Cfg<PREC>::kFmt << 7)          // A format
+         | ((uint32_t)Cfg<PREC>::kFmt << 10)         // B format
+         | ((uint32_t)(BN >> 3) << 17)               // N
+         | ((uint32_t)(BM >> 4) << 24);              // M
+}
+
+template <int PREC>
+__device__ __forceinline__ void mma(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t acc) {
+  constexpr uint32_t idesc = instr_desc<PREC>();
+  if constexpr (PREC == PREC_TF32) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc));
+  } else {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc));
+  }
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(saddr(bar))
+               : "memory");
+}
+
+struct TmaMaps {
+  CUtensorMap a[3];
+  CUtensorMap b[3];
+};
+
+template <int PREC>
+__global__ void __launch_bounds__(kThreads, 1) k_cgemm_tc(const __grid_constant__ TmaMaps maps, int k_tiles,
+                                                          long long M, long long N2, float *__restrict__ C,
+                                                          int *status) {
+  using CF = Cfg<PREC>;
+  constexpr int S = CF::kStages;
+  constexpr int stage_bytes = CF::kParts * (kTileA + kTileB);
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  // 1024-byte alignment of every tile (required by the 128-byte swizzle pattern)
+  unsigned char *smem = reinterpret_cast<unsigned char *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  __shared__ __align__(8) uint64_t full[S], empty[S], done;
+  __shared__ uint32_t tmem_base;
+  __shared__ int abort_flag;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int n0 = blockIdx.x * BN, m0 = blockIdx.y * BM, bz = blockIdx.z;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(&done, 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 2) {  // the whole warp allocates BN fp32 columns of tensor memory
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(&tmem_base)),
+                 "r"(BN));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem_d = tmem_base;
+
+  if (warp == 0 && lane == 0) {
+    // TMA producer
+    for (int kt = 0; kt < k_tiles; ++kt) {
+      const int s = kt % S;
+      if (kt >= S && !mbar_wait(&empty[s], ((kt / S) - 1) & 1, status)) {
+        abort_flag = 1;
+        break;
+      }
+      mbar_expect_tx(&full[s], stage_bytes);
+      unsigned char *st = smem + (size_t)s * stage_bytes;
+      const int kc = kt * (KBYTES / CF::kElem);
+      for (int p = 0; p < CF::kParts; ++p) {
+        tma_load_3d(st + p * kTileA, &maps.a[p], &full[s], kc, m0, bz);
+        tma_load_3d(st + CF::kParts * kTileA + p * kTileB, &maps.b[p], &full[s], kc, n0, bz);
+      }
+    }
+  } else if (warp == 1 && lane == 0) {
+    // MMA issuer
+    bool ok = true;
+    for (int kt = 0; kt < k_tiles; ++kt) {
+      const int s = kt % S;
+      if (!mbar_wait(&full[s], (kt / S) & 1, status)) {
+        ok = false;
+        abort_flag = 1;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t st = saddr(smem + (size_t)s * stage_bytes);
+#pragma unroll
+      for (int p = 0; p < CF::kProducts; ++p) {
+        const uint32_t a_base = st + CF::pa(p) * kTileA;
+        const uint32_t b_base = st + CF::kParts * kTileA + CF::pb(p) * kTileB;
+#pragma unroll
+        for (int kk = 0; kk < KBYTES / (CF::kMmaK * CF::kElem); ++kk) {
+          const uint32_t off = kk * CF::kMmaK * CF::kElem;  // 32 bytes per MMA along K
+          mma<PREC>(tmem_d, smem_desc(a_base + off), smem_desc(b_base + off), (kt > 0 || p > 0 || kk > 0) ? 1u : 0u);
+        }
+      }
+      mma_commit(&empty[s]);  // frees the stage once these MMAs have read it
+    }
+    if (ok) mma_commit(&done);
+  }
+  __syncwarp();
+
+  // epilogue: every warp drains its 32 TMEM lanes (= 32 rows of the tile)
+  bool have = !abort_flag && mbar_wait(&done, 0, status);
+  have = __all_sync(0xFFFFFFFFu, have);  // tcgen05.ld is warp-collective: decide per warp
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (have) {
+    const long long row = m0 + warp * 32 + lane;
+    float *crow = C + ((long long)bz * M + row) * N2 + n0;
+#pragma unroll 1
+    for (int c = 0; c < BN; c += 32) {
+      uint32_t r[32];
+      const uint32_t taddr = tmem_d + ((uint32_t)(warp * 32) << 16) + (uint32_t)c;
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+          "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+            "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+            "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+            "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+          : "r"(taddr));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      float4 *dst = reinterpret_cast<float4 *>(crow + c);
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        dst[q] = make_float4(__uint_as_float(r[4 * q]), __uint_as_float(r[4 * q + 1]), __uint_as_float(r[4 * q + 2]),
+                             __uint_as_float(r[4 * q + 3]));
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (abort_flag && threadIdx.x == 0) {
+    // let copies already in flight land before the CTA's shared memory is released
+    for (int s = 0; s < S; ++s) mbar_wait(&full[s], 0, nullptr);
+  }
+  if (warp == 2) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_d), "r"(BN));
+  }
+}
+
+// ------------------------------------------------------------------------------ prep kernels
+
+__device__ __forceinline__ float tf32_rna(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+// A (real view [rows][cols]) -> parts
+template <int PREC>
+__global__ void k_split(const float *__restrict__ x, long long n, void *p0, void *p1, void *p2) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const float v = x[i];
+    if constexpr (PREC == PREC_TF32) {
+      const float hi = tf32_rna(v);
+      static_cast<float *>(p0)[i] = hi;
+      static_cast<float *>(p1)[i] = v - hi;
+    } else {
+      const __nv_bfloat16 b0 = __float2bfloat16_rn(v);
+      const float r1 = v - __bfloat162float(b0);
+      const __nv_bfloat16 b1 = __float2bfloat16_rn(r1);
+      const float r2 = r1 - __bfloat162float(b1);
+      static_cast<__nv_bfloat16 *>(p0)[i] = b0;
+      static_cast<__nv_bfloat16 *>(p1)[i] = b1;
+      static_cast<__nv_bfloat16 *>(p2)[i] = __float2bfloat16_rn(r2);
+    }
+  }
+}
+
+// B (complex [N][K]) -> 2x2 real embedding [2N][2K], then split.
+template <int PREC>
+__global__ void k_embed_split(const float2 *__restrict__ b, long long N, long long K, long long batch, void *p0,
+                              void *p1, void *p2) {
+  const long long total = batch * N * K;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long bb = i / (N * K), r = i % (N * K), n = r / K, k = r % K;
+    const float2 v = b[i];
+    const long long base = bb * (2 * N) * (2 * K);
+    const long long i0 = base + (2 * n) * (2 * K) + 2 * k;      // row 2n:   (re, -im)
+    const long long i1 = base + (2 * n + 1) * (2 * K) + 2 * k;  // row 2n+1: (im,  re)
+    const float e[4] = {v.x, -v.y, v.y, v.x};
+    const long long at[4] = {i0, i0 + 1, i1, i1 + 1};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float x = e[q];
+      if constexpr (PREC == PREC_TF32) {
+        const float hi = tf32_rna(x);
+        static_cast<float *>(p0)[at[q]] = hi;
+        static_cast<float *>(p1)[at[q]] = x - hi;
+      } else {
+        const __nv_bfloat16 b0 = __float2bfloat16_rn(x);
+        const float r1 = x - __bfloat162float(b0);
+        const __nv_bfloat16 b1 = __float2bfloat16_rn(r1);
+        const float r2 = r1 - __bfloat162float(b1);
+        static_cast<__nv_bfloat16 *>(p0)[at[q]] = b0;
+        static_cast<__nv_bfloat16 *>(p1)[at[q]] = b1;
+        static_cast<__nv_bfloat16 *>(p2)[at[q]] = __float2bfloat16_rn(r2);
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------ host side
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static std::once_flag once;
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  std::call_once(once, [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
+bool make_map(CUtensorMap *m, const void *base, int elem, long long cols, long long rows, long long batch, int box_rows) {
+  auto enc = encode_fn();
+  if (!enc) return false;
+  const CUtensorMapDataType dt = elem == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+  cuuint64_t dims[3] = {(cuuint64_t)cols, (cuuint64_t)rows, (cuuint64_t)batch};
+  cuuint64_t strides[2] = {(cuuint64_t)cols * elem, (cuuint64_t)cols * rows * elem};
+  cuuint32_t box[3] = {(cuuint32_t)(KBYTES / elem), (cuuint32_t)box_rows, 1};
+  cuuint32_t es[3] = {1, 1, 1};
+  return enc(m, dt, 3, const_cast<void *>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+bool tc_shape_ok(int precision, long long M, long long N, long long K) {
+  const long long kelems = KBYTES / (precision == TN_PREC_3XTF32 ? 4 : 2);  // real K elements per stage
+  return M % BM == 0 && (2 * N) % BN == 0 && (2 * K) % kelems == 0 && M > 0 && N > 0 && K > 0 &&
+         M * 2 * N < (1ll << 40);
+}
+
+size_t part_bytes(int precision, long long rows, long long cols, long long batch) {
+  return (size_t)rows * cols * batch * (precision == TN_PREC_3XTF32 ? 4 : 2);
+}
+
+size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+template <int PREC>
+cudaError_t run_tc(long long batch, long long M, long long N, long long K, const float2 *A, const float2 *B, float2 *C,
+                   void *ws, cudaStream_t s) {
+  using CF = Cfg<PREC>;
+  const int prec_abi = PREC == PREC_TF32 ? TN_PREC_3XTF32 : TN_PREC_SPLIT_BF16;
+  const size_t pa = align256(part_bytes(prec_abi, M, 2 * K, batch));
+  const size_t pb = align256(part_bytes(prec_abi, 2 * N, 2 * K, batch));
+  char *w = static_cast<char *>(ws);
+  void *ap[3] = {w, w + pa, w + 2 * pa};
+  char *wb = w + CF::kParts * pa;
+  void *bp[3] = {wb, wb + pb, wb + 2 * pb};
+  const long long na = batch * M * 2 * K;
+  k_split<PREC><<<(unsigned)std::min<long long>((na + 255) / 256, 65535), 256, 0, s>>>(
+      reinterpret_cast<const float *>(A), na, ap[0], ap[1], ap[2]);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const long long nb = batch * N * K;
+  k_embed_split<PREC><<<(unsigned)std::min<long long>((nb + 255) / 256, 65535), 256, 0, s>>>(B, N, K, batch, bp[0],
+                                                                                           bp[1], bp[2]);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  TmaMaps maps;
+  std::memset(&maps, 0, sizeof(maps));
+  for (int p = 0; p < CF::kParts; ++p) {
+    if (!make_map(&maps.a[p], ap[p], CF::kElem, 2 * K, M, batch, BM)) return cudaErrorInvalidValue;
+    if (!make_map(&maps.b[p], bp[p], CF::kElem, 2 * K, 2 * N, batch, BN)) return cudaErrorInvalidValue;
+  }
+  const size_t smem = (size_t)CF::kStages * CF::kParts * (kTileA + kTileB) + 1024;
+  static bool configured = false;
+  if (!configured) {
+    e = cudaFuncSetAttribute(k_cgemm_tc<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  const int k_tiles = (int)((2 * K * CF::kElem) / KBYTES);
+  dim3 grid((unsigned)((2 * N) / BN), (unsigned)(M / BM), (unsigned)batch);
+  k_cgemm_tc<PREC><<<grid, kThreads, smem, s>>>(maps, k_tiles, M, 2 * N, reinterpret_cast<float *>(C),
+                                                static_cast<int *>(status_word_ptr()));
+  return cudaGetLastError();
+}
+
+}  // namespace
+
 size_t cgemm_workspace(int precision, long long batch, long long M, long long N, long long K) {
-  (void)precision; (void)batch; (void)M; (void)N; (void)K;
-  return 0;
+  if (precision == TN_PREC_FP32 || !tc_shape_ok(precision, M, N, K)) return 0;
+  const int parts = precision == TN_PREC_3XTF32 ? 2 : 3;
+  return parts * (align256(part_bytes(precision, M, 2 * K, batch)) + align256(part_bytes(precision, 2 * N, 2 * K, batch)));
 }
 
 cudaError_t launch_cgemm(int precision, long long batch, long long M, long long N, long long K, const float2 *A,
                          const float2 *B, float2 *C, void *ws, size_t ws_bytes, cudaStream_t s) {
-  (void)ws; (void)ws_bytes;
   if (precision == TN_PREC_FP32) return launch_cgemm_fp32(batch, M, N, K, A, B, C, s);
-  return cudaErrorNotSupported;
+  if (!tc_shape_ok(precision, M, N, K)) return cudaErrorNotSupported;
+  if (batch > 65535 || M / BM > 65535) return cudaErrorNotSupported;
+  if (ws_bytes < cgemm_workspace(precision, batch, M, N, K)) return cudaErrorInvalidValue;
+  if (precision == TN_PREC_3XTF32) return run_tc<PREC_TF32>(batch, M, N, K, A, B, C, ws, s);
+  return run_tc<PREC_BF16>(batch, M, N, K, A, B, C, ws, s);
 }
 
 }  // namespace tnq

@@ -23,7 +23,7 @@ namespace {
 
 constexpr int kPermThreads = 256;
 constexpr int kPermStages = 2;
-constexpr long long kSpinLimit = 1ll << 26;
+constexpr unsigned long long kWaitNs = 2000000000ull;  // bound of every mbarrier wait
 
 struct PermParams {
   int n, lo, e, n_outer;
@@ -65,9 +65,20 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
       : "memory");
 }
 
+__device__ __forceinline__ unsigned long long now_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+// Bounded wait (about two seconds of wall time): false, and the status word set, on expiry.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, int *status) {
-  for (long long it = 0; it < kSpinLimit; ++it)
-    if (mbar_try_wait(bar, parity)) return true;
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = now_ns();
+  for (;;) {
+    for (int i = 0; i < 256; ++i)
+      if (mbar_try_wait(bar, parity)) return true;
+    if (now_ns() - t0 > kWaitNs) break;
+  }
   if (status) atomicCAS(status, 0, (int)TN_ERR_TIMEOUT);
   return false;
 }

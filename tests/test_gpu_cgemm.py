@@ -1,0 +1,68 @@
+"""Kernel (c): batched complex GEMM against an FP64 product (GPU).
+
+C[b][m][n] = sum_k A[b][m][k] B[b][n][k].  Bar: relative Frobenius error <= 1e-5 for
+every precision (plain FP32 on CUDA cores, 3xTF32 and 3-way split BF16 on tcgen05).
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+TOL = 1e-5
+
+
+def _tn():
+    from paper_2108_06831_gb300 import tn
+    return tn
+
+
+def _run(prec, batch, M, N, K, seed=0, scale=1.0):
+    tn = _tn()
+    rng = np.random.default_rng(seed)
+    A = (rng.normal(size=(batch, M, K)) + 1j * rng.normal(size=(batch, M, K))) * scale
+    B = (rng.normal(size=(batch, N, K)) + 1j * rng.normal(size=(batch, N, K))) * scale
+    a = torch.as_tensor(A.astype(np.complex64), device="cuda")
+    b = torch.as_tensor(B.astype(np.complex64), device="cuda")
+    c = torch.full((batch, M, N), complex(float("nan"), 0), dtype=torch.complex64, device="cuda")
+    wsb = tn.cgemm_workspace_bytes(prec, batch, M, N, K)
+    ws = torch.empty(max(wsb, 16), dtype=torch.uint8, device="cuda")
+    tn.cgemm_batched(prec, batch, M, N, K, a, b, c, ws, wsb)
+    torch.cuda.synchronize()
+    assert tn.sync_status() == tn.OK
+    # reference from the complex64 inputs the GPU saw, in complex128
+    ref = np.einsum("bmk,bnk->bmn", A.astype(np.complex64).astype(np.complex128),
+                    B.astype(np.complex64).astype(np.complex128))
+    got = c.cpu().numpy().astype(np.complex128)
+    return float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+
+
+@pytest.mark.parametrize("shape", [(1, 128, 64, 16), (2, 256, 128, 64), (3, 128, 192, 32), (1, 384, 256, 256)])
+@pytest.mark.parametrize("prec", [0, 1, 2])
+def test_cgemm_precisions(prec, shape):
+    batch, M, N, K = shape
+    if prec == 2 and K % 32:
+        pytest.skip("split-BF16 path needs K % 32 == 0")
+    assert _run(prec, batch, M, N, K, seed=sum(shape) + prec) <= TOL
+
+
+def test_cgemm_fp32_ragged_shapes():
+    for shape in [(1, 5, 7, 3), (2, 65, 33, 17), (1, 1, 1, 1), (3, 130, 70, 9)]:
+        assert _run(0, *shape, seed=7) <= TOL
+
+
+def test_cgemm_large_dynamic_range():
+    # entries spanning several orders of magnitude: the split keeps FP32-level relative error
+    assert _run(1, 1, 256, 128, 128, seed=3, scale=1e-3) <= TOL
+    assert _run(2, 1, 256, 128, 128, seed=4, scale=1e3) <= TOL
+
+
+def test_cgemm_unsupported_tensor_shape():
+    tn = _tn()
+    a = torch.zeros((1, 100, 16), dtype=torch.complex64, device="cuda")
+    b = torch.zeros((1, 64, 16), dtype=torch.complex64, device="cuda")
+    c = torch.zeros((1, 100, 64), dtype=torch.complex64, device="cuda")
+    with pytest.raises(tn.TnError) as e:
+        tn.cgemm_batched(1, 1, 100, 64, 16, a, b, c)
+    assert e.value.status == tn.ERR_UNSUPPORTED
