@@ -40,7 +40,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="state24", choices=["state24", "state10", "grad20"])
+    ap.add_argument("--workload", default="state24",
+                    choices=["state24", "state10", "grad20", "gemm_fp32", "gemm_3xtf32", "gemm_bf16x3"])
     ap.add_argument("--tile", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -162,6 +163,10 @@ def run_oracle_sample(kind: str, n: int, depth: int, seed: int, budget: float):
 
 WORKLOADS = {
     "state24": dict(kind="state", n=24, depth=20, seed=1001, batch=1),
+    # batched complex GEMM of a pairwise merge (kernel c): C[b] = A[b] B[b]^T, complex64
+    "gemm_fp32": dict(kind="gemm", prec=0, M=4096, N=4096, K=4096, batch=1, n=0, depth=0, seed=7),
+    "gemm_3xtf32": dict(kind="gemm", prec=1, M=4096, N=4096, K=4096, batch=1, n=0, depth=0, seed=7),
+    "gemm_bf16x3": dict(kind="gemm", prec=2, M=4096, N=4096, K=4096, batch=1, n=0, depth=0, seed=7),
     "state10": dict(kind="state", n=10, depth=8, seed=1000, batch=512),
     "grad20": dict(kind="grad", n=20, depth=10, seed=4000, batch=64),
 }
@@ -210,7 +215,7 @@ def main():
 
     # the CPU baseline runs first, in a fresh process, before this process touches the GPU
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and wl["kind"] != "gemm":
         info, err = run_oracle_sample(wl["kind"], wl["n"], wl["depth"], wl["seed"], 12.0)
         unit = "amplitudes/s" if wl["kind"] == "state" else "grads/s"
         if info is not None:
@@ -260,6 +265,22 @@ def main():
         kernel_launches = fst["n_passes"]
         alg_bytes = fst["hbm_bytes"] * batch
         alg_flops = fst["flops"] * batch
+    elif wl["kind"] == "gemm":
+        batch, M, N, K, prec = wl["batch"], wl["M"], wl["N"], wl["K"], wl["prec"]
+        g = torch.Generator(device=dev).manual_seed(wl["seed"])
+        a = torch.randn((batch, M, K), dtype=torch.complex64, device=dev, generator=g)
+        bm = torch.randn((batch, N, K), dtype=torch.complex64, device=dev, generator=g)
+        cm = torch.empty((batch, M, N), dtype=torch.complex64, device=dev)
+        wsb = tn.cgemm_workspace_bytes(prec, batch, M, N, K)
+        ws = torch.empty(max(wsb, 16), dtype=torch.uint8, device=dev)
+        units_per_step = 8.0 * batch * M * N * K / 1e12  # algorithmic TFLOP (complex, 4-multiply form)
+        unit = "TFLOP/s"
+
+        def step():
+            tn.cgemm_batched(prec, batch, M, N, K, a, bm, cm, ws, wsb)
+        launches_per_step = 1 if prec == 0 else 3
+        kernel_only = None
+        ctr = None
     else:
         circ = C.hea(wl["n"], wl["depth"])
         batch = wl["batch"]
@@ -316,8 +337,8 @@ def main():
             "warmup": max(args.warmup, 3), "ms_per_step": t_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "c64 (f32)", "data": "synthetic",
             "config": {"workload": args.workload, "n_qubits": wl["n"], "depth": wl["depth"], "batch": batch,
-                       "tile_qubits": ctr.plan.stats()["tile_qubits"],
-                       "specialized_kernels": bool(ctr.plan.stats()["specialized"]),
+                       "tile_qubits": ctr.plan.stats()["tile_qubits"] if ctr is not None else None,
+                       "specialized_kernels": bool(ctr.plan.stats()["specialized"]) if ctr is not None else None,
                        "l2": "256 MiB buffer written between timed steps (untimed)",
                        "parallelism": f"replicas x{world}"},
             "clocks": clk.summary()}
@@ -366,7 +387,7 @@ def main():
         line["e2e"] = {"value": units_per_step * args.steps / (sum(ems) / 1000), "unit": unit,
                        "h2d_bytes_per_step": int(h_params.numel() * 8),
                        "d2h_bytes_per_step": int(h_out.numel() * 8)}
-    elif not args.no_e2e:
+    elif not args.no_e2e and wl["kind"] == "grad":
         h_params = torch.as_tensor(params).pin_memory()
         h_g = torch.empty_like(g_out, device="cpu").pin_memory()
         h_e = torch.empty_like(e_out, device="cpu").pin_memory()
@@ -382,6 +403,32 @@ def main():
         line["e2e"] = {"value": units_per_step * args.steps / (sum(ems) / 1000), "unit": unit,
                        "h2d_bytes_per_step": int(h_params.numel() * 8),
                        "d2h_bytes_per_step": int((h_g.numel() + h_e.numel()) * 8)}
+    if wl["kind"] == "gemm":
+        # tensor-pipe roofline of the whole call (operand split + GEMM), against the peak of the
+        # arithmetic the tensor cores run: TF32 = measured bf16 peak x nominal 1.1/2.25
+        bf16_peak = 1886.8
+        try:
+            with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+                bf16_peak = float(json.load(f)["bf16_tflops"])
+        except Exception:
+            pass
+        per_step_s = t_max / args.steps / 1000.0
+        alg = 8.0 * batch * wl["M"] * wl["N"] * wl["K"]
+        line["config"].update({"M": wl["M"], "N": wl["N"], "K": wl["K"], "precision": wl["prec"]})
+        if wl["prec"] == 0:
+            line["roofline"] = {"bound": "alu", "achieved": alg / per_step_s / 1e12, "peak": FP32_ALU_PEAK_TFLOPS,
+                                "unit": "TFLOP/s", "frac": alg / per_step_s / 1e12 / FP32_ALU_PEAK_TFLOPS,
+                                "traffic": None, "kernel": "k_cgemm_fp32"}
+        else:
+            products = 3 if wl["prec"] == 1 else 6
+            executed = products * alg  # real tensor flops: products x (2M)(2N)(2K)/... = products x 8MNK
+            peak = bf16_peak * (1.1 / 2.25) if wl["prec"] == 1 else bf16_peak
+            ach = executed / per_step_s / 1e12
+            line["roofline"] = {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                                "frac": ach / peak, "traffic": None,
+                                "kernel": "k_cgemm_tc (+ operand split kernels)",
+                                "peak_source": "MEASURED_PEAKS.json bf16_tflops" + (" x 1.1/2.25 (TF32 nominal ratio)"
+                                                                                   if wl["prec"] == 1 else "")}
     if cpu is not None:
         line["cpu_baseline"] = cpu
     if rank == 0:

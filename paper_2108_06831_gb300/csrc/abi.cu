@@ -231,7 +231,10 @@ tn_status tn_plan_contraction(const tn_circuit *c, const tn_plan_opts *opts, tn_
   std::string err;
   const tn_circuit fwd_circ = push_phases(*c);
   tn_status st = build_pass_plan(fwd_circ, T, K, false, p->slots, p->fwd, err);
-  if (st == TN_OK && o.target == TN_TARGET_EXPECTATION) st = build_pass_plan(*c, T, K, true, p->slots, p->bwd, err);
+  // the adjoint sweep stages two tiles (psi, lambda), double-buffered: at most 2^11 amplitudes each
+  const int T_bwd = std::min(T, 11);
+  if (st == TN_OK && o.target == TN_TARGET_EXPECTATION)
+    st = build_pass_plan(*c, T_bwd, std::min(T_bwd, 4), true, p->slots, p->bwd, err);
   if (st != TN_OK) {
     set_error("planner: %s", err.c_str());
     delete p;
@@ -270,7 +273,12 @@ tn_status tn_plan_contraction(const tn_circuit *c, const tn_plan_opts *opts, tn_
     std::vector<int> kinds(p->fwd.ops.size());
     for (size_t i = 0; i < kinds.size(); ++i) kinds[i] = fwd_circ.gates[(size_t)p->fwd.op_gate[i]].kind;
     std::string jerr;
-    tn_status u = jit_build(*p, kinds, true, jerr);
+    tn_status u = jit_build(*p, kinds, false, true, jerr);
+    if (u == TN_OK && jit_bwd_supported(*p)) {
+      std::vector<int> bk(p->bwd.ops.size());
+      for (size_t i = 0; i < bk.size(); ++i) bk[i] = c->gates[(size_t)p->bwd.op_gate[i]].kind;
+      u = jit_build(*p, bk, true, true, jerr);
+    }
     if (u != TN_OK) {
       set_error("plan-specialised kernels: %s", jerr.c_str());
       delete p;
@@ -304,7 +312,12 @@ tn_status tn_plan_contraction(const tn_circuit *c, const tn_plan_opts *opts, tn_
       std::vector<int> kinds(p->fwd.ops.size());
       for (size_t i = 0; i < kinds.size(); ++i) kinds[i] = fwd_circ.gates[(size_t)p->fwd.op_gate[i]].kind;
       std::string jerr;
-      u = jit_build(*p, kinds, false, jerr);
+      u = jit_build(*p, kinds, false, false, jerr);
+      if (u == TN_OK && jit_bwd_supported(*p)) {
+        std::vector<int> bk(p->bwd.ops.size());
+        for (size_t i = 0; i < bk.size(); ++i) bk[i] = c->gates[(size_t)p->bwd.op_gate[i]].kind;
+        u = jit_build(*p, bk, true, false, jerr);
+      }
       if (u != TN_OK) set_error("plan-specialised kernels: %s", jerr.c_str());
     }
     if (u != TN_OK) {

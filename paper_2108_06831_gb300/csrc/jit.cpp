@@ -17,6 +17,7 @@
 #include <unistd.h>
 
 #include <algorithm>
+#include <cctype>
 #include <atomic>
 #include <cstdio>
 #include <cstdlib>
@@ -440,6 +441,290 @@ std::string gen_pass(const tn_plan &p, int pi, const std::vector<int> &op_kind, 
   return E.o.str();
 }
 
+
+// Derivative dot 2 Re <lambda| D |psi> of one parameter of an op, reduced over the warp and
+// added to the pass's accumulation slot.  D has the structure of the gate kind.
+void emit_grad(Emitter &E, const OpDesc &op, int kind, const GradRec &gr, int nwarps) {
+  const int R = E.R;
+  char buf[320];
+  auto mat = [&](int k) {
+    snprintf(buf, sizeof buf, "f2(M4[%d], %d)", (gr.mat + k) >> 1, (gr.mat + k) & 1);
+    return std::string(buf);
+  };
+  E.line("{ float acc = 0.f;");
+  if (op.type == OP_G1) {
+    const int r = op.a_pos;
+    const char *fn = (kind == TN_GATE_RY || kind == TN_GATE_SY || kind == TN_GATE_H) ? "rr"
+                     : (kind == TN_GATE_RX || kind == TN_GATE_SX) ? "ri" : "cm2";
+    E.line("  const float2 d00 = " + mat(0) + ", d01 = " + mat(1) + ", d10 = " + mat(2) + ", d11 = " + mat(3) + ";");
+    for (int j = 0; j < R; ++j) {
+      if (j & (1 << r)) continue;
+      const int j1 = j | (1 << r);
+      std::string z0, z1;
+      if (std::string(fn) == "rr") {
+        z0 = "rr(d00.x, x, d01.x, y)";
+        z1 = "rr(d10.x, x, d11.x, y)";
+      } else if (std::string(fn) == "ri") {
+        z0 = "ri(d00.x, x, d01.y, y)";
+        z1 = "ri(d11.x, y, d10.y, x)";
+      } else {
+        z0 = "cm2(d00, x, d01, y)";
+        z1 = "cm2(d10, x, d11, y)";
+      }
+      snprintf(buf, sizeof buf,
+               "  { const float2 x = a[%d], y = a[%d]; const float2 z0 = %s, z1 = %s; "
+               "acc = fmaf(l[%d].x, z0.x, acc); acc = fmaf(l[%d].y, z0.y, acc); "
+               "acc = fmaf(l[%d].x, z1.x, acc); acc = fmaf(l[%d].y, z1.y, acc); }",
+               j, j1, z0.c_str(), z1.c_str(), j, j, j1, j1);
+      E.line(buf);
+    }
+  } else if (op.type == OP_D1) {
+    E.line("  const float2 d0 = " + mat(0) + ", d1 = " + mat(1) + ";");
+    if (op.a_kind == SRC_REG) {
+      for (int j = 0; j < R; ++j) {
+        snprintf(buf, sizeof buf, "  { const float2 z = cm(a[%d], %s); acc = fmaf(l[%d].x, z.x, acc); acc = fmaf(l[%d].y, z.y, acc); }",
+                 j, (j & (1 << op.a_pos)) ? "d1" : "d0", j, j);
+        E.line(buf);
+      }
+    } else {
+      E.line("  const float2 d = " + cond_expr(op.a_kind, op.a_pos) + " ? d1 : d0;");
+      for (int j = 0; j < R; ++j) {
+        snprintf(buf, sizeof buf, "  { const float2 z = cm(a[%d], d); acc = fmaf(l[%d].x, z.x, acc); acc = fmaf(l[%d].y, z.y, acc); }",
+                 j, j, j);
+        E.line(buf);
+      }
+    }
+  } else if (op.type == OP_DP) {
+    std::string cond;
+    uint32_t mask = (1u << R) - 1u;
+    auto take = [&](uint8_t k, uint8_t p) {
+      if (k == SRC_REG) {
+        uint32_t m = 0;
+        for (int j = 0; j < R; ++j)
+          if (j & (1 << p)) m |= 1u << j;
+        mask &= m;
+      } else {
+        cond += (cond.empty() ? "" : " & ") + cond_expr(k, p);
+      }
+    };
+    take(op.a_kind, op.a_pos);
+    take(op.b_kind, op.b_pos);
+    E.line("  const float2 e = " + mat(0) + ";");
+    if (!cond.empty()) E.line("  if (" + cond + ") {");
+    for (int j = 0; j < R; ++j)
+      if (mask & (1u << j)) {
+        snprintf(buf, sizeof buf, "    { const float2 z = cm(a[%d], e); acc = fmaf(l[%d].x, z.x, acc); acc = fmaf(l[%d].y, z.y, acc); }",
+                 j, j, j);
+        E.line(buf);
+      }
+    if (!cond.empty()) E.line("  }");
+  }
+  E.line("  acc = 2.f * acc;");
+  E.line("  acc += __shfl_xor_sync(0xFFFFFFFFu, acc, 16); acc += __shfl_xor_sync(0xFFFFFFFFu, acc, 8);");
+  E.line("  acc += __shfl_xor_sync(0xFFFFFFFFu, acc, 4); acc += __shfl_xor_sync(0xFFFFFFFFu, acc, 2);");
+  E.line("  acc += __shfl_xor_sync(0xFFFFFFFFu, acc, 1);");
+  snprintf(buf, sizeof buf, "  if (lane == 0) wacc[%d + warp] += acc;", gr.slot * nwarps);
+  E.line(buf);
+  E.line("}");
+}
+
+std::string rename_array(const std::string &code, const char *to) {
+  std::string out;
+  out.reserve(code.size());
+  for (size_t i = 0; i < code.size(); ++i) {
+    // the emitted op code names its register array only as "a[" (never inside another identifier)
+    if (code[i] == 'a' && i + 1 < code.size() && code[i + 1] == '[' &&
+        (i == 0 || !(isalnum((unsigned char)code[i - 1]) || code[i - 1] == '_'))) {
+      out += to;
+      continue;
+    }
+    out += code[i];
+  }
+  return out;
+}
+
+// Adjoint-sweep pass: psi and lambda tiles double-buffered in shared memory, every op
+// applied (conjugate-transposed) to both, derivative dots accumulated per slot.
+std::string gen_bwd_pass(const tn_plan &p, int pi, const std::vector<int> &op_kind, int *threads_out,
+                         size_t *smem_out) {
+  const PassDesc &pd = p.bwd.passes[pi];
+  const int T = pd.T, K = pd.K;
+  const int NTHR = 1 << (T - K);
+  const int NW = NTHR / 32;
+  const int TILE = 1 << T;
+  const int N = p.n;
+  const int mat_n = pd.mat_end - pd.mat_begin;
+  const int SLOTS = pd.grad_slots;
+  Emitter E;
+  E.K = K;
+  E.R = 1 << K;
+  char buf[512];
+  if (SLOTS > 0) {
+    std::string tab;
+    for (int sl = 0; sl < SLOTS; ++sl) tab += (sl ? ", " : "") + std::to_string(p.bwd.grads[(size_t)(pd.grad_begin + sl)].param);
+    snprintf(buf, sizeof buf, "__device__ const int tnq_bp%d[%d] = {", pi, SLOTS);
+    E.line(std::string(buf) + tab + "};");
+  }
+  snprintf(buf, sizeof buf,
+           "extern \"C\" __global__ void __launch_bounds__(%d) tnq_b%d(const float2 *__restrict__ mats_g, long long mstride, "
+           "float2 *__restrict__ psi, float2 *__restrict__ lam, double *__restrict__ grad, int n_params) {",
+           NTHR, pi);
+  E.line(buf);
+  E.line("  extern __shared__ __align__(16) unsigned char smraw[];");
+  E.line("  float2 *const p0 = reinterpret_cast<float2 *>(smraw);");
+  snprintf(buf, sizeof buf, "  float2 *const p1 = p0 + %d; float2 *const l0 = p0 + %d; float2 *const l1 = p0 + %d;", TILE,
+           2 * TILE, 3 * TILE);
+  E.line(buf);
+  snprintf(buf, sizeof buf, "  float4 *const smat = reinterpret_cast<float4 *>(p0 + %d);", 4 * TILE);
+  E.line(buf);
+  const int wacc_n = ((SLOTS * NW) + 1) & ~1;
+  snprintf(buf, sizeof buf, "  float *const wacc = reinterpret_cast<float *>(smat + %d);", mat_n / 2);
+  E.line(buf);
+  snprintf(buf, sizeof buf, "  double *const gacc = reinterpret_cast<double *>(wacc + %d);", wacc_n);
+  E.line(buf);
+  E.line("  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;");
+  E.line("  const long long b = blockIdx.y;");
+  snprintf(buf, sizeof buf, "  { const float4 *src = reinterpret_cast<const float4 *>(mats_g + b * mstride + %d);", pd.mat_begin);
+  E.line(buf);
+  snprintf(buf, sizeof buf, "    for (int i = tid; i < %d; i += %d) smat[i] = src[i]; }", mat_n / 2, NTHR);
+  E.line(buf);
+  snprintf(buf, sizeof buf, "  for (int i = tid; i < %d; i += %d) wacc[i] = 0.f;", wacc_n, NTHR);
+  E.line(buf);
+  snprintf(buf, sizeof buf, "  for (int i = tid; i < %d; i += %d) gacc[i] = 0.0;", SLOTS, NTHR);
+  E.line(buf);
+  snprintf(buf, sizeof buf, "  const float4 *M4 = smat - %d;", pd.mat_begin / 2);
+  E.line(buf);
+  {
+    std::string dep = "0ll";
+    for (int j = 1; j <= T - K; ++j) {
+      snprintf(buf, sizeof buf, " | ((long long)((tid >> %d) & 1) << %d)", j - 1, (int)pd.tile_pos[j]);
+      dep += buf;
+    }
+    E.line("  const long long dep_t = " + dep + ";");
+    E.line("  const int sw_t = swz(2 * tid);");
+  }
+  snprintf(buf, sizeof buf, "  float2 *const gp = psi + (b << %d); float2 *const gl = lam + (b << %d);", N, N);
+  E.line(buf);
+  auto emit_base = [&](const char *tv, const char *bv) {
+    std::string base = "0ull";
+    for (int j = 0; j < pd.n_outer; ++j) {
+      snprintf(buf, sizeof buf, " | ((u64)((%s >> %d) & 1) << %d)", tv, j, (int)pd.outer_pos[j]);
+      base += buf;
+    }
+    return std::string("const u64 ") + bv + " = " + base + ";";
+  };
+  const int chunks = TILE / 2 / NTHR;
+  std::vector<long long> depk(chunks);
+  std::vector<int> swk(chunks);
+  for (int k = 0; k < chunks; ++k) {
+    const int ik = 2 * k * NTHR;
+    long long d = 0;
+    for (int j = 0; j < T; ++j)
+      if ((ik >> j) & 1) d |= 1ll << pd.tile_pos[j];
+    depk[k] = d;
+    swk[k] = swz_host(ik);
+  }
+  E.line("  auto issue = [&](long long t2, float2 *dp, float2 *dl) {");
+  E.line("    " + emit_base("t2", "base2"));
+  E.line("    const float2 *sp = gp + base2 + dep_t; const float2 *sl = gl + base2 + dep_t;");
+  E.line("    const unsigned ap = (unsigned)__cvta_generic_to_shared(dp), al = (unsigned)__cvta_generic_to_shared(dl);");
+  for (int k = 0; k < chunks; ++k) {
+    for (int h = 0; h < 2; ++h) {
+      snprintf(buf, sizeof buf,
+               "    asm volatile(\"cp.async.ca.shared.global [%%0], [%%1], 8;\" :: \"r\"(ap + 8u * (unsigned)(sw_t ^ %d)), \"l\"(sp + %lldll));",
+               swk[k] ^ h, depk[k] + h);
+      E.line(buf);
+      snprintf(buf, sizeof buf,
+               "    asm volatile(\"cp.async.ca.shared.global [%%0], [%%1], 8;\" :: \"r\"(al + 8u * (unsigned)(sw_t ^ %d)), \"l\"(sl + %lldll));",
+               swk[k] ^ h, depk[k] + h);
+      E.line(buf);
+    }
+  }
+  E.line("  };");
+  const long long NT = 1ll << pd.n_outer;
+  snprintf(buf, sizeof buf, "  if (blockIdx.x < %lldll) issue(blockIdx.x, p0, l0);", NT);
+  E.line(buf);
+  E.line("  asm volatile(\"cp.async.commit_group;\" ::: \"memory\");");
+  E.line("  int cur = 0;");
+  snprintf(buf, sizeof buf, "  for (long long t = blockIdx.x; t < %lldll; t += gridDim.x) {", NT);
+  E.line(buf);
+  E.line("    float2 *const smp = cur ? p1 : p0; float2 *const sml = cur ? l1 : l0;");
+  E.line("    " + emit_base("t", "base"));
+  snprintf(buf, sizeof buf, "    if (t + gridDim.x < %lldll) issue(t + gridDim.x, cur ? p0 : p1, cur ? l0 : l1);", NT);
+  E.line(buf);
+  E.line("    asm volatile(\"cp.async.commit_group;\" ::: \"memory\");");
+  E.line("    asm volatile(\"cp.async.wait_group 1;\" ::: \"memory\");");
+  E.line("    __syncthreads();");
+  for (int ph = pd.phase_begin; ph < pd.phase_end; ++ph) {
+    const PhaseDesc &d = p.bwd.phases[ph];
+    E.line("    {");
+    std::string tb = "0";
+    for (int j = 0; j < T - K; ++j) {
+      snprintf(buf, sizeof buf, " | (((tid >> %d) & 1) << %d)", j, (int)d.thr_pos[j]);
+      tb += buf;
+    }
+    E.line("      const int tb = " + tb + ";");
+    E.line("      const int pb = swz(tb);");
+    E.line("      float2 a[" + std::to_string(E.R) + "], l[" + std::to_string(E.R) + "];");
+    int ro[32];
+    for (int j = 0; j < E.R; ++j) {
+      int off = 0;
+      for (int r = 0; r < K; ++r)
+        if ((j >> r) & 1) off |= 1 << d.reg_pos[r];
+      ro[j] = swz_host(off);
+      snprintf(buf, sizeof buf, "      a[%d] = smp[pb ^ %d]; l[%d] = sml[pb ^ %d];", j, ro[j], j, ro[j]);
+      E.line(buf);
+    }
+    for (int o = d.op_begin; o < d.op_end; ++o) {
+      const OpDesc &op = p.bwd.ops[o];
+      Emitter tmp;
+      tmp.K = K;
+      tmp.R = E.R;
+      emit_op(tmp, op, op_kind[o]);
+      const std::string code_a = tmp.o.str();
+      E.o << code_a;  // psi_{k-1} = U^dag psi_k
+      if (op.has_grad)
+        for (int g = 0; g < op.n_grad; ++g) emit_grad(E, op, op_kind[o], p.bwd.grads[(size_t)(op.aux + g)], NW);
+      E.o << rename_array(code_a, "l");  // lambda_{k-1} = U^dag lambda_k
+    }
+    for (int j = 0; j < E.R; ++j) {
+      snprintf(buf, sizeof buf, "      smp[pb ^ %d] = a[%d]; sml[pb ^ %d] = l[%d];", ro[j], j, ro[j], j);
+      E.line(buf);
+    }
+    E.line("    }");
+    E.line("    __syncthreads();");
+  }
+  for (int k = 0; k < chunks; ++k) {
+    snprintf(buf, sizeof buf,
+             "    { const float2 x = smp[sw_t ^ %d], y = smp[sw_t ^ %d ^ 1]; "
+             "*reinterpret_cast<float4 *>(gp + base + dep_t + %lldll) = make_float4(x.x, x.y, y.x, y.y); "
+             "const float2 u = sml[sw_t ^ %d], v = sml[sw_t ^ %d ^ 1]; "
+             "*reinterpret_cast<float4 *>(gl + base + dep_t + %lldll) = make_float4(u.x, u.y, v.x, v.y); }",
+             swk[k], swk[k], depk[k], swk[k], swk[k], depk[k]);
+    E.line(buf);
+  }
+  if (SLOTS > 0) {
+    snprintf(buf, sizeof buf,
+             "    for (int s = tid; s < %d; s += %d) { float v = 0.f; for (int w2 = 0; w2 < %d; ++w2) { v += wacc[s * %d + w2]; "
+             "wacc[s * %d + w2] = 0.f; } gacc[s] += (double)v; }",
+             SLOTS, NTHR, NW, NW, NW);
+    E.line(buf);
+  }
+  E.line("    __syncthreads();");
+  E.line("    cur ^= 1;");
+  E.line("  }");
+  E.line("  asm volatile(\"cp.async.wait_group 0;\" ::: \"memory\");");
+  if (SLOTS > 0) {
+    snprintf(buf, sizeof buf,
+             "  for (int s = tid; s < %d; s += %d) atomicAdd(grad + b * n_params + tnq_bp%d[s], gacc[s]);", SLOTS, NTHR, pi);
+    E.line(buf);
+  }
+  E.line("}");
+  *threads_out = NTHR;
+  *smem_out = (size_t)4 * TILE * 8 + (size_t)mat_n * 8 + (size_t)wacc_n * 4 + (size_t)SLOTS * 8;
+  return E.o.str();
+}
+
 std::mutex g_cache_mu;
 std::map<uint64_t, std::string> g_cubins;
 
@@ -523,10 +808,18 @@ bool jit_supported(const tn_plan &p) {
   return true;
 }
 
-tn_status jit_build(tn_plan &p, const std::vector<int> &op_kind, bool compile_only, std::string &err) {
+bool jit_bwd_supported(const tn_plan &p) {
+  if (p.bwd.passes.empty()) return false;
+  for (const PassDesc &pd : p.bwd.passes)
+    if (pd.K != 4 || pd.T - pd.K < 5) return false;  // whole warps (the dots reduce with shuffles)
+  return true;
+}
+
+tn_status jit_build(tn_plan &p, const std::vector<int> &op_kind, bool backward, bool compile_only, std::string &err) {
   // one NVRTC program per pass: compile time grows faster than linearly with module size,
   // and separate programs compile in parallel and are cached independently
-  const size_t np = p.fwd.passes.size();
+  const PassPlan &pp = backward ? p.bwd : p.fwd;
+  const size_t np = pp.passes.size();
   std::vector<std::string> srcs(np), cubins(np), errs(np);
   std::vector<int> threads(np);
   std::vector<size_t> smem(np);
@@ -534,7 +827,8 @@ tn_status jit_build(tn_plan &p, const std::vector<int> &op_kind, bool compile_on
   for (size_t i = 0; i < np; ++i) {
     int th = 0;
     size_t sm = 0;
-    srcs[i] = std::string(kPrelude) + gen_pass(p, (int)i, op_kind, &th, &sm);
+    srcs[i] = std::string(kPrelude) + (backward ? gen_bwd_pass(p, (int)i, op_kind, &th, &sm)
+                                                : gen_pass(p, (int)i, op_kind, &th, &sm));
     threads[i] = th;
     smem[i] = sm;
     if (const char *dump = getenv("TNQ_JIT_DUMP_DIR")) {
@@ -560,27 +854,29 @@ tn_status jit_build(tn_plan &p, const std::vector<int> &op_kind, bool compile_on
       return sts[i];
     }
   if (compile_only) return TN_OK;
-  p.jit_libs.assign(np, nullptr);
-  p.jit_kernels.assign(np, nullptr);
-  p.jit_threads = threads;
-  p.jit_smem = smem;
+  std::vector<cudaLibrary_t> &libs = backward ? p.jit_bwd_libs : p.jit_libs;
+  std::vector<cudaKernel_t> &kers = backward ? p.jit_bwd_kernels : p.jit_kernels;
+  libs.assign(np, nullptr);
+  kers.assign(np, nullptr);
+  (backward ? p.jit_bwd_threads : p.jit_threads) = threads;
+  (backward ? p.jit_bwd_smem : p.jit_smem) = smem;
   for (size_t i = 0; i < np; ++i) {
-    cudaError_t e = cudaLibraryLoadData(&p.jit_libs[i], cubins[i].data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
+    cudaError_t e = cudaLibraryLoadData(&libs[i], cubins[i].data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
     if (e != cudaSuccess) {
       err = std::string("cudaLibraryLoadData: ") + cudaGetErrorString(e);
       return TN_ERR_CUDA;
     }
     char name[32];
-    snprintf(name, sizeof name, "tnq_p%zu", i);
+    snprintf(name, sizeof name, backward ? "tnq_b%zu" : "tnq_p%zu", i);
     cudaKernel_t k = nullptr;
-    e = cudaLibraryGetKernel(&k, p.jit_libs[i], name);
+    e = cudaLibraryGetKernel(&k, libs[i], name);
     if (e == cudaSuccess && smem[i] > 48 * 1024)
       e = cudaFuncSetAttribute((const void *)k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem[i]);
     if (e != cudaSuccess) {
       err = std::string("loading generated kernel: ") + cudaGetErrorString(e);
       return TN_ERR_CUDA;
     }
-    p.jit_kernels[i] = k;
+    kers[i] = k;
   }
   return TN_OK;
 }
@@ -588,8 +884,12 @@ tn_status jit_build(tn_plan &p, const std::vector<int> &op_kind, bool compile_on
 void jit_release(tn_plan &p) {
   for (cudaLibrary_t l : p.jit_libs)
     if (l) cudaLibraryUnload(l);
+  for (cudaLibrary_t l : p.jit_bwd_libs)
+    if (l) cudaLibraryUnload(l);
   p.jit_libs.clear();
   p.jit_kernels.clear();
+  p.jit_bwd_libs.clear();
+  p.jit_bwd_kernels.clear();
 }
 
 }  // namespace tnq

@@ -236,6 +236,29 @@ cudaError_t launch_bwd_k(const PassDesc &h, const PassDesc *d_pass, const tn_pla
 
 cudaError_t launch_backward(const tn_plan *p, const float2 *mats, long long mstride, float2 *psi, float2 *lam,
                             double *grad, cudaStream_t s) {
+  if (!p->jit_bwd_kernels.empty()) {
+    for (size_t i = 0; i < p->bwd.passes.size(); ++i) {
+      const PassDesc &h = p->bwd.passes[i];
+      const int threads = p->jit_bwd_threads[i];
+      const size_t smem = p->jit_bwd_smem[i];
+      int per_sm = 0;
+      cudaError_t e =
+          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)p->jit_bwd_kernels[i], threads, smem);
+      if (e != cudaSuccess) return e;
+      if (per_sm < 1) per_sm = 1;
+      const long long n_tiles = 1ll << h.n_outer;
+      long long gx = ((long long)num_sms() * per_sm + p->batch - 1) / p->batch;
+      if (gx > n_tiles) gx = n_tiles;
+      if (gx < 1) gx = 1;
+      const float2 *m = mats;
+      int np = p->n_params;
+      void *args[] = {(void *)&m, (void *)&mstride, (void *)&psi, (void *)&lam, (void *)&grad, (void *)&np};
+      e = cudaLaunchKernel((const void *)p->jit_bwd_kernels[i], dim3((unsigned)gx, (unsigned)p->batch), dim3(threads),
+                           args, smem, s);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  }
   for (size_t i = 0; i < p->bwd.passes.size(); ++i) {
     const PassDesc &h = p->bwd.passes[i];
     cudaError_t e = cudaSuccess;

@@ -77,6 +77,21 @@ __device__ __forceinline__ double block_sum(double v, double *scratch) {
 
 }  // namespace
 
+// Terms of a pass as the tile loop reads them: shared-memory copies with the tile-local
+// Z mask (zl) and, per tile, the parity of the Z mask on the tile's outer bits (sb).
+struct TermSm {
+  float coef;
+  int xl;   // tile-local flip mask
+  int zl;   // tile-local Z/Y mask
+  int ny;
+};
+
+__device__ __forceinline__ int compress_bits(unsigned long long v, const RedPass &rp) {
+  int r = 0;
+  for (int j = 0; j < rp.T; ++j) r |= (int)((v >> rp.tile_pos[j]) & 1ull) << j;
+  return r;
+}
+
 __global__ void __launch_bounds__(kRedThreads) k_expect_pass(const RedPass *__restrict__ passes, int pass_idx,
                                                              int n_passes, const DevTerm *__restrict__ terms,
                                                              const float2 *__restrict__ state, int N,
@@ -89,7 +104,16 @@ __global__ void __launch_bounds__(kRedThreads) k_expect_pass(const RedPass *__re
   __syncthreads();
   TileCtx c;
   float2 *sm = reinterpret_cast<float2 *>(smem_raw);
-  setup_tile(rp, reinterpret_cast<long long *>(smem_raw + ((size_t)sizeof(float2) << rp.T)), c);
+  long long *run_off = reinterpret_cast<long long *>(smem_raw + ((size_t)sizeof(float2) << rp.T));
+  const int n_runs = (1 << (rp.T - (rp.T < kLowBits ? rp.T : kLowBits)));
+  const int nt = rp.term_end - rp.term_begin;
+  TermSm *st_terms = reinterpret_cast<TermSm *>(run_off + (n_runs < 2 ? 2 : n_runs));
+  unsigned char *sb = reinterpret_cast<unsigned char *>(st_terms + nt);  // per-tile base parity
+  setup_tile(rp, run_off, c);
+  for (int k = threadIdx.x; k < nt; k += blockDim.x) {
+    const DevTerm &tm = terms[rp.term_begin + k];
+    st_terms[k] = TermSm{(float)tm.coef, tm.xl, compress_bits(tm.zm, rp), tm.ny};
+  }
   __syncthreads();
   const int b = blockIdx.y;
   const float2 *st = state + ((long long)b << N);
@@ -97,25 +121,24 @@ __global__ void __launch_bounds__(kRedThreads) k_expect_pass(const RedPass *__re
   double acc = 0.0;
   for (long long t = blockIdx.x; t < n_tiles; t += gridDim.x) {
     const unsigned long long base = tile_base(rp, t);
+    for (int k = threadIdx.x; k < nt; k += blockDim.x)
+      sb[k] = (unsigned char)(__popcll(base & terms[rp.term_begin + k].zm) & 1);
     load_tile(sm, st, base, c);
     __syncthreads();
     float tacc = 0.f;
     for (int i = threadIdx.x; i < c.tile; i += blockDim.x) {
-      const unsigned long long x = base + (unsigned long long)c.run_off[i >> c.L] + (unsigned long long)(i & c.lowmask);
       const float2 v = sm[swz(i)];
       const float nrm = fmaf(v.x, v.x, v.y * v.y);
       float s = 0.f;
-      for (int k = rp.term_begin; k < rp.term_end; ++k) {
-        const DevTerm &tm = terms[k];
-        const float cf = (float)tm.coef;
-        const float sgn = (__popcll(x & tm.zm) & 1) ? -cf : cf;
+      for (int k = 0; k < nt; ++k) {
+        const TermSm tm = st_terms[k];
+        const float sgn = ((__popc(i & tm.zl) ^ sb[k]) & 1) ? -tm.coef : tm.coef;
         if (tm.xl == 0) {
           s = fmaf(sgn, nrm, s);  // diagonal term (ny is even and i^ny = +-1)
           continue;
         }
         const float2 w = sm[swz(i ^ tm.xl)];
-        // z = conj(w) * v
-        const float2 z = make_float2(fmaf(w.x, v.x, w.y * v.y), fmaf(w.x, v.y, -w.y * v.x));
+        const float2 z = make_float2(fmaf(w.x, v.x, w.y * v.y), fmaf(w.x, v.y, -w.y * v.x));  // conj(w) v
         s = fmaf(sgn, times_i_pow(z, tm.ny).x, s);
       }
       tacc += s;
@@ -152,7 +175,16 @@ __global__ void __launch_bounds__(kRedThreads) k_hamiltonian_pass(const RedPass 
   __syncthreads();
   TileCtx c;
   float2 *sm = reinterpret_cast<float2 *>(smem_raw);
-  setup_tile(rp, reinterpret_cast<long long *>(smem_raw + ((size_t)sizeof(float2) << rp.T)), c);
+  long long *run_off = reinterpret_cast<long long *>(smem_raw + ((size_t)sizeof(float2) << rp.T));
+  const int n_runs = (1 << (rp.T - (rp.T < kLowBits ? rp.T : kLowBits)));
+  const int nt = rp.term_end - rp.term_begin;
+  TermSm *st_terms = reinterpret_cast<TermSm *>(run_off + (n_runs < 2 ? 2 : n_runs));
+  unsigned char *sb = reinterpret_cast<unsigned char *>(st_terms + nt);
+  setup_tile(rp, run_off, c);
+  for (int k = threadIdx.x; k < nt; k += blockDim.x) {
+    const DevTerm &tm = terms[rp.term_begin + k];
+    st_terms[k] = TermSm{(float)tm.coef, tm.xl, compress_bits(tm.zm, rp), tm.ny};
+  }
   __syncthreads();
   const int b = blockIdx.y;
   const float2 *st = psi + ((long long)b << N);
@@ -160,16 +192,19 @@ __global__ void __launch_bounds__(kRedThreads) k_hamiltonian_pass(const RedPass 
   const long long n_tiles = 1ll << rp.n_outer;
   for (long long t = blockIdx.x; t < n_tiles; t += gridDim.x) {
     const unsigned long long base = tile_base(rp, t);
+    // parity of the Z mask on the outer bits; x ^ xm has the same outer bits as x
+    for (int k = threadIdx.x; k < nt; k += blockDim.x)
+      sb[k] = (unsigned char)(__popcll(base & terms[rp.term_begin + k].zm) & 1);
     load_tile(sm, st, base, c);
     __syncthreads();
     for (int i = threadIdx.x; i < c.tile; i += blockDim.x) {
       const unsigned long long x = base + (unsigned long long)c.run_off[i >> c.L] + (unsigned long long)(i & c.lowmask);
       float2 s = accumulate ? lt[x] : make_float2(0.f, 0.f);
-      for (int k = rp.term_begin; k < rp.term_end; ++k) {
-        const DevTerm &tm = terms[k];
-        const float cf = (float)tm.coef;
-        const float sgn = (__popcll((x ^ tm.xm) & tm.zm) & 1) ? -cf : cf;
-        const float2 w = times_i_pow(sm[swz(i ^ tm.xl)], tm.ny);
+      for (int k = 0; k < nt; ++k) {
+        const TermSm tm = st_terms[k];
+        const int src = i ^ tm.xl;
+        const float sgn = ((__popc(src & tm.zl) ^ sb[k]) & 1) ? -tm.coef : tm.coef;
+        const float2 w = times_i_pow(sm[swz(src)], tm.ny);
         s.x = fmaf(sgn, w.x, s.x);
         s.y = fmaf(sgn, w.y, s.y);
       }
@@ -180,14 +215,17 @@ __global__ void __launch_bounds__(kRedThreads) k_hamiltonian_pass(const RedPass 
 }
 
 namespace {
-size_t red_smem(int T) {
+size_t red_smem(const RedPass &rp) {
+  const int T = rp.T;
   const int L = T < kLowBits ? T : kLowBits;
-  return ((size_t)1 << T) * sizeof(float2) + ((size_t)1 << (T - L)) * sizeof(long long);
+  const size_t runs = ((size_t)1 << (T - L)) < 2 ? 2 : ((size_t)1 << (T - L));
+  const size_t nt = (size_t)(rp.term_end - rp.term_begin);
+  return ((size_t)1 << T) * sizeof(float2) + runs * sizeof(long long) + nt * 16 + ((nt + 15) & ~(size_t)15);
 }
 int red_grid_x(const tn_observable *o, int pass, int batch, const void *fn) {
   const RedPass &rp = o->passes[pass];
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kRedThreads, red_smem(rp.T)) != cudaSuccess ||
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kRedThreads, red_smem(rp)) != cudaSuccess ||
       per_sm < 1)
     per_sm = 1;
   long long gx = ((long long)num_sms() * per_sm + batch - 1) / batch;
@@ -213,7 +251,7 @@ cudaError_t launch_expectation(const tn_observable *o, int batch, const float2 *
   if (np == 0) return cudaMemsetAsync(out, 0, sizeof(double) * batch, s);
   int gx_max = 1;
   for (int p = 0; p < np; ++p) {
-    const size_t smem = red_smem(o->passes[p].T);
+    const size_t smem = red_smem(o->passes[p]);
     cudaError_t e = ensure_smem((const void *)k_expect_pass, smem);
     if (e != cudaSuccess) return e;
     const int gx = red_grid_x(o, p, batch, (const void *)k_expect_pass);
@@ -225,7 +263,7 @@ cudaError_t launch_expectation(const tn_observable *o, int batch, const float2 *
   for (int p = 0; p < np; ++p) {
     const int gx = red_grid_x(o, p, batch, (const void *)k_expect_pass);
     dim3 grid((unsigned)gx, (unsigned)batch);
-    k_expect_pass<<<grid, kRedThreads, red_smem(o->passes[p].T), s>>>(o->d_passes, p, np, o->d_terms, state, o->n,
+    k_expect_pass<<<grid, kRedThreads, red_smem(o->passes[p]), s>>>(o->d_passes, p, np, o->d_terms, state, o->n,
                                                                      part);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -239,7 +277,7 @@ cudaError_t launch_apply_hamiltonian(const tn_observable *o, int batch, const fl
   const int np = (int)o->passes.size();
   if (np == 0) return cudaMemsetAsync(lam, 0, (sizeof(float2) << o->n) * batch, s);
   for (int p = 0; p < np; ++p) {
-    const size_t smem = red_smem(o->passes[p].T);
+    const size_t smem = red_smem(o->passes[p]);
     cudaError_t e = ensure_smem((const void *)k_hamiltonian_pass, smem);
     if (e != cudaSuccess) return e;
     const int gx = red_grid_x(o, p, batch, (const void *)k_hamiltonian_pass);

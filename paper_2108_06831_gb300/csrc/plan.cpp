@@ -84,6 +84,23 @@ double op_flops(int type, int kind) {
   }
 }
 
+// Estimated instructions one op adds to a plan-specialised pass kernel (16 amplitudes per
+// thread): a pass's straight-line code must stay well inside the instruction cache.
+int op_code_cost(int type, int kind, bool adjoint, bool has_grad, int n_grad) {
+  int c;
+  switch (type) {
+    case OP_G1: c = (kind == TN_GATE_X) ? 8 : 110; break;
+    case OP_G2: c = (kind == TN_GATE_SWAP) ? 8 : 290; break;
+    case OP_C1: c = (kind == TN_GATE_CNOT) ? 12 : 70; break;
+    case OP_D1: c = 70; break;
+    case OP_CZ: c = 20; break;
+    default: c = 40; break;
+  }
+  if (adjoint) c = 2 * c + (has_grad ? 150 * n_grad : 0);
+  return c;
+}
+constexpr int kPassCodeBudget = 7000;
+
 int shape_entries(int shape) {
   switch (shape) {
     case SHAPE_M2: return 4;
@@ -300,13 +317,15 @@ tn_status build_pass_plan(const tn_circuit &c, int T, int K, bool adjoint, std::
     pd.n_outer = ol;
     pd.phase_begin = (int)out.phases.size();
     pd.grad_begin = (int)out.grads.size();
+    int pass_code = 0;      // estimated instructions of this pass's specialised kernel
+    bool pass_full = false;  // the code budget is used up: the remaining gates go to the next pass
     pd.mat_begin = slots.empty() ? 0 : slots.back().offset + ((shape_entries(slots.back().shape) + 1) & ~1);
     const int Kp = pd.K;
     int grad_slots = 0;
 
     // ---- 2. phases
     for (;;) {
-      if (pending.empty()) break;
+      if (pending.empty() || pass_full) break;
       // choose register bits R (global positions) among S
       uint64_t R = 0;
       int nR = 0;
@@ -384,6 +403,15 @@ tn_status build_pass_plan(const tn_circuit &c, int T, int K, bool adjoint, std::
         int nn = P.needs(g, nb);
         bool ok = !blk;
         for (int i = 0; i < nn && ok; ++i) ok = (R >> nb[i]) & 1;
+        if (ok && !pass_full) {
+          const GateCls &gq = P.cls[g];
+          const TnGate &tq = c.gates[g];
+          const bool hg = adjoint && tq.param_idx >= 0;
+          const int cost = op_code_cost(gq.type, tq.kind, adjoint, hg, hg ? gate_arity(tq.kind) : 0);
+          if (pass_code > 0 && pass_code + cost > kPassCodeBudget) pass_full = true;
+          else pass_code += cost;
+        }
+        if (pass_full) ok = false;
         // a pass accumulates at most kMaxGradSlots parameter derivatives per tile
         if (ok && adjoint && c.gates[g].param_idx >= 0 &&
             grad_slots + gate_arity(c.gates[g].kind) > kMaxGradSlots)

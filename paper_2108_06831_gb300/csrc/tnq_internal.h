@@ -289,6 +289,10 @@ struct tn_plan {
   std::vector<cudaKernel_t> jit_kernels;
   std::vector<int> jit_threads, jit_grid;
   std::vector<size_t> jit_smem;
+  std::vector<cudaLibrary_t> jit_bwd_libs;
+  std::vector<cudaKernel_t> jit_bwd_kernels;
+  std::vector<int> jit_bwd_threads;
+  std::vector<size_t> jit_bwd_smem;
   size_t ws_bytes = 0;
   // workspace layout (byte offsets)
   size_t ws_mats = 0, ws_psi = 0, ws_lam = 0, ws_part = 0, ws_gacc = 0;

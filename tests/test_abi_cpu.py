@@ -60,7 +60,7 @@ def test_host_only_plans():
         n_u3 = sum(1 for g in c.gates if g.kind == "U3")
         assert s["flops"] == pytest.approx((10.0 * n_u3 + 3.0 * 24) * (1 << 24))
     small = tn.Plan(tn.CircuitHandle(C.brickwork(10, 8, 1000)[0]), host_only=True).stats()
-    assert small["n_passes"] == 1 and small["tile_qubits"] == 10
+    assert small["tile_qubits"] == 10 and small["n_passes"] <= 2  # one tile; code budget may split it
 
 
 def test_plan_option_validation():
