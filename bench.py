@@ -49,6 +49,27 @@ def parse():
     return ap.parse_args()
 
 
+def recorded_traffic():
+    """DRAM bytes per launch of the gate-apply pass kernels from the committed ncu summary,
+    or None when the kernel generator has changed since that capture."""
+    import hashlib
+    import re
+    srcs = ["paper_2108_06831_gb300/csrc/jit.cpp", "paper_2108_06831_gb300/csrc/plan.cpp",
+            "paper_2108_06831_gb300/csrc/tnq_internal.h"]
+    try:
+        h = hashlib.sha256()
+        for f in srcs:
+            with open(os.path.join(ROOT, f), "rb") as fh:
+                h.update(fh.read())
+        with open(os.path.join(ROOT, "profiles", "fused_gate_apply_state24.md")) as fh:
+            m = re.search(r"traffic_bytes_per_launch=(\d+) source_hash=([0-9a-f]+)", fh.read())
+        if m and m.group(2) == h.hexdigest()[:16]:
+            return float(m.group(1))
+    except OSError:
+        pass
+    return None
+
+
 def load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -360,15 +381,17 @@ def main():
         if alu_frac >= hbm_frac:
             line["roofline"] = {"bound": "alu", "achieved": tfl, "peak": FP32_ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
                                 "frac": alu_frac, "traffic": None,
-                                "kernel": "k_fwd_pass<4> (fused gate-apply)",
+                                "kernel": "tnq_p* (fused gate-apply pass kernels)",
                                 "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 x 2070 MHz",
                                 "also": {"hbm_gbs": gbs, "hbm_frac": hbm_frac, "hbm_peak": hbm_peak,
                                          "hbm_peak_source": peak_kind}}
         else:
             line["roofline"] = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": hbm_frac,
-                                "traffic": None, "kernel": "k_fwd_pass<4> (fused gate-apply)",
+                                "traffic": None, "kernel": "tnq_p* (fused gate-apply pass kernels)",
                                 "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})",
                                 "also": {"tflops": tfl, "alu_frac": alu_frac}}
+        if args.workload == "state24" and not args.tile and not args.no_specialize:
+            line["roofline"]["traffic"] = recorded_traffic()
         line["roofline"]["launches_per_step"] = kernel_launches
         line["roofline"]["avg_launch_ms"] = avg_launch_ms
 
