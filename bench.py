@@ -41,7 +41,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="state24",
-                    choices=["state24", "state10", "grad20", "gemm_fp32", "gemm_3xtf32", "gemm_bf16x3"])
+                    choices=["state24", "state10", "grad20", "gemm_fp32", "gemm_3xtf32", "gemm_bf16x3",
+                             "serving512"])
     ap.add_argument("--tile", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -185,6 +186,8 @@ def run_oracle_sample(kind: str, n: int, depth: int, seed: int, budget: float):
 WORKLOADS = {
     "state24": dict(kind="state", n=24, depth=20, seed=1001, batch=1),
     # batched complex GEMM of a pairwise merge (kernel c): C[b] = A[b] B[b]^T, complex64
+    # batched serving mix: 512 circuits, n ~ U[8, 22], depth ~ U[4, 30], half brickwork, half QFT
+    "serving512": dict(kind="serve", n=0, depth=0, seed=5000, batch=512),
     "gemm_fp32": dict(kind="gemm", prec=0, M=4096, N=4096, K=4096, batch=1, n=0, depth=0, seed=7),
     "gemm_3xtf32": dict(kind="gemm", prec=1, M=4096, N=4096, K=4096, batch=1, n=0, depth=0, seed=7),
     "gemm_bf16x3": dict(kind="gemm", prec=2, M=4096, N=4096, K=4096, batch=1, n=0, depth=0, seed=7),
@@ -236,7 +239,7 @@ def main():
 
     # the CPU baseline runs first, in a fresh process, before this process touches the GPU
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline and wl["kind"] != "gemm":
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and wl["kind"] in ("state", "grad"):
         info, err = run_oracle_sample(wl["kind"], wl["n"], wl["depth"], wl["seed"], 12.0)
         unit = "amplitudes/s" if wl["kind"] == "state" else "grads/s"
         if info is not None:
@@ -286,6 +289,37 @@ def main():
         kernel_launches = fst["n_passes"]
         alg_bytes = fst["hbm_bytes"] * batch
         alg_flops = fst["flops"] * batch
+    elif wl["kind"] == "serve":
+        circs = C.serving_mix(wl["batch"], wl["seed"])
+        handles = [tn.CircuitHandle(c) for c in circs]
+        plans = [tn.Plan(h, specialize=False) for h in handles]
+        bat = tn.Batch(plans)
+        states = torch.empty(bat.state_elems, dtype=torch.complex64, device=dev)
+        bws = torch.empty(bat.workspace_bytes, dtype=torch.uint8, device=dev)
+        batch = len(circs)
+        units_per_step = float(sum(1 << c.n_qubits for c in circs))
+        unit = "amplitudes/s"
+        tn.batch_run(bat, states, bws)
+        torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        cap = torch.cuda.Stream(device=dev)
+        with torch.cuda.stream(cap):
+            with torch.cuda.graph(graph, stream=cap):
+                tn.batch_run(bat, states, bws)
+        torch.cuda.synchronize()
+
+        def step():
+            graph.replay()
+        launches_per_step = 1
+        kernel_only = None
+        ctr = None
+        # the comparison: every circuit contracted on its own, one after another
+        seq_bufs = [torch.empty(1 << c.n_qubits, dtype=torch.complex64, device=dev) for c in circs]
+        seq_ws = torch.empty(16, dtype=torch.uint8, device=dev)
+
+        def seq_step():
+            for p, buf in zip(plans, seq_bufs):
+                tn.contract_state(p, None, buf, seq_ws)
     elif wl["kind"] == "gemm":
         batch, M, N, K, prec = wl["batch"], wl["M"], wl["N"], wl["K"], wl["prec"]
         g = torch.Generator(device=dev).manual_seed(wl["seed"])
@@ -426,6 +460,15 @@ def main():
         line["e2e"] = {"value": units_per_step * args.steps / (sum(ems) / 1000), "unit": unit,
                        "h2d_bytes_per_step": int(h_params.numel() * 8),
                        "d2h_bytes_per_step": int((h_g.numel() + h_e.numel()) * 8)}
+    if wl["kind"] == "serve":
+        for _ in range(2):
+            seq_step()
+        sms = timed(seq_step, max(1, args.steps // 2))
+        line["config"].update({"circuits": batch, "amplitudes_per_step": units_per_step,
+                               "launch": "one persistent kernel in a CUDA graph"})
+        line["sequential"] = {"value": units_per_step / (statistics.mean(sms) / 1000.0), "unit": unit,
+                              "ms_per_step": statistics.mean(sms),
+                              "what": "the same circuits contracted one after another (tn_contract_state each)"}
     if wl["kind"] == "gemm":
         # tensor-pipe roofline of the whole call (operand split + GEMM), against the peak of the
         # arithmetic the tensor cores run: TF32 = measured bf16 peak x nominal 1.1/2.25

@@ -248,6 +248,28 @@ tn_status tn_cgemm_batched(int32_t precision, int64_t batch, int64_t M, int64_t 
                            size_t workspace_bytes, tn_stream_t s);
 
 /* ---------------------------------------------------------------------------------------
+ * Batched execution: the contractions of many circuits of uneven size in one persistent
+ * launch (work items = (circuit, pass, tile), claimed in pass-major order; a tile waits,
+ * bounded, until the previous pass of its circuit is complete).  Sec. 2.2.3 / Sec. 3: each
+ * circuit's contraction order is its plan; the batch only interleaves independent circuits.
+ * ------------------------------------------------------------------------------------- */
+typedef struct tn_batch tn_batch; /* opaque, library-owned, holds device tables */
+
+/* Group plans (fixed-angle circuits, batch 1, TN_TARGET_STATE or any target, tile qubits in
+ * [6, 12]) for one launch.  The plans must outlive the batch.  TN_ERR_UNSUPPORTED for plans
+ * with parameters or batch > 1. */
+tn_status tn_batch_build(const tn_plan *const *plans, int32_t n_plans, tn_batch **out);
+/* complex64 entries of the output buffer (all states, each 16-byte aligned) and workspace bytes. */
+tn_status tn_batch_sizes(const tn_batch *b, int64_t *state_elems, size_t *workspace_bytes);
+/* offsets[i] = first complex64 entry of circuit i's state in the output buffer. */
+tn_status tn_batch_state_offsets(const tn_batch *b, int64_t *offsets);
+/* Contract every circuit: states_dev receives all final states.  Enqueues one memset of the
+ * workspace (its counters) and one kernel launch on s; capturable in a CUDA graph.  A wait that
+ * runs out (about 2 s) is reported by tn_sync_status as TN_ERR_TIMEOUT. */
+tn_status tn_batch_run(const tn_batch *b, void *states_dev, void *workspace_dev, tn_stream_t s);
+void tn_free_batch(tn_batch *b);
+
+/* ---------------------------------------------------------------------------------------
  * Status.
  * ------------------------------------------------------------------------------------- */
 

@@ -656,6 +656,45 @@ tn_status tn_cgemm_batched(int32_t precision, int64_t batch, int64_t M, int64_t 
   return TN_OK;
 }
 
+tn_status tn_batch_build(const tn_plan *const *plans, int32_t n_plans, tn_batch **out) {
+  TN_CHECK_ARG(out != nullptr && (n_plans == 0 || plans != nullptr), "NULL argument");
+  TN_CHECK_ARG(n_plans >= 1 && n_plans <= (1 << 20), "n_plans=%d out of range", n_plans);
+  *out = nullptr;
+  for (int i = 0; i < n_plans; ++i) {
+    TN_CHECK_ARG(plans[i] != nullptr, "plan %d is NULL", i);
+    tn_status st = check_device(plans[i]->device);
+    if (st != TN_OK) return st;
+  }
+  return batch_build(plans, n_plans, out);
+}
+
+tn_status tn_batch_sizes(const tn_batch *b, int64_t *state_elems, size_t *workspace_bytes) {
+  TN_CHECK_ARG(b != nullptr && state_elems != nullptr && workspace_bytes != nullptr, "NULL argument");
+  long long e = 0;
+  size_t w = 0;
+  batch_sizes(b, &e, &w);
+  *state_elems = e;
+  *workspace_bytes = w;
+  return TN_OK;
+}
+
+tn_status tn_batch_state_offsets(const tn_batch *b, int64_t *offsets) {
+  TN_CHECK_ARG(b != nullptr && offsets != nullptr, "NULL argument");
+  return batch_offsets(b, reinterpret_cast<long long *>(offsets));
+}
+
+tn_status tn_batch_run(const tn_batch *b, void *states_dev, void *workspace_dev, tn_stream_t s) {
+  TN_CHECK_ARG(b != nullptr && states_dev != nullptr && workspace_dev != nullptr, "NULL argument");
+  TN_CHECK_ARG(((uintptr_t)states_dev & 15) == 0, "states_dev must be 16-byte aligned");
+  tn_status st = check_device(batch_device(b));
+  if (st != TN_OK) return st;
+  TN_CUDA(batch_run(b, static_cast<float2 *>(states_dev), workspace_dev, reinterpret_cast<cudaStream_t>(s)),
+          "batched executor");
+  return TN_OK;
+}
+
+void tn_free_batch(tn_batch *b) { batch_free(b); }
+
 tn_status tn_sync_status(tn_stream_t s) {
   int v = 0;
   cudaError_t e = read_and_clear_status(&v, reinterpret_cast<cudaStream_t>(s));

@@ -1,0 +1,358 @@
+// Persistent batched executor: the passes of many circuits of uneven size in one launch.
+//
+// Every circuit's contraction is a chain of passes (rank-growing contractions grouped by
+// the planner, Sec. 2.2.3: the order is fixed before evaluation); a pass is a set of
+// independent tiles.  The executor lays all (circuit, pass, tile) work items out in one
+// list, pass-major across circuits, and each CTA of a grid sized to full co-residency
+// claims the next item with one atomic counter.  A tile of pass p of a circuit may start
+// only once every tile of pass p-1 of that circuit has been stored; since items are claimed
+// in list order and every earlier item is held by a resident CTA, the wait always ends
+// (it is nevertheless bounded: after ~2 s the executor records TN_ERR_TIMEOUT, raises a
+// global abort flag that every CTA checks, and returns).  Circuits that fit in one tile
+// run all of their passes inside one item without going back to HBM.
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "apply_common.cuh"
+#include "kernels.h"
+
+namespace tnq {
+
+struct alignas(16) BatchCirc {
+  long long state_off;  // complex64 offset of the circuit's state in the output buffer
+  unsigned long long init;
+  const PhaseDesc *phases;
+  const OpDesc *ops;
+  const float2 *mats;
+  int N;
+  int pad[3];
+};
+
+struct alignas(16) BatchTask {
+  long long item_begin;  // first global item index of this task
+  int circ;
+  int pass;  // index into the batch's PassDesc array
+  int prev;  // task that must complete first, -1 if none
+  int n_tiles;
+};
+
+namespace {
+
+constexpr int kBatchThreads = 256;  // 2^(12 - 4): the largest tile (12 qubits) with 4 register qubits
+constexpr int kBatchT = 12;
+constexpr unsigned long long kWaitNs = 2000000000ull;
+
+__device__ __forceinline__ unsigned long long now_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ int ld_acquire(const int *p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__global__ void __launch_bounds__(kBatchThreads) k_batch_exec(const BatchTask *__restrict__ tasks, int n_tasks,
+                                                              const BatchCirc *__restrict__ circs,
+                                                              const PassDesc *__restrict__ passes,
+                                                              float2 *__restrict__ states, int *done,
+                                                              unsigned long long *next_item, int *abort_flag,
+                                                              long long total_items, int *status) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ PassDesc pd;
+  __shared__ long long s_item;
+  __shared__ int s_task, s_go;
+  constexpr int K = 4;
+  float2 *sm = reinterpret_cast<float2 *>(smem_raw);
+  long long *run_off = reinterpret_cast<long long *>(smem_raw + ((size_t)sizeof(float2) << kBatchT));
+  const uint32_t full = 0xFFFFu;
+
+  for (;;) {
+    if (threadIdx.x == 0) {
+      s_item = (long long)atomicAdd(next_item, 1ull);
+      s_go = (s_item < total_items && ld_acquire(abort_flag) == 0) ? 1 : 0;
+      if (s_go) {
+        int lo = 0, hi = n_tasks - 1;  // last task with item_begin <= item
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (tasks[mid].item_begin <= s_item) lo = mid;
+          else hi = mid - 1;
+        }
+        s_task = lo;
+        const int prev = tasks[lo].prev;
+        if (prev >= 0) {
+          const int need = tasks[prev].n_tiles;
+          if (ld_acquire(done + prev) < need) {
+            const unsigned long long t0 = now_ns();
+            for (;;) {
+              if (ld_acquire(done + prev) >= need) break;
+              if (ld_acquire(abort_flag) != 0 || now_ns() - t0 > kWaitNs) {
+                atomicCAS(status, 0, (int)TN_ERR_TIMEOUT);
+                atomicExch(abort_flag, 1);
+                s_go = 0;
+                break;
+              }
+              __nanosleep(200);
+            }
+          }
+        }
+      }
+    }
+    __syncthreads();
+    if (!s_go) break;
+    const BatchTask task = tasks[s_task];
+    const BatchCirc circ = circs[task.circ];
+    for (int i = threadIdx.x; i < (int)(sizeof(PassDesc) / 4); i += blockDim.x)
+      reinterpret_cast<int *>(&pd)[i] = reinterpret_cast<const int *>(passes + task.pass)[i];
+    __syncthreads();
+    const int T = pd.T;
+    const int L = T < kLowBits ? T : kLowBits;
+    const int tile = 1 << T;
+    const int lowmask = (1 << L) - 1;
+    for (int r = threadIdx.x; r < (1 << (T - L)); r += blockDim.x) {
+      long long off = 0;
+      for (int j = 0; j < T - L; ++j)
+        if ((r >> j) & 1) off |= 1ll << pd.tile_pos[L + j];
+      run_off[r] = off;
+    }
+    const long long t = s_item - task.item_begin;
+    unsigned long long base = 0, outer_mask = 0;
+    for (int j = 0; j < pd.n_outer; ++j) {
+      base |= (unsigned long long)((t >> j) & 1) << pd.outer_pos[j];
+      outer_mask |= 1ull << pd.outer_pos[j];
+    }
+    float2 *st = states + circ.state_off;
+    __syncthreads();
+    if (pd.init_mode) {
+      for (int i = threadIdx.x; i < tile; i += blockDim.x) sm[swz(i)] = make_float2(0.f, 0.f);
+      __syncthreads();
+      if (threadIdx.x == 0 && (circ.init & outer_mask) == base) {
+        int li = 0;
+        for (int j = 0; j < T; ++j) li |= (int)((circ.init >> pd.tile_pos[j]) & 1ull) << j;
+        sm[swz(li)] = make_float2(1.f, 0.f);
+      }
+    } else {
+      // written by other CTAs during the previous pass: read through L2, never a stale L1 line
+      for (int c = threadIdx.x; c < (tile >> 1); c += blockDim.x) {
+        const int i = c << 1;
+        const long long g = (long long)base + run_off[i >> L] + (i & lowmask);
+        const float4 v = __ldcg(reinterpret_cast<const float4 *>(st + g));
+        sm[swz(i)] = make_float2(v.x, v.y);
+        sm[swz(i + 1)] = make_float2(v.z, v.w);
+      }
+    }
+    __syncthreads();
+    const bool active = threadIdx.x < (1 << (T - K));
+    for (int p = pd.phase_begin; p < pd.phase_end; ++p) {
+      if (active) {
+        const PhaseDesc &ph = circ.phases[p];
+        BitCtx ctx;
+        ctx.tb = deposit(threadIdx.x, ph.thr_pos, T - K);
+        ctx.base = base;
+        ctx.full = full;
+        const int pb = swz(ctx.tb);
+        int ro[1 << K];
+        ro[0] = 0;
+#pragma unroll
+        for (int r = 0; r < K; ++r) {
+          const int d = swz(1 << ph.reg_pos[r]);
+#pragma unroll
+          for (int j = 0; j < (1 << r); ++j) ro[j | (1 << r)] = ro[j] ^ d;
+        }
+        float2 a[1 << K];
+#pragma unroll
+        for (int j = 0; j < (1 << K); ++j) a[j] = sm[pb ^ ro[j]];
+        uint32_t neg = 0;
+        for (int o = ph.op_begin; o < ph.op_end; ++o) {
+          OpDesc op;
+          *reinterpret_cast<int4 *>(&op) = *reinterpret_cast<const int4 *>(circ.ops + o);
+          apply_op<K>(a, op, ctx, circ.mats, neg);
+        }
+        if (neg) reg_flush_sign<K>(a, neg);
+#pragma unroll
+        for (int j = 0; j < (1 << K); ++j) sm[pb ^ ro[j]] = a[j];
+      }
+      __syncthreads();
+    }
+    for (int c = threadIdx.x; c < (tile >> 1); c += blockDim.x) {
+      const int i = c << 1;
+      const long long g = (long long)base + run_off[i >> L] + (i & lowmask);
+      const float2 x = sm[swz(i)], y = sm[swz(i + 1)];
+      *reinterpret_cast<float4 *>(st + g) = make_float4(x.x, x.y, y.x, y.y);
+    }
+    __threadfence();  // this thread's stores are visible device-wide before the tile is counted
+    __syncthreads();
+    if (threadIdx.x == 0) atomicAdd(done + s_task, 1);
+  }
+}
+
+}  // namespace
+
+}  // namespace tnq
+
+// ------------------------------------------------------------------------------ host side
+
+struct tn_batch {
+  int n;
+  int device;
+  std::vector<long long> offsets;
+  long long total_elems = 0;
+  long long total_items = 0;
+  int n_tasks = 0;
+  tnq::BatchTask *d_tasks = nullptr;
+  tnq::BatchCirc *d_circs = nullptr;
+  tnq::PassDesc *d_passes = nullptr;
+  size_t ws_bytes = 0;
+};
+
+namespace tnq {
+
+tn_status batch_build(const tn_plan *const *plans, int n, tn_batch **out) {
+  std::vector<BatchCirc> circs((size_t)n);
+  std::vector<PassDesc> passes;
+  std::vector<std::vector<int>> circ_pass((size_t)n);  // batch pass indices per circuit
+  tn_batch *b = new tn_batch();
+  b->n = n;
+  b->offsets.resize((size_t)n);
+  long long off = 0;
+  for (int i = 0; i < n; ++i) {
+    const tn_plan *p = plans[i];
+    if (p == nullptr || p->host_only) {
+      delete b;
+      set_error("plan %d is NULL or host-only", i);
+      return TN_ERR_INVALID_ARG;
+    }
+    if (p->param_dependent || p->batch != 1) {
+      delete b;
+      set_error("plan %d: the batched executor takes fixed-angle circuits with batch 1", i);
+      return TN_ERR_UNSUPPORTED;
+    }
+    if (p->K != 4 || p->T > kBatchT || p->T < kLowBits + 2) {
+      delete b;
+      set_error("plan %d: the batched executor needs 6 <= tile qubits <= 12 (circuit of %d qubits)", i, p->n);
+      return TN_ERR_UNSUPPORTED;
+    }
+    BatchCirc &c = circs[(size_t)i];
+    std::memset(&c, 0, sizeof(c));
+    c.state_off = off;
+    c.init = p->init;
+    c.phases = p->d_fwd_phase;
+    c.ops = p->d_fwd_ops;
+    c.mats = reinterpret_cast<const float2 *>(p->d_fixed_mats);
+    c.N = p->n;
+    b->offsets[(size_t)i] = off;
+    off += 1ll << p->n;
+    off = (off + 1) & ~1ll;  // keep every state 16-byte aligned
+    const bool one_tile = p->fwd.passes.front().n_outer == 0;
+    if (one_tile) {  // the whole state is one tile: every pass runs in the same item
+      PassDesc m = p->fwd.passes.front();
+      m.phase_end = p->fwd.passes.back().phase_end;
+      m.op_end = p->fwd.passes.back().op_end;
+      m.mat_end = p->fwd.passes.back().mat_end;
+      circ_pass[(size_t)i].push_back((int)passes.size());
+      passes.push_back(m);
+    } else {
+      for (const PassDesc &pd : p->fwd.passes) {
+        circ_pass[(size_t)i].push_back((int)passes.size());
+        passes.push_back(pd);
+      }
+    }
+  }
+  b->total_elems = off;
+  // pass-major task list
+  std::vector<BatchTask> tasks;
+  std::vector<int> last_task((size_t)n, -1);
+  size_t max_p = 0;
+  for (auto &v : circ_pass) max_p = std::max(max_p, v.size());
+  long long items = 0;
+  for (size_t pi = 0; pi < max_p; ++pi)
+    for (int i = 0; i < n; ++i) {
+      if (pi >= circ_pass[(size_t)i].size()) continue;
+      BatchTask t;
+      std::memset(&t, 0, sizeof(t));
+      t.item_begin = items;
+      t.circ = i;
+      t.pass = circ_pass[(size_t)i][pi];
+      t.prev = last_task[(size_t)i];
+      t.n_tiles = 1 << passes[(size_t)t.pass].n_outer;
+      items += t.n_tiles;
+      last_task[(size_t)i] = (int)tasks.size();
+      tasks.push_back(t);
+    }
+  b->total_items = items;
+  b->n_tasks = (int)tasks.size();
+  b->ws_bytes = ((size_t)b->n_tasks * sizeof(int) + 255) / 256 * 256 + 256;
+  cudaError_t e = cudaGetDevice(&b->device);
+  auto up = [&](const void *src, size_t bytes, void **dst) {
+    if (e != cudaSuccess) return;
+    e = cudaMalloc(dst, bytes);
+    if (e == cudaSuccess) e = cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice);
+  };
+  up(tasks.data(), sizeof(BatchTask) * tasks.size(), (void **)&b->d_tasks);
+  up(circs.data(), sizeof(BatchCirc) * circs.size(), (void **)&b->d_circs);
+  up(passes.data(), sizeof(PassDesc) * passes.size(), (void **)&b->d_passes);
+  if (e != cudaSuccess) {
+    cudaFree(b->d_tasks);
+    cudaFree(b->d_circs);
+    cudaFree(b->d_passes);
+    delete b;
+    return cuda_fail(e, "batched executor tables");
+  }
+  *out = b;
+  return TN_OK;
+}
+
+cudaError_t batch_run(const tn_batch *b, float2 *states, void *ws, cudaStream_t s) {
+  // workspace: [done counters per task][next item (u64)][abort flag]
+  char *w = static_cast<char *>(ws);
+  int *done = reinterpret_cast<int *>(w);
+  const size_t counters = ((size_t)b->n_tasks * sizeof(int) + 255) / 256 * 256;
+  unsigned long long *next = reinterpret_cast<unsigned long long *>(w + counters);
+  int *abort_flag = reinterpret_cast<int *>(w + counters + 8);
+  cudaError_t e = cudaMemsetAsync(ws, 0, b->ws_bytes, s);
+  if (e != cudaSuccess) return e;
+  const size_t smem = ((size_t)sizeof(float2) << kBatchT) + ((size_t)1 << (kBatchT - kLowBits)) * sizeof(long long);
+  static bool configured = false;
+  if (!configured) {
+    e = cudaFuncSetAttribute(k_batch_exec, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_exec, kBatchThreads, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) per_sm = 1;
+  // never more CTAs than can be resident at once: a CTA may wait for items held by others
+  long long grid = (long long)num_sms() * per_sm;
+  if (grid > b->total_items) grid = b->total_items;
+  if (grid < 1) return cudaSuccess;
+  k_batch_exec<<<(unsigned)grid, kBatchThreads, smem, s>>>(b->d_tasks, b->n_tasks, b->d_circs, b->d_passes, states,
+                                                           done, next, abort_flag, b->total_items,
+                                                           static_cast<int *>(status_word_ptr()));
+  return cudaGetLastError();
+}
+
+tn_status batch_sizes(const tn_batch *b, long long *elems, size_t *ws) {
+  *elems = b->total_elems;
+  *ws = b->ws_bytes;
+  return TN_OK;
+}
+
+tn_status batch_offsets(const tn_batch *b, long long *offsets) {
+  for (int i = 0; i < b->n; ++i) offsets[i] = b->offsets[(size_t)i];
+  return TN_OK;
+}
+
+int batch_device(const tn_batch *b) { return b->device; }
+
+void batch_free(tn_batch *b) {
+  if (!b) return;
+  cudaFree(b->d_tasks);
+  cudaFree(b->d_circs);
+  cudaFree(b->d_passes);
+  delete b;
+}
+
+}  // namespace tnq

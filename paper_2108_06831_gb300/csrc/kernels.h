@@ -41,6 +41,14 @@ size_t cgemm_workspace(int precision, long long batch, long long M, long long N,
 cudaError_t launch_cgemm(int precision, long long batch, long long M, long long N, long long K, const float2 *A,
                          const float2 *B, float2 *C, void *ws, size_t ws_bytes, cudaStream_t s);
 
+// Persistent batched executor.
+tn_status batch_build(const tn_plan *const *plans, int n, tn_batch **out);
+cudaError_t batch_run(const tn_batch *b, float2 *states, void *ws, cudaStream_t s);
+void batch_free(tn_batch *b);
+tn_status batch_sizes(const tn_batch *b, long long *elems, size_t *ws);
+tn_status batch_offsets(const tn_batch *b, long long *offsets);
+int batch_device(const tn_batch *b);
+
 // Device status word (timeouts, non-finite values).
 void *status_word_ptr();
 cudaError_t read_and_clear_status(int *value, cudaStream_t s);

@@ -76,6 +76,11 @@ _sigs = {
     "tn_permute": [C.c_int32, C.POINTER(C.c_int32), C.c_int64, _vp, _vp, _vp],
     "tn_cgemm_workspace_bytes": [C.c_int32, C.c_int64, C.c_int64, C.c_int64, C.c_int64, C.POINTER(C.c_size_t)],
     "tn_cgemm_batched": [C.c_int32, C.c_int64, C.c_int64, C.c_int64, C.c_int64, _vp, _vp, _vp, _vp, C.c_size_t, _vp],
+    "tn_batch_build": [C.POINTER(_vp), C.c_int32, C.POINTER(_vp)],
+    "tn_batch_sizes": [_vp, C.POINTER(C.c_int64), C.POINTER(C.c_size_t)],
+    "tn_batch_state_offsets": [_vp, C.POINTER(C.c_int64)],
+    "tn_batch_run": [_vp, _vp, _vp, _vp],
+    "tn_free_batch": [_vp],
     "tn_sync_status": [_vp],
     "tn_last_error": [],
     "tn_version": [],
@@ -269,6 +274,33 @@ def cgemm_batched(precision: int, batch: int, M: int, N: int, K: int, A, B, Cm, 
                   stream=None) -> None:
     _check(_lib.tn_cgemm_batched(precision, batch, M, N, K, _ptr(A), _ptr(B), _ptr(Cm), _ptr(workspace),
                                  workspace_bytes, _stream(stream)), "tn_cgemm_batched")
+
+
+class Batch:
+    """Many fixed-angle circuits contracted by one persistent launch (tn_batch_*)."""
+
+    def __init__(self, plans: Sequence[Plan]):
+        arr = (_vp * len(plans))(*[p._h for p in plans])
+        h = _vp()
+        _check(_lib.tn_batch_build(arr, len(plans), C.byref(h)), "tn_batch_build")
+        self._h = h
+        self.plans = list(plans)
+        e = C.c_int64()
+        w = C.c_size_t()
+        _check(_lib.tn_batch_sizes(h, C.byref(e), C.byref(w)), "tn_batch_sizes")
+        self.state_elems, self.workspace_bytes = e.value, w.value
+        offs = (C.c_int64 * len(plans))()
+        _check(_lib.tn_batch_state_offsets(h, offs), "tn_batch_state_offsets")
+        self.offsets = list(offs)
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            _lib.tn_free_batch(self._h)
+            self._h = None
+
+
+def batch_run(batch: Batch, states, workspace, stream=None) -> None:
+    _check(_lib.tn_batch_run(batch._h, _ptr(states), _ptr(workspace), _stream(stream)), "tn_batch_run")
 
 
 def sync_status(stream=None) -> int:

@@ -1,0 +1,85 @@
+"""Persistent batched executor (many circuits, one launch) against the FP64 oracle (GPU)."""
+import numpy as np
+import pytest
+
+from paper_2108_06831_gb300 import circuits as C
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+TOL = 1e-5
+
+
+def _mix():
+    rng = np.random.default_rng(11)
+    out = []
+    for i in range(20):
+        n = int(rng.integers(6, 17))
+        if i % 3 == 0:
+            out.append(C.qft(n, int(rng.integers(0, 1 << n))))
+        elif i % 3 == 1:
+            out.append(C.brickwork(n, int(rng.integers(2, 12)), 300 + i)[0])
+        else:
+            c = C.random_circuit(n, 6 * n, 500 + i)
+            c.init_basis = int(rng.integers(0, 1 << n))
+            out.append(c)
+    return out
+
+
+def _run_batch(circs, tile=0):
+    from paper_2108_06831_gb300 import tn
+    handles = [tn.CircuitHandle(c) for c in circs]
+    plans = [tn.Plan(h, tile_qubits=min(tile, c.n_qubits) if tile else 0, specialize=False)
+             for h, c in zip(handles, circs)]
+    b = tn.Batch(plans)
+    states = torch.full((b.state_elems,), complex(float("nan"), 0), dtype=torch.complex64, device="cuda")
+    ws = torch.empty(b.workspace_bytes, dtype=torch.uint8, device="cuda")
+    return tn, b, plans, handles, states, ws
+
+
+def test_batch_matches_oracle():
+    from oracle.statevector import simulate_state
+    circs = _mix()
+    tn, b, plans, handles, states, ws = _run_batch(circs)
+    tn.batch_run(b, states, ws)
+    torch.cuda.synchronize()
+    assert tn.sync_status() == tn.OK
+    got = states.cpu().numpy()
+    for c, off in zip(circs, b.offsets):
+        ref = simulate_state(c)
+        s = got[off:off + (1 << c.n_qubits)]
+        assert np.linalg.norm(s - ref) / np.linalg.norm(ref) <= TOL, c.name
+
+
+def test_batch_small_tiles_many_passes_and_graph_replay():
+    """8-qubit tiles force multi-pass circuits; the launch is captured in a CUDA graph and replayed."""
+    from oracle.statevector import simulate_state
+    circs = _mix()[:10]
+    tn, b, plans, handles, states, ws = _run_batch(circs, tile=8)
+    stream = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    tn.batch_run(b, states, ws)  # first call outside capture (sets kernel attributes)
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        with torch.cuda.graph(g, stream=stream):
+            tn.batch_run(b, states, ws)
+    for _ in range(2):
+        states.fill_(float("nan"))
+        g.replay()
+        torch.cuda.synchronize()
+        assert tn.sync_status() == tn.OK
+        got = states.cpu().numpy()
+        for c, off in zip(circs, b.offsets):
+            ref = simulate_state(c)
+            s = got[off:off + (1 << c.n_qubits)]
+            assert np.linalg.norm(s - ref) / np.linalg.norm(ref) <= TOL, c.name
+
+
+def test_batch_rejects_parameterised_plans():
+    from paper_2108_06831_gb300 import tn
+    c, _ = C.brickwork(8, 2, 1, parameterized=True)
+    p = tn.Plan(tn.CircuitHandle(c), specialize=False)
+    with pytest.raises(tn.TnError) as e:
+        tn.Batch([p])
+    assert e.value.status == tn.ERR_UNSUPPORTED
