@@ -279,10 +279,13 @@ std::string gen_pass(const tn_plan &p, int pi, const std::vector<int> &op_kind, 
   E.K = K;
   E.R = 1 << K;
   char buf[512];
+  // resident CTAs per SM requested from the register allocator (TNQ_JIT_MIN_BLOCKS, default 2)
+  int min_blocks = 2;
+  if (const char *mb = getenv("TNQ_JIT_MIN_BLOCKS")) min_blocks = std::max(1, std::min(4, atoi(mb)));
   snprintf(buf, sizeof buf,
-           "extern \"C\" __global__ void __launch_bounds__(%d) tnq_p%d(const float2 *__restrict__ mats_g, long long mstride, "
+           "extern \"C\" __global__ void __launch_bounds__(%d, %d) tnq_p%d(const float2 *__restrict__ mats_g, long long mstride, "
            "float2 *__restrict__ state, long long work, u64 init_basis) {",
-           NTHR, pi);
+           NTHR, min_blocks, pi);
   E.line(buf);
   E.line("  extern __shared__ __align__(16) unsigned char smraw[];");
   const int nbuf = pd.init_mode ? 1 : 2;  // loaded passes double-buffer their tiles
@@ -496,7 +499,7 @@ void emit_grad(Emitter &E, const OpDesc &op, int kind, const GradRec &gr, int nw
     }
   } else if (op.type == OP_DP) {
     std::string cond;
-    uint32_t mask = (1u << R) - 1u;
+    uint32_t mask = R >= 32 ? 0xFFFFFFFFu : ((1u << R) - 1u);
     auto take = [&](uint8_t k, uint8_t p) {
       if (k == SRC_REG) {
         uint32_t m = 0;
