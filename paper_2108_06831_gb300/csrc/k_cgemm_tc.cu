@@ -14,8 +14,12 @@
 //               C = x0y0 + x0y1 + x1y0 + x0y2 + x1y1 + x2y0 (kind::f16 with bf16 operands).
 // The split and the embedding are written once per call into the workspace by small
 // prep kernels; the GEMM kernel streams the parts with TMA (128-byte swizzle) through a
-// multi-stage mbarrier pipeline, a single thread issues tcgen05.mma into a 128 x BN FP32
-// accumulator in tensor memory, and all four warps drain it with tcgen05.ld.
+// multi-stage mbarrier pipeline, a single thread issues tcgen05.mma into four 128 x BN FP32
+// accumulators in tensor memory, and all four warps drain them with tcgen05.ld.  Inside the
+// MMA an addend loses its low bits against a large accumulator, so, following Ootomo and
+// Yokota's error-corrected TF32 GEMM, the correction products are summed apart from the
+// leading one, and the leading product itself is spread over three accumulators (K tiles
+// round robin); the epilogue adds the four in round-to-nearest FP32.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
@@ -36,6 +40,8 @@ constexpr int BM = 128;          // rows of A per CTA (MMA M)
 constexpr int BN = 128;          // real columns of C per CTA (MMA N) = 64 complex columns
 constexpr int KBYTES = 128;      // bytes of K per stage and operand row (one 128-byte swizzle span)
 constexpr int kThreads = 128;
+constexpr int kMain = 3;                      // leading-product accumulators, used round robin by K tile
+constexpr int kTmemCols = (kMain + 1) * BN;   // + one correction accumulator = all 512 columns
 constexpr unsigned long long kWaitNs = 2000000000ull;  // bound of every mbarrier wait
 
 enum : int { PREC_TF32 = 1, PREC_BF16 = 2 };
@@ -144,6 +150,19 @@ __device__ __forceinline__ void mma_commit(uint64_t *bar) {
                : "memory");
 }
 
+// 32 consecutive fp32 columns of this warp's 32 TMEM lanes (one per thread); completes at
+// the next tcgen05.wait::ld.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+}
+
 struct TmaMaps {
   CUtensorMap a[3];
   CUtensorMap b[3];
@@ -175,9 +194,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_cgemm_tc(const __grid_constant_
     abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 2) {  // the whole warp allocates BN fp32 columns of tensor memory
+  if (warp == 2) {  // the whole warp allocates 2 x BN fp32 columns of tensor memory
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(&tmem_base)),
-                 "r"(BN));
+                 "r"(kTmemCols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -220,7 +239,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_cgemm_tc(const __grid_constant_
 #pragma unroll
         for (int kk = 0; kk < KBYTES / (CF::kMmaK * CF::kElem); ++kk) {
           const uint32_t off = kk * CF::kMmaK * CF::kElem;  // 32 bytes per MMA along K
-          mma<PREC>(tmem_d, smem_desc(a_base + off), smem_desc(b_base + off), (kt > 0 || p > 0 || kk > 0) ? 1u : 0u);
+          // product 0 (the leading parts) of K tile kt accumulates in columns [j BN, (j+1) BN),
+          // j = kt mod kMain; the correction products in [kMain BN, (kMain+1) BN).  Small terms
+          // never meet the large running sum inside the MMA, and each leading accumulator sees
+          // a third of the K steps.
+          const int j = kt % kMain;
+          const uint32_t dst = tmem_d + (uint32_t)((p == 0 ? j : kMain) * BN);
+          const bool acc = p == 0 ? (kt >= kMain || kk > 0) : (kt > 0 || kk > 0 || p > 1);
+          mma<PREC>(dst, smem_desc(a_base + off), smem_desc(b_base + off), acc ? 1u : 0u);
         }
       }
       mma_commit(&empty[s]);  // frees the stage once these MMAs have read it
@@ -237,23 +263,27 @@ __global__ void __launch_bounds__(kThreads, 1) k_cgemm_tc(const __grid_constant_
     const long long row = m0 + warp * 32 + lane;
     float *crow = C + ((long long)bz * M + row) * N2 + n0;
 #pragma unroll 1
+    const int n_main = k_tiles < kMain ? k_tiles : kMain;  // accumulators that were written
     for (int c = 0; c < BN; c += 32) {
-      uint32_t r[32];
       const uint32_t taddr = tmem_d + ((uint32_t)(warp * 32) << 16) + (uint32_t)c;
-      asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-          "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-            "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-            "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-            "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-          : "r"(taddr));
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      float v[32];
+      {
+        uint32_t e[32];
+        tmem_ld32(taddr + kMain * BN, e);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(e[i]);
+      }
+      for (int j = 0; j < n_main; ++j) {  // corrections first, then the leading sums in order
+        uint32_t r[32];
+        tmem_ld32(taddr + j * BN, r);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int i = 0; i < 32; ++i) v[i] += __uint_as_float(r[i]);
+      }
       float4 *dst = reinterpret_cast<float4 *>(crow + c);
 #pragma unroll
-      for (int q = 0; q < 8; ++q)
-        dst[q] = make_float4(__uint_as_float(r[4 * q]), __uint_as_float(r[4 * q + 1]), __uint_as_float(r[4 * q + 2]),
-                             __uint_as_float(r[4 * q + 3]));
+      for (int q = 0; q < 8; ++q) dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -264,7 +294,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_cgemm_tc(const __grid_constant_
   }
   if (warp == 2) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_d), "r"(BN));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_d), "r"(kTmemCols));
   }
 }
 

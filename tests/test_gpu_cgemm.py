@@ -47,6 +47,13 @@ def test_cgemm_precisions(prec, shape):
     assert _run(prec, batch, M, N, K, seed=sum(shape) + prec) <= TOL
 
 
+@pytest.mark.parametrize("prec", [0, 1, 2])
+def test_cgemm_deep_contraction(prec):
+    # K = 4096: a long sum, where tensor-core accumulation truncates addends against the
+    # running total; the split accumulators keep the error within the FP32 bar
+    assert _run(prec, 1, 256, 128, 4096, seed=11 + prec) <= TOL
+
+
 def test_cgemm_fp32_ragged_shapes():
     for shape in [(1, 5, 7, 3), (2, 65, 33, 17), (1, 1, 1, 1), (3, 130, 70, 9)]:
         assert _run(0, *shape, seed=7) <= TOL
