@@ -131,3 +131,97 @@ def contract_amplitude(c: Circuit, x: int, params: Optional[np.ndarray] = None, 
 def contract_amplitudes(c: Circuit, xs: Sequence[int], params: Optional[np.ndarray] = None,
                         max_log2: int = 34) -> np.ndarray:
     return np.array([contract_amplitude(c, int(x), params, max_log2) for x in xs], dtype=np.complex128)
+
+
+# ----------------------------------------------------------------------------------------
+# Amplitudes of larger circuits: diagonal two-qubit gates as shared indices, qubit sweep.
+# ----------------------------------------------------------------------------------------
+
+def _diag2(kind):
+    return kind in ("CZ", "CP")
+
+
+def build_network_shared(c: Circuit, x: int, params: Optional[np.ndarray] = None):
+    """Nodes (data, labels, group) of <x|C|x0> with every diagonal two-qubit gate as a rank-2
+    factor on the two qubits' current indices.
+
+    A diagonal gate leaves both basis values unchanged (Sec. 2.1 action on basis states), so
+    its tensor d[a,b] = U[ab,ab] joins the indices that carry those values before and after
+    it; an index may then be shared by more than two nodes.  A node's group is the largest
+    qubit it touches; the output leg of qubit q is closed by the covector <x_q| (Sec. 2.2.3).
+    """
+    n = c.n_qubits
+    nodes = []
+    nxt = [0]
+
+    def new():
+        nxt[0] += 1
+        return nxt[0] - 1
+
+    cur = []
+    for q in range(n):
+        lab = new()
+        v = np.zeros(2, dtype=np.complex128)
+        v[(c.init_basis >> (n - 1 - q)) & 1] = 1.0
+        nodes.append((v, [lab], q))
+        cur.append(lab)
+    for g in c.gates:
+        U = gate_matrix(c, g, params)
+        if len(g.qubits) == 1:
+            q = g.qubits[0]
+            out = new()
+            nodes.append((U, [out, cur[q]], q))
+            cur[q] = out
+        elif _diag2(g.kind):
+            a, b = g.qubits
+            nodes.append((np.diag(U).reshape(2, 2), [cur[a], cur[b]], max(a, b)))
+        else:
+            a, b = g.qubits
+            oa, ob = new(), new()
+            nodes.append((U.reshape(2, 2, 2, 2), [oa, ob, cur[a], cur[b]], max(a, b)))
+            cur[a], cur[b] = oa, ob
+    for q in range(n):
+        v = np.zeros(2, dtype=np.complex128)
+        v[(x >> (n - 1 - q)) & 1] = 1.0
+        nodes.append((v, [cur[q]], q))
+    return nodes
+
+
+def _einsum_merge(a, la, b, lb, keep):
+    """Sum over the labels of a and b that are not in `keep`; result labels in first-seen order."""
+    labels = []
+    for l in la + lb:
+        if l not in labels:
+            labels.append(l)
+    out = [l for l in labels if l in keep]
+    idx = {l: i for i, l in enumerate(labels)}
+    data = np.einsum(a, [idx[l] for l in la], b, [idx[l] for l in lb], [idx[l] for l in out])
+    return data, out
+
+
+def contract_amplitude_sweep(c: Circuit, x: int, params: Optional[np.ndarray] = None) -> complex:
+    """<x|C|x0>: the nodes of each qubit (by group) are multiplied into one block, and the
+    blocks are absorbed into a running tensor in qubit order, summing every index as soon
+    as no remaining node carries it."""
+    nodes = build_network_shared(c, int(x), params)
+    remaining = {}
+    for _, labs, _ in nodes:
+        for l in labs:
+            remaining[l] = remaining.get(l, 0) + 1
+    F, LF = np.ones(()), []
+    for q in range(c.n_qubits):
+        group = [(d, l) for d, l, g in nodes if g == q]
+        if not group:
+            continue
+        blk, lb = group[0]
+        for l in lb:
+            remaining[l] -= 1
+        for d, l in group[1:]:
+            for ll in l:
+                remaining[ll] -= 1
+            keep = {ll for ll in set(lb) | set(l) if remaining[ll] > 0 or (ll in LF)}
+            blk, lb = _einsum_merge(blk, lb, d, l, keep)
+        keep = {ll for ll in set(LF) | set(lb) if remaining[ll] > 0}
+        F, LF = _einsum_merge(F, LF, blk, lb, keep)
+    assert LF == [], LF
+    return complex(F)

@@ -256,3 +256,21 @@ def test_param_shift_u3_and_cp():
     H = C.random_pauli_sum(2, 6, 1)
     p = np.random.default_rng(3).uniform(-3, 3, size=7)
     assert np.abs(GR.param_shift_grad(c, H, p) - GR.finite_diff_grad(c, H, p, h=1e-4)).max() < 1e-7
+
+
+@pytest.mark.parametrize("maker", [
+    lambda: C.grid(4, 4, 12, 21),
+    lambda: C.grid(3, 5, 9, 2),
+    lambda: C.random_circuit(9, 70, 13),
+    lambda: C.qft(8, 77),
+    lambda: C.hea(6, 2),
+])
+def test_sweep_amplitudes_equal_state_entries(maker):
+    """The shared-index network (diagonal gates as couplings), swept qubit by qubit, gives the
+    state-vector entries."""
+    c = maker()
+    p = C.hea_params(c.n_params, 1, 3)[0] if c.n_params else None
+    psi = SV.simulate_state(c, p)
+    xs = C.random_bitstrings(c.n_qubits, 6, 12)
+    for x in xs:
+        assert abs(TN.contract_amplitude_sweep(c, int(x), p) - psi[int(x)]) < 1e-12
