@@ -42,7 +42,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="state24",
                     choices=["state24", "state10", "grad20", "gemm_fp32", "gemm_3xtf32", "gemm_bf16x3",
-                             "serving512"])
+                             "serving512", "amps36"])
+    ap.add_argument("--prec", type=int, default=1, help="amps36: GEMM precision (0 FP32, 1 3xTF32, 2 split BF16)")
     ap.add_argument("--tile", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -186,6 +187,8 @@ def run_oracle_sample(kind: str, n: int, depth: int, seed: int, budget: float):
 WORKLOADS = {
     "state24": dict(kind="state", n=24, depth=20, seed=1001, batch=1),
     # batched complex GEMM of a pairwise merge (kernel c): C[b] = A[b] B[b]^T, complex64
+    # 6x6 grid, depth 12, 4096 random bitstrings, amplitudes by network contraction (64 per call)
+    "amps36": dict(kind="amps", n=36, depth=12, seed=3003, batch=4096, chunk=64),
     # batched serving mix: 512 circuits, n ~ U[8, 22], depth ~ U[4, 30], half brickwork, half QFT
     "serving512": dict(kind="serve", n=0, depth=0, seed=5000, batch=512),
     "gemm_fp32": dict(kind="gemm", prec=0, M=4096, N=4096, K=4096, batch=1, n=0, depth=0, seed=7),
@@ -320,6 +323,26 @@ def main():
         def seq_step():
             for p, buf in zip(plans, seq_bufs):
                 tn.contract_state(p, None, buf, seq_ws)
+    elif wl["kind"] == "amps":
+        circ = C.grid(6, 6, wl["depth"], wl["seed"])
+        chunk = wl["chunk"]
+        ctr = None
+        plan = tn.Plan(tn.CircuitHandle(circ), target=tn.TARGET_AMPLITUDES, network_bitstrings=chunk,
+                       precision=args.prec)
+        nst = plan.stats()
+        aws = torch.empty(plan.workspace_bytes, dtype=torch.uint8, device=dev)
+        xs_h = C.random_bitstrings(36, wl["batch"], wl["seed"] + 1)
+        xs = torch.as_tensor(xs_h.astype(np.int64), device=dev)
+        amps = torch.empty(wl["batch"], dtype=torch.complex64, device=dev)
+        batch = wl["batch"]
+        units_per_step = float(batch)
+        unit = "amplitudes/s"
+
+        def step():
+            for i in range(0, batch, chunk):
+                tn.contract_amplitudes(plan, None, xs[i:i + chunk], amps[i:i + chunk], aws)
+        launches_per_step = None
+        kernel_only = None
     elif wl["kind"] == "gemm":
         batch, M, N, K, prec = wl["batch"], wl["M"], wl["N"], wl["K"], wl["prec"]
         g = torch.Generator(device=dev).manual_seed(wl["seed"])
@@ -460,6 +483,20 @@ def main():
         line["e2e"] = {"value": units_per_step * args.steps / (sum(ems) / 1000), "unit": unit,
                        "h2d_bytes_per_step": int(h_params.numel() * 8),
                        "d2h_bytes_per_step": int((h_g.numel() + h_e.numel()) * 8)}
+    if wl["kind"] == "amps":
+        per_step_s = t_max / args.steps / 1000.0
+        a = amps.cpu().numpy().astype(np.complex128)
+        line["config"].update({"grid": "6x6", "bitstrings": batch, "bitstrings_per_call": wl["chunk"],
+                               "precision": args.prec, "merges_per_call": nst["net_merges"],
+                               "largest_intermediate_log2": nst["net_max_log2"],
+                               "tensor_core_merges_per_call": nst["net_tensor_merges"]})
+        alg = nst["flops"] * (batch // wl["chunk"])
+        line["roofline"] = {"bound": "tensor", "achieved": alg / per_step_s / 1e12, "unit": "TFLOP/s",
+                            "note": "algorithmic complex-GEMM flops of all merges per second; the merges have "
+                                    "N = K = 64 and run HBM-bound",
+                            "peak": None, "frac": None, "traffic": None}
+        # Porter-Thomas check of the amplitudes: mean |a|^2 2^36 should be near 1
+        line["porter_thomas_mean"] = float(np.mean(np.abs(a) ** 2) * 2.0 ** 36)
     if wl["kind"] == "serve":
         for _ in range(2):
             seq_step()

@@ -101,6 +101,10 @@ typedef enum { TN_TARGET_STATE = 0, TN_TARGET_AMPLITUDES = 1, TN_TARGET_EXPECTAT
 typedef enum { TN_PREC_FP32 = 0, TN_PREC_3XTF32 = 1, TN_PREC_SPLIT_BF16 = 2 } tn_precision;
 
 #define TN_PLAN_HOST_ONLY 1 /* plan without touching the GPU: only tn_plan_get_stats may use it */
+#define TN_PLAN_NETWORK 4 /* TN_TARGET_AMPLITUDES by contracting the circuit's tensor network pairwise
+                            * (permutations + batched complex GEMMs in opts->precision) instead of
+                            * contracting the state; allows up to 63 qubits.  opts->amp_batch (a power of
+                            * two) is the number of bitstrings per call the plan is sized for. */
 #define TN_PLAN_NO_SPECIALIZE 2 /* run the interpreting gate-apply kernel instead of plan-specialised
                                  * kernels (those are generated as CUDA C++ and compiled with NVRTC
                                  * when the plan is built; compiled code is cached on disk) */
@@ -113,7 +117,8 @@ typedef struct {
   int32_t max_intermediate_log2; /* 0 = 28; largest intermediate tensor (complex64 entries) a plan may create */
   int32_t flags;                 /* TN_PLAN_* bits */
   uint64_t seed;                 /* planner tie-break seed */
-  int64_t reserved[6];           /* must be zero */
+  int64_t amp_batch;             /* TN_PLAN_NETWORK: bitstrings per call (power of two), else 0 */
+  int64_t reserved[5];           /* must be zero */
 } tn_plan_opts;
 
 /* Plan summary (for measurement and tests). */
@@ -130,7 +135,10 @@ typedef struct {
   double flops;         /* algorithmic FP32 flops of one tn_contract_state call (per batch element) */
   int32_t n_bwd_passes; /* passes of the adjoint sweep */
   int32_t specialized;  /* 1 if the forward passes run plan-specialised kernels */
-  int32_t reserved[6];
+  int32_t net_merges;   /* TN_PLAN_NETWORK: pairwise merges (each a permute pair + one GEMM) */
+  int32_t net_max_log2; /* TN_PLAN_NETWORK: log2 entries of the largest intermediate */
+  int32_t net_tensor_merges; /* TN_PLAN_NETWORK: merges whose GEMM runs on the tensor cores */
+  int32_t reserved[3];
 } tn_plan_stats;
 
 /* Pauli sum H = sum_t coef[t] * P_t (host memory, read during tn_build_observable only).
@@ -147,7 +155,8 @@ typedef struct {
 
 /* Build the network of an n_qubits circuit (Sec. 2.2.2: gate tensors joined to the
  * register's input legs |init_basis>).  gates[0..n_gates) in time order, host memory.
- * Returns TN_ERR_INVALID_ARG for n_qubits outside [1, 34], a bad kind or qubit, equal
+ * Returns TN_ERR_INVALID_ARG for n_qubits outside [1, 63] (plans other than TN_PLAN_NETWORK
+ * accept at most 34), a bad kind or qubit, equal
  * qubits of a two-qubit gate, a parameter index on a fixed kind, init_basis >= 2^n. */
 tn_status tn_build_from_circuit(int32_t n_qubits, const tn_gate *gates, int64_t n_gates,
                                 uint64_t init_basis, tn_circuit **out);

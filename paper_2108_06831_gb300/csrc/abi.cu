@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "jit.h"
+#include "network.h"
 #include "kernels.h"
 #include "tnq_internal.h"
 
@@ -146,7 +147,7 @@ tn_status tn_build_from_circuit(int32_t n_qubits, const tn_gate *gates, int64_t 
                                 tn_circuit **out) {
   TN_CHECK_ARG(out != nullptr, "out is NULL");
   *out = nullptr;
-  TN_CHECK_ARG(n_qubits >= 1 && n_qubits <= kMaxQubits, "n_qubits=%d outside [1, %d]", n_qubits, kMaxQubits);
+  TN_CHECK_ARG(n_qubits >= 1 && n_qubits <= 63, "n_qubits=%d outside [1, 63]", n_qubits);
   TN_CHECK_ARG(n_gates >= 0 && n_gates <= (1ll << 26), "n_gates=%lld out of range", (long long)n_gates);
   TN_CHECK_ARG(n_gates == 0 || gates != nullptr, "gates is NULL");
   TN_CHECK_ARG(init_basis < (1ull << n_qubits), "init_basis >= 2^%d", n_qubits);
@@ -210,7 +211,17 @@ tn_status tn_plan_contraction(const tn_circuit *c, const tn_plan_opts *opts, tn_
   TN_CHECK_ARG(o.precision >= TN_PREC_FP32 && o.precision <= TN_PREC_SPLIT_BF16, "bad precision %d", o.precision);
   TN_CHECK_ARG(o.tile_qubits == 0 || (o.tile_qubits >= kLowBits + 2 && o.tile_qubits <= kMaxTile), "tile_qubits=%d not in {0, 6..%d}",
                o.tile_qubits, kMaxTile);
-  for (int i = 0; i < 6; ++i) TN_CHECK_ARG(o.reserved[i] == 0, "reserved fields must be zero");
+  for (int i = 0; i < 5; ++i) TN_CHECK_ARG(o.reserved[i] == 0, "reserved fields must be zero");
+  if (o.flags & TN_PLAN_NETWORK) {
+    TN_CHECK_ARG(o.target == TN_TARGET_AMPLITUDES, "TN_PLAN_NETWORK needs TN_TARGET_AMPLITUDES");
+    TN_CHECK_ARG(o.batch == 1, "TN_PLAN_NETWORK takes one parameter set (batch 1)");
+    TN_CHECK_ARG(o.amp_batch >= 1 && o.amp_batch <= (1 << 20) && (o.amp_batch & (o.amp_batch - 1)) == 0,
+                 "amp_batch=%lld must be a power of two in [1, 2^20]", (long long)o.amp_batch);
+    TN_CHECK_ARG(c->n_params == 0, "TN_PLAN_NETWORK takes fixed-angle circuits");
+  } else {
+    TN_CHECK_ARG(c->n <= kMaxQubits, "state contraction holds at most %d qubits (circuit has %d); "
+                 "use TN_PLAN_NETWORK for amplitudes", kMaxQubits, c->n);
+  }
   if (o.max_intermediate_log2 == 0) o.max_intermediate_log2 = 28;
   // the state of every batch element must be addressable with 64-bit offsets
   TN_CHECK_ARG((double)o.batch * (double)(1ull << c->n) < 9.0e18, "batch * 2^N too large");
@@ -229,6 +240,28 @@ tn_status tn_plan_contraction(const tn_circuit *c, const tn_plan_opts *opts, tn_
   p->T = T;
   p->K = K;
   std::string err;
+  if (o.flags & TN_PLAN_NETWORK) {
+    p->net = new NetPlan();
+    int lb = 0;
+    while ((1ll << lb) < o.amp_batch) ++lb;
+    tn_status s2 = build_network(*c, lb, *p->net, err);
+    if (s2 == TN_OK) s2 = plan_network(*p->net, o.max_intermediate_log2, err);
+    if (s2 == TN_OK) s2 = lower_network(*p->net, o.precision, err);
+    if (s2 == TN_OK && !p->host_only) {
+      TN_CUDA(cudaGetDevice(&p->device), "cudaGetDevice");
+      s2 = upload_network(*p->net, err);
+    }
+    if (s2 != TN_OK) {
+      set_error("network plan: %s", err.c_str());
+      if (p->net) free_network(*p->net);
+      delete p->net;
+      delete p;
+      return s2;
+    }
+    p->ws_bytes = p->net->ws_bytes;
+    *out = p;
+    return TN_OK;
+  }
   const tn_circuit fwd_circ = push_phases(*c);
   tn_status st = build_pass_plan(fwd_circ, T, K, false, p->slots, p->fwd, err);
   // the adjoint sweep stages two tiles (psi, lambda), double-buffered: at most 2^11 amplitudes each
@@ -354,11 +387,26 @@ tn_status tn_plan_get_stats(const tn_plan *p, tn_plan_stats *st) {
   st->hbm_bytes = bytes;
   st->n_bwd_passes = (int)p->bwd.passes.size();
   st->specialized = p->jit_kernels.empty() ? 0 : 1;
+  if (p->net) {
+    st->n_passes = 0;
+    st->net_merges = (int)p->net->steps.size();
+    st->net_max_log2 = p->net->max_log2;
+    st->flops = p->net->flops;
+    int tc = 0;
+    for (const NetLaunch &L : p->net->launches) tc += L.precision != TN_PREC_FP32;
+    st->net_tensor_merges = tc;
+  }
   return TN_OK;
 }
 
 void tn_free_plan(tn_plan *p) {
   if (!p) return;
+  if (p->net) {
+    if (!p->host_only) free_network(*p->net);
+    delete p->net;
+    delete p;
+    return;
+  }
   jit_release(*p);
   if (!p->host_only) free_plan_device(p);
   delete p;
@@ -522,6 +570,14 @@ tn_status tn_contract_amplitudes(const tn_plan *p, const double *params_dev, con
   long long mstride = 0;
   st = call_mats(p, params_dev, workspace_dev, cs, &mats, &mstride);
   if (st != TN_OK) return st;
+  if (p->net) {
+    const long long cap = 1ll << p->net->log2_batch;
+    TN_CHECK_ARG(n_bitstrings <= cap, "this network plan takes at most %lld bitstrings per call", cap);
+    if (n_bitstrings == 0) return TN_OK;
+    TN_CUDA(run_network(*p->net, bitstrings_dev, n_bitstrings, static_cast<float2 *>(amps_dev), workspace_dev, cs),
+            "network contraction");
+    return TN_OK;
+  }
   float2 *psi = reinterpret_cast<float2 *>(static_cast<char *>(workspace_dev) + p->ws_psi);
   TN_CUDA(launch_forward(p, mats, mstride, psi, cs), "gate-apply kernel");
   TN_CUDA(launch_gather(psi, p->n, p->batch, bitstrings_dev, n_bitstrings, static_cast<float2 *>(amps_dev), cs),

@@ -1,0 +1,372 @@
+// Amplitudes by contracting the circuit's tensor network (host side: network, order, lowering).
+//
+// Sec. 2.2.2-2.2.3: the state is the network of gate tensors joined to the input legs; an
+// amplitude <x|C|x0> closes every output leg with a basis covector and contracts all
+// indices; the order is a free choice made before evaluation.  Here:
+//   - a qubit's world line is a chain of indices; consecutive one-qubit gates are multiplied
+//     (FP64) into one 2x2 tensor, the input vector |x0_q> into the first one; diagonal
+//     two-qubit gates (CZ, CP) leave both values unchanged, so they are rank-2 couplings on
+//     the two current indices (hyperedges shared with the surrounding tensors), and other
+//     two-qubit gates are tensors T[out_a, out_b, in_a, in_b];
+//   - every output leg is closed by u_q^b = <x_q^b| M_q (M_q the qubit's trailing one-qubit
+//     product), a [B x 2] tensor sharing the bitstring index b (a hyperedge over all outputs)
+//     -- built on the device from the bitstrings at call time;
+//   - pairs of nodes sharing an index are merged greedily by size reduction (randomised
+//     trials, the best kept); an index carried by more than the two merged tensors (a
+//     hyperedge, e.g. the bitstring index) is a batch index of the merge;
+//   - each merge is lowered to two permutations (kernel b) that group its legs as
+//     [batch][free][contracted] and one batched complex GEMM (kernel c).
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstring>
+#include <map>
+#include <set>
+#include <string>
+#include <vector>
+
+#include "network.h"
+#include "tnq_internal.h"
+
+namespace tnq {
+
+namespace {
+
+using cd = std::complex<double>;
+
+struct Mat2 {
+  cd m[4];
+};
+Mat2 eye2() { return Mat2{{1.0, 0.0, 0.0, 1.0}}; }
+Mat2 mul2(const Mat2 &a, const Mat2 &b) {  // a * b
+  Mat2 r;
+  r.m[0] = a.m[0] * b.m[0] + a.m[1] * b.m[2];
+  r.m[1] = a.m[0] * b.m[1] + a.m[1] * b.m[3];
+  r.m[2] = a.m[2] * b.m[0] + a.m[3] * b.m[2];
+  r.m[3] = a.m[2] * b.m[1] + a.m[3] * b.m[3];
+  return r;
+}
+
+void gate_mat(const TnGate &g, cd *out, int *dim) {
+  double tmp[32];
+  *dim = gate_matrix(g.kind, FORM_U, g.angle, g.mat, tmp);
+  for (int i = 0; i < (*dim) * (*dim); ++i) out[i] = cd(tmp[2 * i], tmp[2 * i + 1]);
+}
+
+}  // namespace
+
+bool is_diag2(int kind) { return kind == TN_GATE_CZ || kind == TN_GATE_CP; }
+
+tn_status build_network(const tn_circuit &c, int log2_batch, NetPlan &net, std::string &err) {
+  for (const TnGate &g : c.gates)
+    if (g.param_idx >= 0) {
+      err = "network contraction takes fixed-angle circuits";
+      return TN_ERR_UNSUPPORTED;
+    }
+  const int n = c.n;
+  net = NetPlan();
+  net.n = n;
+  net.log2_batch = log2_batch;
+  net.label_dim.push_back(log2_batch);  // label 0: the bitstring index (2^log2_batch values)
+  auto new_label = [&]() {
+    net.label_dim.push_back(1);
+    return (int)net.label_dim.size() - 1;
+  };
+  // World line of qubit q: label cur[q] carries the qubit's basis value from the last
+  // non-diagonal gate on; one-qubit gates accumulate in pend[q] until something couples to
+  // the value (a diagonal two-qubit gate) or the line ends.  While in_open[q], cur[q] is the
+  // input leg and the input vector |x0_q> has not been placed yet.
+  std::vector<int> cur((size_t)n);
+  std::vector<char> in_open((size_t)n, 1);
+  std::vector<Mat2> pend((size_t)n, eye2());
+  std::vector<char> pend_id((size_t)n, 1);
+  for (int q = 0; q < n; ++q) cur[(size_t)q] = new_label();
+  auto bit0 = [&](int q) { return (int)((c.init >> (n - 1 - q)) & 1); };
+  int cur_group = 0;  // qubit the node being added belongs to (the largest qubit it touches)
+  auto add_fixed = [&](std::vector<int> legs, std::vector<cd> data) {
+    NetNode nd;
+    nd.kind = NODE_FIXED;
+    nd.legs = std::move(legs);
+    nd.data = std::move(data);
+    nd.group = cur_group;
+    net.nodes.push_back(std::move(nd));
+  };
+  // make cur[q] carry the value after pend[q] (a tensor U[out, in], or the vector U|x0>)
+  auto flush = [&](int q) {
+    if (in_open[(size_t)q]) {
+      const Mat2 &M = pend[(size_t)q];
+      const int x0 = bit0(q);
+      const int l = cur[(size_t)q];
+      add_fixed({l}, {M.m[0 + x0], M.m[2 + x0]});
+      in_open[(size_t)q] = 0;
+    } else if (!pend_id[(size_t)q]) {
+      const int out = new_label();
+      const Mat2 &M = pend[(size_t)q];
+      add_fixed({out, cur[(size_t)q]}, {M.m[0], M.m[1], M.m[2], M.m[3]});
+      cur[(size_t)q] = out;
+    }
+    pend[(size_t)q] = eye2();
+    pend_id[(size_t)q] = 1;
+  };
+  for (const TnGate &g : c.gates) {
+    cd U[16];
+    int dim = 0;
+    gate_mat(g, U, &dim);
+    if (dim == 2) {
+      Mat2 m{{U[0], U[1], U[2], U[3]}};
+      pend[(size_t)g.q[0]] = mul2(m, pend[(size_t)g.q[0]]);
+      pend_id[(size_t)g.q[0]] = 0;
+      continue;
+    }
+    const int qa = g.q[0], qb = g.q[1];
+    cur_group = qa;
+    flush(qa);
+    cur_group = qb;
+    flush(qb);
+    cur_group = std::max(qa, qb);
+    if (is_diag2(g.kind)) {
+      // diagonal: the two values pass through; the gate couples them, d[a][b] = U[ab][ab]
+      add_fixed({cur[(size_t)qa], cur[(size_t)qb]}, {U[0], U[5], U[10], U[15]});
+      continue;
+    }
+    const int oa = new_label(), ob = new_label();
+    std::vector<cd> d(16);
+    for (int i = 0; i < 16; ++i) d[(size_t)i] = U[i];  // legs (out_a, out_b, in_a, in_b)
+    add_fixed({oa, ob, cur[(size_t)qa], cur[(size_t)qb]}, d);
+    cur[(size_t)qa] = oa;
+    cur[(size_t)qb] = ob;
+  }
+  // output closures: u_q^b = <x_q^b| M_q on the line's last value, or the scalar <x_q^b| M_q |x0_q>
+  for (int q = 0; q < n; ++q) {
+    NetNode node;
+    node.kind = NODE_OUTPUT;
+    node.qubit = q;
+    node.group = q;
+    const Mat2 &M = pend[(size_t)q];
+    if (!in_open[(size_t)q]) {
+      node.legs = {0, cur[(size_t)q]};
+      node.rows = {M.m[0], M.m[1], M.m[2], M.m[3]};  // row x of M
+    } else {
+      const int i0 = bit0(q);
+      node.legs = {0};
+      node.rows = {M.m[0 + i0], 0.0, M.m[2 + i0], 0.0};  // <x|M|x0> for x = 0, 1
+    }
+    net.nodes.push_back(node);
+  }
+  return TN_OK;
+}
+
+namespace {
+
+struct Trial {
+  std::vector<NetStep> steps;
+  std::vector<std::vector<int>> legs;
+  int max_log2 = 0;
+  double flops = 0;
+};
+
+// Contraction state shared by the order heuristics: live tensors, index ownership, steps.
+struct Contractor {
+  const NetPlan &net;
+  std::vector<std::vector<int>> legs;
+  std::vector<char> live;
+  std::map<int, std::vector<int>> where;  // label -> live tensors carrying it
+  Trial tr;
+  explicit Contractor(const NetPlan &n) : net(n) {
+    for (const NetNode &nd : net.nodes) legs.push_back(nd.legs);
+    live.assign(legs.size(), 1);
+    for (size_t i = 0; i < legs.size(); ++i)
+      for (int x : legs[i]) where[x].push_back((int)i);
+  }
+  int bits_of(const std::vector<int> &ls) const {
+    int b = 0;
+    for (int x : ls) b += net.label_dim[(size_t)x];
+    return b;
+  }
+  void merged(int i, int j, std::vector<int> &res, std::vector<int> &batch, std::vector<int> &contr) {
+    res.clear();
+    batch.clear();
+    contr.clear();
+    const std::vector<int> &li = legs[(size_t)i], &lj = legs[(size_t)j];
+    for (int x : li) {
+      if (std::find(lj.begin(), lj.end(), x) != lj.end()) {
+        if (where[x].size() > 2 || x == 0) batch.push_back(x);
+        else contr.push_back(x);
+      } else {
+        res.push_back(x);
+      }
+    }
+    for (int x : lj)
+      if (std::find(li.begin(), li.end(), x) == li.end()) res.push_back(x);
+    res.insert(res.begin(), batch.begin(), batch.end());
+  }
+  int merge(int bi, int bj) {
+    std::vector<int> res, batch, contr;
+    merged(bi, bj, res, batch, contr);
+    NetStep st;
+    st.a = bi;
+    st.b = bj;
+    st.out = (int)legs.size();
+    st.batch = batch;
+    st.contr = contr;
+    st.out_legs = res;
+    tr.max_log2 = std::max(tr.max_log2, bits_of(res));
+    int mb = 0, nb = 0;
+    for (int x : legs[(size_t)bi])
+      if (std::find(batch.begin(), batch.end(), x) == batch.end() && std::find(contr.begin(), contr.end(), x) == contr.end())
+        mb += net.label_dim[(size_t)x];
+    for (int x : legs[(size_t)bj])
+      if (std::find(batch.begin(), batch.end(), x) == batch.end() && std::find(contr.begin(), contr.end(), x) == contr.end())
+        nb += net.label_dim[(size_t)x];
+    tr.flops += 8.0 * std::ldexp(1.0, bits_of(batch) + mb + nb + bits_of(contr));
+    const int out = (int)legs.size();
+    for (int x : legs[(size_t)bi]) {
+      auto &w = where[x];
+      w.erase(std::remove(w.begin(), w.end(), bi), w.end());
+    }
+    for (int x : legs[(size_t)bj]) {
+      auto &w = where[x];
+      w.erase(std::remove(w.begin(), w.end(), bj), w.end());
+    }
+    for (int x : contr) where.erase(x);
+    legs.push_back(res);
+    live.push_back(1);
+    live[(size_t)bi] = live[(size_t)bj] = 0;
+    for (int x : res) where[x].push_back(out);
+    tr.steps.push_back(st);
+    return out;
+  }
+  // greedy by size reduction among live tensors whose flag is set in `allowed` (all if empty)
+  void greedy(double temperature, uint64_t seed, const std::vector<char> &allowed_in) {
+    uint64_t rs = seed * 6364136223846793005ull + 1442695040888963407ull;
+    auto uniform = [&]() {
+      rs = rs * 6364136223846793005ull + 1442695040888963407ull;
+      return ((rs >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+    };
+    std::vector<char> allowed = allowed_in;
+    std::vector<int> res, batch, contr;
+    for (;;) {
+      double best = 1e300;
+      int bi = -1, bj = -1;
+      for (auto &kv : where) {
+        if (kv.first == 0) continue;
+        const std::vector<int> &own = kv.second;
+        if (own.size() < 2) continue;
+        for (size_t u = 0; u < own.size(); ++u)
+          for (size_t v = u + 1; v < own.size(); ++v) {
+            const int i = std::min(own[u], own[v]), j = std::max(own[u], own[v]);
+            if (!allowed.empty() && (!allowed[(size_t)i] || !allowed[(size_t)j])) continue;
+            merged(i, j, res, batch, contr);
+            const double sr = std::ldexp(1.0, bits_of(res)), sa = std::ldexp(1.0, bits_of(legs[(size_t)i])),
+                         sb = std::ldexp(1.0, bits_of(legs[(size_t)j]));
+            double score = (sr - sa - sb) / std::max(sa, sb);
+            if (temperature > 0) score -= temperature * std::log(-std::log(uniform()));
+            if (score < best) {
+              best = score;
+              bi = i;
+              bj = j;
+            }
+          }
+      }
+      if (bi < 0) break;
+      const int out = merge(bi, bj);
+      if (!allowed.empty()) {
+        allowed.resize(legs.size(), 0);
+        allowed[(size_t)out] = 1;
+      }
+    }
+  }
+  // join whatever is left (connected only through the bitstring index)
+  void finish() {
+    for (;;) {
+      int bi = -1, bj = -1;
+      for (size_t i = 0; i < legs.size() && bj < 0; ++i) {
+        if (!live[i]) continue;
+        if (bi < 0) bi = (int)i;
+        else bj = (int)i;
+      }
+      if (bj < 0) break;
+      merge(bi, bj);
+    }
+    tr.legs = legs;
+  }
+};
+
+// One greedy contraction path: candidates are pairs of live tensors sharing an index other
+// than the bitstring index; the pair minimising size(result) - size(A) - size(B) is merged
+// (with Gumbel noise of the given temperature for the randomised trials).
+void greedy_trial(const NetPlan &net, double temperature, uint64_t seed, Trial &tr) {
+  Contractor ct(net);
+  ct.greedy(temperature, seed, {});
+  ct.finish();
+  tr = std::move(ct.tr);
+}
+
+// Sweep order: each qubit's own tensors (its line, its output closure, and the couplings to
+// lower qubits) are contracted into a block first, then the blocks are absorbed one by one
+// in qubit order into a single frontier tensor (for a 2D grid numbered row by row this is a
+// row-by-row boundary contraction).
+void sweep_trial(const NetPlan &net, double temperature, uint64_t seed, Trial &tr) {
+  Contractor ct(net);
+  int frontier = -1;
+  for (int q = 0; q < net.n; ++q) {
+    std::vector<char> allowed(ct.legs.size(), 0);
+    int members = 0, last = -1;
+    for (size_t i = 0; i < net.nodes.size(); ++i)
+      if (ct.live[i] && net.nodes[i].group == q) {
+        allowed[i] = 1;
+        ++members;
+        last = (int)i;
+      }
+    if (members == 0) continue;
+    const size_t before = ct.legs.size();
+    ct.greedy(temperature, seed + (uint64_t)q, allowed);
+    // the block is whatever live tensors of this group remain (normally one)
+    std::vector<int> parts;
+    for (size_t i = 0; i < ct.legs.size(); ++i) {
+      if (!ct.live[i]) continue;
+      const bool mine = (i < net.nodes.size()) ? (net.nodes[i].group == q) : (i >= before);
+      if (mine) parts.push_back((int)i);
+    }
+    if (parts.empty()) parts.push_back(last);
+    int block = parts[0];
+    for (size_t k = 1; k < parts.size(); ++k) block = ct.merge(block, parts[k]);
+    frontier = frontier < 0 ? block : ct.merge(frontier, block);
+  }
+  ct.finish();
+  tr = std::move(ct.tr);
+}
+
+}  // namespace
+
+tn_status plan_network(NetPlan &net, int max_log2, std::string &err) {
+  // the deterministic greedy plus randomised trials; keep the smallest peak, then fewest flops
+  Trial best;
+  bool have = false;
+  const int trials = 128;
+  for (int t = 0; t < trials; ++t) {
+    Trial tr;
+    const double temp = (t % 64) == 0 ? 0.0 : 0.05 + 0.5 * (double)(t % 16) / 16.0;
+    const uint64_t seed = 0x9E3779B97F4A7C15ull * (uint64_t)(t + 1);
+    if (t < trials / 2) greedy_trial(net, temp, seed, tr);
+    else sweep_trial(net, temp, seed, tr);
+    const bool better = !have || tr.max_log2 < best.max_log2 ||
+                        (tr.max_log2 == best.max_log2 && tr.flops < best.flops);
+    if (better) {
+      best = std::move(tr);
+      have = true;
+    }
+  }
+  net.steps = best.steps;
+  net.all_legs = best.legs;
+  net.max_log2 = best.max_log2;
+  net.flops = best.flops;
+  if (net.max_log2 > max_log2) {
+    err = "network contraction would create a 2^" + std::to_string(net.max_log2) + "-entry intermediate (cap 2^" +
+          std::to_string(max_log2) + ")";
+    return TN_ERR_UNSUPPORTED;
+  }
+  return TN_OK;
+}
+
+}  // namespace tnq

@@ -263,7 +263,12 @@ struct PassPlan {
   int max_grad_slots = 0;
 };
 
+namespace tnq {
+struct NetPlan;
+}
+
 struct tn_plan {
+  tnq::NetPlan *net = nullptr;  // TN_PLAN_NETWORK plans: pairwise network contraction
   int n;
   long long n_gates;
   int batch;

@@ -25,6 +25,7 @@ TARGET_STATE, TARGET_AMPLITUDES, TARGET_EXPECTATION = 0, 1, 2
 PREC_FP32, PREC_3XTF32, PREC_SPLIT_BF16 = 0, 1, 2
 PLAN_HOST_ONLY = 1
 PLAN_NO_SPECIALIZE = 2
+PLAN_NETWORK = 4
 
 GATE_KINDS = {name: i for i, name in enumerate(
     ["H", "X", "Y", "Z", "S", "SDG", "T", "TDG", "SX", "SY", "SW", "RX", "RY", "RZ", "U3",
@@ -40,7 +41,7 @@ class TnGate(C.Structure):
 class TnPlanOpts(C.Structure):
     _fields_ = [("target", C.c_int32), ("precision", C.c_int32), ("batch", C.c_int32),
                 ("tile_qubits", C.c_int32), ("max_intermediate_log2", C.c_int32), ("flags", C.c_int32),
-                ("seed", C.c_uint64), ("reserved", C.c_int64 * 6)]
+                ("seed", C.c_uint64), ("amp_batch", C.c_int64), ("reserved", C.c_int64 * 5)]
 
 
 class TnPlanStats(C.Structure):
@@ -48,7 +49,8 @@ class TnPlanStats(C.Structure):
                 ("n_passes", C.c_int32), ("n_phases", C.c_int32), ("n_ops", C.c_int64),
                 ("tile_qubits", C.c_int32), ("reg_qubits", C.c_int32), ("hbm_bytes", C.c_double),
                 ("flops", C.c_double), ("n_bwd_passes", C.c_int32), ("specialized", C.c_int32),
-                ("reserved", C.c_int32 * 6)]
+                ("net_merges", C.c_int32), ("net_max_log2", C.c_int32), ("net_tensor_merges", C.c_int32),
+                ("reserved", C.c_int32 * 3)]
 
 
 class TnPauliSum(C.Structure):
@@ -164,10 +166,15 @@ class CircuitHandle:
 
 class Plan:
     def __init__(self, ch: CircuitHandle, target: int = TARGET_STATE, precision: int = PREC_FP32, batch: int = 1,
-                 tile_qubits: int = 0, host_only: bool = False, specialize: bool = True):
+                 tile_qubits: int = 0, host_only: bool = False, specialize: bool = True, network_bitstrings: int = 0,
+                 max_intermediate_log2: int = 0):
         o = TnPlanOpts()
         o.target, o.precision, o.batch, o.tile_qubits = target, precision, batch, tile_qubits
+        o.max_intermediate_log2 = max_intermediate_log2
         o.flags = (PLAN_HOST_ONLY if host_only else 0) | (0 if specialize else PLAN_NO_SPECIALIZE)
+        if network_bitstrings:
+            o.flags |= PLAN_NETWORK
+            o.amp_batch = network_bitstrings
         h = _vp()
         _check(_lib.tn_plan_contraction(ch._h, C.byref(o), C.byref(h)), "tn_plan_contraction")
         self._h = h

@@ -1,0 +1,83 @@
+"""Amplitudes by network contraction (permutations + batched complex GEMMs) vs the FP64 oracle."""
+import numpy as np
+import pytest
+
+from paper_2108_06831_gb300 import circuits as C
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+TOL = 1e-5
+
+
+def _amps(circ, xs, B, precision):
+    from paper_2108_06831_gb300 import tn
+    ch = tn.CircuitHandle(circ)
+    p = tn.Plan(ch, target=tn.TARGET_AMPLITUDES, network_bitstrings=B, precision=precision)
+    ws = torch.empty(max(p.workspace_bytes, 16), dtype=torch.uint8, device="cuda")
+    x = torch.as_tensor(np.asarray(xs, dtype=np.uint64).astype(np.int64), device="cuda")
+    out = torch.full((len(xs),), complex(float("nan"), 0), dtype=torch.complex64, device="cuda")
+    tn.contract_amplitudes(p, None, x, out, ws)
+    torch.cuda.synchronize()
+    assert tn.sync_status() == tn.OK
+    return out.cpu().numpy(), p.stats()
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.mark.parametrize("precision", [0, 1, 2])
+def test_grid_4x4_depth12(precision):
+    from oracle.statevector import simulate_state
+    c = C.grid(4, 4, 12, 21)
+    psi = simulate_state(c)
+    xs = C.random_bitstrings(16, 200, 5)
+    got, st = _amps(c, xs, 256, precision)
+    assert st["net_merges"] > 0
+    assert _rel(got, psi[xs.astype(np.int64)]) <= TOL
+
+
+@pytest.mark.parametrize("maker,B", [
+    (lambda: C.random_circuit(10, 90, 41), 64),
+    (lambda: C.brickwork(14, 8, 9)[0], 128),
+    (lambda: C.qft(9, 300), 16),
+    (lambda: C.paper_fig31(12, 4, 6), 32),
+    (lambda: C.ghz(11), 8),
+])
+def test_circuit_families(maker, B):
+    from oracle.statevector import simulate_state
+    c = maker()
+    psi = simulate_state(c)
+    xs = C.random_bitstrings(c.n_qubits, B - 3, 77)  # fewer than the plan's batch: padded
+    xs[0], xs[-1] = 0, (1 << c.n_qubits) - 1  # GHZ has weight only on these two
+    got, _ = _amps(c, xs, B, 1)
+    assert _rel(got, psi[xs.astype(np.int64)]) <= TOL
+
+
+def test_grid_4x5_split_bf16_against_fp32():
+    """Same bitstrings through the FP32 and the split-BF16 GEMMs: both within the bar of the oracle."""
+    from oracle.statevector import simulate_state
+    c = C.grid(4, 5, 12, 33)
+    psi = simulate_state(c)
+    xs = C.random_bitstrings(20, 256, 8)
+    ref = psi[xs.astype(np.int64)]
+    a32, _ = _amps(c, xs, 256, 0)
+    abf, _ = _amps(c, xs, 256, 2)
+    assert _rel(a32, ref) <= TOL and _rel(abf, ref) <= TOL
+
+
+def test_cfg3_grid_6x6_depth12_sampled():
+    """The 36-qubit configuration in the bench's launch configuration (64 bitstrings per call,
+    3xTF32 merges): three amplitudes against the oracle's own network sweep (FP64), and the
+    Porter-Thomas statistic over the 64 (mean |a|^2 2^36 near 1)."""
+    from oracle.tn import contract_amplitude_sweep
+    c = C.grid(6, 6, 12, 3003)
+    xs = C.random_bitstrings(36, 64, 3004)
+    got, st = _amps(c, xs, 64, 1)
+    assert st["net_max_log2"] <= 28
+    ref = np.array([contract_amplitude_sweep(c, int(x)) for x in xs[:3]])
+    assert _rel(got[:3], ref) <= TOL
+    pt = float(np.mean(np.abs(got.astype(np.complex128)) ** 2) * 2.0 ** 36)
+    assert 0.5 < pt < 1.6
