@@ -42,7 +42,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="state24",
                     choices=["state24", "state10", "grad20", "gemm_fp32", "gemm_3xtf32", "gemm_bf16x3",
-                             "serving512", "amps36"])
+                             "serving512", "amps36", "permute28"])
     ap.add_argument("--prec", type=int, default=1, help="amps36: GEMM precision (0 FP32, 1 3xTF32, 2 split BF16)")
     ap.add_argument("--tile", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -194,6 +194,9 @@ WORKLOADS = {
     "gemm_fp32": dict(kind="gemm", prec=0, M=4096, N=4096, K=4096, batch=1, n=0, depth=0, seed=7),
     "gemm_3xtf32": dict(kind="gemm", prec=1, M=4096, N=4096, K=4096, batch=1, n=0, depth=0, seed=7),
     "gemm_bf16x3": dict(kind="gemm", prec=2, M=4096, N=4096, K=4096, batch=1, n=0, depth=0, seed=7),
+    # index permutation (kernel b) of a 2^28-leg complex64 tensor (2 GiB): low legs kept, full
+    # reversal, and a seeded random permutation, one launch each per step
+    "permute28": dict(kind="permute", n=28, depth=0, seed=2800, batch=1),
     "state10": dict(kind="state", n=10, depth=8, seed=1000, batch=512),
     "grad20": dict(kind="grad", n=20, depth=10, seed=4000, batch=64),
 }
@@ -343,6 +346,24 @@ def main():
                 tn.contract_amplitudes(plan, None, xs[i:i + chunk], amps[i:i + chunk], aws)
         launches_per_step = None
         kernel_only = None
+    elif wl["kind"] == "permute":
+        n = wl["n"]
+        batch = 1
+        g = torch.Generator(device=dev).manual_seed(wl["seed"])
+        px = torch.randn(1 << n, dtype=torch.complex64, device=dev, generator=g)
+        py = torch.empty_like(px)
+        rng = np.random.default_rng(wl["seed"])
+        high = [int(v) for v in rng.permutation(n - 5)]
+        perms = [high + list(range(n - 5, n)), list(range(n))[::-1], [int(v) for v in rng.permutation(n)]]
+        units_per_step = len(perms) * 16.0 * (1 << n) / 1e9  # algorithmic GB: read + write every element
+        unit = "GB/s"
+
+        def step():
+            for pm in perms:
+                tn.permute(n, pm, 1, px, py)
+        launches_per_step = len(perms)
+        kernel_only = None
+        ctr = None
     elif wl["kind"] == "gemm":
         batch, M, N, K, prec = wl["batch"], wl["M"], wl["N"], wl["K"], wl["prec"]
         g = torch.Generator(device=dev).manual_seed(wl["seed"])
@@ -506,6 +527,14 @@ def main():
         line["sequential"] = {"value": units_per_step / (statistics.mean(sms) / 1000.0), "unit": unit,
                               "ms_per_step": statistics.mean(sms),
                               "what": "the same circuits contracted one after another (tn_contract_state each)"}
+    if wl["kind"] == "permute":
+        per_step_s = t_max / args.steps / 1000.0
+        ach = units_per_step / per_step_s
+        line["config"].update({"legs": wl["n"], "tensor_bytes": 8 << wl["n"],
+                               "permutations": "low 5 legs kept / all legs reversed / seeded random"})
+        line["roofline"] = {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
+                            "frac": ach / hbm_peak, "traffic": None, "kernel": "k_permute",
+                            "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})"}
     if wl["kind"] == "gemm":
         # tensor-pipe roofline of the whole call (operand split + GEMM), against the peak of the
         # arithmetic the tensor cores run: TF32 = measured bf16 peak x nominal 1.1/2.25

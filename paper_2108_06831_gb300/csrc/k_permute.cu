@@ -5,8 +5,10 @@
 // deployed).  For a tensor of n legs of size 2, out[y] = in[x] where output leg j holds
 // input leg perm[j].  The kernel is a generalised transpose and HBM-bound (8 bytes read and
 // 8 written per element):
-//   - a tile is 2^e rows of 2^lo input-contiguous elements (lo = min(5, n) low input bits;
-//     the e "extra" bits are the input bits that feed the lo low output bits);
+//   - a tile is 2^R rows of 2^lo input-contiguous elements (lo = 5 low input bits); the
+//     first e row bits are the "extra" input bits that feed the lo low output bits, the other
+//     R - e are "passive" outer bits (lowest input bits first) that only make the tile large
+//     enough (up to 64 rows, 16 KB) to keep the copy engine busy whatever the permutation;
 //   - each row is fetched by the bulk-copy (TMA) engine straight into shared memory
 //     (cp.async.bulk, completion counted on an mbarrier), two tiles in flight per CTA;
 //   - every warp then writes whole 2^lo-element output runs with coalesced stores.
@@ -25,13 +27,16 @@ constexpr int kPermThreads = 256;
 constexpr int kPermStages = 2;
 constexpr unsigned long long kWaitNs = 2000000000ull;  // bound of every mbarrier wait
 
+constexpr int kPermMaxRowBits = 6;  // at most 64 rows of 32 elements per tile
+
 struct PermParams {
-  int n, lo, e, n_outer;
+  int n, lo, e, r, n_outer;       // r = row bits of a tile (e extra + r - e passive)
   int row_stride;                 // shared-memory row stride (elements, multiple of 2)
   uint8_t extra_in[8];            // input bit of extra (row) bit q
   uint8_t col_from_k[8];          // for output low bit j: input bit o_in[j]
   uint8_t m_in[8];                // input low bits not feeding output low bits (run-index bits)
   uint8_t m_out[8];               // their output bit positions
+  uint8_t pas_in[8], pas_out[8];  // passive row bits: input and output bit positions
   uint8_t outer_in[40], outer_out[40];
   int *status;
 };
@@ -88,11 +93,11 @@ __global__ void __launch_bounds__(kPermThreads) k_permute(PermParams P, long lon
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bars[kPermStages];
   __shared__ int lane_off[32];
-  __shared__ int m_off[32];
-  __shared__ long long m_out_off[32];
-  __shared__ long long row_in_off[32];
+  __shared__ int m_off[1 << kPermMaxRowBits];
+  __shared__ long long m_out_off[1 << kPermMaxRowBits];
+  __shared__ long long row_in_off[1 << kPermMaxRowBits];
   __shared__ int abort_flag;
-  const int rows = 1 << P.e;
+  const int rows = 1 << P.r;
   const int runlen = 1 << P.lo;
   const int stage_elems = rows * P.row_stride;
   float2 *stage = reinterpret_cast<float2 *>(smem_raw);
@@ -111,6 +116,8 @@ __global__ void __launch_bounds__(kPermThreads) k_permute(PermParams P, long lon
     lane_off[k] = row * P.row_stride + col;
   }
   if (threadIdx.x < rows) {
+    // row m of the tile: bits [0, e) extra, bits [e, r) passive.  As a write index, the low
+    // e bits of m are the run-index bits m_in instead (same count as the extra bits).
     const int m = threadIdx.x;
     int col = 0;
     long long yo = 0, xo = 0;
@@ -120,7 +127,12 @@ __global__ void __launch_bounds__(kPermThreads) k_permute(PermParams P, long lon
       yo |= (long long)v << P.m_out[q];
       xo |= (long long)v << P.extra_in[q];
     }
-    m_off[m] = col;
+    for (int q = P.e; q < P.r; ++q) {
+      const int v = (m >> q) & 1;
+      yo |= (long long)v << P.pas_out[q - P.e];
+      xo |= (long long)v << P.pas_in[q - P.e];
+    }
+    m_off[m] = col + ((m >> P.e) << P.e) * P.row_stride;
     m_out_off[m] = yo;
     row_in_off[m] = xo;
   }
@@ -232,6 +244,7 @@ cudaError_t launch_permute(int n, const int32_t *perm, long long batch, const fl
     }
   }
   P.e = e;
+  P.r = e;
   // input low bits that do not feed an output low bit index the output runs
   int mq = 0;
   for (int b = 0; b < lo; ++b) {
@@ -243,16 +256,24 @@ cudaError_t launch_permute(int n, const int32_t *perm, long long batch, const fl
       ++mq;
     }
   }
+  // passive row bits (lowest remaining input bits) fill the tile up to 64 rows; the rest
+  // index tiles
   int no = 0;
   for (int b = 0; b < n; ++b)
     if (!in_S[b]) {
+      if (P.r < kPermMaxRowBits) {
+        P.pas_in[P.r - e] = (uint8_t)b;
+        P.pas_out[P.r - e] = (uint8_t)out_of_in[b];
+        ++P.r;
+        continue;
+      }
       P.outer_in[no] = (uint8_t)b;
       P.outer_out[no] = (uint8_t)out_of_in[b];
       ++no;
     }
   P.n_outer = no;
   P.row_stride = (1 << lo) + 2;
-  const size_t smem = (size_t)kPermStages * (1 << e) * P.row_stride * sizeof(float2);
+  const size_t smem = (size_t)kPermStages * (1 << P.r) * P.row_stride * sizeof(float2);
   int per_sm = 0;
   cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_permute, kPermThreads, smem);
   if (err != cudaSuccess) return err;

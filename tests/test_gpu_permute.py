@@ -28,6 +28,33 @@ def test_random_permutations(n, batch, seed):
         assert np.array_equal(out.cpu().numpy(), _ref(x, n, perm))
 
 
+@pytest.mark.parametrize("n", [5, 6, 7, 8, 11, 14, 20])
+@pytest.mark.parametrize("n_low_moved", [0, 1, 2, 5])
+def test_low_leg_classes(n, n_low_moved):
+    """Permutations that move exactly `n_low_moved` of the five fastest legs (tiles whose rows
+    mix transposed and passive legs), batch 2."""
+    from paper_2108_06831_gb300 import tn
+    if n_low_moved and n < 5 + n_low_moved:
+        pytest.skip("not enough slow legs to swap with")
+    rng = np.random.default_rng(100 * n + n_low_moved)
+    perm = list(range(n))
+    high = perm[: n - 5]
+    rng.shuffle(high)
+    perm[: n - 5] = high
+    low_pos = list(rng.choice(np.arange(n - 5, n), size=n_low_moved, replace=False))
+    high_pos = list(rng.choice(np.arange(0, n - 5), size=n_low_moved, replace=False))
+    for a, b in zip(low_pos, high_pos):
+        perm[a], perm[b] = perm[b], perm[a]
+    perm = [int(v) for v in perm]
+    x = (rng.normal(size=(2, 1 << n)) + 1j * rng.normal(size=(2, 1 << n))).astype(np.complex64)
+    xin = torch.as_tensor(x, device="cuda")
+    out = torch.empty_like(xin)
+    tn.permute(n, perm, 2, xin, out)
+    torch.cuda.synchronize()
+    assert tn.sync_status() == tn.OK
+    assert np.array_equal(out.cpu().numpy(), _ref(x, n, perm))
+
+
 def test_identity_and_reversal_24():
     from paper_2108_06831_gb300 import tn
     n = 24
