@@ -377,7 +377,8 @@ def main():
 
         def step():
             tn.cgemm_batched(prec, batch, M, N, K, a, bm, cm, ws, wsb)
-        launches_per_step = 1 if prec == 0 else 3
+        # + B embed/split; + A split unless 3xTF32 splits A on chip (at most two 128-column tiles)
+        launches_per_step = {0: 1, 1: 2 if 2 * N // 128 <= 2 else 3, 2: 3}[prec]
         kernel_only = None
         ctr = None
     else:

@@ -12,10 +12,15 @@
 //               C = hi*hi + hi*lo + lo*hi (kind::tf32, three MMAs per K slice);
 //   SPLIT_BF16: x = x0 + x1 + x2 with x0 = bf16(x), x1 = bf16(x - x0), x2 = bf16(x - x0 - x1);
 //               C = x0y0 + x0y1 + x1y0 + x0y2 + x1y1 + x2y0 (kind::f16 with bf16 operands).
-// The split and the embedding are written once per call into the workspace by small
-// prep kernels; the GEMM kernel streams the parts with TMA (128-byte swizzle) through a
-// multi-stage mbarrier pipeline, a single thread issues tcgen05.mma into four 128 x BN FP32
-// accumulators in tensor memory, and all four warps drain them with tcgen05.ld.  Inside the
+// The embedding and split of B are written once per call into the workspace by a small prep
+// kernel.  For 3XTF32 with at most two column tiles (HBM-bound merges) the A operand is
+// split inside the GEMM: its FP32 tile arrives by TMA,
+// and four converter warps overwrite it with hi and write lo beside it (same element size and
+// swizzle, so the split is elementwise at equal offsets) before the MMAs read the stage; A
+// then crosses HBM once, as FP32.  Otherwise A is split by a prep kernel too.  The GEMM
+// streams the parts with TMA (128-byte swizzle) through a multi-stage mbarrier pipeline, a
+// single thread issues tcgen05.mma into four 128 x BN FP32 accumulators in tensor memory,
+// and the four converter/epilogue warps drain them with tcgen05.ld.  Inside the
 // MMA an addend loses its low bits against a large accumulator, so, following Ootomo and
 // Yokota's error-corrected TF32 GEMM, the correction products are summed apart from the
 // leading one, and the leading product itself is spread over three accumulators (K tiles
@@ -39,7 +44,10 @@ namespace {
 constexpr int BM = 128;          // rows of A per CTA (MMA M)
 constexpr int BN = 128;          // real columns of C per CTA (MMA N) = 64 complex columns
 constexpr int KBYTES = 128;      // bytes of K per stage and operand row (one 128-byte swizzle span)
-constexpr int kThreads = 128;
+// warps 0-3: A split (3XTF32) and epilogue (warp w owns TMEM lanes 32w..32w+31);
+// warp 4: TMA producer; warp 5: TMEM allocation and MMA issue
+constexpr int kThreads = 192;
+constexpr int kConvThreads = 128;
 constexpr int kMain = 3;                      // leading-product accumulators, used round robin by K tile
 constexpr int kTmemCols = (kMain + 1) * BN;   // + one correction accumulator = all 512 columns
 constexpr unsigned long long kWaitNs = 2000000000ull;  // bound of every mbarrier wait
@@ -168,17 +176,31 @@ struct TmaMaps {
   CUtensorMap b[3];
 };
 
-template <int PREC>
+__device__ __forceinline__ float tf32_rna(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(b)) : "memory");
+}
+
+// SPLIT_A (3XTF32 only): A arrives as FP32 and is split in shared memory by warps 0-3.
+template <int PREC, bool SPLIT_A>
 __global__ void __launch_bounds__(kThreads, 1) k_cgemm_tc(const __grid_constant__ TmaMaps maps, int k_tiles,
                                                           long long M, long long N2, float *__restrict__ C,
                                                           int *status) {
   using CF = Cfg<PREC>;
+  static_assert(!SPLIT_A || PREC == PREC_TF32, "on-chip split is the TF32 form");
   constexpr int S = CF::kStages;
   constexpr int stage_bytes = CF::kParts * (kTileA + kTileB);
+  // bytes the TMA delivers per stage: A once as FP32 when it is split here, else its parts
+  constexpr uint32_t tx_bytes = (SPLIT_A ? kTileA : CF::kParts * kTileA) + CF::kParts * kTileB;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   // 1024-byte alignment of every tile (required by the 128-byte swizzle pattern)
   unsigned char *smem = reinterpret_cast<unsigned char *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  __shared__ __align__(8) uint64_t full[S], empty[S], done;
+  __shared__ __align__(8) uint64_t full[S], conv[S], empty[S], done;
   __shared__ uint32_t tmem_base;
   __shared__ int abort_flag;
 
@@ -188,13 +210,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_cgemm_tc(const __grid_constant_
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
       mbar_init(&full[s], 1);
+      mbar_init(&conv[s], kConvThreads);
       mbar_init(&empty[s], 1);
     }
     mbar_init(&done, 1);
     abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 2) {  // the whole warp allocates 2 x BN fp32 columns of tensor memory
+  if (warp == 5) {  // the whole warp allocates the accumulators' columns of tensor memory
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(&tmem_base)),
                  "r"(kTmemCols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
@@ -204,65 +227,87 @@ __global__ void __launch_bounds__(kThreads, 1) k_cgemm_tc(const __grid_constant_
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem_d = tmem_base;
 
-  if (warp == 0 && lane == 0) {
-    // TMA producer
-    for (int kt = 0; kt < k_tiles; ++kt) {
-      const int s = kt % S;
-      if (kt >= S && !mbar_wait(&empty[s], ((kt / S) - 1) & 1, status)) {
-        abort_flag = 1;
-        break;
-      }
-      mbar_expect_tx(&full[s], stage_bytes);
-      unsigned char *st = smem + (size_t)s * stage_bytes;
-      const int kc = kt * (KBYTES / CF::kElem);
-      for (int p = 0; p < CF::kParts; ++p) {
-        tma_load_3d(st + p * kTileA, &maps.a[p], &full[s], kc, m0, bz);
-        tma_load_3d(st + CF::kParts * kTileA + p * kTileB, &maps.b[p], &full[s], kc, n0, bz);
+  if (warp == 4) {
+    if (lane == 0) {  // TMA producer
+      for (int kt = 0; kt < k_tiles; ++kt) {
+        const int s = kt % S;
+        if (kt >= S && !mbar_wait(&empty[s], ((kt / S) - 1) & 1, status)) {
+          abort_flag = 1;
+          break;
+        }
+        mbar_expect_tx(&full[s], tx_bytes);
+        unsigned char *st = smem + (size_t)s * stage_bytes;
+        const int kc = kt * (KBYTES / CF::kElem);
+        const int a_loads = SPLIT_A ? 1 : CF::kParts;
+        for (int p = 0; p < a_loads; ++p) tma_load_3d(st + p * kTileA, &maps.a[p], &full[s], kc, m0, bz);
+        for (int p = 0; p < CF::kParts; ++p)
+          tma_load_3d(st + CF::kParts * kTileA + p * kTileB, &maps.b[p], &full[s], kc, n0, bz);
       }
     }
-  } else if (warp == 1 && lane == 0) {
-    // MMA issuer
-    bool ok = true;
+  } else if (warp == 5) {
+    if (lane == 0) {  // MMA issuer
+      bool ok = true;
+      for (int kt = 0; kt < k_tiles; ++kt) {
+        const int s = kt % S;
+        if (!mbar_wait(SPLIT_A ? &conv[s] : &full[s], (kt / S) & 1, status)) {
+          ok = false;
+          abort_flag = 1;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t st = saddr(smem + (size_t)s * stage_bytes);
+#pragma unroll
+        for (int p = 0; p < CF::kProducts; ++p) {
+          const uint32_t a_base = st + CF::pa(p) * kTileA;
+          const uint32_t b_base = st + CF::kParts * kTileA + CF::pb(p) * kTileB;
+#pragma unroll
+          for (int kk = 0; kk < KBYTES / (CF::kMmaK * CF::kElem); ++kk) {
+            const uint32_t off = kk * CF::kMmaK * CF::kElem;  // 32 bytes per MMA along K
+            // product 0 (the leading parts) of K tile kt accumulates in columns [j BN, (j+1) BN),
+            // j = kt mod kMain; the correction products in [kMain BN, (kMain+1) BN).  Small terms
+            // never meet the large running sum inside the MMA, and each leading accumulator sees
+            // a third of the K steps.
+            const int j = kt % kMain;
+            const uint32_t dst = tmem_d + (uint32_t)((p == 0 ? j : kMain) * BN);
+            const bool acc = p == 0 ? (kt >= kMain || kk > 0) : (kt > 0 || kk > 0 || p > 1);
+            mma<PREC>(dst, smem_desc(a_base + off), smem_desc(b_base + off), acc ? 1u : 0u);
+          }
+        }
+        mma_commit(&empty[s]);  // frees the stage once these MMAs have read it
+      }
+      if (ok) mma_commit(&done);
+    }
+  } else if constexpr (SPLIT_A) {
+    // A split: x -> hi = TF32(x) (in place), lo = x - hi (part 1 of the stage), then make the
+    // generic-proxy writes visible to the tensor cores and report the stage converted
     for (int kt = 0; kt < k_tiles; ++kt) {
       const int s = kt % S;
       if (!mbar_wait(&full[s], (kt / S) & 1, status)) {
-        ok = false;
         abort_flag = 1;
         break;
       }
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t st = saddr(smem + (size_t)s * stage_bytes);
-#pragma unroll
-      for (int p = 0; p < CF::kProducts; ++p) {
-        const uint32_t a_base = st + CF::pa(p) * kTileA;
-        const uint32_t b_base = st + CF::kParts * kTileA + CF::pb(p) * kTileB;
-#pragma unroll
-        for (int kk = 0; kk < KBYTES / (CF::kMmaK * CF::kElem); ++kk) {
-          const uint32_t off = kk * CF::kMmaK * CF::kElem;  // 32 bytes per MMA along K
-          // product 0 (the leading parts) of K tile kt accumulates in columns [j BN, (j+1) BN),
-          // j = kt mod kMain; the correction products in [kMain BN, (kMain+1) BN).  Small terms
-          // never meet the large running sum inside the MMA, and each leading accumulator sees
-          // a third of the K steps.
-          const int j = kt % kMain;
-          const uint32_t dst = tmem_d + (uint32_t)((p == 0 ? j : kMain) * BN);
-          const bool acc = p == 0 ? (kt >= kMain || kk > 0) : (kt > 0 || kk > 0 || p > 1);
-          mma<PREC>(dst, smem_desc(a_base + off), smem_desc(b_base + off), acc ? 1u : 0u);
-        }
+      float4 *hi = reinterpret_cast<float4 *>(smem + (size_t)s * stage_bytes);
+      float4 *lo = reinterpret_cast<float4 *>(smem + (size_t)s * stage_bytes + kTileA);
+#pragma unroll 4
+      for (int c = threadIdx.x; c < kTileA / 16; c += kConvThreads) {
+        const float4 v = hi[c];
+        const float4 h = make_float4(tf32_rna(v.x), tf32_rna(v.y), tf32_rna(v.z), tf32_rna(v.w));
+        lo[c] = make_float4(v.x - h.x, v.y - h.y, v.z - h.z, v.w - h.w);
+        hi[c] = h;
       }
-      mma_commit(&empty[s]);  // frees the stage once these MMAs have read it
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_arrive(&conv[s]);
     }
-    if (ok) mma_commit(&done);
   }
   __syncwarp();
 
-  // epilogue: every warp drains its 32 TMEM lanes (= 32 rows of the tile)
+  // epilogue: warps 0-3 drain their 32 TMEM lanes (= 32 rows of the tile)
   bool have = !abort_flag && mbar_wait(&done, 0, status);
   have = __all_sync(0xFFFFFFFFu, have);  // tcgen05.ld is warp-collective: decide per warp
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  if (have) {
+  if (have && warp < 4) {
     const long long row = m0 + warp * 32 + lane;
     float *crow = C + ((long long)bz * M + row) * N2 + n0;
-#pragma unroll 1
     const int n_main = k_tiles < kMain ? k_tiles : kMain;  // accumulators that were written
     for (int c = 0; c < BN; c += 32) {
       const uint32_t taddr = tmem_d + ((uint32_t)(warp * 32) << 16) + (uint32_t)c;
@@ -292,19 +337,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_cgemm_tc(const __grid_constant_
     // let copies already in flight land before the CTA's shared memory is released
     for (int s = 0; s < S; ++s) mbar_wait(&full[s], 0, nullptr);
   }
-  if (warp == 2) {
+  if (warp == 5) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_d), "r"(kTmemCols));
   }
 }
 
 // ------------------------------------------------------------------------------ prep kernels
-
-__device__ __forceinline__ float tf32_rna(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return __uint_as_float(r);
-}
 
 // A (real view [rows][cols]) -> parts
 template <int PREC>
@@ -401,22 +440,32 @@ size_t part_bytes(int precision, long long rows, long long cols, long long batch
 
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
-template <int PREC>
+// A is split on chip when few CTAs read each A tile (HBM-bound merges: the split copy would
+// cost more traffic than the GEMM); with many column tiles the one-pass prep split is
+// cheaper than converting every tile again in every CTA.
+bool split_a_on_chip(int precision, long long N) { return precision == TN_PREC_3XTF32 && (2 * N) / BN <= 2; }
+
+template <int PREC, bool SPLIT_A>
 cudaError_t run_tc(long long batch, long long M, long long N, long long K, const float2 *A, const float2 *B, float2 *C,
                    void *ws, cudaStream_t s) {
   using CF = Cfg<PREC>;
   const int prec_abi = PREC == PREC_TF32 ? TN_PREC_3XTF32 : TN_PREC_SPLIT_BF16;
-  const size_t pa = align256(part_bytes(prec_abi, M, 2 * K, batch));
+  const size_t pa = SPLIT_A ? 0 : align256(part_bytes(prec_abi, M, 2 * K, batch));
   const size_t pb = align256(part_bytes(prec_abi, 2 * N, 2 * K, batch));
   char *w = static_cast<char *>(ws);
   void *ap[3] = {w, w + pa, w + 2 * pa};
   char *wb = w + CF::kParts * pa;
   void *bp[3] = {wb, wb + pb, wb + 2 * pb};
-  const long long na = batch * M * 2 * K;
-  k_split<PREC><<<(unsigned)std::min<long long>((na + 255) / 256, 65535), 256, 0, s>>>(
-      reinterpret_cast<const float *>(A), na, ap[0], ap[1], ap[2]);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
+  cudaError_t e = cudaSuccess;
+  if (SPLIT_A) {
+    ap[0] = const_cast<float2 *>(A);  // the GEMM reads A itself (FP32) and splits it on chip
+  } else {
+    const long long na = batch * M * 2 * K;
+    k_split<PREC><<<(unsigned)std::min<long long>((na + 255) / 256, 65535), 256, 0, s>>>(
+        reinterpret_cast<const float *>(A), na, ap[0], ap[1], ap[2]);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
   const long long nb = batch * N * K;
   k_embed_split<PREC><<<(unsigned)std::min<long long>((nb + 255) / 256, 65535), 256, 0, s>>>(B, N, K, batch, bp[0],
                                                                                            bp[1], bp[2]);
@@ -425,19 +474,20 @@ cudaError_t run_tc(long long batch, long long M, long long N, long long K, const
   TmaMaps maps;
   std::memset(&maps, 0, sizeof(maps));
   for (int p = 0; p < CF::kParts; ++p) {
-    if (!make_map(&maps.a[p], ap[p], CF::kElem, 2 * K, M, batch, BM)) return cudaErrorInvalidValue;
+    if ((!SPLIT_A || p == 0) && !make_map(&maps.a[p], ap[p], CF::kElem, 2 * K, M, batch, BM))
+      return cudaErrorInvalidValue;
     if (!make_map(&maps.b[p], bp[p], CF::kElem, 2 * K, 2 * N, batch, BN)) return cudaErrorInvalidValue;
   }
   const size_t smem = (size_t)CF::kStages * CF::kParts * (kTileA + kTileB) + 1024;
   static bool configured = false;
   if (!configured) {
-    e = cudaFuncSetAttribute(k_cgemm_tc<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaFuncSetAttribute(k_cgemm_tc<PREC, SPLIT_A>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     configured = true;
   }
   const int k_tiles = (int)((2 * K * CF::kElem) / KBYTES);
   dim3 grid((unsigned)((2 * N) / BN), (unsigned)(M / BM), (unsigned)batch);
-  k_cgemm_tc<PREC><<<grid, kThreads, smem, s>>>(maps, k_tiles, M, 2 * N, reinterpret_cast<float *>(C),
+  k_cgemm_tc<PREC, SPLIT_A><<<grid, kThreads, smem, s>>>(maps, k_tiles, M, 2 * N, reinterpret_cast<float *>(C),
                                                 static_cast<int *>(status_word_ptr()));
   return cudaGetLastError();
 }
@@ -447,6 +497,8 @@ cudaError_t run_tc(long long batch, long long M, long long N, long long K, const
 size_t cgemm_workspace(int precision, long long batch, long long M, long long N, long long K) {
   if (precision == TN_PREC_FP32 || !tc_shape_ok(precision, M, N, K)) return 0;
   const int parts = precision == TN_PREC_3XTF32 ? 2 : 3;
+  // A split on chip: only B's parts are stored
+  if (split_a_on_chip(precision, N)) return parts * align256(part_bytes(precision, 2 * N, 2 * K, batch));
   return parts * (align256(part_bytes(precision, M, 2 * K, batch)) + align256(part_bytes(precision, 2 * N, 2 * K, batch)));
 }
 
@@ -456,8 +508,10 @@ cudaError_t launch_cgemm(int precision, long long batch, long long M, long long 
   if (!tc_shape_ok(precision, M, N, K)) return cudaErrorNotSupported;
   if (batch > 65535 || M / BM > 65535) return cudaErrorNotSupported;
   if (ws_bytes < cgemm_workspace(precision, batch, M, N, K)) return cudaErrorInvalidValue;
-  if (precision == TN_PREC_3XTF32) return run_tc<PREC_TF32>(batch, M, N, K, A, B, C, ws, s);
-  return run_tc<PREC_BF16>(batch, M, N, K, A, B, C, ws, s);
+  if (precision == TN_PREC_3XTF32)
+    return split_a_on_chip(precision, N) ? run_tc<PREC_TF32, true>(batch, M, N, K, A, B, C, ws, s)
+                                         : run_tc<PREC_TF32, false>(batch, M, N, K, A, B, C, ws, s);
+  return run_tc<PREC_BF16, false>(batch, M, N, K, A, B, C, ws, s);
 }
 
 }  // namespace tnq

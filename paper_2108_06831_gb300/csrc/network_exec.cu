@@ -176,10 +176,17 @@ tn_status lower_network(NetPlan &net, int precision, std::string &err) {
     net.launches.push_back(L);
   }
   if (getenv("TNQ_DEBUG_NET")) {  // diagnostic listing of the lowered merges (stderr)
-    for (const NetLaunch &L : net.launches)
-      fprintf(stderr, "merge %d x %d -> %d: batch %lld M %lld N %lld K %lld prec %d perm %d/%d gflop %.3f\n", L.a_id,
+    for (const NetLaunch &L : net.launches) {
+      fprintf(stderr, "merge %d x %d -> %d: batch %lld M %lld N %lld K %lld prec %d perm %d/%d gflop %.3f", L.a_id,
               L.b_id, L.out_id, L.batch, L.M, L.N, L.K, L.precision, (int)!L.perm_a.empty(), (int)!L.perm_b.empty(),
               8.0 * L.batch * L.M * L.N * L.K / 1e9);
+      for (const auto *pv : {&L.perm_a, &L.perm_b}) {
+        fprintf(stderr, " [");
+        for (int v : *pv) fprintf(stderr, "%d ", v);
+        fprintf(stderr, "]");
+      }
+      fprintf(stderr, "\n");
+    }
   }
   const int last = net.steps.empty() ? 0 : net.steps.back().out;
   if (net.all_legs[(size_t)last].size() != 1 || net.all_legs[(size_t)last][0] != 0) {
