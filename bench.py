@@ -299,7 +299,12 @@ def main():
         circs = C.serving_mix(wl["batch"], wl["seed"])
         handles = [tn.CircuitHandle(c) for c in circs]
         plans = [tn.Plan(h, specialize=False) for h in handles]
-        bat = tn.Batch(plans)
+        t_tune = time.perf_counter()
+        bat = tn.Batch.tuned(handles)  # tile sizes picked by measurement (untimed setup)
+        t_tune = time.perf_counter() - t_tune
+        tiles_by_n = {}
+        for c, t in zip(circs, bat.tiles):
+            tiles_by_n.setdefault(c.n_qubits, set()).add(t)
         states = torch.empty(bat.state_elems, dtype=torch.complex64, device=dev)
         bws = torch.empty(bat.workspace_bytes, dtype=torch.uint8, device=dev)
         batch = len(circs)
@@ -524,7 +529,9 @@ def main():
             seq_step()
         sms = timed(seq_step, max(1, args.steps // 2))
         line["config"].update({"circuits": batch, "amplitudes_per_step": units_per_step,
-                               "launch": "one persistent kernel in a CUDA graph"})
+                               "launch": "one persistent kernel in a CUDA graph",
+                               "tiles_by_qubits": {str(k): sorted(v) for k, v in sorted(tiles_by_n.items())},
+                               "autotune_seconds": round(t_tune, 1)})
         line["sequential"] = {"value": units_per_step / (statistics.mean(sms) / 1000.0), "unit": unit,
                               "ms_per_step": statistics.mean(sms),
                               "what": "the same circuits contracted one after another (tn_contract_state each)"}

@@ -278,6 +278,25 @@ tn_status tn_batch_state_offsets(const tn_batch *b, int64_t *offsets);
 tn_status tn_batch_run(const tn_batch *b, void *states_dev, void *workspace_dev, tn_stream_t s);
 void tn_free_batch(tn_batch *b);
 
+/* Tile autotuner (the paper fixes the contraction order ahead of evaluation, Sec. 2.2.3 /
+ * Sec. 3; how a plan is cut into tiles is left to the implementation and chosen here by
+ * measurement).  Plans every circuit (fixed angles, 1..34 qubits) for the batched executor
+ * and picks each circuit's tile size (qubits per tile) from candidates: circuits are grouped
+ * by qubit count, classes are visited in order of decreasing work, and each candidate is
+ * timed by launching the whole batch (1 warm-up + reps timed launches, CUDA events on s, the
+ * fastest kept).  Blocking: allocates and frees its own scratch device memory, synchronises s.
+ * *out receives a batch that owns its plans (tn_free_batch frees them); tiles_out (optional,
+ * n_circuits entries) receives the chosen tile sizes.  A circuit of n <= 12 qubits may also run
+ * as one tile (T = n). */
+typedef struct {
+  int32_t candidates[8]; /* tile sizes in [6, 12], 0-terminated; all zero = {8, 9, 10, 11, 12} */
+  int32_t reps;          /* timed launches per candidate; 0 = 3 */
+  int32_t flags;         /* must be 0 */
+  int64_t reserved[4];   /* must be 0 */
+} tn_tune_opts;
+tn_status tn_batch_build_tuned(const tn_circuit *const *circuits, int32_t n_circuits, const tn_tune_opts *opts,
+                               tn_stream_t s, tn_batch **out, int32_t *tiles_out);
+
 /* ---------------------------------------------------------------------------------------
  * Status.
  * ------------------------------------------------------------------------------------- */

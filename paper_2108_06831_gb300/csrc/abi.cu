@@ -749,6 +749,28 @@ tn_status tn_batch_run(const tn_batch *b, void *states_dev, void *workspace_dev,
   return TN_OK;
 }
 
+tn_status tn_batch_build_tuned(const tn_circuit *const *circuits, int32_t n_circuits, const tn_tune_opts *opts,
+                               tn_stream_t s, tn_batch **out, int32_t *tiles_out) {
+  TN_CHECK_ARG(out != nullptr && circuits != nullptr, "NULL argument");
+  TN_CHECK_ARG(n_circuits >= 1 && n_circuits <= (1 << 20), "n_circuits=%d out of range", n_circuits);
+  *out = nullptr;
+  tn_tune_opts o;
+  std::memset(&o, 0, sizeof(o));
+  if (opts) o = *opts;
+  for (int i = 0; i < 8 && o.candidates[i] != 0; ++i)
+    TN_CHECK_ARG(o.candidates[i] >= kLowBits + 2 && o.candidates[i] <= 12, "candidate tile %d not in [6, 12]",
+                 o.candidates[i]);
+  TN_CHECK_ARG(o.reps >= 0 && o.reps <= 100, "reps=%d out of range", o.reps);
+  TN_CHECK_ARG(o.flags == 0, "flags must be zero");
+  for (int i = 0; i < 4; ++i) TN_CHECK_ARG(o.reserved[i] == 0, "reserved fields must be zero");
+  for (int i = 0; i < n_circuits; ++i) {
+    TN_CHECK_ARG(circuits[i] != nullptr, "circuit %d is NULL", i);
+    TN_CHECK_ARG(circuits[i]->n_params == 0, "circuit %d has parameters (the executor takes fixed angles)", i);
+    TN_CHECK_ARG(circuits[i]->n >= 1 && circuits[i]->n <= kMaxQubits, "circuit %d: %d qubits", i, circuits[i]->n);
+  }
+  return batch_build_tuned(circuits, n_circuits, o, reinterpret_cast<cudaStream_t>(s), out, tiles_out);
+}
+
 void tn_free_batch(tn_batch *b) { batch_free(b); }
 
 tn_status tn_sync_status(tn_stream_t s) {

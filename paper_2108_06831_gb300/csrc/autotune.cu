@@ -1,0 +1,196 @@
+// Tile autotuner of the batched executor.
+//
+// The contraction order of every circuit is fixed by its plan (Sec. 2.2.3: chosen before
+// evaluation); what remains free is how the order is cut into work: the tile size T (qubits
+// per tile) decides how many passes a circuit takes, how many independent tiles each pass
+// offers the persistent executor, and whether a small circuit runs as one item.  No cost
+// model predicts the interleaving of hundreds of uneven circuits on 152 SMs well, so the
+// tuner measures: circuits are grouped by qubit count, classes are visited in order of
+// decreasing work (amplitudes x gates), and for each class every candidate T is tried with
+// the other classes held at their current choice; the whole batch is launched and timed
+// with CUDA events on the caller's stream, and the fastest T is kept (one coordinate-descent
+// sweep).  Planning here is host work; the timed launches are the real executor.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <vector>
+
+#include "kernels.h"
+#include "tnq_internal.h"
+
+namespace tnq {
+
+namespace {
+
+struct DevBuf {
+  void *p = nullptr;
+  size_t bytes = 0;
+  cudaError_t reserve(size_t n) {
+    if (n <= bytes) return cudaSuccess;
+    cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+    cudaError_t e = cudaMalloc(&p, n);
+    if (e == cudaSuccess) bytes = n;
+    return e;
+  }
+  ~DevBuf() { cudaFree(p); }
+};
+
+}  // namespace
+
+tn_status batch_build_tuned(const tn_circuit *const *circuits, int n, const tn_tune_opts &o, cudaStream_t s,
+                            tn_batch **out, int32_t *tiles_out) {
+  std::vector<int> cands;
+  for (int i = 0; i < 8 && o.candidates[i] != 0; ++i) cands.push_back(o.candidates[i]);
+  if (cands.empty()) cands = {8, 9, 10, 11, 12};
+  const int reps = o.reps > 0 ? o.reps : 3;
+
+  // plans per (circuit, T), made on demand; the chosen ones end up owned by the batch
+  std::map<std::pair<int, int>, tn_plan *> plans;
+  auto release_all = [&](const std::vector<int> *keep) {
+    for (auto &kv : plans)
+      if (!keep || (*keep)[(size_t)kv.first.first] != kv.first.second) tn_free_plan(kv.second);
+    plans.clear();
+  };
+  auto plan_of = [&](int i, int T, tn_status *st) -> tn_plan * {
+    auto it = plans.find({i, T});
+    if (it != plans.end()) return it->second;
+    tn_plan_opts po;
+    std::memset(&po, 0, sizeof(po));
+    po.target = TN_TARGET_STATE;
+    po.batch = 1;
+    po.tile_qubits = T;
+    po.flags = TN_PLAN_NO_SPECIALIZE;  // the executor runs the plan's tables, not generated kernels
+    tn_plan *p = nullptr;
+    *st = tn_plan_contraction(circuits[i], &po, &p);
+    if (*st == TN_OK) plans[{i, T}] = p;
+    return p;
+  };
+
+  // classes by qubit count, most work first
+  std::map<int, std::vector<int>> by_n;
+  std::map<int, double> work;
+  for (int i = 0; i < n; ++i) {
+    by_n[circuits[i]->n].push_back(i);
+    work[circuits[i]->n] += std::ldexp(1.0, circuits[i]->n) * (double)(circuits[i]->gates.size() + 1);
+  }
+  std::vector<int> order;
+  for (auto &kv : by_n) order.push_back(kv.first);
+  std::sort(order.begin(), order.end(), [&](int a, int b) { return work[a] > work[b]; });
+
+  std::vector<int> T((size_t)n);
+  for (int i = 0; i < n; ++i) T[(size_t)i] = std::min(circuits[i]->n, 12);
+
+  DevBuf states, ws;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t ce = cudaEventCreate(&e0);
+  if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
+  if (ce != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return cuda_fail(ce, "autotune events");
+  }
+  // time the batch for the current choice T (fastest of reps launches, ms)
+  auto measure = [&](double *ms) -> tn_status {
+    std::vector<const tn_plan *> ps((size_t)n);
+    for (int i = 0; i < n; ++i) {
+      tn_status st = TN_OK;
+      ps[(size_t)i] = plan_of(i, T[(size_t)i], &st);
+      if (st != TN_OK) return st;
+    }
+    tn_batch *b = nullptr;
+    tn_status st = batch_build(ps.data(), n, &b);
+    if (st != TN_OK) return st;
+    long long elems = 0;
+    size_t wsb = 0;
+    batch_sizes(b, &elems, &wsb);
+    cudaError_t e = states.reserve((size_t)elems * sizeof(float2));
+    if (e == cudaSuccess) e = ws.reserve(wsb);
+    float best = 1e30f;
+    for (int r = 0; e == cudaSuccess && r <= reps; ++r) {  // launch 0 warms up
+      e = cudaEventRecord(e0, s);
+      if (e == cudaSuccess) e = batch_run(b, static_cast<float2 *>(states.p), ws.p, s);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float t = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+      if (e == cudaSuccess && r > 0) best = std::min(best, t);
+    }
+    batch_free(b);
+    if (e != cudaSuccess) return cuda_fail(e, "autotune launch");
+    int dev_status = TN_OK;
+    e = read_and_clear_status(&dev_status, s);
+    if (e != cudaSuccess) return cuda_fail(e, "autotune status");
+    if (dev_status != TN_OK) {
+      set_error("autotune: executor reported status %d", dev_status);
+      return (tn_status)dev_status;
+    }
+    *ms = best;
+    return TN_OK;
+  };
+
+  double cur = 0;
+  tn_status st = measure(&cur);
+  for (size_t ci = 0; st == TN_OK && ci < order.size(); ++ci) {
+    const int nq = order[ci];
+    const std::vector<int> &members = by_n[nq];
+    std::vector<int> opts;
+    for (int c : cands)
+      if (c >= kLowBits + 2 && c <= std::min(nq, 12)) opts.push_back(c);
+    if (nq <= 12) opts.push_back(nq);  // the whole circuit as one tile
+    std::sort(opts.begin(), opts.end());
+    opts.erase(std::unique(opts.begin(), opts.end()), opts.end());
+    const int start = T[(size_t)members.front()];
+    int best_t = start;
+    double best_ms = cur;
+    for (int t : opts) {
+      if (t == start) continue;
+      for (int i : members) T[(size_t)i] = t;
+      double ms = 0;
+      tn_status s2 = measure(&ms);
+      if (s2 == TN_ERR_CUDA || s2 == TN_ERR_TIMEOUT) {
+        st = s2;
+        break;
+      }
+      if (s2 == TN_OK && ms < best_ms) {
+        best_ms = ms;
+        best_t = t;
+      }
+    }
+    for (int i : members) T[(size_t)i] = best_t;
+    cur = best_ms;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != TN_OK) {
+    release_all(nullptr);
+    return st;
+  }
+  // final batch over the chosen plans, which it adopts
+  std::vector<const tn_plan *> ps((size_t)n);
+  std::vector<tn_plan *> owned((size_t)n);
+  for (int i = 0; i < n; ++i) {
+    tn_status s2 = TN_OK;
+    owned[(size_t)i] = plan_of(i, T[(size_t)i], &s2);
+    ps[(size_t)i] = owned[(size_t)i];
+    if (s2 != TN_OK) {
+      release_all(nullptr);
+      return s2;
+    }
+  }
+  tn_batch *b = nullptr;
+  st = batch_build(ps.data(), n, &b);
+  if (st != TN_OK) {
+    release_all(nullptr);
+    return st;
+  }
+  release_all(&T);  // frees every plan that was not chosen
+  batch_adopt_plans(b, owned);
+  if (tiles_out)
+    for (int i = 0; i < n; ++i) tiles_out[i] = T[(size_t)i];
+  *out = b;
+  return TN_OK;
+}
+
+}  // namespace tnq

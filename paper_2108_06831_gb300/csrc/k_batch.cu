@@ -205,6 +205,7 @@ struct tn_batch {
   tnq::BatchCirc *d_circs = nullptr;
   tnq::PassDesc *d_passes = nullptr;
   size_t ws_bytes = 0;
+  std::vector<tn_plan *> owned;  // plans made for this batch (tile autotuner)
 };
 
 namespace tnq {
@@ -352,7 +353,12 @@ void batch_free(tn_batch *b) {
   cudaFree(b->d_tasks);
   cudaFree(b->d_circs);
   cudaFree(b->d_passes);
+  for (tn_plan *p : b->owned) tn_free_plan(p);
   delete b;
+}
+
+void batch_adopt_plans(tn_batch *b, const std::vector<tn_plan *> &plans) {
+  b->owned.insert(b->owned.end(), plans.begin(), plans.end());
 }
 
 }  // namespace tnq

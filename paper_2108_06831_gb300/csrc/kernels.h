@@ -1,6 +1,8 @@
 // Launchers of libtnq's CUDA kernels (host declarations).
 #pragma once
 
+#include <vector>
+
 #include "tnq_internal.h"
 
 namespace tnq {
@@ -48,6 +50,11 @@ void batch_free(tn_batch *b);
 tn_status batch_sizes(const tn_batch *b, long long *elems, size_t *ws);
 tn_status batch_offsets(const tn_batch *b, long long *offsets);
 int batch_device(const tn_batch *b);
+// The batch takes ownership of plans (freed with it).
+void batch_adopt_plans(tn_batch *b, const std::vector<tn_plan *> &plans);
+// Tile autotuner: plans every circuit at measured-best tile sizes and batches them.
+tn_status batch_build_tuned(const tn_circuit *const *circuits, int n, const tn_tune_opts &o, cudaStream_t s,
+                            tn_batch **out, int32_t *tiles_out);
 
 // Device status word (timeouts, non-finite values).
 void *status_word_ptr();

@@ -53,6 +53,11 @@ class TnPlanStats(C.Structure):
                 ("reserved", C.c_int32 * 3)]
 
 
+class TnTuneOpts(C.Structure):
+    _fields_ = [("candidates", C.c_int32 * 8), ("reps", C.c_int32), ("flags", C.c_int32),
+                ("reserved", C.c_int64 * 4)]
+
+
 class TnPauliSum(C.Structure):
     _fields_ = [("n_terms", C.c_int32), ("coef", C.POINTER(C.c_double)), ("paulis", C.POINTER(C.c_uint8))]
 
@@ -83,6 +88,8 @@ _sigs = {
     "tn_batch_state_offsets": [_vp, C.POINTER(C.c_int64)],
     "tn_batch_run": [_vp, _vp, _vp, _vp],
     "tn_free_batch": [_vp],
+    "tn_batch_build_tuned": [C.POINTER(_vp), C.c_int32, C.POINTER(TnTuneOpts), _vp, C.POINTER(_vp),
+                             C.POINTER(C.c_int32)],
     "tn_sync_status": [_vp],
     "tn_last_error": [],
     "tn_version": [],
@@ -290,13 +297,37 @@ class Batch:
         arr = (_vp * len(plans))(*[p._h for p in plans])
         h = _vp()
         _check(_lib.tn_batch_build(arr, len(plans), C.byref(h)), "tn_batch_build")
-        self._h = h
         self.plans = list(plans)
+        self.tiles = [p.stats()["tile_qubits"] for p in plans]
+        self._init(h, len(plans))
+
+    @classmethod
+    def tuned(cls, circuits: Sequence["CircuitHandle"], candidates: Sequence[int] = (), reps: int = 3,
+              stream=None) -> "Batch":
+        """Batch whose tile sizes are picked by measurement (tn_batch_build_tuned); it owns its plans."""
+        o = TnTuneOpts()
+        for i, c in enumerate(list(candidates)[:8]):
+            o.candidates[i] = int(c)
+        o.reps = reps
+        arr = (_vp * len(circuits))(*[c._h for c in circuits])
+        tiles = (C.c_int32 * len(circuits))()
+        h = _vp()
+        _check(_lib.tn_batch_build_tuned(arr, len(circuits), C.byref(o), _stream(stream), C.byref(h), tiles),
+               "tn_batch_build_tuned")
+        self = cls.__new__(cls)
+        self.plans = []
+        self.circuits = list(circuits)
+        self.tiles = list(tiles)
+        self._init(h, len(circuits))
+        return self
+
+    def _init(self, h, n):
+        self._h = h
         e = C.c_int64()
         w = C.c_size_t()
         _check(_lib.tn_batch_sizes(h, C.byref(e), C.byref(w)), "tn_batch_sizes")
         self.state_elems, self.workspace_bytes = e.value, w.value
-        offs = (C.c_int64 * len(plans))()
+        offs = (C.c_int64 * n)()
         _check(_lib.tn_batch_state_offsets(h, offs), "tn_batch_state_offsets")
         self.offsets = list(offs)
 

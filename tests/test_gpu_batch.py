@@ -83,3 +83,39 @@ def test_batch_rejects_parameterised_plans():
     with pytest.raises(tn.TnError) as e:
         tn.Batch([p])
     assert e.value.status == tn.ERR_UNSUPPORTED
+
+
+def test_tuned_batch_matches_oracle():
+    """The tile autotuner: every chosen tile is a candidate (or the circuit's own width), the
+    batch it returns owns its plans, and its states match the oracle."""
+    from oracle.statevector import simulate_state
+    from paper_2108_06831_gb300 import tn
+    circs = _mix()[:12]
+    handles = [tn.CircuitHandle(c) for c in circs]
+    b = tn.Batch.tuned(handles, candidates=(6, 8, 10, 12), reps=1)
+    for c, t in zip(circs, b.tiles):
+        assert t in (6, 8, 10, 12) or t == c.n_qubits
+        assert t <= min(c.n_qubits, 12)
+    del handles  # the batch must not depend on the circuit handles
+    states = torch.full((b.state_elems,), complex(float("nan"), 0), dtype=torch.complex64, device="cuda")
+    ws = torch.empty(b.workspace_bytes, dtype=torch.uint8, device="cuda")
+    tn.batch_run(b, states, ws)
+    torch.cuda.synchronize()
+    assert tn.sync_status() == tn.OK
+    got = states.cpu().numpy()
+    for c, off in zip(circs, b.offsets):
+        ref = simulate_state(c)
+        s = got[off:off + (1 << c.n_qubits)]
+        assert np.linalg.norm(s - ref) / np.linalg.norm(ref) <= TOL, c.name
+
+
+def test_tuned_batch_rejects_bad_options():
+    from paper_2108_06831_gb300 import tn
+    h = [tn.CircuitHandle(C.brickwork(8, 3, 1)[0])]
+    with pytest.raises(tn.TnError):
+        tn.Batch.tuned(h, candidates=(5,))
+    with pytest.raises(tn.TnError):
+        tn.Batch.tuned(h, candidates=(13,))
+    hp = [tn.CircuitHandle(C.brickwork(8, 3, 1, parameterized=True)[0])]
+    with pytest.raises(tn.TnError):
+        tn.Batch.tuned(hp)
