@@ -37,7 +37,7 @@
 namespace tnq {
 
 cudaError_t launch_cgemm_fp32(long long batch, long long M, long long N, long long K, const float2 *A, const float2 *B,
-                              float2 *C, cudaStream_t s);
+                              float2 *C, cudaStream_t s, const OutMap *om);
 
 namespace {
 
@@ -48,6 +48,8 @@ constexpr int KBYTES = 128;      // bytes of K per stage and operand row (one 12
 // warp 4: TMA producer; warp 5: TMEM allocation and MMA issue
 constexpr int kThreads = 192;
 constexpr int kConvThreads = 128;
+constexpr int kColBits = 6;  // log2 of the complex columns of a tile (BN / 2)
+static_assert(BN / 2 == 1 << kColBits, "column table covers one tile");
 constexpr int kMain = 3;                      // leading-product accumulators, used round robin by K tile
 constexpr int kTmemCols = (kMain + 1) * BN;   // + one correction accumulator = all 512 columns
 constexpr unsigned long long kWaitNs = 2000000000ull;  // bound of every mbarrier wait
@@ -171,6 +173,29 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
       : "r"(taddr));
 }
 
+// Output index of natural flat index bits [lo, nbits) of f under the map.
+__device__ __forceinline__ long long map_bits(const OutMap &om, long long f, int lo) {
+  long long r = 0;
+  for (int i = lo; i < om.nbits; ++i)
+    if ((f >> i) & 1) r |= 1ll << om.pos[i];
+  return r;
+}
+
+// One 32-column chunk (16 complex values, interleaved) of a row of C, either row-major
+// (identity map) or at mapped positions: rowaddr = map of the row and column-tile bits,
+// ctab[j] = map of the tile-local column bits (j < 64).
+__device__ __forceinline__ void store_chunk(const OutMap &om, float *crow, float2 *C2, long long rowaddr,
+                                            const long long *ctab, int c, const float (&v)[32]) {
+  if (om.identity) {
+    float4 *dst = reinterpret_cast<float4 *>(crow + c);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) dst[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+  } else {
+#pragma unroll
+    for (int q = 0; q < 16; ++q) C2[rowaddr + ctab[c / 2 + q]] = make_float2(v[2 * q], v[2 * q + 1]);
+  }
+}
+
 struct TmaMaps {
   CUtensorMap a[3];
   CUtensorMap b[3];
@@ -190,7 +215,7 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *b) {
 template <int PREC, bool SPLIT_A>
 __global__ void __launch_bounds__(kThreads, 1) k_cgemm_tc(const __grid_constant__ TmaMaps maps, int k_tiles,
                                                           long long M, long long N2, float *__restrict__ C,
-                                                          int *status) {
+                                                          int *status, const __grid_constant__ OutMap om) {
   using CF = Cfg<PREC>;
   static_assert(!SPLIT_A || PREC == PREC_TF32, "on-chip split is the TF32 form");
   constexpr int S = CF::kStages;
@@ -203,9 +228,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_cgemm_tc(const __grid_constant_
   __shared__ __align__(8) uint64_t full[S], conv[S], empty[S], done;
   __shared__ uint32_t tmem_base;
   __shared__ int abort_flag;
+  __shared__ long long ctab[BN / 2];
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int n0 = blockIdx.x * BN, m0 = blockIdx.y * BM, bz = blockIdx.z;
+  if (threadIdx.x < BN / 2) ctab[threadIdx.x] = om.identity ? 0 : map_bits(om, threadIdx.x, 0);
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
@@ -308,6 +335,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_cgemm_tc(const __grid_constant_
   if (have && warp < 4) {
     const long long row = m0 + warp * 32 + lane;
     float *crow = C + ((long long)bz * M + row) * N2 + n0;
+    long long rowaddr = 0;
+    if (!om.identity) {
+      int lgn = 0;
+      while ((2ll << lgn) < N2) ++lgn;  // complex columns = 2^lgn
+      rowaddr = map_bits(om, (((long long)bz * M + row) << lgn) | (long long)(n0 / 2), kColBits);
+    }
     const int n_main = k_tiles < kMain ? k_tiles : kMain;  // accumulators that were written
     for (int c = 0; c < BN; c += 32) {
       const uint32_t taddr = tmem_d + ((uint32_t)(warp * 32) << 16) + (uint32_t)c;
@@ -326,9 +359,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_cgemm_tc(const __grid_constant_
 #pragma unroll
         for (int i = 0; i < 32; ++i) v[i] += __uint_as_float(r[i]);
       }
-      float4 *dst = reinterpret_cast<float4 *>(crow + c);
-#pragma unroll
-      for (int q = 0; q < 8; ++q) dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+      store_chunk(om, crow, reinterpret_cast<float2 *>(C), rowaddr, ctab, c, v);
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -336,6 +367,278 @@ __global__ void __launch_bounds__(kThreads, 1) k_cgemm_tc(const __grid_constant_
   if (abort_flag && threadIdx.x == 0) {
     // let copies already in flight land before the CTA's shared memory is released
     for (int s = 0; s < S; ++s) mbar_wait(&full[s], 0, nullptr);
+  }
+  if (warp == 5) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_d), "r"(kTmemCols));
+  }
+}
+
+// Persistent form for short, HBM-bound merges (3XTF32, A split on chip, at most
+// kStreamMaxKTiles K tiles; a network merge has N = K = 64 and thousands of 128-row tiles):
+// one CTA per SM walks the tiles (column tile fastest, then row tile, then batch), the TMA
+// stage ring runs on across tile boundaries, and the accumulators are double-buffered in
+// TMEM (leading + correction product per buffer, 2 x 2 x BN columns), so dedicated epilogue
+// warps drain tile i while tile i+1 is loaded, split and multiplied.
+// Warps 0-3: A split; warp 4: TMA; warp 5: TMEM allocation and MMA issue; warps 6-9:
+// epilogue (warp w owns TMEM lanes 32 (w mod 4)..+31).
+constexpr int kStreamThreads = 320;
+constexpr int kStreamMaxKTiles = 8;  // a single leading accumulator per tile stays accurate
+constexpr int kStgStride = 17;       // staging row stride (complex): rows fall in different banks
+
+__global__ void __launch_bounds__(kStreamThreads, 1)
+    k_cgemm_tc_stream(const __grid_constant__ TmaMaps maps, int k_tiles, int tiles_n, int tiles_m,
+                      long long total_tiles, long long M, long long N2, float *__restrict__ C, int *status,
+                      const __grid_constant__ OutMap om) {
+  using CF = Cfg<PREC_TF32>;
+  constexpr int S = CF::kStages;
+  constexpr int stage_bytes = CF::kParts * (kTileA + kTileB);
+  constexpr uint32_t tx_bytes = kTileA + CF::kParts * kTileB;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char *smem = reinterpret_cast<unsigned char *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  __shared__ __align__(8) uint64_t full[S], conv[S], empty[S], acc_full[2], acc_empty[2];
+  __shared__ uint32_t tmem_base;
+  __shared__ int abort_flag;
+  __shared__ int issued_parity[S];  // parity of the last TMA phase issued per stage, -1 if none
+  // Permuted epilogue: a warp stages 32 rows x 16 complex columns (one 32-float chunk of its
+  // rows) and writes them back in stored-index order.  The chunk's 9 local bits (5 row, 4
+  // column) are enumerated by increasing stored position (u); u -> staging offset and u ->
+  // stored offset are linear in u's bits, tabulated for u's low 5 and high 4 bits.
+  __shared__ float2 stage_c[4][32 * kStgStride];
+  __shared__ int sm_lo[32], sm_hi[16];
+  __shared__ long long g_lo[32], g_hi[16];
+  __shared__ int pairs_contig;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (!om.identity && threadIdx.x == 0) {
+    int lgn = 0;
+    while ((2ll << lgn) < N2) ++lgn;
+    // local bit b: b < 4 column bit b (stored at pos[b]); b >= 4 row bit b - 4 (pos[lgn + b - 4])
+    int spos[9], order[9];
+    for (int b = 0; b < 9; ++b) {
+      spos[b] = b < 4 ? om.pos[b] : om.pos[lgn + b - 4];
+      order[b] = b;
+    }
+    for (int i = 1; i < 9; ++i)  // insertion sort by stored position
+      for (int j = i; j > 0 && spos[order[j - 1]] > spos[order[j]]; --j) {
+        const int t = order[j];
+        order[j] = order[j - 1];
+        order[j - 1] = t;
+      }
+    auto contrib_s = [&](int b) { return b < 4 ? (1 << b) : (kStgStride << (b - 4)); };
+    for (int u = 0; u < 32; ++u) {
+      int so = 0;
+      long long go = 0;
+      for (int k = 0; k < 5; ++k)
+        if ((u >> k) & 1) {
+          so += contrib_s(order[k]);
+          go += 1ll << spos[order[k]];
+        }
+      sm_lo[u] = so;
+      g_lo[u] = go;
+    }
+    for (int u = 0; u < 16; ++u) {
+      int so = 0;
+      long long go = 0;
+      for (int k = 0; k < 4; ++k)
+        if ((u >> k) & 1) {
+          so += contrib_s(order[5 + k]);
+          go += 1ll << spos[order[5 + k]];
+        }
+      sm_hi[u] = so;
+      g_hi[u] = go;
+    }
+    pairs_contig = spos[order[0]] == 0 ? 1 : 0;
+  }
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&conv[s], kConvThreads);
+      mbar_init(&empty[s], 1);
+      issued_parity[s] = -1;
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&acc_full[b], 1);
+      mbar_init(&acc_empty[b], 128);
+    }
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 5) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(&tmem_base)),
+                 "r"(kTmemCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem_d = tmem_base;
+
+  auto aborted = [&]() { return *reinterpret_cast<volatile int *>(&abort_flag) != 0; };
+  auto decode = [&](long long t, int &nt, int &mt, int &bz) {
+    nt = (int)(t % tiles_n);
+    const long long r = t / tiles_n;
+    mt = (int)(r % tiles_m);
+    bz = (int)(r / tiles_m);
+  };
+
+  if (warp == 4) {
+    if (lane == 0) {  // TMA producer
+      long long g = 0;
+      for (long long t = blockIdx.x; t < total_tiles && !aborted(); t += gridDim.x) {
+        int nt, mt, bz;
+        decode(t, nt, mt, bz);
+        for (int kt = 0; kt < k_tiles; ++kt, ++g) {
+          const int s = (int)(g % S);
+          if (g >= S && !mbar_wait(&empty[s], (uint32_t)(((g / S) - 1) & 1), status)) {
+            abort_flag = 1;
+            break;
+          }
+          mbar_expect_tx(&full[s], tx_bytes);
+          issued_parity[s] = (int)((g / S) & 1);
+          unsigned char *st = smem + (size_t)s * stage_bytes;
+          const int kc = kt * (KBYTES / CF::kElem);
+          tma_load_3d(st, &maps.a[0], &full[s], kc, mt * BM, bz);
+          for (int p = 0; p < CF::kParts; ++p)
+            tma_load_3d(st + CF::kParts * kTileA + p * kTileB, &maps.b[p], &full[s], kc, nt * BN, bz);
+        }
+      }
+    }
+  } else if (warp == 5) {
+    if (lane == 0) {  // MMA issuer
+      long long g = 0, li = 0;
+      for (long long t = blockIdx.x; t < total_tiles && !aborted(); t += gridDim.x, ++li) {
+        const int ab = (int)(li & 1);
+        if (li >= 2 && !mbar_wait(&acc_empty[ab], (uint32_t)(((li / 2) - 1) & 1), status)) {
+          abort_flag = 1;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t base = tmem_d + (uint32_t)(ab * 2 * BN);
+        bool ok = true;
+        for (int kt = 0; kt < k_tiles; ++kt, ++g) {
+          const int s = (int)(g % S);
+          if (!mbar_wait(&conv[s], (uint32_t)((g / S) & 1), status)) {
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t st = saddr(smem + (size_t)s * stage_bytes);
+#pragma unroll
+          for (int p = 0; p < CF::kProducts; ++p) {
+            const uint32_t a_base = st + CF::pa(p) * kTileA;
+            const uint32_t b_base = st + CF::kParts * kTileA + CF::pb(p) * kTileB;
+#pragma unroll
+            for (int kk = 0; kk < KBYTES / (CF::kMmaK * CF::kElem); ++kk) {
+              const uint32_t off = kk * CF::kMmaK * CF::kElem;
+              const uint32_t dst = p == 0 ? base : base + BN;
+              const bool acc = p == 0 ? (kt > 0 || kk > 0) : (kt > 0 || kk > 0 || p > 1);
+              mma<PREC_TF32>(dst, smem_desc(a_base + off), smem_desc(b_base + off), acc ? 1u : 0u);
+            }
+          }
+          mma_commit(&empty[s]);
+        }
+        if (!ok) {
+          abort_flag = 1;
+          break;
+        }
+        mma_commit(&acc_full[ab]);
+      }
+    }
+  } else if (warp < 4) {  // A split, as in k_cgemm_tc
+    long long g = 0;
+    for (long long t = blockIdx.x; t < total_tiles; t += gridDim.x) {
+      bool ok = true;
+      for (int kt = 0; kt < k_tiles; ++kt, ++g) {
+        const int s = (int)(g % S);
+        if (!mbar_wait(&full[s], (uint32_t)((g / S) & 1), status)) {
+          ok = false;
+          break;
+        }
+        float4 *hi = reinterpret_cast<float4 *>(smem + (size_t)s * stage_bytes);
+        float4 *lo = reinterpret_cast<float4 *>(smem + (size_t)s * stage_bytes + kTileA);
+#pragma unroll 4
+        for (int c = threadIdx.x; c < kTileA / 16; c += kConvThreads) {
+          const float4 v = hi[c];
+          const float4 h = make_float4(tf32_rna(v.x), tf32_rna(v.y), tf32_rna(v.z), tf32_rna(v.w));
+          lo[c] = make_float4(v.x - h.x, v.y - h.y, v.z - h.z, v.w - h.w);
+          hi[c] = h;
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive(&conv[s]);
+      }
+      if (!ok) {
+        abort_flag = 1;
+        break;
+      }
+    }
+  } else {  // epilogue warps 6-9
+    const int q = warp & 3;  // TMEM lane quarter this warp may access
+    int lgn = 0;
+    while ((2ll << lgn) < N2) ++lgn;  // complex columns = 2^lgn
+    long long li = 0;
+    for (long long t = blockIdx.x; t < total_tiles; t += gridDim.x, ++li) {
+      const int ab = (int)(li & 1);
+      bool have = mbar_wait(&acc_full[ab], (uint32_t)((li / 2) & 1), status);
+      have = __all_sync(0xFFFFFFFFu, have);
+      if (!have) {
+        abort_flag = 1;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      int nt, mt, bz;
+      decode(t, nt, mt, bz);
+      const long long row = (long long)mt * BM + q * 32 + lane;
+      float *crow = C + ((long long)bz * M + row) * N2 + (long long)nt * BN;
+      const long long row0 = (long long)bz * M + (long long)mt * BM + q * 32;  // the warp's first row
+      const uint32_t base = tmem_d + ((uint32_t)(q * 32) << 16) + (uint32_t)(ab * 2 * BN);
+      float2 *stg = stage_c[q];
+      for (int c = 0; c < BN; c += 32) {
+        uint32_t r[32], e[32];
+        tmem_ld32(base + BN + c, e);  // corrections
+        tmem_ld32(base + c, r);       // leading product
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        float v[32];
+#pragma unroll
+        for (int k = 0; k < 32; ++k) v[k] = __uint_as_float(e[k]) + __uint_as_float(r[k]);
+        if (om.identity) {
+          float4 *dst = reinterpret_cast<float4 *>(crow + c);
+#pragma unroll
+          for (int k = 0; k < 8; ++k) dst[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+          continue;
+        }
+        // stored offset of everything but the chunk's local bits (lane row bits, 4 column bits)
+        const long long gbase = map_bits(om, (row0 << lgn) | ((long long)nt * (BN / 2) + c / 2), 0);
+#pragma unroll
+        for (int k = 0; k < 16; ++k) stg[lane * kStgStride + k] = make_float2(v[2 * k], v[2 * k + 1]);
+        __syncwarp();
+        float2 *C2 = reinterpret_cast<float2 *>(C);
+#pragma unroll
+        for (int it = 0; it < 8; ++it) {
+          const int u = 64 * it + 2 * lane;  // even: u and u + 1 differ in the lowest sorted bit
+          const float2 x0 = stg[sm_lo[u & 31] + sm_hi[u >> 5]];
+          const float2 x1 = stg[sm_lo[(u + 1) & 31] + sm_hi[(u + 1) >> 5]];
+          const long long g0 = gbase + g_lo[u & 31] + g_hi[u >> 5];
+          if (pairs_contig) {
+            *reinterpret_cast<float4 *>(C2 + g0) = make_float4(x0.x, x0.y, x1.x, x1.y);
+          } else {
+            C2[g0] = x0;
+            C2[gbase + g_lo[(u + 1) & 31] + g_hi[(u + 1) >> 5]] = x1;
+          }
+        }
+        __syncwarp();
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      mbar_arrive(&acc_empty[ab]);
+    }
+  }
+  __syncwarp();
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (abort_flag && threadIdx.x == 0) {
+    // let copies already in flight land before the CTA's shared memory is released
+    for (int s = 0; s < S; ++s)
+      if (issued_parity[s] >= 0) mbar_wait(&full[s], (uint32_t)issued_parity[s], nullptr);
   }
   if (warp == 5) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -447,7 +750,7 @@ bool split_a_on_chip(int precision, long long N) { return precision == TN_PREC_3
 
 template <int PREC, bool SPLIT_A>
 cudaError_t run_tc(long long batch, long long M, long long N, long long K, const float2 *A, const float2 *B, float2 *C,
-                   void *ws, cudaStream_t s) {
+                   void *ws, cudaStream_t s, const OutMap &om) {
   using CF = Cfg<PREC>;
   const int prec_abi = PREC == PREC_TF32 ? TN_PREC_3XTF32 : TN_PREC_SPLIT_BF16;
   const size_t pa = SPLIT_A ? 0 : align256(part_bytes(prec_abi, M, 2 * K, batch));
@@ -479,16 +782,33 @@ cudaError_t run_tc(long long batch, long long M, long long N, long long K, const
     if (!make_map(&maps.b[p], bp[p], CF::kElem, 2 * K, 2 * N, batch, BN)) return cudaErrorInvalidValue;
   }
   const size_t smem = (size_t)CF::kStages * CF::kParts * (kTileA + kTileB) + 1024;
+  const int k_tiles = (int)((2 * K * CF::kElem) / KBYTES);
+  if constexpr (SPLIT_A) {
+    if (k_tiles <= kStreamMaxKTiles) {  // short merge: persistent CTAs with overlapped epilogue
+      static bool configured_stream = false;
+      if (!configured_stream) {
+        e = cudaFuncSetAttribute(k_cgemm_tc_stream, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        configured_stream = true;
+      }
+      const int tiles_n = (int)((2 * N) / BN), tiles_m = (int)(M / BM);
+      const long long total = (long long)tiles_n * tiles_m * batch;
+      const long long grid = std::min<long long>(total, num_sms());
+      k_cgemm_tc_stream<<<(unsigned)grid, kStreamThreads, smem, s>>>(
+          maps, k_tiles, tiles_n, tiles_m, total, M, 2 * N, reinterpret_cast<float *>(C),
+          static_cast<int *>(status_word_ptr()), om);
+      return cudaGetLastError();
+    }
+  }
   static bool configured = false;
   if (!configured) {
     e = cudaFuncSetAttribute(k_cgemm_tc<PREC, SPLIT_A>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     configured = true;
   }
-  const int k_tiles = (int)((2 * K * CF::kElem) / KBYTES);
   dim3 grid((unsigned)((2 * N) / BN), (unsigned)(M / BM), (unsigned)batch);
   k_cgemm_tc<PREC, SPLIT_A><<<grid, kThreads, smem, s>>>(maps, k_tiles, M, 2 * N, reinterpret_cast<float *>(C),
-                                                static_cast<int *>(status_word_ptr()));
+                                                         static_cast<int *>(status_word_ptr()), om);
   return cudaGetLastError();
 }
 
@@ -503,15 +823,17 @@ size_t cgemm_workspace(int precision, long long batch, long long M, long long N,
 }
 
 cudaError_t launch_cgemm(int precision, long long batch, long long M, long long N, long long K, const float2 *A,
-                         const float2 *B, float2 *C, void *ws, size_t ws_bytes, cudaStream_t s) {
-  if (precision == TN_PREC_FP32) return launch_cgemm_fp32(batch, M, N, K, A, B, C, s);
+                         const float2 *B, float2 *C, void *ws, size_t ws_bytes, cudaStream_t s, const OutMap *om) {
+  if (precision == TN_PREC_FP32) return launch_cgemm_fp32(batch, M, N, K, A, B, C, s, om);
+  const OutMap ident;
+  const OutMap &m = om ? *om : ident;
   if (!tc_shape_ok(precision, M, N, K)) return cudaErrorNotSupported;
   if (batch > 65535 || M / BM > 65535) return cudaErrorNotSupported;
   if (ws_bytes < cgemm_workspace(precision, batch, M, N, K)) return cudaErrorInvalidValue;
   if (precision == TN_PREC_3XTF32)
-    return split_a_on_chip(precision, N) ? run_tc<PREC_TF32, true>(batch, M, N, K, A, B, C, ws, s)
-                                         : run_tc<PREC_TF32, false>(batch, M, N, K, A, B, C, ws, s);
-  return run_tc<PREC_BF16, false>(batch, M, N, K, A, B, C, ws, s);
+    return split_a_on_chip(precision, N) ? run_tc<PREC_TF32, true>(batch, M, N, K, A, B, C, ws, s, m)
+                                         : run_tc<PREC_TF32, false>(batch, M, N, K, A, B, C, ws, s, m);
+  return run_tc<PREC_BF16, false>(batch, M, N, K, A, B, C, ws, s, m);
 }
 
 }  // namespace tnq

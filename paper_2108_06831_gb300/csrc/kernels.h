@@ -39,9 +39,19 @@ cudaError_t launch_permute(int n_legs, const int32_t *perm, long long batch, con
                            cudaStream_t s);
 
 // Kernel (c): batched complex GEMM C[b] = A[b] * B[b]^T (K-contiguous operands).
+// Output map: with batch, M and N powers of two, element (b, m, n) has the natural flat index
+// f = (b M + m) N + n; a non-identity map stores it at sum_i bit_i(f) << pos[i] instead, so a
+// merge writes its result directly in the leg order its consumer reads (a permutation of
+// binary legs fused into the epilogue).
+struct OutMap {
+  int identity = 1;
+  int nbits = 0;
+  uint8_t pos[64] = {};
+};
 size_t cgemm_workspace(int precision, long long batch, long long M, long long N, long long K);
 cudaError_t launch_cgemm(int precision, long long batch, long long M, long long N, long long K, const float2 *A,
-                         const float2 *B, float2 *C, void *ws, size_t ws_bytes, cudaStream_t s);
+                         const float2 *B, float2 *C, void *ws, size_t ws_bytes, cudaStream_t s,
+                         const OutMap *om = nullptr);
 
 // Persistent batched executor.
 tn_status batch_build(const tn_plan *const *plans, int n, tn_batch **out);

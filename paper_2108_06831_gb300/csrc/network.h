@@ -5,6 +5,7 @@
 #include <string>
 #include <vector>
 
+#include "kernels.h"
 #include "tnq_internal.h"
 
 namespace tnq {
@@ -25,7 +26,8 @@ struct NetStep {
   std::vector<int> batch, contr, out_legs;
 };
 
-// Lowered step: permutations of the two operands, one batched complex GEMM.
+// Lowered step: permutations of initial operands, one batched complex GEMM whose output is
+// written in the leg order its consumer reads (out_map; identity for the last merge).
 struct NetLaunch {
   int a_id, b_id, out_id;
   int a_bits, b_bits;                  // binary legs of the operands
@@ -36,6 +38,7 @@ struct NetLaunch {
   long long off_gemm_ws;               // bytes offset of the GEMM split workspace (-1: none)
   size_t gemm_ws_bytes;
   int precision;                       // tn_precision used for this merge
+  OutMap out_map;                      // natural [batch][M][N] index -> stored index
 };
 
 struct NetPlan {

@@ -131,34 +131,90 @@ tn_status lower_network(NetPlan &net, int precision, std::string &err) {
       hw = std::max(hw, al.top);
     }
   }
-  net.launches.clear();
-  for (size_t si = 0; si < net.steps.size(); ++si) {
-    const NetStep &st = net.steps[si];
-    NetLaunch L;
+  // Layouts, decided from the last merge back to the first.  Every intermediate has one
+  // consumer, which fixes the leg order it reads ([batch][free][contracted]); the producing
+  // merge then orders its own batch, row (M) and column (N) legs as they appear in that
+  // target, so that its GEMM's output map is monotone within each group, and stores the
+  // result directly in the target order (the permutation fused into the GEMM epilogue).
+  // Within the contracted group, legs that the operand's producer computes as columns come
+  // last: a producer tile (all N bits and the lowest 7 M bits) then lands in a contiguous
+  // block of its output.  Only initial tensors are permuted by kernel (b).
+  const size_t n_steps = net.steps.size();
+  std::vector<int> producer((size_t)n_tensors, -1);
+  for (size_t si = 0; si < n_steps; ++si) producer[(size_t)net.steps[si].out] = (int)si;
+  auto in = [](const std::vector<int> &v, int x) { return std::find(v.begin(), v.end(), x) != v.end(); };
+  auto free_of = [&](const NetStep &st, int id) {
+    std::vector<int> f;
+    for (int x : net.all_legs[(size_t)id])
+      if (!in(st.batch, x) && !in(st.contr, x)) f.push_back(x);
+    return f;
+  };
+  auto map_to = [&](const std::vector<int> &nat, const std::vector<int> &dst, OutMap &om) {
+    const auto en = expand(nat), ed = expand(dst);
+    const int nb = (int)en.size();
+    om = OutMap();
+    om.nbits = nb;
+    bool ident = true;
+    for (int i = 0; i < nb; ++i) {  // flat bit i is expansion entry nb - 1 - i (MSB first)
+      const int j = (int)(std::find(ed.begin(), ed.end(), en[(size_t)(nb - 1 - i)]) - ed.begin());
+      om.pos[i] = (uint8_t)(nb - 1 - j);
+      ident &= om.pos[i] == i;
+    }
+    om.identity = ident ? 1 : 0;
+  };
+  // order legs by their position in a target order
+  auto by_target = [&](std::vector<int> v, const std::vector<int> &tgt) {
+    std::stable_sort(v.begin(), v.end(), [&](int x, int y) {
+      return std::find(tgt.begin(), tgt.end(), x) < std::find(tgt.begin(), tgt.end(), y);
+    });
+    return v;
+  };
+  std::vector<std::vector<int>> target((size_t)n_tensors);
+  net.launches.assign(n_steps, NetLaunch());
+  for (size_t k = n_steps; k-- > 0;) {
+    const NetStep &st = net.steps[k];
+    NetLaunch &L = net.launches[k];
     L.a_id = st.a;
     L.b_id = st.b;
     L.out_id = st.out;
-    const auto &la = net.all_legs[(size_t)st.a], &lb = net.all_legs[(size_t)st.b];
-    std::vector<int> free_a, free_b;
-    auto in = [](const std::vector<int> &v, int x) { return std::find(v.begin(), v.end(), x) != v.end(); };
-    for (int x : la)
-      if (!in(st.batch, x) && !in(st.contr, x)) free_a.push_back(x);
-    for (int x : lb)
-      if (!in(st.batch, x) && !in(st.contr, x)) free_b.push_back(x);
-    std::vector<int> ta = st.batch, tb = st.batch;
+    const std::vector<int> &tgt = target[(size_t)st.out].empty() ? net.all_legs[(size_t)st.out] : target[(size_t)st.out];
+    const std::vector<int> batch = by_target(st.batch, tgt);
+    const std::vector<int> free_a = by_target(free_of(st, st.a), tgt);
+    const std::vector<int> free_b = by_target(free_of(st, st.b), tgt);
+    // contracted legs: those the producer of A (else of B) computes as columns go last
+    std::vector<int> contr = st.contr;
+    int pa = producer[(size_t)st.a] >= 0 ? producer[(size_t)st.a] : producer[(size_t)st.b];
+    if (pa >= 0) {
+      const NetStep &ps = net.steps[(size_t)pa];
+      const std::vector<int> cols = free_of(ps, ps.b);
+      std::stable_partition(contr.begin(), contr.end(), [&](int x) { return !in(cols, x); });
+    }
+    std::vector<int> ta = batch, tb = batch, gemm_out = batch;
     ta.insert(ta.end(), free_a.begin(), free_a.end());
-    ta.insert(ta.end(), st.contr.begin(), st.contr.end());
+    ta.insert(ta.end(), contr.begin(), contr.end());
     tb.insert(tb.end(), free_b.begin(), free_b.end());
-    tb.insert(tb.end(), st.contr.begin(), st.contr.end());
-    perm_to(la, ta, L.perm_a);
-    perm_to(lb, tb, L.perm_b);
-    L.a_bits = bits_of(la);
-    L.b_bits = bits_of(lb);
-    L.batch = 1ll << bits_of(st.batch);
+    tb.insert(tb.end(), contr.begin(), contr.end());
+    gemm_out.insert(gemm_out.end(), free_a.begin(), free_a.end());
+    gemm_out.insert(gemm_out.end(), free_b.begin(), free_b.end());
+    map_to(gemm_out, tgt, L.out_map);
+    for (int side = 0; side < 2; ++side) {
+      const int id = side ? st.b : st.a;
+      const std::vector<int> &want = side ? tb : ta;
+      if (producer[(size_t)id] >= 0) target[(size_t)id] = want;  // its producer stores it this way
+      else perm_to(net.all_legs[(size_t)id], want, side ? L.perm_b : L.perm_a);
+    }
+    L.a_bits = bits_of(net.all_legs[(size_t)st.a]);
+    L.b_bits = bits_of(net.all_legs[(size_t)st.b]);
+    L.batch = 1ll << bits_of(batch);
     L.M = 1ll << bits_of(free_a);
     L.N = 1ll << bits_of(free_b);
-    L.K = 1ll << bits_of(st.contr);
+    L.K = 1ll << bits_of(contr);
     L.precision = tc_ok(precision, L.M, L.N, L.K) ? precision : TN_PREC_FP32;
+  }
+  // workspace, in execution order (operands freed after their merge)
+  for (size_t si = 0; si < n_steps; ++si) {
+    const NetStep &st = net.steps[si];
+    NetLaunch &L = net.launches[si];
     L.off_pa = L.perm_a.empty() ? -1 : (long long)(al.alloc(bytes_of[(size_t)st.a]) / sizeof(float2));
     L.off_pb = L.perm_b.empty() ? -1 : (long long)(al.alloc(bytes_of[(size_t)st.b]) / sizeof(float2));
     L.gemm_ws_bytes = cgemm_workspace(L.precision, L.batch, L.M, L.N, L.K);
@@ -173,17 +229,21 @@ tn_status lower_network(NetPlan &net, int precision, std::string &err) {
     if (L.off_gemm_ws >= 0) al.release((size_t)L.off_gemm_ws, L.gemm_ws_bytes);
     if (net.tensor_off[(size_t)st.a] >= 0) al.release((size_t)net.tensor_off[(size_t)st.a] * sizeof(float2), bytes_of[(size_t)st.a]);
     if (net.tensor_off[(size_t)st.b] >= 0) al.release((size_t)net.tensor_off[(size_t)st.b] * sizeof(float2), bytes_of[(size_t)st.b]);
-    net.launches.push_back(L);
   }
   if (getenv("TNQ_DEBUG_NET")) {  // diagnostic listing of the lowered merges (stderr)
     for (const NetLaunch &L : net.launches) {
-      fprintf(stderr, "merge %d x %d -> %d: batch %lld M %lld N %lld K %lld prec %d perm %d/%d gflop %.3f", L.a_id,
-              L.b_id, L.out_id, L.batch, L.M, L.N, L.K, L.precision, (int)!L.perm_a.empty(), (int)!L.perm_b.empty(),
-              8.0 * L.batch * L.M * L.N * L.K / 1e9);
+      fprintf(stderr, "merge %d x %d -> %d: batch %lld M %lld N %lld K %lld prec %d perm %d/%d map %d gflop %.3f",
+              L.a_id, L.b_id, L.out_id, L.batch, L.M, L.N, L.K, L.precision, (int)!L.perm_a.empty(),
+              (int)!L.perm_b.empty(), (int)!L.out_map.identity, 8.0 * L.batch * L.M * L.N * L.K / 1e9);
       for (const auto *pv : {&L.perm_a, &L.perm_b}) {
         fprintf(stderr, " [");
         for (int v : *pv) fprintf(stderr, "%d ", v);
         fprintf(stderr, "]");
+      }
+      if (!L.out_map.identity) {  // stored bit of each natural bit, LSB first
+        fprintf(stderr, " map{");
+        for (int i = 0; i < L.out_map.nbits; ++i) fprintf(stderr, "%d ", (int)L.out_map.pos[i]);
+        fprintf(stderr, "}");
       }
       fprintf(stderr, "\n");
     }
@@ -269,7 +329,8 @@ cudaError_t run_network(const NetPlan &net, const uint64_t *bitstrings, long lon
       b = w + L.off_pb;
     }
     void *gws = L.off_gemm_ws >= 0 ? static_cast<void *>(static_cast<char *>(ws) + L.off_gemm_ws) : nullptr;
-    cudaError_t e = launch_cgemm(L.precision, L.batch, L.M, L.N, L.K, a, b, w + L.off_out, gws, L.gemm_ws_bytes, s);
+    cudaError_t e =
+        launch_cgemm(L.precision, L.batch, L.M, L.N, L.K, a, b, w + L.off_out, gws, L.gemm_ws_bytes, s, &L.out_map);
     if (e != cudaSuccess) return e;
   }
   return cudaMemcpyAsync(amps, w + net.final_off, sizeof(float2) * (size_t)n_bits, cudaMemcpyDeviceToDevice, s);
