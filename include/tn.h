@@ -135,10 +135,11 @@ typedef struct {
   double flops;         /* algorithmic FP32 flops of one tn_contract_state call (per batch element) */
   int32_t n_bwd_passes; /* passes of the adjoint sweep */
   int32_t specialized;  /* 1 if the forward passes run plan-specialised kernels */
-  int32_t net_merges;   /* TN_PLAN_NETWORK: pairwise merges (each a permute pair + one GEMM) */
+  int32_t net_merges;   /* TN_PLAN_NETWORK: merges launched per call (one batched GEMM each) */
   int32_t net_max_log2; /* TN_PLAN_NETWORK: log2 entries of the largest intermediate */
-  int32_t net_tensor_merges; /* TN_PLAN_NETWORK: merges whose GEMM runs on the tensor cores */
-  int32_t reserved[3];
+  int32_t net_tensor_merges; /* TN_PLAN_NETWORK: launched merges whose GEMM runs on the tensor cores */
+  int32_t net_folded_merges; /* TN_PLAN_NETWORK: bitstring-independent merges evaluated at plan time (FP64) */
+  int32_t reserved[2];
 } tn_plan_stats;
 
 /* Pauli sum H = sum_t coef[t] * P_t (host memory, read during tn_build_observable only).

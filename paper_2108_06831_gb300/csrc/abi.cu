@@ -389,7 +389,8 @@ tn_status tn_plan_get_stats(const tn_plan *p, tn_plan_stats *st) {
   st->specialized = p->jit_kernels.empty() ? 0 : 1;
   if (p->net) {
     st->n_passes = 0;
-    st->net_merges = (int)p->net->steps.size();
+    st->net_merges = (int)p->net->launches.size();
+    st->net_folded_merges = p->net->folded_merges;
     st->net_max_log2 = p->net->max_log2;
     st->flops = p->net->flops;
     int tc = 0;

@@ -26,20 +26,22 @@ struct NetStep {
   std::vector<int> batch, contr, out_legs;
 };
 
-// Lowered step: permutations of initial operands, one batched complex GEMM whose output is
-// written in the leg order its consumer reads (out_map; identity for the last merge).
+// Launched merge: one batched complex GEMM whose operands are already laid out as it reads
+// them and whose output is written in the leg order its consumer reads (out_map; identity
+// for the last merge).
 struct NetLaunch {
-  int a_id, b_id, out_id;
-  int a_bits, b_bits;                  // binary legs of the operands
-  std::vector<int> perm_a, perm_b;     // tn_permute permutations (empty: already in place)
-  long long batch, M, N, K;
-  long long off_a, off_b, off_out;     // workspace offsets (complex64) of operands / result
-  long long off_pa, off_pb;            // scratch for the permuted operands (-1: not needed)
-  long long off_gemm_ws;               // bytes offset of the GEMM split workspace (-1: none)
-  size_t gemm_ws_bytes;
-  int precision;                       // tn_precision used for this merge
-  OutMap out_map;                      // natural [batch][M][N] index -> stored index
+  int a_id = -1, b_id = -1, out_id = -1;
+  long long batch = 1, M = 1, N = 1, K = 1;
+  long long off_out = -1;        // workspace offset (complex64) of the result
+  long long off_gemm_ws = -1;    // bytes offset of the GEMM split workspace (-1: none)
+  size_t gemm_ws_bytes = 0;
+  int precision = TN_PREC_FP32;  // tn_precision used for this merge
+  OutMap out_map;                // natural [batch][M][N] index -> stored index
 };
+
+// Constant folding budget (merges of bitstring-independent tensors evaluated at plan time).
+constexpr int kFoldMaxLog2 = 20;       // largest folded result: 2^20 entries
+constexpr double kFoldMaxWork = 2e8;   // complex multiply-adds over all folded merges
 
 struct NetPlan {
   int n = 0;
@@ -51,10 +53,12 @@ struct NetPlan {
   int max_log2 = 0;
   double flops = 0;  // 8 M N K summed over merges
   // lowering
-  std::vector<NetLaunch> launches;
-  std::vector<long long> tensor_off;  // workspace offset (complex64) of every tensor id; -1 = plan table
-  long long fixed_elems = 0;          // complex64 entries of the fixed node table
-  std::vector<long long> fixed_off;   // offset of each fixed node in that table
+  std::vector<NetLaunch> launches;    // launched (bitstring-dependent) merges, in order
+  int folded_merges = 0;              // merges evaluated at plan time
+  std::vector<long long> tensor_off;  // workspace offset (complex64) of every tensor id, -1 if none
+  std::vector<long long> table_off;   // offset in the static table (complex64), -1 if not there
+  std::vector<std::complex<double>> table_host;  // static operands of launched merges, as read
+  std::vector<char> closure_trans;    // output closure stored [leg][b]
   size_t ws_bytes = 0;
   long long final_off = 0;
   // device copies

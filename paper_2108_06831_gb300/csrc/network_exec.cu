@@ -7,6 +7,7 @@
 #include <map>
 #include <utility>
 #include <vector>
+#include <complex>
 
 #include "kernels.h"
 #include "network.h"
@@ -20,6 +21,8 @@ struct OutDesc {  // one output closure on the device
   long long off;  // complex64 offset in the workspace
   int qubit;
   int has_leg;
+  int trans;      // stored [leg][b] instead of [b][leg] (the order its merge reads)
+  int pad;
 };
 
 // u_q^b[i] = rows[2 x_q^b + i] (or the scalar rows[2 x_q^b]); padded bitstrings get zeros.
@@ -35,7 +38,8 @@ __global__ void k_build_outputs(const OutDesc *__restrict__ outs, int n_out, con
     if (d.has_leg) {
       for (int k = 0; k < 2; ++k) {
         const int r = 2 * x + k;
-        ws[d.off + 2 * b + k] = pad ? make_float2(0.f, 0.f) : make_float2(d.rows[2 * r], d.rows[2 * r + 1]);
+        ws[d.off + (d.trans ? k * B + b : 2 * b + k)] =
+            pad ? make_float2(0.f, 0.f) : make_float2(d.rows[2 * r], d.rows[2 * r + 1]);
       }
     } else {
       const int r = 2 * x;
@@ -86,9 +90,67 @@ bool tc_ok(int precision, long long M, long long N, long long K) {
 
 }  // namespace
 
+// Tensor of a folded merge, on the host in FP64: out (legs lo) = sum over contr of A (legs
+// la) x B (legs lb); every leg binary, first leg most significant.
+std::vector<std::complex<double>> contract_host(const std::vector<int> &la, const std::vector<std::complex<double>> &A,
+                                                const std::vector<int> &lb, const std::vector<std::complex<double>> &B,
+                                                const std::vector<int> &contr, const std::vector<int> &lo) {
+  auto stride = [](const std::vector<int> &ls, int x) -> long long {
+    for (size_t p = 0; p < ls.size(); ++p)
+      if (ls[p] == x) return 1ll << (ls.size() - 1 - p);
+    return 0;
+  };
+  const int no = (int)lo.size(), nc = (int)contr.size();
+  std::vector<long long> ca(1ull << nc, 0), cb(1ull << nc, 0);
+  for (long long c = 0; c < (1ll << nc); ++c)
+    for (int p = 0; p < nc; ++p)
+      if ((c >> (nc - 1 - p)) & 1) {
+        ca[(size_t)c] += stride(la, contr[(size_t)p]);
+        cb[(size_t)c] += stride(lb, contr[(size_t)p]);
+      }
+  std::vector<long long> sa((size_t)no), sb((size_t)no);
+  for (int p = 0; p < no; ++p) {
+    sa[(size_t)p] = stride(la, lo[(size_t)p]);
+    sb[(size_t)p] = stride(lb, lo[(size_t)p]);
+  }
+  std::vector<std::complex<double>> out(1ull << no);
+  for (long long o = 0; o < (1ll << no); ++o) {
+    long long ao = 0, bo = 0;
+    for (int p = 0; p < no; ++p)
+      if ((o >> (no - 1 - p)) & 1) {
+        ao += sa[(size_t)p];
+        bo += sb[(size_t)p];
+      }
+    std::complex<double> acc = 0;
+    for (long long c = 0; c < (1ll << nc); ++c) acc += A[(size_t)(ao + ca[(size_t)c])] * B[(size_t)(bo + cb[(size_t)c])];
+    out[(size_t)o] = acc;
+  }
+  return out;
+}
+
+// The same tensor with its legs reordered from `from` to `to` (binary legs).
+std::vector<std::complex<double>> reorder_host(const std::vector<std::complex<double>> &x, const std::vector<int> &from,
+                                               const std::vector<int> &to) {
+  const int n = (int)from.size();
+  std::vector<long long> st((size_t)n);  // stride in `from` of the leg at position p of `to`
+  for (int p = 0; p < n; ++p) {
+    const int q = (int)(std::find(from.begin(), from.end(), to[(size_t)p]) - from.begin());
+    st[(size_t)p] = 1ll << (n - 1 - q);
+  }
+  std::vector<std::complex<double>> y(x.size());
+  for (long long o = 0; o < (1ll << n); ++o) {
+    long long i = 0;
+    for (int p = 0; p < n; ++p)
+      if ((o >> (n - 1 - p)) & 1) i += st[(size_t)p];
+    y[(size_t)o] = x[(size_t)i];
+  }
+  return y;
+}
+
 tn_status lower_network(NetPlan &net, int precision, std::string &err) {
   const int n_init = (int)net.nodes.size();
-  const int n_tensors = n_init + (int)net.steps.size();
+  const size_t n_steps = net.steps.size();
+  const int n_tensors = n_init + (int)n_steps;
   auto bits_of = [&](const std::vector<int> &ls) {
     int b = 0;
     for (int x : ls) b += net.label_dim[(size_t)x];
@@ -101,47 +163,44 @@ tn_status lower_network(NetPlan &net, int precision, std::string &err) {
       for (int k = 0; k < net.label_dim[(size_t)x]; ++k) e.push_back({x, k});
     return e;
   };
-  auto perm_to = [&](const std::vector<int> &src, const std::vector<int> &dst, std::vector<int> &perm) {
-    const auto es = expand(src), ed = expand(dst);
-    perm.assign(ed.size(), 0);
-    bool ident = true;
-    for (size_t j = 0; j < ed.size(); ++j) {
-      const auto it = std::find(es.begin(), es.end(), ed[j]);
-      perm[j] = (int)(it - es.begin());
-      ident &= perm[j] == (int)j;
-    }
-    if (ident) perm.clear();
-  };
-  net.tensor_off.assign((size_t)n_tensors, -1);
-  Allocator al;
-  size_t hw = 0;  // high-water mark of the workspace
-  std::vector<size_t> bytes_of((size_t)n_tensors, 0);
-  for (int id = 0; id < n_tensors; ++id) bytes_of[(size_t)id] = (sizeof(float2) << bits_of(net.all_legs[(size_t)id]));
-  // fixed nodes live in the plan's table, output closures in the workspace
-  net.fixed_off.assign((size_t)n_init, -1);
-  net.fixed_elems = 0;
-  for (int id = 0; id < n_init; ++id) {
-    const NetNode &nd = net.nodes[(size_t)id];
-    if (nd.kind == NODE_FIXED) {
-      net.fixed_off[(size_t)id] = net.fixed_elems;
-      net.fixed_elems += ((long long)1 << bits_of(nd.legs));
-      net.fixed_elems = (net.fixed_elems + 31) & ~31ll;
-    } else {
-      net.tensor_off[(size_t)id] = (long long)(al.alloc(bytes_of[(size_t)id]) / sizeof(float2));
-      hw = std::max(hw, al.top);
-    }
-  }
-  // Layouts, decided from the last merge back to the first.  Every intermediate has one
-  // consumer, which fixes the leg order it reads ([batch][free][contracted]); the producing
-  // merge then orders its own batch, row (M) and column (N) legs as they appear in that
-  // target, so that its GEMM's output map is monotone within each group, and stores the
-  // result directly in the target order (the permutation fused into the GEMM epilogue).
-  // Within the contracted group, legs that the operand's producer computes as columns come
-  // last: a producer tile (all N bits and the lowest 7 M bits) then lands in a contiguous
-  // block of its output.  Only initial tensors are permuted by kernel (b).
-  const size_t n_steps = net.steps.size();
   std::vector<int> producer((size_t)n_tensors, -1);
   for (size_t si = 0; si < n_steps; ++si) producer[(size_t)net.steps[si].out] = (int)si;
+
+  // 1. Constant folding.  A tensor that does not depend on the bitstrings (the gate tensors
+  // and every merge of two such tensors) is the same for every call: those merges are
+  // evaluated once here, in FP64, within a size and work budget.
+  std::vector<char> is_static((size_t)n_tensors, 0), folded(n_steps, 0);
+  for (int id = 0; id < n_init; ++id) is_static[(size_t)id] = net.nodes[(size_t)id].kind == NODE_FIXED;
+  std::vector<std::vector<std::complex<double>>> sdata((size_t)n_tensors);
+  for (int id = 0; id < n_init; ++id)
+    if (is_static[(size_t)id]) sdata[(size_t)id] = net.nodes[(size_t)id].data;
+  double fold_work = 0;
+  net.folded_merges = 0;
+  for (size_t si = 0; si < n_steps; ++si) {
+    const NetStep &st = net.steps[si];
+    if (!is_static[(size_t)st.a] || !is_static[(size_t)st.b]) continue;
+    const int ob = bits_of(net.all_legs[(size_t)st.out]), cb = bits_of(st.contr);
+    const double work = std::ldexp(1.0, ob + cb);
+    if (ob > kFoldMaxLog2 || fold_work + work > kFoldMaxWork) continue;
+    fold_work += work;
+    sdata[(size_t)st.out] = contract_host(net.all_legs[(size_t)st.a], sdata[(size_t)st.a], net.all_legs[(size_t)st.b],
+                                          sdata[(size_t)st.b], st.contr, net.all_legs[(size_t)st.out]);
+    sdata[(size_t)st.a].clear();
+    sdata[(size_t)st.b].clear();
+    is_static[(size_t)st.out] = 1;
+    folded[si] = 1;
+    ++net.folded_merges;
+  }
+
+  // 2. Layouts of the launched merges, from the last back to the first.  Every tensor has one
+  // consumer, which fixes the leg order it reads ([batch][free][contracted]):
+  //   - a launched merge's result is stored in that order by its own GEMM (output map); the
+  //     producing merge orders its batch, row (M) and column (N) legs as they appear in the
+  //     target, so the map is monotone within each group;
+  //   - a static tensor is laid out in that order on the host before upload;
+  //   - an output closure [b][leg] is built in either order by the closure kernel.
+  // Within the contracted group, legs that the operand's producer computes as columns go
+  // last: a producer tile (its N bits and 7 lowest M bits) then lands in few contiguous runs.
   auto in = [](const std::vector<int> &v, int x) { return std::find(v.begin(), v.end(), x) != v.end(); };
   auto free_of = [&](const NetStep &st, int id) {
     std::vector<int> f;
@@ -162,7 +221,6 @@ tn_status lower_network(NetPlan &net, int precision, std::string &err) {
     }
     om.identity = ident ? 1 : 0;
   };
-  // order legs by their position in a target order
   auto by_target = [&](std::vector<int> v, const std::vector<int> &tgt) {
     std::stable_sort(v.begin(), v.end(), [&](int x, int y) {
       return std::find(tgt.begin(), tgt.end(), x) < std::find(tgt.begin(), tgt.end(), y);
@@ -170,10 +228,16 @@ tn_status lower_network(NetPlan &net, int precision, std::string &err) {
     return v;
   };
   std::vector<std::vector<int>> target((size_t)n_tensors);
-  net.launches.assign(n_steps, NetLaunch());
+  std::vector<int> launch_of(n_steps, -1);
+  int n_launch = 0;
+  for (size_t si = 0; si < n_steps; ++si)
+    if (!folded[si]) launch_of[si] = n_launch++;
+  net.launches.assign((size_t)n_launch, NetLaunch());
+  std::vector<char> closure_trans((size_t)n_tensors, 0);
   for (size_t k = n_steps; k-- > 0;) {
+    if (folded[k]) continue;
     const NetStep &st = net.steps[k];
-    NetLaunch &L = net.launches[k];
+    NetLaunch &L = net.launches[(size_t)launch_of[k]];
     L.a_id = st.a;
     L.b_id = st.b;
     L.out_id = st.out;
@@ -181,9 +245,9 @@ tn_status lower_network(NetPlan &net, int precision, std::string &err) {
     const std::vector<int> batch = by_target(st.batch, tgt);
     const std::vector<int> free_a = by_target(free_of(st, st.a), tgt);
     const std::vector<int> free_b = by_target(free_of(st, st.b), tgt);
-    // contracted legs: those the producer of A (else of B) computes as columns go last
     std::vector<int> contr = st.contr;
-    int pa = producer[(size_t)st.a] >= 0 ? producer[(size_t)st.a] : producer[(size_t)st.b];
+    int pa = producer[(size_t)st.a] >= 0 && !folded[(size_t)producer[(size_t)st.a]] ? producer[(size_t)st.a] : -1;
+    if (pa < 0 && producer[(size_t)st.b] >= 0 && !folded[(size_t)producer[(size_t)st.b]]) pa = producer[(size_t)st.b];
     if (pa >= 0) {
       const NetStep &ps = net.steps[(size_t)pa];
       const std::vector<int> cols = free_of(ps, ps.b);
@@ -199,47 +263,60 @@ tn_status lower_network(NetPlan &net, int precision, std::string &err) {
     map_to(gemm_out, tgt, L.out_map);
     for (int side = 0; side < 2; ++side) {
       const int id = side ? st.b : st.a;
-      const std::vector<int> &want = side ? tb : ta;
-      if (producer[(size_t)id] >= 0) target[(size_t)id] = want;  // its producer stores it this way
-      else perm_to(net.all_legs[(size_t)id], want, side ? L.perm_b : L.perm_a);
+      target[(size_t)id] = side ? tb : ta;
+      if (id < n_init && !is_static[(size_t)id]) {  // output closure: [b][leg] or [leg][b]
+        const std::vector<int> &w = target[(size_t)id];
+        closure_trans[(size_t)id] = w.size() == 2 && w[0] != 0;
+      }
     }
-    L.a_bits = bits_of(net.all_legs[(size_t)st.a]);
-    L.b_bits = bits_of(net.all_legs[(size_t)st.b]);
     L.batch = 1ll << bits_of(batch);
     L.M = 1ll << bits_of(free_a);
     L.N = 1ll << bits_of(free_b);
     L.K = 1ll << bits_of(contr);
     L.precision = tc_ok(precision, L.M, L.N, L.K) ? precision : TN_PREC_FP32;
   }
-  // workspace, in execution order (operands freed after their merge)
-  for (size_t si = 0; si < n_steps; ++si) {
-    const NetStep &st = net.steps[si];
-    NetLaunch &L = net.launches[si];
-    L.off_pa = L.perm_a.empty() ? -1 : (long long)(al.alloc(bytes_of[(size_t)st.a]) / sizeof(float2));
-    L.off_pb = L.perm_b.empty() ? -1 : (long long)(al.alloc(bytes_of[(size_t)st.b]) / sizeof(float2));
+
+  // 3. The table of static operands of launched merges, each in the order its merge reads.
+  net.table_off.assign((size_t)n_tensors, -1);
+  net.table_host.clear();
+  for (const NetLaunch &L : net.launches)
+    for (int id : {L.a_id, L.b_id}) {
+      if (!is_static[(size_t)id]) continue;
+      const std::vector<std::complex<double>> d =
+          reorder_host(sdata[(size_t)id], net.all_legs[(size_t)id], target[(size_t)id]);
+      net.table_off[(size_t)id] = (long long)net.table_host.size();
+      net.table_host.insert(net.table_host.end(), d.begin(), d.end());
+      net.table_host.resize((net.table_host.size() + 31) & ~(size_t)31);  // 256-byte alignment
+    }
+
+  // 4. Workspace, in execution order: output closures, then every launched result (operands
+  // freed after their merge).
+  net.tensor_off.assign((size_t)n_tensors, -1);
+  net.closure_trans.assign(closure_trans.begin(), closure_trans.end());
+  Allocator al;
+  size_t hw = 0;
+  auto bytes_of = [&](int id) { return sizeof(float2) << bits_of(net.all_legs[(size_t)id]); };
+  for (int id = 0; id < n_init; ++id)
+    if (!is_static[(size_t)id]) {
+      net.tensor_off[(size_t)id] = (long long)(al.alloc(bytes_of(id)) / sizeof(float2));
+      hw = std::max(hw, al.top);
+    }
+  for (NetLaunch &L : net.launches) {
     L.gemm_ws_bytes = cgemm_workspace(L.precision, L.batch, L.M, L.N, L.K);
     L.off_gemm_ws = L.gemm_ws_bytes ? (long long)al.alloc(L.gemm_ws_bytes) : -1;
-    net.tensor_off[(size_t)st.out] = (long long)(al.alloc(bytes_of[(size_t)st.out]) / sizeof(float2));
-    L.off_out = net.tensor_off[(size_t)st.out];
+    net.tensor_off[(size_t)L.out_id] = (long long)(al.alloc(bytes_of(L.out_id)) / sizeof(float2));
+    L.off_out = net.tensor_off[(size_t)L.out_id];
     hw = std::max(hw, al.top);
-    L.off_a = net.tensor_off[(size_t)st.a];
-    L.off_b = net.tensor_off[(size_t)st.b];
-    if (L.off_pa >= 0) al.release((size_t)L.off_pa * sizeof(float2), bytes_of[(size_t)st.a]);
-    if (L.off_pb >= 0) al.release((size_t)L.off_pb * sizeof(float2), bytes_of[(size_t)st.b]);
     if (L.off_gemm_ws >= 0) al.release((size_t)L.off_gemm_ws, L.gemm_ws_bytes);
-    if (net.tensor_off[(size_t)st.a] >= 0) al.release((size_t)net.tensor_off[(size_t)st.a] * sizeof(float2), bytes_of[(size_t)st.a]);
-    if (net.tensor_off[(size_t)st.b] >= 0) al.release((size_t)net.tensor_off[(size_t)st.b] * sizeof(float2), bytes_of[(size_t)st.b]);
+    for (int id : {L.a_id, L.b_id})
+      if (net.tensor_off[(size_t)id] >= 0) al.release((size_t)net.tensor_off[(size_t)id] * sizeof(float2), bytes_of(id));
   }
   if (getenv("TNQ_DEBUG_NET")) {  // diagnostic listing of the lowered merges (stderr)
+    fprintf(stderr, "folded %d of %zu merges\n", net.folded_merges, n_steps);
     for (const NetLaunch &L : net.launches) {
-      fprintf(stderr, "merge %d x %d -> %d: batch %lld M %lld N %lld K %lld prec %d perm %d/%d map %d gflop %.3f",
-              L.a_id, L.b_id, L.out_id, L.batch, L.M, L.N, L.K, L.precision, (int)!L.perm_a.empty(),
-              (int)!L.perm_b.empty(), (int)!L.out_map.identity, 8.0 * L.batch * L.M * L.N * L.K / 1e9);
-      for (const auto *pv : {&L.perm_a, &L.perm_b}) {
-        fprintf(stderr, " [");
-        for (int v : *pv) fprintf(stderr, "%d ", v);
-        fprintf(stderr, "]");
-      }
+      fprintf(stderr, "merge %d x %d -> %d: batch %lld M %lld N %lld K %lld prec %d static %d/%d map %d gflop %.3f",
+              L.a_id, L.b_id, L.out_id, L.batch, L.M, L.N, L.K, L.precision, (int)is_static[(size_t)L.a_id],
+              (int)is_static[(size_t)L.b_id], (int)!L.out_map.identity, 8.0 * L.batch * L.M * L.N * L.K / 1e9);
       if (!L.out_map.identity) {  // stored bit of each natural bit, LSB first
         fprintf(stderr, " map{");
         for (int i = 0; i < L.out_map.nbits; ++i) fprintf(stderr, "%d ", (int)L.out_map.pos[i]);
@@ -248,40 +325,39 @@ tn_status lower_network(NetPlan &net, int precision, std::string &err) {
       fprintf(stderr, "\n");
     }
   }
-  const int last = net.steps.empty() ? 0 : net.steps.back().out;
-  if (net.all_legs[(size_t)last].size() != 1 || net.all_legs[(size_t)last][0] != 0) {
+  if (net.launches.empty() || net.all_legs[(size_t)net.launches.back().out_id].size() != 1 ||
+      net.all_legs[(size_t)net.launches.back().out_id][0] != 0) {
     err = "network contraction did not end in the bitstring index alone";
     return TN_ERR_UNSUPPORTED;
   }
-  net.final_off = net.tensor_off[(size_t)last];
+  net.final_off = net.tensor_off[(size_t)net.launches.back().out_id];
   net.ws_bytes = hw + 256;
   return TN_OK;
 }
 
 tn_status upload_network(NetPlan &net, std::string &err) {
-  std::vector<float2> fixed((size_t)std::max<long long>(net.fixed_elems, 1), make_float2(0.f, 0.f));
+  std::vector<float2> table(std::max<size_t>(net.table_host.size(), 1), make_float2(0.f, 0.f));
+  for (size_t k = 0; k < net.table_host.size(); ++k)
+    table[k] = make_float2((float)net.table_host[k].real(), (float)net.table_host[k].imag());
   std::vector<OutDesc> outs;
   for (size_t id = 0; id < net.nodes.size(); ++id) {
     const NetNode &nd = net.nodes[id];
-    if (nd.kind == NODE_FIXED) {
-      for (size_t k = 0; k < nd.data.size(); ++k)
-        fixed[(size_t)net.fixed_off[id] + k] = make_float2((float)nd.data[k].real(), (float)nd.data[k].imag());
-    } else {
-      OutDesc d;
-      std::memset(&d, 0, sizeof(d));
-      for (int k = 0; k < 4; ++k) {
-        d.rows[2 * k] = (float)nd.rows[(size_t)k].real();
-        d.rows[2 * k + 1] = (float)nd.rows[(size_t)k].imag();
-      }
-      d.off = net.tensor_off[id];
-      d.qubit = nd.qubit;
-      d.has_leg = nd.legs.size() == 2 ? 1 : 0;
-      outs.push_back(d);
+    if (nd.kind == NODE_FIXED || net.tensor_off[id] < 0) continue;
+    OutDesc d;
+    std::memset(&d, 0, sizeof(d));
+    for (int k = 0; k < 4; ++k) {
+      d.rows[2 * k] = (float)nd.rows[(size_t)k].real();
+      d.rows[2 * k + 1] = (float)nd.rows[(size_t)k].imag();
     }
+    d.off = net.tensor_off[id];
+    d.qubit = nd.qubit;
+    d.has_leg = nd.legs.size() == 2 ? 1 : 0;
+    d.trans = net.closure_trans[id] ? 1 : 0;
+    outs.push_back(d);
   }
   net.n_outputs = (int)outs.size();
-  cudaError_t e = cudaMalloc(&net.d_fixed, fixed.size() * sizeof(float2));
-  if (e == cudaSuccess) e = cudaMemcpy(net.d_fixed, fixed.data(), fixed.size() * sizeof(float2), cudaMemcpyHostToDevice);
+  cudaError_t e = cudaMalloc(&net.d_fixed, table.size() * sizeof(float2));
+  if (e == cudaSuccess) e = cudaMemcpy(net.d_fixed, table.data(), table.size() * sizeof(float2), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMalloc(&net.d_outputs, std::max<size_t>(outs.size(), 1) * sizeof(OutDesc));
   if (e == cudaSuccess && !outs.empty())
     e = cudaMemcpy(net.d_outputs, outs.data(), outs.size() * sizeof(OutDesc), cudaMemcpyHostToDevice);
@@ -311,26 +387,14 @@ cudaError_t run_network(const NetPlan &net, const uint64_t *bitstrings, long lon
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
-  const int n_init = (int)net.nodes.size();
   auto ptr = [&](int id) -> const float2 * {
-    if (id < n_init && net.nodes[(size_t)id].kind == NODE_FIXED) return fixed + net.fixed_off[(size_t)id];
+    if (net.table_off[(size_t)id] >= 0) return fixed + net.table_off[(size_t)id];
     return w + net.tensor_off[(size_t)id];
   };
   for (const NetLaunch &L : net.launches) {
-    const float2 *a = ptr(L.a_id), *b = ptr(L.b_id);
-    if (!L.perm_a.empty()) {
-      cudaError_t e = launch_permute(L.a_bits, L.perm_a.data(), 1, a, w + L.off_pa, s);
-      if (e != cudaSuccess) return e;
-      a = w + L.off_pa;
-    }
-    if (!L.perm_b.empty()) {
-      cudaError_t e = launch_permute(L.b_bits, L.perm_b.data(), 1, b, w + L.off_pb, s);
-      if (e != cudaSuccess) return e;
-      b = w + L.off_pb;
-    }
     void *gws = L.off_gemm_ws >= 0 ? static_cast<void *>(static_cast<char *>(ws) + L.off_gemm_ws) : nullptr;
-    cudaError_t e =
-        launch_cgemm(L.precision, L.batch, L.M, L.N, L.K, a, b, w + L.off_out, gws, L.gemm_ws_bytes, s, &L.out_map);
+    cudaError_t e = launch_cgemm(L.precision, L.batch, L.M, L.N, L.K, ptr(L.a_id), ptr(L.b_id), w + L.off_out, gws,
+                                 L.gemm_ws_bytes, s, &L.out_map);
     if (e != cudaSuccess) return e;
   }
   return cudaMemcpyAsync(amps, w + net.final_off, sizeof(float2) * (size_t)n_bits, cudaMemcpyDeviceToDevice, s);
