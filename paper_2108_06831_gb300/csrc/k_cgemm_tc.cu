@@ -588,8 +588,6 @@ __global__ void __launch_bounds__(kStreamThreads, 1)
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       int nt, mt, bz;
       decode(t, nt, mt, bz);
-      const long long row = (long long)mt * BM + q * 32 + lane;
-      float *crow = C + ((long long)bz * M + row) * N2 + (long long)nt * BN;
       const long long row0 = (long long)bz * M + (long long)mt * BM + q * 32;  // the warp's first row
       const uint32_t base = tmem_d + ((uint32_t)(q * 32) << 16) + (uint32_t)(ab * 2 * BN);
       float2 *stg = stage_c[q];
@@ -602,9 +600,20 @@ __global__ void __launch_bounds__(kStreamThreads, 1)
 #pragma unroll
         for (int k = 0; k < 32; ++k) v[k] = __uint_as_float(e[k]) + __uint_as_float(r[k]);
         if (om.identity) {
-          float4 *dst = reinterpret_cast<float4 *>(crow + c);
+          // row-major: stage, then 8 lanes write each row's 128 bytes (4 rows per store)
 #pragma unroll
-          for (int k = 0; k < 8; ++k) dst[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+          for (int k = 0; k < 16; ++k) stg[lane * kStgStride + k] = make_float2(v[2 * k], v[2 * k + 1]);
+          __syncwarp();
+          const float *cbase = C + ((long long)row0 * N2 + (long long)nt * BN + c);
+#pragma unroll
+          for (int it = 0; it < 8; ++it) {
+            const int pr = it * 32 + lane;  // pair index: row pr / 8, complex pair pr % 8
+            const int rr = pr >> 3, cc = 2 * (pr & 7);
+            const float2 x0 = stg[rr * kStgStride + cc], x1 = stg[rr * kStgStride + cc + 1];
+            *reinterpret_cast<float4 *>(const_cast<float *>(cbase) + (long long)rr * N2 + 2 * cc) =
+                make_float4(x0.x, x0.y, x1.x, x1.y);
+          }
+          __syncwarp();
           continue;
         }
         // stored offset of everything but the chunk's local bits (lane row bits, 4 column bits)
