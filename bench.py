@@ -53,25 +53,28 @@ def parse():
     return ap.parse_args()
 
 
-def recorded_traffic():
-    """DRAM bytes per launch of the gate-apply pass kernels from the committed ncu summary,
-    or None when the kernel generator has changed since that capture."""
-    import hashlib
+def recorded_traffic(kernel_hash):
+    """DRAM bytes per launch of the gate-apply pass kernels from the committed ncu summary, or
+    None unless the generated kernel sources hash to the value recorded with that capture."""
     import re
-    srcs = ["paper_2108_06831_gb300/csrc/jit.cpp", "paper_2108_06831_gb300/csrc/plan.cpp",
-            "paper_2108_06831_gb300/csrc/tnq_internal.h"]
     try:
-        h = hashlib.sha256()
-        for f in srcs:
-            with open(os.path.join(ROOT, f), "rb") as fh:
-                h.update(fh.read())
         with open(os.path.join(ROOT, "profiles", "fused_gate_apply_state24.md")) as fh:
-            m = re.search(r"traffic_bytes_per_launch=(\d+) source_hash=([0-9a-f]+)", fh.read())
-        if m and m.group(2) == h.hexdigest()[:16]:
+            m = re.search(r"traffic_bytes_per_launch=(\d+) kernel_hash=([0-9a-f]+)", fh.read())
+        if m and m.group(2) == kernel_hash:
             return float(m.group(1))
     except OSError:
         pass
     return None
+
+
+def jit_source_hash(dump_dir):
+    """sha256 (16 hex digits) of the generated kernel sources written to dump_dir."""
+    import hashlib
+    h = hashlib.sha256()
+    for name in sorted(os.listdir(dump_dir)):
+        with open(os.path.join(dump_dir, name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
 def load_peaks():
@@ -291,7 +294,14 @@ def main():
         def step():
             tn.contract_state(ctr.plan, p_dev, out, ctr.workspace)
         launches_per_step = 1 + ctr.plan.stats()["n_passes"]
+        import tempfile
+        dump = tempfile.mkdtemp(prefix="tnq_src_")
+        os.environ["TNQ_JIT_DUMP_DIR"] = dump  # the timed plan's generated sources, hashed below
         fixed = tn.Contractor(circ_f, batch=batch, tile_qubits=args.tile, device=dev, specialize=spec)
+        del os.environ["TNQ_JIT_DUMP_DIR"]
+        kernel_hash = jit_source_hash(dump)
+        import shutil
+        shutil.rmtree(dump, ignore_errors=True)
         fst = fixed.plan.stats()
 
         def kernel_only():
@@ -412,6 +422,10 @@ def main():
         launches_per_step = None
         kernel_only = None
 
+        def backward_only():  # forward recompute + H psi + adjoint sweep (the adjoint kernels dominate)
+            tn.expectation_backward(ctr.plan, obs, p_dev, None, g_out, ctr.workspace)
+        bwd_alg_flops = (st["flops"] + st["bwd_flops"]) * batch
+
     def timed(fn, k):
         times = []
         for _ in range(k):
@@ -482,7 +496,8 @@ def main():
                                 "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})",
                                 "also": {"tflops": tfl, "alu_frac": alu_frac}}
         if args.workload == "state24" and not args.tile and not args.no_specialize:
-            line["roofline"]["traffic"] = recorded_traffic()
+            line["roofline"]["traffic"] = recorded_traffic(kernel_hash)
+            line["roofline"]["kernel_source_hash"] = kernel_hash
         line["roofline"]["launches_per_step"] = kernel_launches
         line["roofline"]["avg_launch_ms"] = avg_launch_ms
 
@@ -565,6 +580,17 @@ def main():
                             "flops_per_s_all_merges": nst["flops"] * (batch // wl["chunk"]) / per_step_s}
         # Porter-Thomas check of the amplitudes: mean |a|^2 2^36 should be near 1
         line["porter_thomas_mean"] = float(np.mean(np.abs(a) ** 2) * 2.0 ** 36)
+    if wl["kind"] == "grad":
+        for _ in range(3):
+            backward_only()
+        bms = statistics.mean(timed(backward_only, args.steps))
+        tfl = bwd_alg_flops / (bms / 1000.0) / 1e12
+        line["roofline"] = {"bound": "alu", "achieved": tfl, "peak": FP32_ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
+                            "frac": tfl / FP32_ALU_PEAK_TFLOPS, "traffic": None,
+                            "kernel": "tn_expectation_backward: forward recompute (tnq_p*) + H psi + adjoint sweep "
+                                      "(tnq_b*, every op on psi and lambda plus derivative dots)",
+                            "avg_call_ms": bms, "algorithmic_flops_per_call": bwd_alg_flops,
+                            "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 x 2070 MHz"}
     if wl["kind"] == "serve":
         for _ in range(2):
             seq_step()
@@ -576,6 +602,13 @@ def main():
         line["sequential"] = {"value": units_per_step / (statistics.mean(sms) / 1000.0), "unit": unit,
                               "ms_per_step": statistics.mean(sms),
                               "what": "the same circuits contracted one after another (tn_contract_state each)"}
+        # the persistent executor (the step's one kernel) against the FP32 ALU roof: algorithmic
+        # flops of every circuit's gates
+        alg = sum(p.stats()["flops"] for p in plans)
+        tfl = alg / (t_max / args.steps / 1000.0) / 1e12
+        line["roofline"] = {"bound": "alu", "achieved": tfl, "peak": FP32_ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
+                            "frac": tfl / FP32_ALU_PEAK_TFLOPS, "traffic": None, "kernel": "k_batch_exec",
+                            "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 x 2070 MHz"}
     if wl["kind"] == "permute":
         per_step_s = t_max / args.steps / 1000.0
         ach = units_per_step / per_step_s

@@ -139,7 +139,8 @@ typedef struct {
   int32_t net_max_log2; /* TN_PLAN_NETWORK: log2 entries of the largest intermediate */
   int32_t net_tensor_merges; /* TN_PLAN_NETWORK: launched merges whose GEMM runs on the tensor cores */
   int32_t net_folded_merges; /* TN_PLAN_NETWORK: bitstring-independent merges evaluated at plan time (FP64) */
-  int32_t reserved[2];
+  double bwd_flops;     /* TN_TARGET_EXPECTATION: algorithmic FP32 flops of the adjoint sweep per batch element
+                           (every op on psi and lambda, derivative products and dots) */
 } tn_plan_stats;
 
 /* Pauli sum H = sum_t coef[t] * P_t (host memory, read during tn_build_observable only).

@@ -386,6 +386,7 @@ tn_status tn_plan_get_stats(const tn_plan *p, tn_plan_stats *st) {
   for (const PassDesc &pd : p->fwd.passes) bytes += (pd.init_mode ? 8.0 : 16.0) * (double)(1ull << p->n);
   st->hbm_bytes = bytes;
   st->n_bwd_passes = (int)p->bwd.passes.size();
+  st->bwd_flops = 2.0 * p->bwd.flops + p->bwd.grad_flops;
   st->specialized = p->jit_kernels.empty() ? 0 : 1;
   if (p->net) {
     st->n_passes = 0;

@@ -436,6 +436,9 @@ tn_status build_pass_plan(const tn_circuit &c, int T, int K, bool adjoint, std::
           op.n_grad = (uint8_t)ar;
           op.aux = (int)out.grads.size();
           for (int a = 0; a < ar; ++a) {
+            // the derivative matrix applied to psi (same structure as the gate) and the real
+            // part of <lambda|.> (two FMAs per amplitude)
+            out.grad_flops += (op_flops(gc.type, tg.kind) + 4.0) * (double)(1ull << N);
             GradRec gr;
             gr.mat = add_slot(g, FORM_D0 + a, gc.shape);
             gr.param = tg.param_idx + a;

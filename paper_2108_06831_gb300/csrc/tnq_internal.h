@@ -260,6 +260,7 @@ struct PassPlan {
   std::vector<int> op_gate;  // circuit gate index of every op
   std::vector<tnq::GradRec> grads;
   double flops = 0;   // per batch element
+  double grad_flops = 0;  // adjoint plans: derivative products and dots, per batch element
   int max_grad_slots = 0;
 };
 
