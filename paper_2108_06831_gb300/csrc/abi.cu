@@ -637,6 +637,35 @@ tn_status tn_expectation_backward(const tn_plan *p, const tn_observable *H, cons
   return TN_OK;
 }
 
+tn_status tn_expectation_value_and_grad(const tn_plan *p, const tn_observable *H, const double *params_dev,
+                                        double *out_dev, double *grad_params_dev, void *workspace_dev,
+                                        tn_stream_t s) {
+  tn_status st = common_checks(p);
+  if (st != TN_OK) return st;
+  TN_CHECK_ARG(H != nullptr && out_dev != nullptr && workspace_dev != nullptr, "NULL argument");
+  TN_CHECK_ARG(p->opts.target == TN_TARGET_EXPECTATION, "plan target must be EXPECTATION");
+  TN_CHECK_ARG(H->n == p->n, "observable has %d qubits, circuit %d", H->n, p->n);
+  TN_CHECK_ARG(p->n_params == 0 || grad_params_dev != nullptr, "grad_params_dev is NULL");
+  st = check_device(H->device);
+  if (st != TN_OK) return st;
+  cudaStream_t cs = reinterpret_cast<cudaStream_t>(s);
+  const float2 *mats = nullptr;
+  long long mstride = 0;
+  st = call_mats(p, params_dev, workspace_dev, cs, &mats, &mstride);
+  if (st != TN_OK) return st;
+  char *ws = static_cast<char *>(workspace_dev);
+  float2 *psi = reinterpret_cast<float2 *>(ws + p->ws_psi);
+  float2 *lam = reinterpret_cast<float2 *>(ws + p->ws_lam);
+  TN_CUDA(launch_forward(p, mats, mstride, psi, cs), "gate-apply kernel");
+  TN_CUDA(launch_expectation(H, p->batch, psi, reinterpret_cast<double *>(ws + p->ws_part), out_dev, cs),
+          "expectation kernel");
+  if (p->n_params == 0) return TN_OK;
+  TN_CUDA(launch_apply_hamiltonian(H, p->batch, psi, lam, cs), "H psi kernel");
+  TN_CUDA(cudaMemsetAsync(grad_params_dev, 0, sizeof(double) * (size_t)p->batch * p->n_params, cs), "memset grad");
+  TN_CUDA(launch_backward(p, mats, mstride, psi, lam, grad_params_dev, cs), "adjoint kernel");
+  return TN_OK;
+}
+
 tn_status tn_state_expectation_workspace_bytes(const tn_observable *H, int32_t batch, size_t *bytes) {
   TN_CHECK_ARG(H != nullptr && bytes != nullptr, "NULL argument");
   TN_CHECK_ARG(batch >= 1, "batch < 1");

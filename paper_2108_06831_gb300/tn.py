@@ -77,6 +77,7 @@ _sigs = {
     "tn_contract_amplitudes": [_vp, _vp, _vp, C.c_int64, _vp, _vp, _vp],
     "tn_expectation": [_vp, _vp, _vp, _vp, _vp, _vp],
     "tn_expectation_backward": [_vp, _vp, _vp, _vp, _vp, _vp, _vp],
+    "tn_expectation_value_and_grad": [_vp, _vp, _vp, _vp, _vp, _vp, _vp],
     "tn_state_expectation_workspace_bytes": [_vp, C.c_int32, C.POINTER(C.c_size_t)],
     "tn_state_expectation": [_vp, C.c_int32, _vp, _vp, _vp, C.c_size_t, _vp],
     "tn_state_expectation_noalloc": [_vp, C.c_int32, _vp, _vp, _vp],
@@ -256,6 +257,11 @@ def expectation_backward(plan: Plan, obs: Observable, params, grad_out, grad_par
                                         _ptr(workspace), _stream(stream)), "tn_expectation_backward")
 
 
+def expectation_value_and_grad(plan: Plan, obs: Observable, params, out, grad_params, workspace, stream=None) -> None:
+    _check(_lib.tn_expectation_value_and_grad(plan._h, obs._h, _ptr(params), _ptr(out), _ptr(grad_params),
+                                              _ptr(workspace), _stream(stream)), "tn_expectation_value_and_grad")
+
+
 def state_expectation_workspace_bytes(obs: Observable, batch: int) -> int:
     b = C.c_size_t()
     _check(_lib.tn_state_expectation_workspace_bytes(obs._h, batch, C.byref(b)), "tn_state_expectation_workspace_bytes")
@@ -394,6 +400,14 @@ class Contractor:
             out = torch.empty((self.batch, self.n_params), dtype=torch.float64, device=self.device)
         expectation_backward(self.plan, obs, params, grad_out, out, self.workspace)
         return out
+
+    def expectation_value_and_grad(self, obs: Observable, params):
+        """(energies [batch], gradients [batch][n_params]) with one forward contraction."""
+        torch = _torch()
+        e = torch.empty(self.batch, dtype=torch.float64, device=self.device)
+        g = torch.empty((self.batch, self.n_params), dtype=torch.float64, device=self.device)
+        expectation_value_and_grad(self.plan, obs, params, e, g, self.workspace)
+        return e, g
 
 
 def _make_expectation_fn():

@@ -43,6 +43,34 @@ def test_hea_tfim_expectation_and_gradient(n, layers, tile):
         assert np.linalg.norm(G[b] - gref) / max(np.linalg.norm(gref), 1e-3) <= 1e-4
 
 
+@pytest.mark.parametrize("n,layers,tile", [(6, 3, 0), (13, 2, 8)])
+def test_value_and_grad_matches_separate_calls_and_oracle(n, layers, tile):
+    """tn_expectation_value_and_grad contracts the forward state once; energies and gradients
+    equal the two-call path and the oracle (parameter shift)."""
+    from oracle import gradients as GR
+    from oracle import observables as OB
+    tn = _tn()
+    c = C.hea(n, layers)
+    H = C.tfim(n)
+    batch = 2
+    params = C.hea_params(c.n_params, batch, 70 + n)
+    ctr = tn.Contractor(c, target=tn.TARGET_EXPECTATION, batch=batch, tile_qubits=tile)
+    obs = tn.Observable(H)
+    e1, g1 = ctr.expectation_value_and_grad(obs, _dev(params))
+    e0 = ctr.expectation(obs, _dev(params))
+    g0 = ctr.expectation_backward(obs, _dev(params))
+    torch.cuda.synchronize()
+    assert tn.sync_status() == tn.OK
+    E, G = e1.cpu().numpy(), g1.cpu().numpy()
+    assert np.allclose(E, e0.cpu().numpy(), rtol=1e-12, atol=1e-12)
+    assert np.allclose(G, g0.cpu().numpy(), rtol=1e-9, atol=1e-12)
+    for b in range(batch):
+        Eref = OB.expectation(c, H, params[b])
+        assert abs(E[b] - Eref) <= 1e-4 * max(1.0, abs(Eref))
+        gref = GR.param_shift_grad(c, H, params[b])
+        assert np.linalg.norm(G[b] - gref) / max(np.linalg.norm(gref), 1e-3) <= 1e-4
+
+
 def test_theta_zero_energy_20q():
     tn = _tn()
     n = 20
