@@ -41,6 +41,7 @@ namespace {
 
 constexpr int kBatchThreads = 256;  // 2^(12 - 4): the largest tile (12 qubits) with 4 register qubits
 constexpr int kBatchT = 12;
+constexpr size_t kBatchStageMax = 32 * 1024;  // shared memory for a pass's staged records
 constexpr unsigned long long kWaitNs = 2000000000ull;
 
 __device__ __forceinline__ unsigned long long now_ns() {
@@ -59,7 +60,7 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch_exec(const BatchTask *_
                                                               const PassDesc *__restrict__ passes,
                                                               float2 *__restrict__ states, int *done,
                                                               unsigned long long *next_item, int *abort_flag,
-                                                              long long total_items, int *status) {
+                                                              long long total_items, int *status, int stage_cap) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ PassDesc pd;
   __shared__ long long s_item;
@@ -117,6 +118,26 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch_exec(const BatchTask *_
         if ((r >> j) & 1) off |= 1ll << pd.tile_pos[L + j];
       run_off[r] = off;
     }
+    // the pass's phase and op records and matrix entries: staged in shared memory when they fit
+    // (the gate loop then never waits on a dependent global load)
+    const int n_ph = pd.phase_end - pd.phase_begin, n_ops = pd.op_end - pd.op_begin;
+    const int n_mat = pd.mat_end - pd.mat_begin;
+    const int need = n_ph * (int)sizeof(PhaseDesc) + n_ops * (int)sizeof(OpDesc) + n_mat * (int)sizeof(float2);
+    const PhaseDesc *phs = circ.phases;
+    const OpDesc *ops = circ.ops;
+    const float2 *mats = circ.mats;
+    if (need <= stage_cap) {
+      PhaseDesc *s_ph = reinterpret_cast<PhaseDesc *>(run_off + (1 << (kBatchT - kLowBits)));
+      OpDesc *s_ops = reinterpret_cast<OpDesc *>(s_ph + n_ph);
+      float2 *s_mat = reinterpret_cast<float2 *>(s_ops + n_ops);
+      stage_int4(reinterpret_cast<int4 *>(s_ph), reinterpret_cast<const int4 *>(circ.phases + pd.phase_begin),
+                 n_ph * (int)(sizeof(PhaseDesc) / 16));
+      stage_int4(reinterpret_cast<int4 *>(s_ops), reinterpret_cast<const int4 *>(circ.ops + pd.op_begin), n_ops);
+      for (int i = threadIdx.x; i < n_mat; i += blockDim.x) s_mat[i] = circ.mats[pd.mat_begin + i];
+      phs = s_ph - pd.phase_begin;
+      ops = s_ops - pd.op_begin;
+      mats = s_mat - pd.mat_begin;
+    }
     const long long t = s_item - task.item_begin;
     unsigned long long base = 0, outer_mask = 0;
     for (int j = 0; j < pd.n_outer; ++j) {
@@ -147,7 +168,7 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch_exec(const BatchTask *_
     const bool active = threadIdx.x < (1 << (T - K));
     for (int p = pd.phase_begin; p < pd.phase_end; ++p) {
       if (active) {
-        const PhaseDesc &ph = circ.phases[p];
+        const PhaseDesc &ph = phs[p];
         BitCtx ctx;
         ctx.tb = deposit(threadIdx.x, ph.thr_pos, T - K);
         ctx.base = base;
@@ -167,8 +188,8 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch_exec(const BatchTask *_
         uint32_t neg = 0;
         for (int o = ph.op_begin; o < ph.op_end; ++o) {
           OpDesc op;
-          *reinterpret_cast<int4 *>(&op) = *reinterpret_cast<const int4 *>(circ.ops + o);
-          apply_op<K>(a, op, ctx, circ.mats, neg);
+          *reinterpret_cast<int4 *>(&op) = *reinterpret_cast<const int4 *>(ops + o);
+          apply_op<K>(a, op, ctx, mats, neg);
         }
         if (neg) reg_flush_sign<K>(a, neg);
 #pragma unroll
@@ -205,6 +226,7 @@ struct tn_batch {
   tnq::BatchCirc *d_circs = nullptr;
   tnq::PassDesc *d_passes = nullptr;
   size_t ws_bytes = 0;
+  int stage_cap = 0;             // shared-memory bytes for a pass's records (largest pass, capped)
   std::vector<tn_plan *> owned;  // plans made for this batch (tile autotuner)
 };
 
@@ -262,6 +284,13 @@ tn_status batch_build(const tn_plan *const *plans, int n, tn_batch **out) {
     }
   }
   b->total_elems = off;
+  // staging budget: the largest pass's phase/op records and matrix entries, up to 32 KB
+  size_t stage = 0;
+  for (const PassDesc &pd : passes)
+    stage = std::max(stage, (size_t)(pd.phase_end - pd.phase_begin) * sizeof(PhaseDesc) +
+                                (size_t)(pd.op_end - pd.op_begin) * sizeof(OpDesc) +
+                                (size_t)(pd.mat_end - pd.mat_begin) * sizeof(float2));
+  b->stage_cap = (int)std::min<size_t>((stage + 15) & ~(size_t)15, kBatchStageMax);
   // pass-major task list
   std::vector<BatchTask> tasks;
   std::vector<int> last_task((size_t)n, -1);
@@ -314,10 +343,13 @@ cudaError_t batch_run(const tn_batch *b, float2 *states, void *ws, cudaStream_t 
   int *abort_flag = reinterpret_cast<int *>(w + counters + 8);
   cudaError_t e = cudaMemsetAsync(ws, 0, b->ws_bytes, s);
   if (e != cudaSuccess) return e;
-  const size_t smem = ((size_t)sizeof(float2) << kBatchT) + ((size_t)1 << (kBatchT - kLowBits)) * sizeof(long long);
+  const size_t smem = ((size_t)sizeof(float2) << kBatchT) + ((size_t)1 << (kBatchT - kLowBits)) * sizeof(long long) +
+                      (size_t)b->stage_cap;
   static bool configured = false;
-  if (!configured) {
-    e = cudaFuncSetAttribute(k_batch_exec, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (!configured) {  // the largest request any batch can make
+    const size_t most = ((size_t)sizeof(float2) << kBatchT) +
+                        ((size_t)1 << (kBatchT - kLowBits)) * sizeof(long long) + kBatchStageMax;
+    e = cudaFuncSetAttribute(k_batch_exec, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)most);
     if (e != cudaSuccess) return e;
     configured = true;
   }
@@ -331,7 +363,7 @@ cudaError_t batch_run(const tn_batch *b, float2 *states, void *ws, cudaStream_t 
   if (grid < 1) return cudaSuccess;
   k_batch_exec<<<(unsigned)grid, kBatchThreads, smem, s>>>(b->d_tasks, b->n_tasks, b->d_circs, b->d_passes, states,
                                                            done, next, abort_flag, b->total_items,
-                                                           static_cast<int *>(status_word_ptr()));
+                                                           static_cast<int *>(status_word_ptr()), b->stage_cap);
   return cudaGetLastError();
 }
 
