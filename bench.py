@@ -77,6 +77,22 @@ def jit_source_hash(dump_dir):
     return h.hexdigest()[:16]
 
 
+def max_over_ranks(total_ms, world, device):
+    """The slowest rank's timed total (ms): replicas finish when the last one does."""
+    if world <= 1:
+        return total_ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([total_ms], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(units_per_step, steps, world, t_max_ms):
+    """Units processed by all ranks per second of the slowest rank's time (weak scaling)."""
+    return units_per_step * steps * world / (t_max_ms / 1000.0)
+
+
 def load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -446,13 +462,8 @@ def main():
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
-    total_ms = sum(ms)
-    t_max = total_ms
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-    value = units_per_step * args.steps * world / (t_max / 1000.0)
+    t_max = max_over_ranks(sum(ms), world, dev)
+    value = whole_job_value(units_per_step, args.steps, world, t_max)
     assert tn.sync_status() == tn.OK
 
     line = {"metric": METRIC, "value": value, "unit": unit, "n_gpus": world, "steps": args.steps,
