@@ -6,8 +6,9 @@
 // reference the tensor-core forms are measured against, and the form used for merges too
 // narrow for the tensor-core tiles.  One template covers the shapes a network contraction
 // produces: a CTA of 256 threads computes a BM x BN tile in TM x TN complex blocks per
-// thread, streaming BK-deep slices of both operands through shared memory (stored
-// transposed, so a warp's reads along rows are conflict-free), with FFMA accumulation.
+// thread, streaming BK-deep slices of both operands through shared memory (two slices in
+// flight, copied asynchronously; rows padded so a warp's reads fall in distinct banks), with
+// FFMA accumulation.
 // The tile is fitted to the operand shape: narrow N (down to 8 columns) takes tall tiles so
 // that no column work is wasted, and short K (8) takes an 8-deep slice.
 #include <algorithm>
@@ -39,16 +40,24 @@ __device__ __forceinline__ long long map_bits(const OutMap &om, long long f, int
   return r;
 }
 
+__device__ __forceinline__ void cp_async8(void *dst, const void *src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
 template <int BM, int BN, int BK, int TM, int TN>
 __global__ void __launch_bounds__(kThreads, 2) k_cgemm_fp32(long long M, long long N, long long K,
                                                          const float2 *__restrict__ A, const float2 *__restrict__ B,
                                                          float2 *__restrict__ C, const __grid_constant__ StagedMap om) {
   static_assert((BM / TM) * (BN / TN) == kThreads, "one thread per TM x TN block");
-  // operand slices during the K loop; the C tile (row stride BN + 1) in the permuted epilogue
-  constexpr int kAB = BK * (BM + 1) + BK * (BN + 1), kTile = BM * (BN + 1);
-  __shared__ float2 smem[kAB > kTile ? kAB : kTile];
-  float2(*As)[BM + 1] = reinterpret_cast<float2(*)[BM + 1]>(smem);
-  float2(*Bs)[BN + 1] = reinterpret_cast<float2(*)[BN + 1]>(smem + BK * (BM + 1));
+  // two K slices of both operands in flight (row-major, row stride BK + 1: a warp's reads across
+  // rows fall in distinct banks); the C tile (row stride BN + 1) in the permuted epilogue
+  constexpr int kLd = BK + 1;
+  constexpr int kSlice = (BM + BN) * kLd, kTile = BM * (BN + 1);
+  __shared__ float2 smem[2 * kSlice > kTile ? 2 * kSlice : kTile];
   const long long b = blockIdx.z;
   const long long m0 = (long long)blockIdx.y * BM, n0 = (long long)blockIdx.x * BN;
   const float2 *Ab = A + b * M * K;
@@ -61,46 +70,43 @@ __global__ void __launch_bounds__(kThreads, 2) k_cgemm_fp32(long long M, long lo
   for (int i = 0; i < TM; ++i)
 #pragma unroll
     for (int j = 0; j < TN; ++j) acc[i][j] = make_float2(0.f, 0.f);
-  // K-contiguous operands: pairs of complex numbers (16 bytes) per load when K is even
-  const bool vec = (K % 2) == 0;
-  for (long long k0 = 0; k0 < K; k0 += BK) {
-    if (vec) {
-      for (int e = threadIdx.x; e < BM * (BK / 2); e += kThreads) {
-        const int r = e / (BK / 2), c = 2 * (e % (BK / 2));
-        const long long gm = m0 + r, gk = k0 + c;
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (gm < M && gk < K) v = *reinterpret_cast<const float4 *>(Ab + gm * K + gk);
-        As[c][r] = make_float2(v.x, v.y);
-        As[c + 1][r] = make_float2(v.z, v.w);
-      }
-      for (int e = threadIdx.x; e < BN * (BK / 2); e += kThreads) {
-        const int r = e / (BK / 2), c = 2 * (e % (BK / 2));
-        const long long gn = n0 + r, gk = k0 + c;
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (gn < N && gk < K) v = *reinterpret_cast<const float4 *>(Bb + gn * K + gk);
-        Bs[c][r] = make_float2(v.x, v.y);
-        Bs[c + 1][r] = make_float2(v.z, v.w);
-      }
-    } else {
-      for (int e = threadIdx.x; e < BM * BK; e += kThreads) {
-        const int r = e / BK, c = e % BK;
-        const long long gm = m0 + r, gk = k0 + c;
-        As[c][r] = (gm < M && gk < K) ? Ab[gm * K + gk] : make_float2(0.f, 0.f);
-      }
-      for (int e = threadIdx.x; e < BN * BK; e += kThreads) {
-        const int r = e / BK, c = e % BK;
-        const long long gn = n0 + r, gk = k0 + c;
-        Bs[c][r] = (gn < N && gk < K) ? Bb[gn * K + gk] : make_float2(0.f, 0.f);
+  // slice k0 of A (BM rows) and B (BN rows) into buffer sb: asynchronous copies of the
+  // elements in range, zeros for the ragged edges
+  auto load_slice = [&](int sb, long long k0) {
+    float2 *as = smem + sb * kSlice, *bs = as + BM * kLd;
+    for (int e = threadIdx.x; e < (BM + BN) * BK; e += kThreads) {
+      const int r = e / BK, c = e % BK;
+      const long long gk = k0 + c;
+      if (r < BM) {
+        const long long gm = m0 + r;
+        if (gm < M && gk < K) cp_async8(as + r * kLd + c, Ab + gm * K + gk);
+        else as[r * kLd + c] = make_float2(0.f, 0.f);
+      } else {
+        const long long gn = n0 + (r - BM);
+        if (gn < N && gk < K) cp_async8(bs + (r - BM) * kLd + c, Bb + gn * K + gk);
+        else bs[(r - BM) * kLd + c] = make_float2(0.f, 0.f);
       }
     }
+    cp_async_commit();
+  };
+  int sb = 0;
+  if (K > 0) load_slice(0, 0);
+  for (long long k0 = 0; k0 < K; k0 += BK) {
+    if (k0 + BK < K) {
+      load_slice(sb ^ 1, k0 + BK);
+      cp_async_wait<1>();  // the current slice has landed (the next may still be in flight)
+    } else {
+      cp_async_wait<0>();
+    }
     __syncthreads();
+    const float2 *as = smem + sb * kSlice, *bs = as + BM * kLd;
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
       float2 a[TM], bb[TN];
 #pragma unroll
-      for (int i = 0; i < TM; ++i) a[i] = As[kk][ty + (BM / TM) * i];
+      for (int i = 0; i < TM; ++i) a[i] = as[(ty + (BM / TM) * i) * kLd + kk];
 #pragma unroll
-      for (int j = 0; j < TN; ++j) bb[j] = Bs[kk][tx + NX * j];
+      for (int j = 0; j < TN; ++j) bb[j] = bs[(tx + NX * j) * kLd + kk];
 #pragma unroll
       for (int i = 0; i < TM; ++i)
 #pragma unroll
@@ -111,7 +117,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_cgemm_fp32(long long M, long lo
           acc[i][j].y = fmaf(a[i].y, bb[j].x, acc[i][j].y);
         }
     }
-    __syncthreads();
+    __syncthreads();  // the buffer is free for the slice after next
+    sb ^= 1;
   }
   if (om.map.identity) {
 #pragma unroll
@@ -209,7 +216,7 @@ cudaError_t launch_shape(long long batch, long long M, long long N, long long K,
 template <int BK>
 cudaError_t launch_k(long long batch, long long M, long long N, long long K, const float2 *A, const float2 *B,
                      float2 *C, const OutMap &om, cudaStream_t s) {
-  if (N <= 8) return launch_shape<256, 8, BK, 4, 2>(batch, M, N, K, A, B, C, om, s);
+  if (N <= 8) return launch_shape<128, 8, BK, 2, 2>(batch, M, N, K, A, B, C, om, s);
   if (N <= 16) return launch_shape<128, 16, BK, 4, 2>(batch, M, N, K, A, B, C, om, s);
   if (N <= 32) return launch_shape<128, 32, BK, 4, 4>(batch, M, N, K, A, B, C, om, s);
   return launch_shape<64, 64, BK, 4, 4>(batch, M, N, K, A, B, C, om, s);
