@@ -74,3 +74,37 @@ def test_plan_option_validation():
         tn.Plan(ch, batch=-1, host_only=True)
     p = tn.Plan(ch, target=tn.TARGET_EXPECTATION, batch=4, host_only=True)
     assert p.workspace_bytes >= 2 * 4 * 8 * 32
+
+
+def test_network_plan_6x6_grid_host_only():
+    """Network lowering for the 6x6 depth-12 grid (64 bitstrings per call), without a device:
+    every merge is either folded at plan time or launched, the largest intermediate stays within
+    2^27 entries, and the dense merges (and only fitting shapes) go to the tensor cores."""
+    from paper_2108_06831_gb300 import tn
+    ch = tn.CircuitHandle(C.grid(6, 6, 12, 3003))
+    stats = {}
+    for prec in (tn.PREC_FP32, tn.PREC_3XTF32, tn.PREC_SPLIT_BF16):
+        p = tn.Plan(ch, target=tn.TARGET_AMPLITUDES, host_only=True, network_bitstrings=64, precision=prec)
+        stats[prec] = s = p.stats()
+        assert s["net_max_log2"] <= 27
+        assert s["net_merges"] + s["net_folded_merges"] == stats[tn.PREC_FP32]["net_merges"] + \
+            stats[tn.PREC_FP32]["net_folded_merges"]
+        assert 0 < s["net_merges"] < 200 and s["net_folded_merges"] > 300
+        assert p.workspace_bytes < 4 << 30
+    assert stats[tn.PREC_FP32]["net_tensor_merges"] == 0
+    assert stats[tn.PREC_3XTF32]["net_tensor_merges"] >= 8
+    assert stats[tn.PREC_SPLIT_BF16]["net_tensor_merges"] >= 8
+    # the planner is deterministic: the same circuit gives the same plan
+    again = tn.Plan(ch, target=tn.TARGET_AMPLITUDES, host_only=True, network_bitstrings=64,
+                    precision=tn.PREC_3XTF32).stats()
+    assert again == stats[tn.PREC_3XTF32]
+
+
+def test_network_plan_rejects_bad_options():
+    from paper_2108_06831_gb300 import tn
+    ch = tn.CircuitHandle(C.grid(3, 3, 4, 1))
+    with pytest.raises(tn.TnError):  # bitstring batch must be a power of two
+        tn.Plan(ch, target=tn.TARGET_AMPLITUDES, host_only=True, network_bitstrings=48)
+    chp = tn.CircuitHandle(C.brickwork(6, 2, 1, parameterized=True)[0])
+    with pytest.raises(tn.TnError):  # network plans take fixed angles
+        tn.Plan(chp, target=tn.TARGET_AMPLITUDES, host_only=True, network_bitstrings=16)
