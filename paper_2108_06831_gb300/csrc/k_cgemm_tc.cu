@@ -374,7 +374,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_cgemm_tc(const __grid_constant_
   }
 }
 
-// Persistent form for short, HBM-bound merges (3XTF32, A split on chip, at most
+// Persistent form for short, HBM-bound merges (3XTF32 or SPLIT_BF16, A split on chip, at most
 // kStreamMaxKTiles K tiles; a network merge has N = K = 64 and thousands of 128-row tiles):
 // one CTA per SM walks the tiles (column tile fastest, then row tile, then batch), the TMA
 // stage ring runs on across tile boundaries, and the accumulators are double-buffered in
@@ -386,14 +386,63 @@ constexpr int kStreamThreads = 320;
 constexpr int kStreamMaxKTiles = 8;  // a single leading accumulator per tile stays accurate
 constexpr int kStgStride = 17;       // staging row stride (complex): rows fall in different banks
 
+// Split of one A stage from FP32 into three BF16 parts, in place: the FP32 tile is two 128-byte
+// boxes (K elements 32j..32j+31 of every row, 16-byte chunks swizzled by row mod 8); part p is a
+// 128 x 64 BF16 tile at p x 16 KB (chunk d = K elements 8d..8d+7, same swizzle).  Each of the 128
+// converter threads first reads its 8 output chunks' sources, then (after a named barrier: the
+// parts overwrite the FP32 tile) writes x0 = bf16(x), x1 = bf16(x - x0), x2 = bf16(x - x0 - x1).
+__device__ __forceinline__ void split_bf16_in_place(unsigned char *st) {
+  float v[8][8];
+#pragma unroll
+  for (int it = 0; it < 8; ++it) {
+    const int item = threadIdx.x + kConvThreads * it, r = item >> 3, d = item & 7;
+    const unsigned char *row = st + (d >> 2) * kTileA + r * 128;
+    const int c0 = 2 * (d & 3);
+    const float4 a = *reinterpret_cast<const float4 *>(row + ((c0 ^ (r & 7)) << 4));
+    const float4 b = *reinterpret_cast<const float4 *>(row + (((c0 + 1) ^ (r & 7)) << 4));
+    v[it][0] = a.x, v[it][1] = a.y, v[it][2] = a.z, v[it][3] = a.w;
+    v[it][4] = b.x, v[it][5] = b.y, v[it][6] = b.z, v[it][7] = b.w;
+  }
+  asm volatile("bar.sync 1, %0;" ::"n"(kConvThreads) : "memory");
+#pragma unroll
+  for (int it = 0; it < 8; ++it) {
+    const int item = threadIdx.x + kConvThreads * it, r = item >> 3, d = item & 7;
+    uint32_t w[3][4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      uint32_t h[3][2];
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        const float x = v[it][2 * q + e];
+        const __nv_bfloat16 b0 = __float2bfloat16_rn(x);
+        const float r1 = x - __bfloat162float(b0);
+        const __nv_bfloat16 b1 = __float2bfloat16_rn(r1);
+        const __nv_bfloat16 b2 = __float2bfloat16_rn(r1 - __bfloat162float(b1));
+        h[0][e] = __bfloat16_as_ushort(b0);
+        h[1][e] = __bfloat16_as_ushort(b1);
+        h[2][e] = __bfloat16_as_ushort(b2);
+      }
+#pragma unroll
+      for (int p = 0; p < 3; ++p) w[p][q] = h[p][0] | (h[p][1] << 16);
+    }
+#pragma unroll
+    for (int p = 0; p < 3; ++p)
+      *reinterpret_cast<uint4 *>(st + p * kTileA + r * 128 + ((d ^ (r & 7)) << 4)) =
+          make_uint4(w[p][0], w[p][1], w[p][2], w[p][3]);
+  }
+}
+
+template <int PREC>
 __global__ void __launch_bounds__(kStreamThreads, 1)
     k_cgemm_tc_stream(const __grid_constant__ TmaMaps maps, int k_tiles, int tiles_n, int tiles_m,
                       long long total_tiles, long long M, long long N2, float *__restrict__ C, int *status,
                       const __grid_constant__ OutMap om) {
-  using CF = Cfg<PREC_TF32>;
+  using CF = Cfg<PREC>;
   constexpr int S = CF::kStages;
   constexpr int stage_bytes = CF::kParts * (kTileA + kTileB);
-  constexpr uint32_t tx_bytes = kTileA + CF::kParts * kTileB;
+  // A arrives as FP32: one 128-byte box per row and K tile for TF32, two for BF16 (64 elements)
+  constexpr int a_boxes = PREC == PREC_TF32 ? 1 : 2;
+  constexpr uint32_t tx_bytes = a_boxes * kTileA + CF::kParts * kTileB;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char *smem = reinterpret_cast<unsigned char *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   __shared__ __align__(8) uint64_t full[S], conv[S], empty[S], acc_full[2], acc_empty[2];
@@ -497,8 +546,8 @@ __global__ void __launch_bounds__(kStreamThreads, 1)
           mbar_expect_tx(&full[s], tx_bytes);
           issued_parity[s] = (int)((g / S) & 1);
           unsigned char *st = smem + (size_t)s * stage_bytes;
-          const int kc = kt * (KBYTES / CF::kElem);
-          tma_load_3d(st, &maps.a[0], &full[s], kc, mt * BM, bz);
+          const int kc = kt * (KBYTES / CF::kElem);  // K elements before this tile
+          for (int j = 0; j < a_boxes; ++j) tma_load_3d(st + j * kTileA, &maps.a[0], &full[s], kc + 32 * j, mt * BM, bz);
           for (int p = 0; p < CF::kParts; ++p)
             tma_load_3d(st + CF::kParts * kTileA + p * kTileB, &maps.b[p], &full[s], kc, nt * BN, bz);
         }
@@ -533,7 +582,7 @@ __global__ void __launch_bounds__(kStreamThreads, 1)
               const uint32_t off = kk * CF::kMmaK * CF::kElem;
               const uint32_t dst = p == 0 ? base : base + BN;
               const bool acc = p == 0 ? (kt > 0 || kk > 0) : (kt > 0 || kk > 0 || p > 1);
-              mma<PREC_TF32>(dst, smem_desc(a_base + off), smem_desc(b_base + off), acc ? 1u : 0u);
+              mma<PREC>(dst, smem_desc(a_base + off), smem_desc(b_base + off), acc ? 1u : 0u);
             }
           }
           mma_commit(&empty[s]);
@@ -555,14 +604,18 @@ __global__ void __launch_bounds__(kStreamThreads, 1)
           ok = false;
           break;
         }
-        float4 *hi = reinterpret_cast<float4 *>(smem + (size_t)s * stage_bytes);
-        float4 *lo = reinterpret_cast<float4 *>(smem + (size_t)s * stage_bytes + kTileA);
+        if constexpr (PREC == PREC_TF32) {
+          float4 *hi = reinterpret_cast<float4 *>(smem + (size_t)s * stage_bytes);
+          float4 *lo = reinterpret_cast<float4 *>(smem + (size_t)s * stage_bytes + kTileA);
 #pragma unroll 4
-        for (int c = threadIdx.x; c < kTileA / 16; c += kConvThreads) {
-          const float4 v = hi[c];
-          const float4 h = make_float4(tf32_rna(v.x), tf32_rna(v.y), tf32_rna(v.z), tf32_rna(v.w));
-          lo[c] = make_float4(v.x - h.x, v.y - h.y, v.z - h.z, v.w - h.w);
-          hi[c] = h;
+          for (int c = threadIdx.x; c < kTileA / 16; c += kConvThreads) {
+            const float4 v = hi[c];
+            const float4 h = make_float4(tf32_rna(v.x), tf32_rna(v.y), tf32_rna(v.z), tf32_rna(v.w));
+            lo[c] = make_float4(v.x - h.x, v.y - h.y, v.z - h.z, v.w - h.w);
+            hi[c] = h;
+          }
+        } else {
+          split_bf16_in_place(smem + (size_t)s * stage_bytes);
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         mbar_arrive(&conv[s]);
@@ -755,7 +808,12 @@ size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 // A is split on chip when few CTAs read each A tile (HBM-bound merges: the split copy would
 // cost more traffic than the GEMM); with many column tiles the one-pass prep split is
 // cheaper than converting every tile again in every CTA.
-bool split_a_on_chip(int precision, long long N) { return precision == TN_PREC_3XTF32 && (2 * N) / BN <= 2; }
+bool split_a_on_chip(int precision, long long N, long long K) {
+  if ((2 * N) / BN > 2) return false;
+  if (precision == TN_PREC_3XTF32) return true;
+  // BF16 parts are made on chip by the streaming kernel only (short K)
+  return precision == TN_PREC_SPLIT_BF16 && (2 * K * 2) / KBYTES <= kStreamMaxKTiles;
+}
 
 template <int PREC, bool SPLIT_A>
 cudaError_t run_tc(long long batch, long long M, long long N, long long K, const float2 *A, const float2 *B, float2 *C,
@@ -786,7 +844,8 @@ cudaError_t run_tc(long long batch, long long M, long long N, long long K, const
   TmaMaps maps;
   std::memset(&maps, 0, sizeof(maps));
   for (int p = 0; p < CF::kParts; ++p) {
-    if ((!SPLIT_A || p == 0) && !make_map(&maps.a[p], ap[p], CF::kElem, 2 * K, M, batch, BM))
+    // A split on chip arrives as FP32 (4-byte elements) whatever the parts' type
+    if ((!SPLIT_A || p == 0) && !make_map(&maps.a[p], ap[p], SPLIT_A ? 4 : CF::kElem, 2 * K, M, batch, BM))
       return cudaErrorInvalidValue;
     if (!make_map(&maps.b[p], bp[p], CF::kElem, 2 * K, 2 * N, batch, BN)) return cudaErrorInvalidValue;
   }
@@ -796,29 +855,33 @@ cudaError_t run_tc(long long batch, long long M, long long N, long long K, const
     if (k_tiles <= kStreamMaxKTiles) {  // short merge: persistent CTAs with overlapped epilogue
       static bool configured_stream = false;
       if (!configured_stream) {
-        e = cudaFuncSetAttribute(k_cgemm_tc_stream, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = cudaFuncSetAttribute(k_cgemm_tc_stream<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         configured_stream = true;
       }
       const int tiles_n = (int)((2 * N) / BN), tiles_m = (int)(M / BM);
       const long long total = (long long)tiles_n * tiles_m * batch;
       const long long grid = std::min<long long>(total, num_sms());
-      k_cgemm_tc_stream<<<(unsigned)grid, kStreamThreads, smem, s>>>(
+      k_cgemm_tc_stream<PREC><<<(unsigned)grid, kStreamThreads, smem, s>>>(
           maps, k_tiles, tiles_n, tiles_m, total, M, 2 * N, reinterpret_cast<float *>(C),
           static_cast<int *>(status_word_ptr()), om);
       return cudaGetLastError();
     }
   }
-  static bool configured = false;
-  if (!configured) {
-    e = cudaFuncSetAttribute(k_cgemm_tc<PREC, SPLIT_A>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    configured = true;
+  if constexpr (SPLIT_A && PREC == PREC_BF16) {
+    return cudaErrorNotSupported;  // the on-chip BF16 split exists in the streaming form only
+  } else {
+    static bool configured = false;
+    if (!configured) {
+      e = cudaFuncSetAttribute(k_cgemm_tc<PREC, SPLIT_A>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      configured = true;
+    }
+    dim3 grid((unsigned)((2 * N) / BN), (unsigned)(M / BM), (unsigned)batch);
+    k_cgemm_tc<PREC, SPLIT_A><<<grid, kThreads, smem, s>>>(maps, k_tiles, M, 2 * N, reinterpret_cast<float *>(C),
+                                                           static_cast<int *>(status_word_ptr()), om);
+    return cudaGetLastError();
   }
-  dim3 grid((unsigned)((2 * N) / BN), (unsigned)(M / BM), (unsigned)batch);
-  k_cgemm_tc<PREC, SPLIT_A><<<grid, kThreads, smem, s>>>(maps, k_tiles, M, 2 * N, reinterpret_cast<float *>(C),
-                                                         static_cast<int *>(status_word_ptr()), om);
-  return cudaGetLastError();
 }
 
 }  // namespace
@@ -827,7 +890,7 @@ size_t cgemm_workspace(int precision, long long batch, long long M, long long N,
   if (precision == TN_PREC_FP32 || !tc_shape_ok(precision, M, N, K)) return 0;
   const int parts = precision == TN_PREC_3XTF32 ? 2 : 3;
   // A split on chip: only B's parts are stored
-  if (split_a_on_chip(precision, N)) return parts * align256(part_bytes(precision, 2 * N, 2 * K, batch));
+  if (split_a_on_chip(precision, N, K)) return parts * align256(part_bytes(precision, 2 * N, 2 * K, batch));
   return parts * (align256(part_bytes(precision, M, 2 * K, batch)) + align256(part_bytes(precision, 2 * N, 2 * K, batch)));
 }
 
@@ -840,9 +903,10 @@ cudaError_t launch_cgemm(int precision, long long batch, long long M, long long 
   if (batch > 65535 || M / BM > 65535) return cudaErrorNotSupported;
   if (ws_bytes < cgemm_workspace(precision, batch, M, N, K)) return cudaErrorInvalidValue;
   if (precision == TN_PREC_3XTF32)
-    return split_a_on_chip(precision, N) ? run_tc<PREC_TF32, true>(batch, M, N, K, A, B, C, ws, s, m)
-                                         : run_tc<PREC_TF32, false>(batch, M, N, K, A, B, C, ws, s, m);
-  return run_tc<PREC_BF16, false>(batch, M, N, K, A, B, C, ws, s, m);
+    return split_a_on_chip(precision, N, K) ? run_tc<PREC_TF32, true>(batch, M, N, K, A, B, C, ws, s, m)
+                                            : run_tc<PREC_TF32, false>(batch, M, N, K, A, B, C, ws, s, m);
+  return split_a_on_chip(precision, N, K) ? run_tc<PREC_BF16, true>(batch, M, N, K, A, B, C, ws, s, m)
+                                          : run_tc<PREC_BF16, false>(batch, M, N, K, A, B, C, ws, s, m);
 }
 
 }  // namespace tnq
