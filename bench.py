@@ -42,7 +42,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="state24",
                     choices=["state24", "state10", "grad20", "gemm_fp32", "gemm_3xtf32", "gemm_bf16x3",
-                             "serving512", "amps36", "permute28", "gemm_merge"])
+                             "serving512", "amps36", "permute28", "gemm_merge", "fig31"])
     ap.add_argument("--batch", type=int, default=0, help="gemm workloads: batch override (small profiling cases)")
     ap.add_argument("--legs", type=int, default=0, help="permute28: tensor legs override (small profiling cases)")
     ap.add_argument("--prec", type=int, default=1, help="amps36: GEMM precision (0 FP32, 1 3xTF32, 2 split BF16)")
@@ -221,6 +221,9 @@ WORKLOADS = {
     # reversal, and a seeded random permutation, one launch each per step
     "permute28": dict(kind="permute", n=28, depth=0, seed=2800, batch=1),
     "state10": dict(kind="state", n=10, depth=8, seed=1000, batch=512),
+    # the paper's Fig. 3.1 test circuits: n in {2, 4, ..., 28} qubits, k in {2, 4, ..., 14} rounds,
+    # full states; a step contracts all 98 of them
+    "fig31": dict(kind="sweep", n=28, depth=14, seed=6000, batch=98),
     "grad20": dict(kind="grad", n=20, depth=10, seed=4000, batch=64),
 }
 
@@ -384,6 +387,22 @@ def main():
         per_call = 1 + nst["net_merges"] + nst["net_tensor_merges"] * (2 if args.prec == 2 else 1)
         launches_per_step = per_call * (batch // chunk)
         kernel_only = None
+    elif wl["kind"] == "sweep":
+        pts = [(n, k) for n in range(2, 29, 2) for k in range(2, 15, 2)]
+        ctrs, outs = {}, {}
+        for i, (n, k) in enumerate(pts):
+            ctrs[(n, k)] = tn.Contractor(C.paper_fig31(n, k, wl["seed"] + i), device=dev)
+            outs[(n, k)] = torch.empty(1 << n, dtype=torch.complex64, device=dev)
+        batch = len(pts)
+        units_per_step = float(sum(1 << n for n, _ in pts))
+        unit = "amplitudes/s"
+
+        def step():
+            for key in pts:
+                tn.contract_state(ctrs[key].plan, None, outs[key], ctrs[key].workspace)
+        launches_per_step = sum(c.plan.stats()["n_passes"] for c in ctrs.values())
+        kernel_only = None
+        ctr = None
     elif wl["kind"] == "permute":
         n = args.legs or wl["n"]
         batch = 1
@@ -613,6 +632,28 @@ def main():
         tfl = alg / (t_max / args.steps / 1000.0) / 1e12
         line["roofline"] = {"bound": "alu", "achieved": tfl, "peak": FP32_ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
                             "frac": tfl / FP32_ALU_PEAK_TFLOPS, "traffic": None, "kernel": "k_batch_exec",
+                            "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 x 2070 MHz"}
+    if wl["kind"] == "sweep":
+        # amplitudes/s of every (n, k) point, each timed on its own; the roofline is the largest
+        # point's (n = 28, k = 14: 2 GiB state) gate work against the FP32 ALU peak
+        sweep = {}
+        for key in pts:
+            c = ctrs[key]
+
+            def one():
+                tn.contract_state(c.plan, None, outs[key], c.workspace)
+            for _ in range(2):
+                one()
+            pms = statistics.mean(timed(one, max(2, args.steps)))
+            sweep[f"n{key[0]}_k{key[1]}"] = round((1 << key[0]) / (pms / 1000.0), 1)
+            if key == pts[-1]:
+                big_ms, big_flops = pms, c.plan.stats()["flops"]
+        tfl = big_flops / (big_ms / 1000.0) / 1e12
+        line["config"].update({"points": "n in 2..28 step 2, k in 2..14 step 2", "circuits_per_step": batch})
+        line["per_point_amplitudes_per_s"] = sweep
+        line["roofline"] = {"bound": "alu", "achieved": tfl, "peak": FP32_ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
+                            "frac": tfl / FP32_ALU_PEAK_TFLOPS, "traffic": None,
+                            "kernel": "tnq_p* (fused gate-apply), Fig. 3.1 circuit n=28 k=14",
                             "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 x 2070 MHz"}
     if wl["kind"] == "permute":
         per_step_s = t_max / args.steps / 1000.0

@@ -68,6 +68,18 @@ def test_grid_4x5_split_bf16_against_fp32():
     assert _rel(a32, ref) <= TOL and _rel(abf, ref) <= TOL
 
 
+@pytest.mark.parametrize("precision", [0, 1, 2])
+def test_grid_5x5_depth12(precision):
+    """25 qubits, the same generator as the 36-qubit configuration: sampled amplitudes against
+    the oracle's FP64 sweep (itself pinned to state vectors on 4x4 and 4x5 grids)."""
+    from oracle.tn import contract_amplitude_sweep
+    c = C.grid(5, 5, 12, 55)
+    xs = C.random_bitstrings(25, 64, 56)
+    got, st = _amps(c, xs, 64, precision)
+    ref = np.array([contract_amplitude_sweep(c, int(x)) for x in xs[:6]])
+    assert _rel(got[:6], ref) <= TOL
+
+
 def test_cfg3_grid_6x6_depth12_sampled():
     """The 36-qubit configuration in the bench's launch configuration (64 bitstrings per call,
     3xTF32 merges): three amplitudes against the oracle's own network sweep (FP64), and the

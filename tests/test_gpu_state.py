@@ -142,3 +142,37 @@ def test_invalid_arguments_rejected():
     ctr = tn.Contractor(C.brickwork(6, 2, 1, parameterized=True)[0])
     with pytest.raises(tn.TnError):
         ctr.state(None)  # parameterised circuit without parameters
+
+
+@pytest.mark.parametrize("n,k", [(2, 14), (6, 2), (14, 8), (20, 14)])
+def test_fig31_sweep_points(n, k):
+    """Points of the paper-shaped sweep (Fig. 3.1 circuits) against the FP64 oracle."""
+    from oracle.statevector import simulate_state
+    from paper_2108_06831_gb300 import tn
+    c = C.paper_fig31(n, k, 6000 + n + k)
+    ctr = tn.Contractor(c)
+    out = torch.empty(1 << n, dtype=torch.complex64, device="cuda")
+    tn.contract_state(ctr.plan, None, out, ctr.workspace)
+    torch.cuda.synchronize()
+    assert tn.sync_status() == tn.OK
+    ref = simulate_state(c)
+    got = out.cpu().numpy().astype(np.complex128)
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= 1e-5
+
+
+def test_fig31_largest_point_norm_and_tiles():
+    """n = 28, k = 14 (2 GiB state): no full-state oracle fits the test budget; the norm is 1 and
+    two different tilings (different pass structures) agree."""
+    from paper_2108_06831_gb300 import tn
+    c = C.paper_fig31(28, 14, 6042)
+    a = tn.Contractor(c)
+    b = tn.Contractor(c, tile_qubits=10)
+    x = torch.empty(1 << 28, dtype=torch.complex64, device="cuda")
+    tn.contract_state(a.plan, None, x, a.workspace)
+    y = torch.empty_like(x)
+    tn.contract_state(b.plan, None, y, b.workspace)
+    torch.cuda.synchronize()
+    assert tn.sync_status() == tn.OK
+    nx = torch.linalg.vector_norm(x.to(torch.complex128)).item()
+    assert abs(nx - 1.0) <= 1e-5
+    assert (torch.linalg.vector_norm((x - y).to(torch.complex128)) / nx).item() <= 1e-5

@@ -261,6 +261,7 @@ def test_param_shift_u3_and_cp():
 @pytest.mark.parametrize("maker", [
     lambda: C.grid(4, 4, 12, 21),
     lambda: C.grid(3, 5, 9, 2),
+    lambda: C.grid(4, 5, 12, 33),
     lambda: C.random_circuit(9, 70, 13),
     lambda: C.qft(8, 77),
     lambda: C.hea(6, 2),
