@@ -4,6 +4,7 @@
 #include <cstdlib>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -53,6 +54,23 @@ int num_sms() {
     g_sms.count[dev] = v > 0 ? v : 1;
   }
   return g_sms.count[dev];
+}
+
+// The dynamic shared-memory limit of a kernel is a per-device function attribute: raise it on
+// the current device when a launch needs more than was set there before.
+cudaError_t ensure_smem(const void *func, size_t bytes) {
+  static std::mutex m;
+  static std::map<std::pair<const void *, int>, size_t> set;
+  if (bytes <= 48 * 1024) return cudaSuccess;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(m);
+  size_t &cur = set[{func, dev}];
+  if (bytes <= cur) return cudaSuccess;
+  e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) cur = bytes;
+  return e;
 }
 
 }  // namespace tnq

@@ -213,14 +213,10 @@ cudaError_t launch_bwd_k(const PassDesc &h, const PassDesc *d_pass, const tn_pla
   const int nwarps = (threads + 31) / 32;
   const size_t smem = 2 * ((size_t)1 << T) * sizeof(float2) + ((size_t)1 << (T - L)) * sizeof(long long) +
                       (size_t)h.grad_slots * sizeof(double) + (size_t)h.grad_slots * nwarps * sizeof(float);
-  static int configured_smem[kMaxReg + 1] = {0};
-  if ((int)smem > configured_smem[K]) {
-    cudaError_t e = cudaFuncSetAttribute(k_bwd_pass<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    configured_smem[K] = (int)smem;
-  }
+  cudaError_t e = ensure_smem(reinterpret_cast<const void *>(k_bwd_pass<K>), smem);
+  if (e != cudaSuccess) return e;
   int per_sm = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bwd_pass<K>, threads, smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bwd_pass<K>, threads, smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) per_sm = 1;
   const long long n_tiles = 1ll << h.n_outer;

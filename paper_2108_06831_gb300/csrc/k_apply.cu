@@ -151,14 +151,10 @@ cudaError_t launch_fwd_k(const PassDesc &h, const PassDesc *d_pass, const PhaseD
   const size_t stage = (size_t)(h.op_end - h.op_begin) * sizeof(OpDesc) + (size_t)(h.mat_end - h.mat_begin) * sizeof(float2);
   const int staged = stage <= kStageBytes ? 1 : 0;
   if (staged) smem += stage;
-  static int configured_smem[kMaxReg + 1] = {0};
-  if ((int)smem > configured_smem[K]) {
-    cudaError_t e = cudaFuncSetAttribute(k_fwd_pass<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    configured_smem[K] = (int)smem;
-  }
+  cudaError_t e = ensure_smem(reinterpret_cast<const void *>(k_fwd_pass<K>), smem);
+  if (e != cudaSuccess) return e;
   int per_sm = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fwd_pass<K>, threads, smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fwd_pass<K>, threads, smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) per_sm = 1;
   const long long work = (long long)batch << h.n_outer;

@@ -345,14 +345,8 @@ cudaError_t batch_run(const tn_batch *b, float2 *states, void *ws, cudaStream_t 
   if (e != cudaSuccess) return e;
   const size_t smem = ((size_t)sizeof(float2) << kBatchT) + ((size_t)1 << (kBatchT - kLowBits)) * sizeof(long long) +
                       (size_t)b->stage_cap;
-  static bool configured = false;
-  if (!configured) {  // the largest request any batch can make
-    const size_t most = ((size_t)sizeof(float2) << kBatchT) +
-                        ((size_t)1 << (kBatchT - kLowBits)) * sizeof(long long) + kBatchStageMax;
-    e = cudaFuncSetAttribute(k_batch_exec, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)most);
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
+  e = ensure_smem(reinterpret_cast<const void *>(k_batch_exec), smem);
+  if (e != cudaSuccess) return e;
   int per_sm = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_exec, kBatchThreads, smem);
   if (e != cudaSuccess) return e;

@@ -853,12 +853,8 @@ cudaError_t run_tc(long long batch, long long M, long long N, long long K, const
   const int k_tiles = (int)((2 * K * CF::kElem) / KBYTES);
   if constexpr (SPLIT_A) {
     if (k_tiles <= kStreamMaxKTiles) {  // short merge: persistent CTAs with overlapped epilogue
-      static bool configured_stream = false;
-      if (!configured_stream) {
-        e = cudaFuncSetAttribute(k_cgemm_tc_stream<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        configured_stream = true;
-      }
+      e = ensure_smem(reinterpret_cast<const void *>(k_cgemm_tc_stream<PREC>), smem);
+      if (e != cudaSuccess) return e;
       const int tiles_n = (int)((2 * N) / BN), tiles_m = (int)(M / BM);
       const long long total = (long long)tiles_n * tiles_m * batch;
       const long long grid = std::min<long long>(total, num_sms());
@@ -871,12 +867,8 @@ cudaError_t run_tc(long long batch, long long M, long long N, long long K, const
   if constexpr (SPLIT_A && PREC == PREC_BF16) {
     return cudaErrorNotSupported;  // the on-chip BF16 split exists in the streaming form only
   } else {
-    static bool configured = false;
-    if (!configured) {
-      e = cudaFuncSetAttribute(k_cgemm_tc<PREC, SPLIT_A>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e != cudaSuccess) return e;
-      configured = true;
-    }
+    e = ensure_smem(reinterpret_cast<const void *>(k_cgemm_tc<PREC, SPLIT_A>), smem);
+    if (e != cudaSuccess) return e;
     dim3 grid((unsigned)((2 * N) / BN), (unsigned)(M / BM), (unsigned)batch);
     k_cgemm_tc<PREC, SPLIT_A><<<grid, kThreads, smem, s>>>(maps, k_tiles, M, 2 * N, reinterpret_cast<float *>(C),
                                                            static_cast<int *>(status_word_ptr()), om);

@@ -235,10 +235,6 @@ int red_grid_x(const tn_observable *o, int pass, int batch, const void *fn) {
   if (gx < 1) gx = 1;
   return (int)gx;
 }
-cudaError_t ensure_smem(const void *fn, size_t smem) {
-  if (smem <= 48 * 1024) return cudaSuccess;
-  return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-}
 }  // namespace
 
 size_t observable_partials(const tn_observable *o, int batch) {

@@ -66,6 +66,9 @@ void batch_adopt_plans(tn_batch *b, const std::vector<tn_plan *> &plans);
 tn_status batch_build_tuned(const tn_circuit *const *circuits, int n, const tn_tune_opts &o, cudaStream_t s,
                             tn_batch **out, int32_t *tiles_out);
 
+// Raise a kernel's dynamic shared-memory limit on the current device if `bytes` needs it.
+cudaError_t ensure_smem(const void *func, size_t bytes);
+
 // Device status word (timeouts, non-finite values).
 void *status_word_ptr();
 cudaError_t read_and_clear_status(int *value, cudaStream_t s);
