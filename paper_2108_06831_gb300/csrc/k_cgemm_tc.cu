@@ -793,10 +793,17 @@ bool make_map(CUtensorMap *m, const void *base, int elem, long long cols, long l
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// K needs no multiple of the K tile: the TMA fills the part of a K tile beyond the operands
+// with zeros (exact zero products); only the row stride must be a multiple of 16 bytes.
 bool tc_shape_ok(int precision, long long M, long long N, long long K) {
-  const long long kelems = KBYTES / (precision == TN_PREC_3XTF32 ? 4 : 2);  // real K elements per stage
-  return M % BM == 0 && (2 * N) % BN == 0 && (2 * K) % kelems == 0 && M > 0 && N > 0 && K > 0 &&
+  const long long elem = precision == TN_PREC_3XTF32 ? 4 : 2;
+  return M % BM == 0 && (2 * N) % BN == 0 && (2 * K * elem) % 16 == 0 && M > 0 && N > 0 && K > 0 &&
          M * 2 * N < (1ll << 40);
+}
+
+int k_tiles_of(int precision, long long K) {
+  const long long elem = precision == TN_PREC_3XTF32 ? 4 : 2;
+  return (int)((2 * K * elem + KBYTES - 1) / KBYTES);
 }
 
 size_t part_bytes(int precision, long long rows, long long cols, long long batch) {
@@ -812,7 +819,7 @@ bool split_a_on_chip(int precision, long long N, long long K) {
   if ((2 * N) / BN > 2) return false;
   if (precision == TN_PREC_3XTF32) return true;
   // BF16 parts are made on chip by the streaming kernel only (short K)
-  return precision == TN_PREC_SPLIT_BF16 && (2 * K * 2) / KBYTES <= kStreamMaxKTiles;
+  return precision == TN_PREC_SPLIT_BF16 && k_tiles_of(precision, K) <= kStreamMaxKTiles;
 }
 
 template <int PREC, bool SPLIT_A>
@@ -850,7 +857,7 @@ cudaError_t run_tc(long long batch, long long M, long long N, long long K, const
     if (!make_map(&maps.b[p], bp[p], CF::kElem, 2 * K, 2 * N, batch, BN)) return cudaErrorInvalidValue;
   }
   const size_t smem = (size_t)CF::kStages * CF::kParts * (kTileA + kTileB) + 1024;
-  const int k_tiles = (int)((2 * K * CF::kElem) / KBYTES);
+  const int k_tiles = k_tiles_of(prec_abi, K);
   if constexpr (SPLIT_A) {
     if (k_tiles <= kStreamMaxKTiles) {  // short merge: persistent CTAs with overlapped epilogue
       e = ensure_smem(reinterpret_cast<const void *>(k_cgemm_tc_stream<PREC>), smem);

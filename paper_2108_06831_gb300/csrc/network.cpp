@@ -163,6 +163,9 @@ struct Trial {
   std::vector<std::vector<int>> legs;
   int max_log2 = 0;
   double flops = 0;
+  // bytes read and written by the merges that depend on the bitstrings (their result carries
+  // the bitstring index, label 0): what a call costs once the rest is folded at plan time
+  double dyn_bytes = 0;
 };
 
 // Contraction state shared by the order heuristics: live tensors, index ownership, steps.
@@ -219,6 +222,9 @@ struct Contractor {
       if (std::find(batch.begin(), batch.end(), x) == batch.end() && std::find(contr.begin(), contr.end(), x) == contr.end())
         nb += net.label_dim[(size_t)x];
     tr.flops += 8.0 * std::ldexp(1.0, bits_of(batch) + mb + nb + bits_of(contr));
+    if (std::find(res.begin(), res.end(), 0) != res.end())
+      tr.dyn_bytes += 8.0 * (std::ldexp(1.0, bits_of(res)) + std::ldexp(1.0, bits_of(legs[(size_t)bi])) +
+                             std::ldexp(1.0, bits_of(legs[(size_t)bj])));
     const int out = (int)legs.size();
     for (int x : legs[(size_t)bi]) {
       auto &w = where[x];
@@ -340,7 +346,10 @@ void sweep_trial(const NetPlan &net, double temperature, uint64_t seed, Trial &t
 }  // namespace
 
 tn_status plan_network(NetPlan &net, int max_log2, std::string &err) {
-  // the deterministic greedy plus randomised trials; keep the smallest peak, then fewest flops
+  // the deterministic greedy plus randomised trials.  Among orders whose largest intermediate
+  // fits the cap, keep the one moving the fewest bytes per call (launched merges are
+  // HBM-bound; bitstring-independent merges are folded at plan time), then the fewest flops;
+  // if none fits, keep the smallest peak (and report it).
   Trial best;
   bool have = false;
   const int trials = 128;
@@ -350,8 +359,12 @@ tn_status plan_network(NetPlan &net, int max_log2, std::string &err) {
     const uint64_t seed = 0x9E3779B97F4A7C15ull * (uint64_t)(t + 1);
     if (t < trials / 2) greedy_trial(net, temp, seed, tr);
     else sweep_trial(net, temp, seed, tr);
-    const bool better = !have || tr.max_log2 < best.max_log2 ||
-                        (tr.max_log2 == best.max_log2 && tr.flops < best.flops);
+    const bool fits = tr.max_log2 <= max_log2, best_fits = have && best.max_log2 <= max_log2;
+    bool better;
+    if (!have) better = true;
+    else if (fits != best_fits) better = fits;
+    else if (!fits) better = tr.max_log2 < best.max_log2 || (tr.max_log2 == best.max_log2 && tr.flops < best.flops);
+    else better = tr.dyn_bytes < best.dyn_bytes || (tr.dyn_bytes == best.dyn_bytes && tr.flops < best.flops);
     if (better) {
       best = std::move(tr);
       have = true;

@@ -82,10 +82,10 @@ struct Allocator {
   }
 };
 
+// tensor-core shapes (kernel c): 128-row tiles, 128 real columns, 16-byte operand rows
 bool tc_ok(int precision, long long M, long long N, long long K) {
   if (precision == TN_PREC_FP32) return false;
-  const long long kq = precision == TN_PREC_3XTF32 ? 16 : 32;
-  return M % 128 == 0 && N % 64 == 0 && K % kq == 0;
+  return M % 128 == 0 && N % 64 == 0 && K % (precision == TN_PREC_3XTF32 ? 2 : 4) == 0;
 }
 
 }  // namespace

@@ -42,9 +42,14 @@ def _run(prec, batch, M, N, K, seed=0, scale=1.0):
 @pytest.mark.parametrize("prec", [0, 1, 2])
 def test_cgemm_precisions(prec, shape):
     batch, M, N, K = shape
-    if prec == 2 and K % 32:
-        pytest.skip("split-BF16 path needs K % 32 == 0")
     assert _run(prec, batch, M, N, K, seed=sum(shape) + prec) <= TOL
+
+
+@pytest.mark.parametrize("shape", [(2, 256, 64, 8), (1, 128, 128, 4), (3, 128, 64, 24), (1, 256, 256, 40)])
+@pytest.mark.parametrize("prec", [1, 2])
+def test_cgemm_k_not_a_tile_multiple(prec, shape):
+    # K tiles partly (or, for split BF16, wholly) beyond K are zero-filled by the TMA
+    assert _run(prec, *shape, seed=sum(shape) + 5 * prec) <= TOL
 
 
 @pytest.mark.parametrize("prec", [0, 1, 2])
