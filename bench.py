@@ -527,6 +527,19 @@ def main():
         line["roofline"]["launches_per_step"] = kernel_launches
         line["roofline"]["avg_launch_ms"] = avg_launch_ms
 
+    if args.workload == "state10":
+        # the configuration is latency-bound: one circuit (batch 1) per call, microseconds per call
+        one = tn.Contractor(circ_p, batch=1, tile_qubits=args.tile, device=dev, specialize=spec)
+        p1 = torch.as_tensor(params0[None, :], device=dev)
+        o1 = torch.empty((1, 1 << wl["n"]), dtype=torch.complex64, device=dev)
+
+        def single():
+            tn.contract_state(one.plan, p1, o1, one.workspace)
+        for _ in range(5):
+            single()
+        line["config"]["us_per_circuit_batch1"] = 1000.0 * statistics.median(timed(single, 50))
+        line["config"]["us_per_circuit_batched"] = 1000.0 * (t_max / args.steps) / batch
+
     # end to end through the public API with host buffers
     if not args.no_e2e and wl["kind"] == "state":
         h_params = torch.as_tensor(params).pin_memory()
