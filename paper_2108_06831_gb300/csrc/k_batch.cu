@@ -55,7 +55,9 @@ __device__ __forceinline__ int ld_acquire(const int *p) {
   return v;
 }
 
-__global__ void __launch_bounds__(kBatchThreads) k_batch_exec(const BatchTask *__restrict__ tasks, int n_tasks,
+// three resident CTAs per SM (the work items are latency-bound: more CTAs to overlap tile loads,
+// barriers and the dependency waits measured faster than the register spill this costs)
+__global__ void __launch_bounds__(kBatchThreads, 3) k_batch_exec(const BatchTask *__restrict__ tasks, int n_tasks,
                                                               const BatchCirc *__restrict__ circs,
                                                               const PassDesc *__restrict__ passes,
                                                               float2 *__restrict__ states, int *done,
