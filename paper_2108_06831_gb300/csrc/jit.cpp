@@ -584,16 +584,16 @@ std::string gen_bwd_pass(const tn_plan &p, int pi, const std::vector<int> &op_ki
     E.line(std::string(buf) + tab + "};");
   }
   snprintf(buf, sizeof buf,
-           "extern \"C\" __global__ void __launch_bounds__(%d) tnq_b%d(const float2 *__restrict__ mats_g, long long mstride, "
+           "extern \"C\" __global__ void __launch_bounds__(%d, 4) tnq_b%d(const float2 *__restrict__ mats_g, long long mstride, "
            "float2 *__restrict__ psi, float2 *__restrict__ lam, double *__restrict__ grad, int n_params) {",
            NTHR, pi);
   E.line(buf);
   E.line("  extern __shared__ __align__(16) unsigned char smraw[];");
   E.line("  float2 *const p0 = reinterpret_cast<float2 *>(smraw);");
-  snprintf(buf, sizeof buf, "  float2 *const p1 = p0 + %d; float2 *const l0 = p0 + %d; float2 *const l1 = p0 + %d;", TILE,
-           2 * TILE, 3 * TILE);
+  // one psi and one lambda tile (no prefetch buffer): four CTAs per SM cover the load latency
+  snprintf(buf, sizeof buf, "  float2 *const l0 = p0 + %d;", TILE);
   E.line(buf);
-  snprintf(buf, sizeof buf, "  float4 *const smat = reinterpret_cast<float4 *>(p0 + %d);", 4 * TILE);
+  snprintf(buf, sizeof buf, "  float4 *const smat = reinterpret_cast<float4 *>(p0 + %d);", 2 * TILE);
   E.line(buf);
   const int wacc_n = ((SLOTS * NW) + 1) & ~1;
   snprintf(buf, sizeof buf, "  float *const wacc = reinterpret_cast<float *>(smat + %d);", mat_n / 2);
@@ -660,18 +660,13 @@ std::string gen_bwd_pass(const tn_plan &p, int pi, const std::vector<int> &op_ki
   }
   E.line("  };");
   const long long NT = 1ll << pd.n_outer;
-  snprintf(buf, sizeof buf, "  if (blockIdx.x < %lldll) issue(blockIdx.x, p0, l0);", NT);
-  E.line(buf);
-  E.line("  asm volatile(\"cp.async.commit_group;\" ::: \"memory\");");
-  E.line("  int cur = 0;");
   snprintf(buf, sizeof buf, "  for (long long t = blockIdx.x; t < %lldll; t += gridDim.x) {", NT);
   E.line(buf);
-  E.line("    float2 *const smp = cur ? p1 : p0; float2 *const sml = cur ? l1 : l0;");
+  E.line("    float2 *const smp = p0; float2 *const sml = l0;");
   E.line("    " + emit_base("t", "base"));
-  snprintf(buf, sizeof buf, "    if (t + gridDim.x < %lldll) issue(t + gridDim.x, cur ? p0 : p1, cur ? l0 : l1);", NT);
-  E.line(buf);
+  E.line("    issue(t, p0, l0);");
   E.line("    asm volatile(\"cp.async.commit_group;\" ::: \"memory\");");
-  E.line("    asm volatile(\"cp.async.wait_group 1;\" ::: \"memory\");");
+  E.line("    asm volatile(\"cp.async.wait_group 0;\" ::: \"memory\");");
   E.line("    __syncthreads();");
   for (int ph = pd.phase_begin; ph < pd.phase_end; ++ph) {
     const PhaseDesc &d = p.bwd.phases[ph];
@@ -729,9 +724,7 @@ std::string gen_bwd_pass(const tn_plan &p, int pi, const std::vector<int> &op_ki
     E.line(buf);
   }
   E.line("    __syncthreads();");
-  E.line("    cur ^= 1;");
   E.line("  }");
-  E.line("  asm volatile(\"cp.async.wait_group 0;\" ::: \"memory\");");
   if (SLOTS > 0) {
     snprintf(buf, sizeof buf,
              "  for (int s = tid; s < %d; s += %d) atomicAdd(grad + b * n_params + tnq_bp%d[s], gacc[s]);", SLOTS, NTHR, pi);
@@ -739,7 +732,7 @@ std::string gen_bwd_pass(const tn_plan &p, int pi, const std::vector<int> &op_ki
   }
   E.line("}");
   *threads_out = NTHR;
-  *smem_out = (size_t)4 * TILE * 8 + (size_t)mat_n * 8 + (size_t)wacc_n * 4 + (size_t)SLOTS * 8;
+  *smem_out = (size_t)2 * TILE * 8 + (size_t)mat_n * 8 + (size_t)wacc_n * 4 + (size_t)SLOTS * 8;
   return E.o.str();
 }
 
