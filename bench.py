@@ -165,33 +165,70 @@ import json, sys, time
 sys.path.insert(0, {root!r})
 import numpy as np
 from paper_2108_06831_gb300 import circuits as C
-from oracle.statevector import basis_state, apply_matrix, gate_matrix
+from oracle.statevector import basis_state, apply_matrix, gate_matrix, simulate_state
 from oracle import observables as OB
-kind = {kind!r}
+from oracle.tn import contract_amplitude_sweep
+kind, budget = {kind!r}, {budget}
+t0 = time.perf_counter()
 if kind == "state":
     c, p = C.brickwork({n}, {depth}, {seed}, parameterized=True)
     psi = basis_state(c.n_qubits, 0)
-    t0 = time.perf_counter()
     done = 0
     for g in c.gates:
         psi = apply_matrix(psi, c.n_qubits, gate_matrix(c, g, p), g.qubits)
         done += 1
-        if time.perf_counter() - t0 > {budget}:
+        if time.perf_counter() - t0 > budget:
             break
     dt = time.perf_counter() - t0
-    per_circuit = dt * len(c.gates) / done
-    print(json.dumps(dict(value=(1 << c.n_qubits) / per_circuit, gates=done, total_gates=len(c.gates), seconds=dt)))
-else:
+    out = dict(value=(1 << c.n_qubits) / (dt * len(c.gates) / done), unit="amplitudes/s", seconds=dt,
+               sample=f"FP64 state-vector oracle, first {{done}} of {{len(c.gates)}} gates of the circuit "
+                      f"({{dt:.1f}} s), scaled to the whole circuit")
+elif kind == "grad":
     c = C.hea({n}, 10)
-    H = C.tfim({n})
-    params = C.hea_params(c.n_params, 1, 4000)[0]
-    t0 = time.perf_counter()
-    e = OB.expectation(c, H, params)
+    e = OB.expectation(c, C.tfim({n}), C.hea_params(c.n_params, 1, 4000)[0])
     dt = time.perf_counter() - t0
-    # parameter shift: 2 expectation evaluations per parameter
-    per_param = 2 * dt
-    print(json.dumps(dict(value=1.0 / per_param, seconds=dt, evals=1)))
+    out = dict(value=1.0 / (2 * dt), unit="grads/s", seconds=dt,
+               sample=f"FP64 oracle expectation of one parameter set ({{dt:.1f}} s); a parameter-shift "
+                      f"gradient entry costs two")
+elif kind == "amps":
+    c = C.grid(6, 6, {depth}, {seed})
+    xs = C.random_bitstrings(36, 4096, {seed} + 1)
+    done = 0
+    while done < len(xs) and (done == 0 or time.perf_counter() - t0 < budget):
+        contract_amplitude_sweep(c, int(xs[done]))
+        done += 1
+    dt = time.perf_counter() - t0
+    out = dict(value=done / dt, unit="amplitudes/s", seconds=dt,
+               sample=f"FP64 oracle network sweep, {{done}} of the 4096 bitstrings ({{dt:.1f}} s)")
+elif kind == "serve":
+    circs = [c for c in C.serving_mix(512, {seed}) if c.n_qubits <= 20]  # a sample bounded in time
+    done = amps = 0
+    for c in circs:
+        if done and time.perf_counter() - t0 > budget:
+            break
+        simulate_state(c)
+        done += 1
+        amps += 1 << c.n_qubits
+    dt = time.perf_counter() - t0
+    out = dict(value=amps / dt, unit="amplitudes/s", seconds=dt,
+               sample=f"FP64 state-vector oracle, the first {{done}} of the mix's circuits of at most 20 qubits "
+                      f"({{dt:.1f}} s)")
+elif kind == "sweep":
+    pts = [(n, k) for n in range(2, 29, 2) for k in range(2, 15, 2)]
+    done = amps = 0
+    for i, (n, k) in enumerate(pts):
+        if done and time.perf_counter() - t0 > budget:
+            break
+        simulate_state(C.paper_fig31(n, k, {seed} + i))
+        done += 1
+        amps += 1 << n
+    dt = time.perf_counter() - t0
+    out = dict(value=amps / dt, unit="amplitudes/s", seconds=dt,
+               sample=f"FP64 state-vector oracle, the {{done}} smallest of the 98 Fig. 3.1 circuits ({{dt:.1f}} s)")
+print(json.dumps(out))
 """
+
+ORACLE_KINDS = ("state", "grad", "amps", "serve", "sweep")
 
 
 def run_oracle_sample(kind: str, n: int, depth: int, seed: int, budget: float):
@@ -233,6 +270,10 @@ def reference_arm(args):
     if rank != 0:
         return 0
     wl = WORKLOADS[args.workload]
+    if wl["kind"] not in ORACLE_KINDS:
+        print(json.dumps({"impl": "reference", "unavailable": "kernel-level workload with no oracle counterpart "
+                          "(the oracle computes states, amplitudes and expectations, not bare GEMMs or permutes)"}))
+        return 0
     vals = []
     info = None
     for _ in range(args.warmup):
@@ -245,11 +286,9 @@ def reference_arm(args):
             return 0
         vals.append(info["value"])
     wall = time.perf_counter() - t0
-    unit = "amplitudes/s" if wl["kind"] == "state" else "grads/s"
+    unit = info["unit"]
     v = statistics.median(vals)
-    sample = (f"oracle state-vector FP64 on the first {info.get('gates')} of {info.get('total_gates')} gates, "
-              f"scaled to the whole circuit" if wl["kind"] == "state" else
-              "oracle: one FP64 expectation of one parameter set; parameter shift = 2 per gradient entry")
+    sample = info["sample"] + ", 1 thread"
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": unit, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * wall / max(args.steps, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -271,18 +310,13 @@ def main():
 
     # the CPU baseline runs first, in a fresh process, before this process touches the GPU
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline and wl["kind"] in ("state", "grad"):
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and wl["kind"] in ORACLE_KINDS:
         info, err = run_oracle_sample(wl["kind"], wl["n"], wl["depth"], wl["seed"], 12.0)
-        unit = "amplitudes/s" if wl["kind"] == "state" else "grads/s"
         if info is not None:
-            sample = (f"FP64 state-vector oracle, first {info['gates']} of {info['total_gates']} gates of the same "
-                      f"circuit ({info['seconds']:.1f} s, 1 thread), scaled to the whole circuit"
-                      if wl["kind"] == "state" else
-                      f"FP64 oracle expectation of one parameter set ({info['seconds']:.1f} s, 1 thread); a "
-                      f"parameter-shift gradient entry costs two")
-            cpu = {"value": info["value"], "unit": unit, "cores": 1, "kind": "oracle", "sample": sample}
+            cpu = {"value": info["value"], "unit": info["unit"], "cores": 1, "kind": "oracle",
+                   "sample": info["sample"] + ", 1 thread"}
         else:
-            cpu = {"value": None, "unit": unit, "cores": 1, "kind": "oracle", "sample": f"failed: {err}"}
+            cpu = {"value": None, "unit": None, "cores": 1, "kind": "oracle", "sample": f"failed: {err}"}
 
     import numpy as np
     import torch
