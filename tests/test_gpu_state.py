@@ -176,3 +176,29 @@ def test_fig31_largest_point_norm_and_tiles():
     nx = torch.linalg.vector_norm(x.to(torch.complex128)).item()
     assert abs(nx - 1.0) <= 1e-5
     assert (torch.linalg.vector_norm((x - y).to(torch.complex128)) / nx).item() <= 1e-5
+
+
+def test_max_size_32_qubits_closed_form():
+    """32 qubits (a 32 GiB complex64 state): U3 on every qubit, then CZ on every neighbour pair.
+    Every amplitude has a closed form, amp(x) = prod_q (U3_q|0>)[x_q] * (-1)^(sum_q x_q x_{q+1}),
+    evaluated in FP64 on 4096 sampled indices."""
+    from oracle.gates import matrix
+    from paper_2108_06831_gb300 import tn
+    n = 32
+    rng = np.random.default_rng(3232)
+    angles = rng.uniform(0.0, 2.0 * np.pi, size=(n, 3))
+    gates = [C.Gate("U3", (q,), tuple(float(a) for a in angles[q])) for q in range(n)]
+    gates += [C.Gate("CZ", (q, q + 1)) for q in range(n - 1)]
+    c = C.Circuit(n, gates)
+    ctr = tn.Contractor(c)
+    out = torch.empty((1, 1 << n), dtype=torch.complex64, device="cuda")
+    tn.contract_state(ctr.plan, None, out, ctr.workspace)
+    torch.cuda.synchronize()
+    assert tn.sync_status() == tn.OK
+    xs = rng.integers(0, 1 << n, size=4096, dtype=np.int64)
+    got = out[0, torch.as_tensor(xs, device="cuda")].cpu().numpy().astype(np.complex128)
+    col = np.array([matrix("U3", tuple(angles[q]))[:, 0] for q in range(n)])  # U3_q |0>
+    bits = (xs[:, None] >> (n - 1 - np.arange(n))[None, :]) & 1  # bit of qubit q (MSB first)
+    ref = np.prod(col[np.arange(n)[None, :], bits], axis=1)
+    ref = ref * (-1.0) ** np.sum(bits[:, :-1] * bits[:, 1:], axis=1)
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= STATE_TOL
