@@ -231,9 +231,10 @@ print(json.dumps(out))
 ORACLE_KINDS = ("state", "grad", "amps", "serve", "sweep")
 
 
-def run_oracle_sample(kind: str, n: int, depth: int, seed: int, budget: float):
+def run_oracle_sample(kind: str, n: int, depth: int, seed: int, budget: float, threads: int = 1):
     code = ORACLE_SNIPPET.format(root=ROOT, kind=kind, n=n, depth=depth, seed=seed, budget=budget)
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1", CUDA_VISIBLE_DEVICES="")
+    t = str(threads)
+    env = dict(os.environ, OMP_NUM_THREADS=t, OPENBLAS_NUM_THREADS=t, MKL_NUM_THREADS=t, CUDA_VISIBLE_DEVICES="")
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=600)
     if r.returncode != 0:
         return None, r.stderr[-400:]
@@ -309,7 +310,7 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
 
     # the CPU baseline runs first, in a fresh process, before this process touches the GPU
-    cpu = None
+    cpu = cpu_all = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and wl["kind"] in ORACLE_KINDS:
         info, err = run_oracle_sample(wl["kind"], wl["n"], wl["depth"], wl["seed"], 12.0)
         if info is not None:
@@ -317,6 +318,12 @@ def main():
                    "sample": info["sample"] + ", 1 thread"}
         else:
             cpu = {"value": None, "unit": None, "cores": 1, "kind": "oracle", "sample": f"failed: {err}"}
+        # the same sample with the BLAS threads on every host core (numpy tensordot / einsum)
+        ncores = os.cpu_count() or 1
+        info_all, _ = run_oracle_sample(wl["kind"], wl["n"], wl["depth"], wl["seed"], 12.0, threads=ncores)
+        if info_all is not None:
+            cpu_all = {"value": info_all["value"], "unit": info_all["unit"], "cores": ncores, "kind": "oracle",
+                       "sample": info_all["sample"] + f", {ncores} BLAS threads"}
 
     import numpy as np
     import torch
@@ -515,13 +522,18 @@ def main():
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
+    # the arithmetic the step computes in: FP32 (complex64 states), or the tensor-core split forms
+    prec_used = args.prec if wl["kind"] == "amps" else wl.get("prec", 0)
+    dtype = {0: "f32", 1: "3xtf32 (f32 accumulate)", 2: "bf16x3 (f32 accumulate)"}[prec_used]
+    if wl["kind"] == "permute":
+        dtype = "c64 (data movement)"
     t_max = max_over_ranks(sum(ms), world, dev)
     value = whole_job_value(units_per_step, args.steps, world, t_max)
     assert tn.sync_status() == tn.OK
 
     line = {"metric": METRIC, "value": value, "unit": unit, "n_gpus": world, "steps": args.steps,
             "warmup": max(args.warmup, 3), "ms_per_step": t_max / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "c64 (f32)", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic",
             "config": {"workload": args.workload, "n_qubits": wl["n"], "depth": wl["depth"], "batch": batch,
                        "tile_qubits": ctr.plan.stats()["tile_qubits"] if ctr is not None else None,
                        "specialized_kernels": bool(ctr.plan.stats()["specialized"]) if ctr is not None else None,
@@ -748,6 +760,8 @@ def main():
                                     for k in ("bound", "achieved", "peak", "unit", "frac")}
     if cpu is not None:
         line["cpu_baseline"] = cpu
+    if cpu_all is not None:
+        line["cpu_baseline_all_cores"] = cpu_all
     if rank == 0:
         print(json.dumps(line))
     if world > 1:
