@@ -46,6 +46,9 @@ def parse():
     ap.add_argument("--batch", type=int, default=0, help="gemm workloads: batch override (small profiling cases)")
     ap.add_argument("--legs", type=int, default=0, help="permute28: tensor legs override (small profiling cases)")
     ap.add_argument("--prec", type=int, default=1, help="amps36: GEMM precision (0 FP32, 1 3xTF32, 2 split BF16)")
+    ap.add_argument("--max-log2", type=int, default=0,
+                    help="amps36: cap on the largest intermediate (log2 entries; 0 = 28); below the "
+                         "best order's peak the planner slices indices")
     ap.add_argument("--tile", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -410,7 +413,7 @@ def main():
         chunk = wl["chunk"]
         ctr = None
         plan = tn.Plan(tn.CircuitHandle(circ), target=tn.TARGET_AMPLITUDES, network_bitstrings=chunk,
-                       precision=args.prec)
+                       precision=args.prec, max_intermediate_log2=args.max_log2)
         nst = plan.stats()
         aws = torch.empty(plan.workspace_bytes, dtype=torch.uint8, device=dev)
         xs_h = C.random_bitstrings(36, wl["batch"], wl["seed"] + 1)
@@ -423,9 +426,14 @@ def main():
         def step():
             for i in range(0, batch, chunk):
                 tn.contract_amplitudes(plan, None, xs[i:i + chunk], amps[i:i + chunk], aws)
-        # per call: the closure kernel, one GEMM per launched merge, B's split per tensor-core merge
-        # (and A's for split BF16)
-        per_call = 1 + nst["net_merges"] + nst["net_tensor_merges"] * (2 if args.prec == 2 else 1)
+        # per pass of the network and slice: the closure kernel, one GEMM per launched merge, B's
+        # split per tensor-core merge (and A's for split BF16); a sliced plan adds the FP64 slice
+        # sum per slice and the final store per pass; a call runs chunk / 2^net_batch_log2 passes
+        n_slices = 1 << nst["net_sliced"]
+        per_pass = n_slices * (1 + nst["net_merges"] + nst["net_tensor_merges"] * (2 if args.prec == 2 else 1))
+        if n_slices > 1:
+            per_pass += n_slices + 1
+        per_call = per_pass * (chunk >> nst["net_batch_log2"])
         launches_per_step = per_call * (batch // chunk)
         kernel_only = None
     elif wl["kind"] == "sweep":
@@ -634,9 +642,11 @@ def main():
         per_step_s = t_max / args.steps / 1000.0
         a = amps.cpu().numpy().astype(np.complex128)
         line["config"].update({"grid": "6x6", "bitstrings": batch, "bitstrings_per_call": wl["chunk"],
-                               "precision": args.prec, "merges_per_call": nst["net_merges"],
+                               "precision": args.prec, "merges_per_pass": nst["net_merges"],
                                "largest_intermediate_log2": nst["net_max_log2"],
-                               "tensor_core_merges_per_call": nst["net_tensor_merges"]})
+                               "max_intermediate_log2": args.max_log2 or 28, "sliced_indices": nst["net_sliced"],
+                               "bitstrings_per_pass": 1 << nst["net_batch_log2"],
+                               "tensor_core_merges_per_pass": nst["net_tensor_merges"]})
         line["config"]["folded_merges"] = nst["net_folded_merges"]
         # the dominant kernel: the dense merges (batch 64, M 32768, N = K = 64), HBM-bound;
         # the same GEMM shape is timed alone here with CUDA events (A read once as FP32 when

@@ -102,9 +102,14 @@ typedef enum { TN_PREC_FP32 = 0, TN_PREC_3XTF32 = 1, TN_PREC_SPLIT_BF16 = 2 } tn
 
 #define TN_PLAN_HOST_ONLY 1 /* plan without touching the GPU: only tn_plan_get_stats may use it */
 #define TN_PLAN_NETWORK 4 /* TN_TARGET_AMPLITUDES by contracting the circuit's tensor network pairwise
-                            * (permutations + batched complex GEMMs in opts->precision) instead of
-                            * contracting the state; allows up to 63 qubits.  opts->amp_batch (a power of
-                            * two) is the number of bitstrings per call the plan is sized for. */
+                            * (batched complex GEMMs in opts->precision) instead of contracting the
+                            * state; allows up to 63 qubits.  opts->amp_batch (a power of two) is the
+                            * number of bitstrings per call the plan is sized for.  When no order found
+                            * keeps every intermediate within 2^max_intermediate_log2 entries, the
+                            * bitstrings are contracted in smaller passes and/or indices are sliced
+                            * (each fixed to 0 and 1 in turn, the slices' amplitudes summed in FP64),
+                            * whichever costs less, at most 2^16 slices; beyond that
+                            * TN_ERR_UNSUPPORTED. */
 #define TN_PLAN_NO_SPECIALIZE 2 /* run the interpreting gate-apply kernel instead of plan-specialised
                                  * kernels (those are generated as CUDA C++ and compiled with NVRTC
                                  * when the plan is built; compiled code is cached on disk) */
@@ -141,6 +146,11 @@ typedef struct {
   int32_t net_folded_merges; /* TN_PLAN_NETWORK: bitstring-independent merges evaluated at plan time (FP64) */
   double bwd_flops;     /* TN_TARGET_EXPECTATION: algorithmic FP32 flops of the adjoint sweep per batch element
                            (every op on psi and lambda, derivative products and dots) */
+  int32_t net_sliced;   /* TN_PLAN_NETWORK: sliced indices (each pass contracts 2^net_sliced slices and sums
+                           them in FP64); 0 when an order within max_intermediate_log2 exists */
+  int32_t net_batch_log2; /* TN_PLAN_NETWORK: log2 bitstrings contracted together; a call of up to amp_batch
+                             bitstrings runs in passes of 2^net_batch_log2 (fewer than amp_batch when that
+                             is the cheaper way to keep intermediates within max_intermediate_log2) */
 } tn_plan_stats;
 
 /* Pauli sum H = sum_t coef[t] * P_t (host memory, read during tn_build_observable only).

@@ -411,6 +411,8 @@ tn_status tn_plan_get_stats(const tn_plan *p, tn_plan_stats *st) {
     st->net_merges = (int)p->net->launches.size();
     st->net_folded_merges = p->net->folded_merges;
     st->net_max_log2 = p->net->max_log2;
+    st->net_sliced = (int)p->net->slices.size();
+    st->net_batch_log2 = p->net->log2_batch;
     st->flops = p->net->flops;
     int tc = 0;
     for (const NetLaunch &L : p->net->launches) tc += L.precision != TN_PREC_FP32;
@@ -591,7 +593,7 @@ tn_status tn_contract_amplitudes(const tn_plan *p, const double *params_dev, con
   st = call_mats(p, params_dev, workspace_dev, cs, &mats, &mstride);
   if (st != TN_OK) return st;
   if (p->net) {
-    const long long cap = 1ll << p->net->log2_batch;
+    const long long cap = 1ll << p->net->call_log2;
     TN_CHECK_ARG(n_bitstrings <= cap, "this network plan takes at most %lld bitstrings per call", cap);
     if (n_bitstrings == 0) return TN_OK;
     TN_CUDA(run_network(*p->net, bitstrings_dev, n_bitstrings, static_cast<float2 *>(amps_dev), workspace_dev, cs),

@@ -71,10 +71,14 @@ __global__ void __launch_bounds__(kBatchThreads, 3) k_batch_exec(const BatchTask
   float2 *sm = reinterpret_cast<float2 *>(smem_raw);
   long long *run_off = reinterpret_cast<long long *>(smem_raw + ((size_t)sizeof(float2) << kBatchT));
   const uint32_t full = 0xFFFFu;
+  // thread 0 claims the next item while the current tile is stored (the claim's round trip
+  // off the path between items); a claimed item only waits on lower items, so holding one
+  // while finishing another cannot deadlock
+  unsigned long long claimed = threadIdx.x == 0 ? atomicAdd(next_item, 1ull) : 0ull;
 
   for (;;) {
     if (threadIdx.x == 0) {
-      s_item = (long long)atomicAdd(next_item, 1ull);
+      s_item = (long long)claimed;
       s_go = (s_item < total_items && ld_acquire(abort_flag) == 0) ? 1 : 0;
       if (s_go) {
         int lo = 0, hi = n_tasks - 1;  // last task with item_begin <= item
@@ -199,15 +203,20 @@ __global__ void __launch_bounds__(kBatchThreads, 3) k_batch_exec(const BatchTask
       }
       __syncthreads();
     }
+    if (threadIdx.x == 0) claimed = atomicAdd(next_item, 1ull);
     for (int c = threadIdx.x; c < (tile >> 1); c += blockDim.x) {
       const int i = c << 1;
       const long long g = (long long)base + run_off[i >> L] + (i & lowmask);
       const float2 x = sm[swz(i)], y = sm[swz(i + 1)];
       *reinterpret_cast<float4 *>(st + g) = make_float4(x.x, x.y, y.x, y.y);
     }
-    __threadfence();  // this thread's stores are visible device-wide before the tile is counted
+    // the barrier orders every thread's stores before thread 0's device-scope fence (which is
+    // cumulative), so the tile is visible device-wide before it is counted
     __syncthreads();
-    if (threadIdx.x == 0) atomicAdd(done + s_task, 1);
+    if (threadIdx.x == 0) {
+      __threadfence();
+      atomicAdd(done + s_task, 1);
+    }
   }
 }
 

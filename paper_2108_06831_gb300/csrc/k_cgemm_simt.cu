@@ -58,8 +58,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_cgemm_fp32(long long M, long lo
   constexpr int kLd = BK + 1;
   constexpr int kSlice = (BM + BN) * kLd, kTile = BM * (BN + 1);
   __shared__ float2 smem[2 * kSlice > kTile ? 2 * kSlice : kTile];
+  // tiles of one batch element along x, n fastest (M may need more than 65535 row tiles)
+  const long long tiles_n = (N + BN - 1) / BN;
   const long long b = blockIdx.z;
-  const long long m0 = (long long)blockIdx.y * BM, n0 = (long long)blockIdx.x * BN;
+  const long long m0 = ((long long)blockIdx.x / tiles_n) * BM, n0 = ((long long)blockIdx.x % tiles_n) * BN;
   const float2 *Ab = A + b * M * K;
   const float2 *Bb = B + b * N * K;
   float2 *Cb = C + b * M * N;
@@ -203,8 +205,9 @@ void build_staged(StagedMap &sm, const OutMap &om, long long M, long long N, int
 template <int BM, int BN, int BK, int TM, int TN>
 cudaError_t launch_shape(long long batch, long long M, long long N, long long K, const float2 *A, const float2 *B,
                          float2 *C, const OutMap &om, cudaStream_t s) {
-  dim3 grid((unsigned)((N + BN - 1) / BN), (unsigned)((M + BM - 1) / BM), (unsigned)batch);
-  if ((N + BN - 1) / BN > 0x7fffffffll || grid.y > 65535) return cudaErrorNotSupported;
+  const long long tiles = ((N + BN - 1) / BN) * ((M + BM - 1) / BM);
+  if (tiles > 0x7fffffffll) return cudaErrorNotSupported;
+  dim3 grid((unsigned)tiles, 1u, (unsigned)batch);
   StagedMap sm;
   std::memset(&sm, 0, sizeof(sm));
   sm.map = om;
@@ -213,16 +216,32 @@ cudaError_t launch_shape(long long batch, long long M, long long N, long long K,
   return cudaGetLastError();
 }
 
+// Tile shape (BM x BN) for an output of N columns.
+inline void tile_for(long long N, int *bm, int *bn) {
+  *bn = N <= 8 ? 8 : N <= 16 ? 16 : N <= 32 ? 32 : 64;
+  *bm = *bn == 64 ? 64 : 128;
+}
+
 template <int BK>
 cudaError_t launch_k(long long batch, long long M, long long N, long long K, const float2 *A, const float2 *B,
                      float2 *C, const OutMap &om, cudaStream_t s) {
-  if (N <= 8) return launch_shape<128, 8, BK, 2, 2>(batch, M, N, K, A, B, C, om, s);
-  if (N <= 16) return launch_shape<128, 16, BK, 4, 2>(batch, M, N, K, A, B, C, om, s);
-  if (N <= 32) return launch_shape<128, 32, BK, 4, 4>(batch, M, N, K, A, B, C, om, s);
+  int bm = 0, bn = 0;
+  tile_for(N, &bm, &bn);
+  if (bn == 8) return launch_shape<128, 8, BK, 2, 2>(batch, M, N, K, A, B, C, om, s);
+  if (bn == 16) return launch_shape<128, 16, BK, 4, 2>(batch, M, N, K, A, B, C, om, s);
+  if (bn == 32) return launch_shape<128, 32, BK, 4, 4>(batch, M, N, K, A, B, C, om, s);
   return launch_shape<64, 64, BK, 4, 4>(batch, M, N, K, A, B, C, om, s);
 }
 
 }  // namespace
+
+double cgemm_fp32_tile_fill(long long M, long long N) {
+  int bm = 0, bn = 0;
+  tile_for(N, &bm, &bn);
+  const double rows = (double)M / (double)(((M + bm - 1) / bm) * bm);
+  const double cols = (double)N / (double)(((N + bn - 1) / bn) * bn);
+  return rows * cols;
+}
 
 cudaError_t launch_cgemm_fp32(long long batch, long long M, long long N, long long K, const float2 *A, const float2 *B,
                               float2 *C, cudaStream_t s, const OutMap *om) {

@@ -49,6 +49,8 @@ struct OutMap {
   uint8_t pos[64] = {};
 };
 size_t cgemm_workspace(int precision, long long batch, long long M, long long N, long long K);
+// Fraction of the FP32 GEMM's tile work that falls inside an M x N output (its tile choice).
+double cgemm_fp32_tile_fill(long long M, long long N);
 cudaError_t launch_cgemm(int precision, long long batch, long long M, long long N, long long K, const float2 *A,
                          const float2 *B, float2 *C, void *ws, size_t ws_bytes, cudaStream_t s,
                          const OutMap *om = nullptr);

@@ -14,11 +14,18 @@
 //   - pairs of nodes sharing an index are merged greedily by size reduction (randomised
 //     trials, the best kept); an index carried by more than the two merged tensors (a
 //     hyperedge, e.g. the bitstring index) is a batch index of the merge;
-//   - each merge is lowered to two permutations (kernel b) that group its legs as
-//     [batch][free][contracted] and one batched complex GEMM (kernel c).
+//   - each merge is lowered to one batched complex GEMM (kernel c) whose operands are laid
+//     out as it reads them;
+//   - when no order found keeps every intermediate within the cap, indices are sliced: each
+//     chosen index is fixed to 0 and to 1 in turn, every slice is the network without it, and
+//     the amplitudes are the sum over all slices (exact: the full contraction sums over that
+//     index too).  Indices are picked greedily on the best order (the one shrinking the most
+//     largest intermediates, then the fewest flops), and the sliced network is planned again.
 #include <algorithm>
 #include <cmath>
 #include <complex>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <set>
@@ -67,6 +74,7 @@ tn_status build_network(const tn_circuit &c, int log2_batch, NetPlan &net, std::
   net = NetPlan();
   net.n = n;
   net.log2_batch = log2_batch;
+  net.call_log2 = log2_batch;
   net.label_dim.push_back(log2_batch);  // label 0: the bitstring index (2^log2_batch values)
   auto new_label = [&]() {
     net.label_dim.push_back(1);
@@ -158,14 +166,23 @@ tn_status build_network(const tn_circuit &c, int log2_batch, NetPlan &net, std::
 
 namespace {
 
+// Arithmetic intensity (complex flops 8 M N K per byte) above which a launched merge is taken
+// to be bound by arithmetic rather than by HBM in the order cost.
+constexpr double kRidge = 32.0;
+
 struct Trial {
   std::vector<NetStep> steps;
   std::vector<std::vector<int>> legs;
   int max_log2 = 0;
   double flops = 0;
-  // bytes read and written by the merges that depend on the bitstrings (their result carries
-  // the bitstring index, label 0): what a call costs once the rest is folded at plan time
-  double dyn_bytes = 0;
+  // cost of the merges that depend on the bitstrings (their result carries the bitstring index,
+  // label 0; the rest is folded at plan time): per merge max(bytes read and written,
+  // flops / kRidge), summed
+  double dyn_cost = 0;
+  // slicing of an order whose peak exceeds the cap: the indices, and the cost of all slices
+  bool sliceable = false;
+  std::vector<int> slices;
+  double sliced_cost = 0, sliced_flops = 0;
 };
 
 // Contraction state shared by the order heuristics: live tensors, index ownership, steps.
@@ -176,7 +193,12 @@ struct Contractor {
   std::map<int, std::vector<int>> where;  // label -> live tensors carrying it
   Trial tr;
   explicit Contractor(const NetPlan &n) : net(n) {
-    for (const NetNode &nd : net.nodes) legs.push_back(nd.legs);
+    for (const NetNode &nd : net.nodes) {  // sliced indices are not part of any slice's network
+      std::vector<int> l;
+      for (int x : nd.legs)
+        if (net.sliced.empty() || !net.sliced[(size_t)x]) l.push_back(x);
+      legs.push_back(l);
+    }
     live.assign(legs.size(), 1);
     for (size_t i = 0; i < legs.size(); ++i)
       for (int x : legs[i]) where[x].push_back((int)i);
@@ -221,10 +243,12 @@ struct Contractor {
     for (int x : legs[(size_t)bj])
       if (std::find(batch.begin(), batch.end(), x) == batch.end() && std::find(contr.begin(), contr.end(), x) == contr.end())
         nb += net.label_dim[(size_t)x];
-    tr.flops += 8.0 * std::ldexp(1.0, bits_of(batch) + mb + nb + bits_of(contr));
+    const double fl = 8.0 * std::ldexp(1.0, bits_of(batch) + mb + nb + bits_of(contr));
+    tr.flops += fl;
     if (std::find(res.begin(), res.end(), 0) != res.end())
-      tr.dyn_bytes += 8.0 * (std::ldexp(1.0, bits_of(res)) + std::ldexp(1.0, bits_of(legs[(size_t)bi])) +
-                             std::ldexp(1.0, bits_of(legs[(size_t)bj])));
+      tr.dyn_cost += std::max(8.0 * (std::ldexp(1.0, bits_of(res)) + std::ldexp(1.0, bits_of(legs[(size_t)bi])) +
+                                     std::ldexp(1.0, bits_of(legs[(size_t)bj]))),
+                              fl / kRidge);
     const int out = (int)legs.size();
     for (int x : legs[(size_t)bi]) {
       auto &w = where[x];
@@ -282,17 +306,29 @@ struct Contractor {
       }
     }
   }
-  // join whatever is left (connected only through the bitstring index)
+  // join whatever is left (connected only through the bitstring index); in a sliced network
+  // also the tensors left without any index (scalars), smallest pair first
   void finish() {
+    const bool by_size = !net.slices.empty();
     for (;;) {
       int bi = -1, bj = -1;
-      for (size_t i = 0; i < legs.size() && bj < 0; ++i) {
+      for (size_t i = 0; i < legs.size(); ++i) {
         if (!live[i]) continue;
-        if (bi < 0) bi = (int)i;
-        else bj = (int)i;
+        if (!by_size) {
+          if (bi < 0) bi = (int)i;
+          else if (bj < 0) bj = (int)i;
+          continue;
+        }
+        const int b = bits_of(legs[i]);
+        if (bi < 0 || b < bits_of(legs[(size_t)bi])) {
+          bj = bi;
+          bi = (int)i;
+        } else if (bj < 0 || b < bits_of(legs[(size_t)bj])) {
+          bj = (int)i;
+        }
       }
       if (bj < 0) break;
-      merge(bi, bj);
+      merge(std::min(bi, bj), std::max(bi, bj));
     }
     tr.legs = legs;
   }
@@ -345,13 +381,131 @@ void sweep_trial(const NetPlan &net, double temperature, uint64_t seed, Trial &t
 
 }  // namespace
 
-tn_status plan_network(NetPlan &net, int max_log2, std::string &err) {
-  // the deterministic greedy plus randomised trials.  Among orders whose largest intermediate
-  // fits the cap, keep the one moving the fewest bytes per call (launched merges are
-  // HBM-bound; bitstring-independent merges are folded at plan time), then the fewest flops;
-  // if none fits, keep the smallest peak (and report it).
+namespace {
+
+// Indices to slice so that every intermediate of `order` fits 2^max_log2 entries, one at a
+// time: among the indices of a largest tensor, the one leaving the smallest peak, then the
+// fewest tensors at that peak, then the fewest flops.  Fills order.slices and the cost of all
+// slices (the per-merge cost of Trial::dyn_cost with the sliced indices dropped, times the
+// number of slices); order.sliceable stays false if more than kMaxSliceBits would be needed.
+void choose_slices(const NetPlan &net, Trial &order, int max_log2) {
+  const size_t nt = order.legs.size(), nl = net.label_dim.size();
+  std::vector<int> size(nt, 0);
+  std::vector<std::vector<int>> tens_of(nl), merges_of(nl);
+  for (size_t t = 0; t < nt; ++t)
+    for (int x : order.legs[t]) {
+      size[t] += net.label_dim[(size_t)x];
+      tens_of[(size_t)x].push_back((int)t);
+    }
+  std::vector<int> ub(order.steps.size(), 0);  // bits of the union of both operands' legs
+  for (size_t k = 0; k < order.steps.size(); ++k) {
+    const NetStep &st = order.steps[k];
+    std::vector<int> u = order.legs[(size_t)st.a];
+    for (int x : order.legs[(size_t)st.b])
+      if (std::find(u.begin(), u.end(), x) == u.end()) u.push_back(x);
+    for (int x : u) {
+      ub[k] += net.label_dim[(size_t)x];
+      merges_of[(size_t)x].push_back((int)k);
+    }
+  }
+  std::vector<int> hist(130, 0);
+  for (int b : size) ++hist[(size_t)b];
+  std::vector<char> in_s(nl, 0);
+  order.slices.clear();
+  order.sliceable = false;
+  for (;;) {
+    int mx = 0;
+    for (int b = 129; b >= 0; --b)
+      if (hist[(size_t)b] > 0) {
+        mx = b;
+        break;
+      }
+    if (mx <= max_log2) break;
+    if ((int)order.slices.size() >= kMaxSliceBits) return;
+    int best_x = -1, best_m = 0, best_cnt = 0;
+    double best_gain = 0;
+    std::vector<char> seen(nl, 0);
+    for (size_t t = 0; t < nt; ++t) {
+      if (size[t] != mx) continue;
+      for (int x : order.legs[t]) {
+        if (x == 0 || in_s[(size_t)x] || seen[(size_t)x] || net.label_dim[(size_t)x] == 0) continue;
+        seen[(size_t)x] = 1;
+        int c_mx = 0, c_mx1 = 0;
+        for (int u : tens_of[(size_t)x]) {
+          c_mx += size[(size_t)u] == mx;
+          c_mx1 += size[(size_t)u] == mx - 1;
+        }
+        int m, cnt;
+        if (c_mx == hist[(size_t)mx]) {
+          m = mx - 1;
+          cnt = hist[(size_t)mx - 1] - c_mx1 + c_mx;
+        } else {
+          m = mx;
+          cnt = hist[(size_t)mx] - c_mx;
+        }
+        double gain = 0;  // flops of one slice saved by fixing x
+        for (int k : merges_of[(size_t)x]) gain += std::ldexp(1.0, ub[(size_t)k] - 1);
+        if (best_x < 0 || m < best_m || (m == best_m && (cnt < best_cnt || (cnt == best_cnt && gain > best_gain)))) {
+          best_x = x;
+          best_m = m;
+          best_cnt = cnt;
+          best_gain = gain;
+        }
+      }
+    }
+    if (best_x < 0) return;  // only the bitstring index is left on a largest tensor
+    in_s[(size_t)best_x] = 1;
+    order.slices.push_back(best_x);
+    for (int u : tens_of[(size_t)best_x]) {
+      --hist[(size_t)size[(size_t)u]];
+      --size[(size_t)u];
+      ++hist[(size_t)size[(size_t)u]];
+    }
+    for (int k : merges_of[(size_t)best_x]) --ub[(size_t)k];
+  }
+  order.sliceable = true;
+  const double n_slices = std::ldexp(1.0, (int)order.slices.size());
+  auto bits = [&](const std::vector<int> &ls) {
+    int b = 0;
+    for (int x : ls)
+      if (!in_s[(size_t)x]) b += net.label_dim[(size_t)x];
+    return b;
+  };
+  double cost = 0, flops = 0;
+  for (size_t k = 0; k < order.steps.size(); ++k) {
+    const NetStep &st = order.steps[k];
+    const double fl = 8.0 * std::ldexp(1.0, ub[k]);
+    flops += fl;
+    const std::vector<int> &res = order.legs[(size_t)st.out];
+    if (std::find(res.begin(), res.end(), 0) != res.end())
+      cost += std::max(8.0 * (std::ldexp(1.0, bits(res)) + std::ldexp(1.0, bits(order.legs[(size_t)st.a])) +
+                              std::ldexp(1.0, bits(order.legs[(size_t)st.b]))),
+                       fl / kRidge);
+  }
+  order.sliced_cost = cost * n_slices;
+  order.sliced_flops = flops * n_slices;
+}
+
+// Order preference: orders whose largest intermediate fits the cap first, the cheapest (then
+// the fewest flops); then orders that fit once sliced, the cheapest over all slices; then the
+// smallest peak.
+bool better_order(const Trial &tr, const Trial &best, int max_log2) {
+  const bool fits = tr.max_log2 <= max_log2, best_fits = best.max_log2 <= max_log2;
+  if (fits != best_fits) return fits;
+  if (fits) return tr.dyn_cost < best.dyn_cost || (tr.dyn_cost == best.dyn_cost && tr.flops < best.flops);
+  if (tr.sliceable != best.sliceable) return tr.sliceable;
+  if (tr.sliceable)
+    return tr.sliced_cost < best.sliced_cost || (tr.sliced_cost == best.sliced_cost && tr.sliced_flops < best.sliced_flops);
+  return tr.max_log2 < best.max_log2 || (tr.max_log2 == best.max_log2 && tr.flops < best.flops);
+}
+
+// The deterministic greedy plus randomised trials (greedy and qubit sweeps); the preferred one.
+// With `slice`, orders that exceed the cap are sliced to fit (choose_slices).  *min_peak (if
+// given) receives the smallest peak of any trial.
+Trial search_orders(const NetPlan &net, int max_log2, bool slice, int *min_peak = nullptr) {
   Trial best;
   bool have = false;
+  if (min_peak) *min_peak = 1 << 30;
   const int trials = 128;
   for (int t = 0; t < trials; ++t) {
     Trial tr;
@@ -359,21 +513,74 @@ tn_status plan_network(NetPlan &net, int max_log2, std::string &err) {
     const uint64_t seed = 0x9E3779B97F4A7C15ull * (uint64_t)(t + 1);
     if (t < trials / 2) greedy_trial(net, temp, seed, tr);
     else sweep_trial(net, temp, seed, tr);
-    const bool fits = tr.max_log2 <= max_log2, best_fits = have && best.max_log2 <= max_log2;
-    bool better;
-    if (!have) better = true;
-    else if (fits != best_fits) better = fits;
-    else if (!fits) better = tr.max_log2 < best.max_log2 || (tr.max_log2 == best.max_log2 && tr.flops < best.flops);
-    else better = tr.dyn_bytes < best.dyn_bytes || (tr.dyn_bytes == best.dyn_bytes && tr.flops < best.flops);
-    if (better) {
+    if (min_peak) *min_peak = std::min(*min_peak, tr.max_log2);
+    if (slice && tr.max_log2 > max_log2) choose_slices(net, tr, max_log2);
+    if (getenv("TNQ_DEBUG_NET"))
+      fprintf(stderr, "trial %d: peak %d flops %.3e cost %.3e sliced %d (%zu) cost %.3e\n", t, tr.max_log2, tr.flops,
+              tr.dyn_cost, (int)tr.sliceable, tr.slices.size(), tr.sliced_cost);
+    if (!have || better_order(tr, best, max_log2)) {
       best = std::move(tr);
       have = true;
     }
   }
+  return best;
+}
+
+// The merges of `order` (planned on the unsliced network) replayed on the sliced one.
+Trial replay_order(const NetPlan &net, const Trial &order) {
+  Contractor ct(net);
+  for (const NetStep &st : order.steps) ct.merge(st.a, st.b);
+  ct.finish();
+  return std::move(ct.tr);
+}
+
+}  // namespace
+
+tn_status plan_network(NetPlan &net, int max_log2, std::string &err) {
+  net.slices.clear();
+  net.sliced.assign(net.label_dim.size(), 0);
+  const int lb = net.call_log2;
+  auto set_batch = [&](int bits) {
+    net.log2_batch = bits;
+    net.label_dim[0] = bits;
+  };
+  set_batch(lb);
+  int min_peak = 0;
+  Trial best = search_orders(net, max_log2, true, &min_peak);
+  if (best.max_log2 > max_log2 && lb > 0) {
+    // Fewer bitstrings per pass: amplitudes of different bitstrings are independent, so a call
+    // may contract its bitstrings 2^j at a time (j passes' worth of launches, no extra flops in
+    // the merges that carry the bitstring index).  The j that brings the smallest peak within
+    // the cap is tried against slicing the whole batch; the cheaper over a full call is kept.
+    const int j = std::min(lb, min_peak - max_log2);
+    set_batch(lb - j);
+    Trial fewer = search_orders(net, max_log2, true);
+    auto usable = [&](const Trial &t) { return t.max_log2 <= max_log2 || t.sliceable; };
+    auto call_cost = [&](const Trial &t, int passes_log2) {
+      return std::ldexp(t.max_log2 <= max_log2 ? t.dyn_cost : t.sliced_cost, passes_log2);
+    };
+    if (usable(fewer) && (!usable(best) || call_cost(fewer, j) < call_cost(best, 0))) best = std::move(fewer);
+    else set_batch(lb);
+  }
+  if (best.max_log2 > max_log2) {
+    if (!best.sliceable) {
+      err = "network contraction would create a 2^" + std::to_string(best.max_log2) + "-entry intermediate (cap 2^" +
+            std::to_string(max_log2) + ") and more than 2^" + std::to_string(kMaxSliceBits) +
+            " slices would be needed to bring it within the cap";
+      return TN_ERR_UNSUPPORTED;
+    }
+    net.slices = best.slices;
+    for (int x : net.slices) net.sliced[(size_t)x] = 1;
+    // the order found above, on the sliced network, fits by construction; a search on the
+    // sliced network itself may find a cheaper one
+    Trial replay = replay_order(net, best);
+    Trial again = search_orders(net, max_log2, false);
+    best = better_order(again, replay, max_log2) ? std::move(again) : std::move(replay);
+  }
   net.steps = best.steps;
   net.all_legs = best.legs;
   net.max_log2 = best.max_log2;
-  net.flops = best.flops;
+  net.flops = std::ldexp(best.flops, (int)net.slices.size());
   if (net.max_log2 > max_log2) {
     err = "network contraction would create a 2^" + std::to_string(net.max_log2) + "-entry intermediate (cap 2^" +
           std::to_string(max_log2) + ")";

@@ -41,26 +41,40 @@ struct NetLaunch {
 
 // Constant folding budget (merges of bitstring-independent tensors evaluated at plan time).
 constexpr int kFoldMaxLog2 = 20;       // largest folded result: 2^20 entries
-constexpr double kFoldMaxWork = 2e8;   // complex multiply-adds over all folded merges
+constexpr double kFoldMaxWork = 2e8;   // complex multiply-adds over all folded merges (all slices)
+
+// Slicing: at most 2^16 slices; the constant table of all slices at most 2^27 entries.
+constexpr int kMaxSliceBits = 16;
+constexpr long long kMaxTableEntries = 1ll << 27;
 
 struct NetPlan {
   int n = 0;
-  int log2_batch = 0;
+  int log2_batch = 0;  // bitstrings contracted together (label 0 carries 2^log2_batch values)
+  int call_log2 = 0;   // bitstrings a call may pass: 2^(call_log2 - log2_batch) passes of the network
   std::vector<int> label_dim;  // bits per label (label 0 = bitstring index)
   std::vector<NetNode> nodes;
   std::vector<NetStep> steps;
   std::vector<std::vector<int>> all_legs;  // legs of every tensor id
-  int max_log2 = 0;
-  double flops = 0;  // 8 M N K summed over merges
+  int max_log2 = 0;   // largest intermediate of one slice
+  double flops = 0;  // 8 M N K summed over merges and slices
+  // Slicing, when no order keeps every intermediate within the cap: the indices in `slices`
+  // are fixed per slice (bit k of a slice number is the value of label slices[k]); a slice is
+  // the network without those indices, and the amplitudes are the sum of all slices' results.
+  std::vector<int> slices;
+  std::vector<char> sliced;           // per label: 1 if sliced (the planner drops it from every tensor)
+  std::vector<uint32_t> slice_dep;    // per tensor id: slice bits its value depends on
   // lowering
   std::vector<NetLaunch> launches;    // launched (bitstring-dependent) merges, in order
   int folded_merges = 0;              // merges evaluated at plan time
   std::vector<long long> tensor_off;  // workspace offset (complex64) of every tensor id, -1 if none
   std::vector<long long> table_off;   // offset in the static table (complex64), -1 if not there
+  std::vector<long long> table_stride;  // entries between two slice copies of a static operand
   std::vector<std::complex<double>> table_host;  // static operands of launched merges, as read
   std::vector<char> closure_trans;    // output closure stored [leg][b]
   size_t ws_bytes = 0;
   long long final_off = 0;
+  long long off_acc = -1;         // bytes offset of the FP64 slice sum (-1: one slice)
+  bool closures_sliced = false;   // some output closure depends on the slice (diagnostic listing)
   // device copies
   void *d_fixed = nullptr;   // complex64 fixed node table
   void *d_outputs = nullptr; // output-node descriptors

@@ -4,6 +4,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <functional>
 #include <map>
 #include <utility>
 #include <vector>
@@ -22,12 +23,14 @@ struct OutDesc {  // one output closure on the device
   int qubit;
   int has_leg;
   int trans;      // stored [leg][b] instead of [b][leg] (the order its merge reads)
-  int pad;
+  int slice_bit;  // the closed leg is sliced: its value is this bit of the slice number (else -1)
 };
 
-// u_q^b[i] = rows[2 x_q^b + i] (or the scalar rows[2 x_q^b]); padded bitstrings get zeros.
+// u_q^b[i] = rows[2 x_q^b + i] (or the scalar rows[2 x_q^b]; with a sliced leg the scalar
+// rows[2 x_q^b + v], v the leg's value in this slice); padded bitstrings get zeros.
 __global__ void k_build_outputs(const OutDesc *__restrict__ outs, int n_out, const uint64_t *__restrict__ xs,
-                                long long n_bits, long long B, int n_qubits, float2 *__restrict__ ws) {
+                                long long n_bits, long long B, int n_qubits, unsigned long long slice,
+                                float2 *__restrict__ ws) {
   const long long total = (long long)n_out * B;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
     const int o = (int)(i / B);
@@ -42,10 +45,46 @@ __global__ void k_build_outputs(const OutDesc *__restrict__ outs, int n_out, con
             pad ? make_float2(0.f, 0.f) : make_float2(d.rows[2 * r], d.rows[2 * r + 1]);
       }
     } else {
-      const int r = 2 * x;
+      const int r = 2 * x + (d.slice_bit >= 0 ? (int)((slice >> d.slice_bit) & 1ull) : 0);
       ws[d.off + b] = pad ? make_float2(0.f, 0.f) : make_float2(d.rows[2 * r], d.rows[2 * r + 1]);
     }
   }
+}
+
+// Slice sum (FP64): acc[b] (+)= x[b] for the amplitudes of one slice.
+__global__ void k_slice_sum(double2 *__restrict__ acc, const float2 *__restrict__ x, long long n, int first) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const float2 v = x[i];
+    if (first) {
+      acc[i] = make_double2((double)v.x, (double)v.y);
+    } else {
+      const double2 a = acc[i];
+      acc[i] = make_double2(a.x + (double)v.x, a.y + (double)v.y);
+    }
+  }
+}
+
+__global__ void k_slice_store(float2 *__restrict__ amps, const double2 *__restrict__ acc, long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double2 a = acc[i];
+    amps[i] = make_float2((float)a.x, (float)a.y);
+  }
+}
+
+// bits of s at the set positions of mask, packed (the index of a slice copy)
+inline long long pack_bits(unsigned long long s, uint32_t mask) {
+  long long r = 0;
+  int k = 0;
+  for (int p = 0; p < 32; ++p)
+    if ((mask >> p) & 1u) r |= (long long)((s >> p) & 1ull) << k++;
+  return r;
+}
+inline unsigned long long unpack_bits(long long c, uint32_t mask) {
+  unsigned long long s = 0;
+  int k = 0;
+  for (int p = 0; p < 32; ++p)
+    if ((mask >> p) & 1u) s |= (unsigned long long)((c >> k++) & 1) << p;
+  return s;
 }
 
 struct Allocator {
@@ -87,6 +126,8 @@ bool tc_ok(int precision, long long M, long long N, long long K) {
   if (precision == TN_PREC_FP32) return false;
   return M % 128 == 0 && N % 64 == 0 && K % (precision == TN_PREC_3XTF32 ? 2 : 4) == 0;
 }
+// rows the tensor-core launch takes (its row tiles index the grid's y dimension)
+bool tc_rows_ok(long long M) { return M / 128 <= 65535; }
 
 }  // namespace
 
@@ -147,6 +188,28 @@ std::vector<std::complex<double>> reorder_host(const std::vector<std::complex<do
   return y;
 }
 
+// A fixed node's data in one slice: sliced legs take their slice value, the others stay.
+static std::vector<std::complex<double>> restrict_node(const NetPlan &net, const NetNode &nd, unsigned long long s) {
+  const int nl = (int)nd.legs.size();
+  long long fixed = 0;
+  std::vector<long long> keep;
+  for (int p = 0; p < nl; ++p) {
+    const long long stride = 1ll << (nl - 1 - p);
+    const auto it = std::find(net.slices.begin(), net.slices.end(), nd.legs[(size_t)p]);
+    if (it == net.slices.end()) keep.push_back(stride);
+    else if ((s >> (it - net.slices.begin())) & 1ull) fixed += stride;
+  }
+  const int nk = (int)keep.size();
+  std::vector<std::complex<double>> out(1ull << nk);
+  for (long long o = 0; o < (1ll << nk); ++o) {
+    long long i = fixed;
+    for (int p = 0; p < nk; ++p)
+      if ((o >> (nk - 1 - p)) & 1) i += keep[(size_t)p];
+    out[(size_t)o] = nd.data[(size_t)i];
+  }
+  return out;
+}
+
 tn_status lower_network(NetPlan &net, int precision, std::string &err) {
   const int n_init = (int)net.nodes.size();
   const size_t n_steps = net.steps.size();
@@ -166,27 +229,35 @@ tn_status lower_network(NetPlan &net, int precision, std::string &err) {
   std::vector<int> producer((size_t)n_tensors, -1);
   for (size_t si = 0; si < n_steps; ++si) producer[(size_t)net.steps[si].out] = (int)si;
 
+  // Slice dependence: a tensor's value depends on the slice bits of the sliced legs of the
+  // nodes below it.
+  net.slice_dep.assign((size_t)n_tensors, 0u);
+  for (int id = 0; id < n_init; ++id)
+    for (int x : net.nodes[(size_t)id].legs)
+      for (size_t k = 0; k < net.slices.size(); ++k)
+        if (net.slices[k] == x) net.slice_dep[(size_t)id] |= 1u << k;
+  for (const NetStep &st : net.steps)
+    net.slice_dep[(size_t)st.out] = net.slice_dep[(size_t)st.a] | net.slice_dep[(size_t)st.b];
+  auto copies = [&](int id) { return 1ll << __builtin_popcount(net.slice_dep[(size_t)id]); };
+  net.closures_sliced = false;
+  for (int id = 0; id < n_init; ++id)
+    net.closures_sliced |= net.nodes[(size_t)id].kind == NODE_OUTPUT && net.slice_dep[(size_t)id] != 0;
+
   // 1. Constant folding.  A tensor that does not depend on the bitstrings (the gate tensors
   // and every merge of two such tensors) is the same for every call: those merges are
-  // evaluated once here, in FP64, within a size and work budget.
+  // evaluated once at plan time, in FP64 (one copy per slice it depends on), within a size
+  // and work budget.  Here the merges are chosen; their values are computed with the table.
   std::vector<char> is_static((size_t)n_tensors, 0), folded(n_steps, 0);
   for (int id = 0; id < n_init; ++id) is_static[(size_t)id] = net.nodes[(size_t)id].kind == NODE_FIXED;
-  std::vector<std::vector<std::complex<double>>> sdata((size_t)n_tensors);
-  for (int id = 0; id < n_init; ++id)
-    if (is_static[(size_t)id]) sdata[(size_t)id] = net.nodes[(size_t)id].data;
   double fold_work = 0;
   net.folded_merges = 0;
   for (size_t si = 0; si < n_steps; ++si) {
     const NetStep &st = net.steps[si];
     if (!is_static[(size_t)st.a] || !is_static[(size_t)st.b]) continue;
     const int ob = bits_of(net.all_legs[(size_t)st.out]), cb = bits_of(st.contr);
-    const double work = std::ldexp(1.0, ob + cb);
+    const double work = std::ldexp(1.0, ob + cb) * (double)copies(st.out);
     if (ob > kFoldMaxLog2 || fold_work + work > kFoldMaxWork) continue;
     fold_work += work;
-    sdata[(size_t)st.out] = contract_host(net.all_legs[(size_t)st.a], sdata[(size_t)st.a], net.all_legs[(size_t)st.b],
-                                          sdata[(size_t)st.b], st.contr, net.all_legs[(size_t)st.out]);
-    sdata[(size_t)st.a].clear();
-    sdata[(size_t)st.b].clear();
     is_static[(size_t)st.out] = 1;
     folded[si] = 1;
     ++net.folded_merges;
@@ -273,20 +344,74 @@ tn_status lower_network(NetPlan &net, int precision, std::string &err) {
     L.M = 1ll << bits_of(free_a);
     L.N = 1ll << bits_of(free_b);
     L.K = 1ll << bits_of(contr);
-    L.precision = tc_ok(precision, L.M, L.N, L.K) ? precision : TN_PREC_FP32;
+    // The GEMM computes C = A B^T with both operands K-contiguous, so the transposed product
+    // B A^T is the same kernel with the operands exchanged; its natural output index
+    // (b N + n) M + m goes to the same stored positions.  Exchanged when the tiles then fit
+    // the shape better: tensor-core tiles only after the exchange, or, on the CUDA cores, a
+    // short row dimension against a long column one (slicing leaves such merges).
+    const bool tc_as_is = tc_ok(precision, L.M, L.N, L.K), tc_swapped = tc_ok(precision, L.N, L.M, L.K) && tc_rows_ok(L.N);
+    const bool swap = !tc_as_is && (tc_swapped || cgemm_fp32_tile_fill(L.N, L.M) > cgemm_fp32_tile_fill(L.M, L.N));
+    if (swap) {
+      const int lgm = bits_of(free_a), lgn = bits_of(free_b);
+      OutMap t = L.out_map;
+      t.identity = 1;
+      for (int i = 0; i < L.out_map.nbits; ++i) {  // bit i of the exchanged product's index
+        const int f = i < lgm ? lgn + i : (i < lgm + lgn ? i - lgm : i);
+        t.pos[i] = L.out_map.pos[f];
+        t.identity &= t.pos[i] == i;
+      }
+      L.out_map = t;
+      std::swap(L.a_id, L.b_id);
+      std::swap(L.M, L.N);
+    }
+    L.precision = tc_ok(precision, L.M, L.N, L.K) && tc_rows_ok(L.M) ? precision : TN_PREC_FP32;
   }
 
-  // 3. The table of static operands of launched merges, each in the order its merge reads.
+  // 3. The table of static operands of launched merges, each in the order its merge reads,
+  // one copy per combination of the slice bits it depends on.
+  std::map<std::pair<int, unsigned long long>, std::vector<std::complex<double>>> memo;
+  std::vector<int> step_of((size_t)n_tensors, -1);
+  for (size_t si = 0; si < n_steps; ++si) step_of[(size_t)net.steps[si].out] = (int)si;
+  std::function<const std::vector<std::complex<double>> &(int, unsigned long long)> value =
+      [&](int id, unsigned long long sl) -> const std::vector<std::complex<double>> & {
+    sl &= net.slice_dep[(size_t)id];
+    const auto key = std::make_pair(id, sl);
+    auto it = memo.find(key);
+    if (it != memo.end()) return it->second;
+    std::vector<std::complex<double>> v;
+    if (id < n_init) {
+      v = restrict_node(net, net.nodes[(size_t)id], sl);
+    } else {
+      const NetStep &st = net.steps[(size_t)step_of[(size_t)id]];
+      const std::vector<std::complex<double>> &A = value(st.a, sl);
+      const std::vector<std::complex<double>> &Bv = value(st.b, sl);
+      v = contract_host(net.all_legs[(size_t)st.a], A, net.all_legs[(size_t)st.b], Bv, st.contr,
+                        net.all_legs[(size_t)st.out]);
+    }
+    return memo.emplace(key, std::move(v)).first->second;
+  };
   net.table_off.assign((size_t)n_tensors, -1);
+  net.table_stride.assign((size_t)n_tensors, 0);
   net.table_host.clear();
   for (const NetLaunch &L : net.launches)
     for (int id : {L.a_id, L.b_id}) {
       if (!is_static[(size_t)id]) continue;
-      const std::vector<std::complex<double>> d =
-          reorder_host(sdata[(size_t)id], net.all_legs[(size_t)id], target[(size_t)id]);
+      const long long entries = 1ll << bits_of(net.all_legs[(size_t)id]);
+      const long long stride = (entries + 31) & ~31ll;  // 256-byte alignment
+      if ((long long)net.table_host.size() + stride * copies(id) > kMaxTableEntries) {
+        err = "the constant operands of all slices exceed 2^27 entries";
+        return TN_ERR_UNSUPPORTED;
+      }
       net.table_off[(size_t)id] = (long long)net.table_host.size();
-      net.table_host.insert(net.table_host.end(), d.begin(), d.end());
-      net.table_host.resize((net.table_host.size() + 31) & ~(size_t)31);  // 256-byte alignment
+      net.table_stride[(size_t)id] = stride;
+      for (long long c = 0; c < copies(id); ++c) {
+        const std::vector<std::complex<double>> d =
+            reorder_host(value(id, unpack_bits(c, net.slice_dep[(size_t)id])), net.all_legs[(size_t)id],
+                         target[(size_t)id]);
+        net.table_host.insert(net.table_host.end(), d.begin(), d.end());
+        net.table_host.resize((size_t)(net.table_off[(size_t)id] + (c + 1) * stride));
+      }
+      memo.clear();  // every tensor has one consumer: nothing below this operand is read again
     }
 
   // 4. Workspace, in execution order: output closures, then every launched result (operands
@@ -312,7 +437,8 @@ tn_status lower_network(NetPlan &net, int precision, std::string &err) {
       if (net.tensor_off[(size_t)id] >= 0) al.release((size_t)net.tensor_off[(size_t)id] * sizeof(float2), bytes_of(id));
   }
   if (getenv("TNQ_DEBUG_NET")) {  // diagnostic listing of the lowered merges (stderr)
-    fprintf(stderr, "folded %d of %zu merges\n", net.folded_merges, n_steps);
+    fprintf(stderr, "folded %d of %zu merges; %zu sliced indices (output closures sliced: %d), constant table %zu entries\n",
+            net.folded_merges, n_steps, net.slices.size(), (int)net.closures_sliced, net.table_host.size());
     for (const NetLaunch &L : net.launches) {
       fprintf(stderr, "merge %d x %d -> %d: batch %lld M %lld N %lld K %lld prec %d static %d/%d map %d gflop %.3f",
               L.a_id, L.b_id, L.out_id, L.batch, L.M, L.N, L.K, L.precision, (int)is_static[(size_t)L.a_id],
@@ -331,6 +457,11 @@ tn_status lower_network(NetPlan &net, int precision, std::string &err) {
     return TN_ERR_UNSUPPORTED;
   }
   net.final_off = net.tensor_off[(size_t)net.launches.back().out_id];
+  net.off_acc = -1;
+  if (!net.slices.empty()) {  // FP64 slice sum after the contraction's own workspace
+    net.off_acc = (long long)((hw + 255) & ~(size_t)255);
+    hw = (size_t)net.off_acc + (sizeof(double2) << net.log2_batch);
+  }
   net.ws_bytes = hw + 256;
   return TN_OK;
 }
@@ -351,8 +482,12 @@ tn_status upload_network(NetPlan &net, std::string &err) {
     }
     d.off = net.tensor_off[id];
     d.qubit = nd.qubit;
-    d.has_leg = nd.legs.size() == 2 ? 1 : 0;
+    d.has_leg = net.all_legs[id].size() == 2 ? 1 : 0;  // legs of the (sliced) network
     d.trans = net.closure_trans[id] ? 1 : 0;
+    d.slice_bit = -1;
+    if (nd.legs.size() == 2)
+      for (size_t k = 0; k < net.slices.size(); ++k)
+        if (net.slices[k] == nd.legs[1]) d.slice_bit = (int)k;
     outs.push_back(d);
   }
   net.n_outputs = (int)outs.size();
@@ -380,24 +515,50 @@ cudaError_t run_network(const NetPlan &net, const uint64_t *bitstrings, long lon
   const long long B = 1ll << net.log2_batch;
   float2 *w = static_cast<float2 *>(ws);
   const float2 *fixed = static_cast<const float2 *>(net.d_fixed);
-  if (net.n_outputs > 0) {
-    const long long total = (long long)net.n_outputs * B;
-    k_build_outputs<<<(unsigned)std::min<long long>((total + 255) / 256, 65535), 256, 0, s>>>(
-        static_cast<const OutDesc *>(net.d_outputs), net.n_outputs, bitstrings, n_bits, B, net.n, w);
-    cudaError_t e = cudaGetLastError();
+  const unsigned long long n_slices = 1ull << net.slices.size();
+  double2 *acc = net.off_acc >= 0 ? reinterpret_cast<double2 *>(static_cast<char *>(ws) + net.off_acc) : nullptr;
+  // the call's bitstrings, B at a time
+  for (long long c0 = 0; c0 < n_bits; c0 += B) {
+    const long long nb = std::min(B, n_bits - c0);
+    const uint64_t *xs = bitstrings + c0;
+    const unsigned grid_b = (unsigned)std::min<long long>((nb + 255) / 256, 1024);
+    for (unsigned long long sl = 0; sl < n_slices; ++sl) {
+      // every slice: the closures' buffers are reused by later merges of the slice before
+      if (net.n_outputs > 0) {
+        const long long total = (long long)net.n_outputs * B;
+        k_build_outputs<<<(unsigned)std::min<long long>((total + 255) / 256, 65535), 256, 0, s>>>(
+            static_cast<const OutDesc *>(net.d_outputs), net.n_outputs, xs, nb, B, net.n, sl, w);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+      }
+      auto ptr = [&](int id) -> const float2 * {
+        if (net.table_off[(size_t)id] >= 0)
+          return fixed + net.table_off[(size_t)id] +
+                 pack_bits(sl, net.slice_dep[(size_t)id]) * net.table_stride[(size_t)id];
+        return w + net.tensor_off[(size_t)id];
+      };
+      for (const NetLaunch &L : net.launches) {
+        void *gws = L.off_gemm_ws >= 0 ? static_cast<void *>(static_cast<char *>(ws) + L.off_gemm_ws) : nullptr;
+        cudaError_t e = launch_cgemm(L.precision, L.batch, L.M, L.N, L.K, ptr(L.a_id), ptr(L.b_id), w + L.off_out,
+                                     gws, L.gemm_ws_bytes, s, &L.out_map);
+        if (e != cudaSuccess) return e;
+      }
+      if (acc) {
+        k_slice_sum<<<grid_b, 256, 0, s>>>(acc, w + net.final_off, nb, sl == 0 ? 1 : 0);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+      }
+    }
+    cudaError_t e;
+    if (acc) {
+      k_slice_store<<<grid_b, 256, 0, s>>>(amps + c0, acc, nb);
+      e = cudaGetLastError();
+    } else {
+      e = cudaMemcpyAsync(amps + c0, w + net.final_off, sizeof(float2) * (size_t)nb, cudaMemcpyDeviceToDevice, s);
+    }
     if (e != cudaSuccess) return e;
   }
-  auto ptr = [&](int id) -> const float2 * {
-    if (net.table_off[(size_t)id] >= 0) return fixed + net.table_off[(size_t)id];
-    return w + net.tensor_off[(size_t)id];
-  };
-  for (const NetLaunch &L : net.launches) {
-    void *gws = L.off_gemm_ws >= 0 ? static_cast<void *>(static_cast<char *>(ws) + L.off_gemm_ws) : nullptr;
-    cudaError_t e = launch_cgemm(L.precision, L.batch, L.M, L.N, L.K, ptr(L.a_id), ptr(L.b_id), w + L.off_out, gws,
-                                 L.gemm_ws_bytes, s, &L.out_map);
-    if (e != cudaSuccess) return e;
-  }
-  return cudaMemcpyAsync(amps, w + net.final_off, sizeof(float2) * (size_t)n_bits, cudaMemcpyDeviceToDevice, s);
+  return cudaSuccess;
 }
 
 }  // namespace tnq

@@ -108,3 +108,26 @@ def test_network_plan_rejects_bad_options():
     chp = tn.CircuitHandle(C.brickwork(6, 2, 1, parameterized=True)[0])
     with pytest.raises(tn.TnError):  # network plans take fixed angles
         tn.Plan(chp, target=tn.TARGET_AMPLITUDES, host_only=True, network_bitstrings=16)
+
+
+def test_network_plan_capped_host_only():
+    """A cap below every contraction order's peak: bitstrings are contracted in smaller passes
+    and/or indices sliced until the largest intermediate fits; a cap that no slicing within
+    2^16 slices reaches is rejected; the default cap needs neither."""
+    from paper_2108_06831_gb300 import tn
+    ch = tn.CircuitHandle(C.grid(5, 5, 10, 7))
+    kw = dict(target=tn.TARGET_AMPLITUDES, host_only=True, network_bitstrings=16, precision=tn.PREC_3XTF32)
+    whole = tn.Plan(ch, **kw).stats()
+    assert whole["net_sliced"] == 0 and whole["net_batch_log2"] == 4
+    prev_batch, prev_sliced = 4, 0
+    for cap in (16, 14, 12, 10, 8, 6):
+        s = tn.Plan(ch, max_intermediate_log2=cap, **kw).stats()
+        assert s["net_max_log2"] <= cap and s["net_sliced"] <= 16
+        assert s["net_batch_log2"] < 4 or s["net_sliced"] > 0
+        # tighter caps never take larger passes or fewer slices here
+        assert s["net_batch_log2"] <= prev_batch and s["net_sliced"] >= prev_sliced
+        prev_batch, prev_sliced = s["net_batch_log2"], s["net_sliced"]
+    assert prev_sliced > 0 and prev_batch == 0
+    with pytest.raises(tn.TnError) as e:
+        tn.Plan(ch, max_intermediate_log2=4, **kw)
+    assert e.value.status == tn.ERR_UNSUPPORTED

@@ -78,3 +78,9 @@ def test_cgemm_unsupported_tensor_shape():
     with pytest.raises(tn.TnError) as e:
         tn.cgemm_batched(1, 1, 100, 64, 16, a, b, c)
     assert e.value.status == tn.ERR_UNSUPPORTED
+
+
+def test_cgemm_fp32_more_than_65535_row_tiles():
+    """A tall, narrow product (8.4M rows, 3 columns, K 5: more than 65535 row tiles of 128 rows,
+    ragged in every dimension), as operand exchange in network merges produces."""
+    assert _run(0, 1, (1 << 23) + 200, 3, 5, seed=11) <= TOL

@@ -11,10 +11,11 @@ torch = pytest.importorskip("torch")
 TOL = 1e-5
 
 
-def _amps(circ, xs, B, precision):
+def _amps(circ, xs, B, precision, max_log2=0):
     from paper_2108_06831_gb300 import tn
     ch = tn.CircuitHandle(circ)
-    p = tn.Plan(ch, target=tn.TARGET_AMPLITUDES, network_bitstrings=B, precision=precision)
+    p = tn.Plan(ch, target=tn.TARGET_AMPLITUDES, network_bitstrings=B, precision=precision,
+                max_intermediate_log2=max_log2)
     ws = torch.empty(max(p.workspace_bytes, 16), dtype=torch.uint8, device="cuda")
     x = torch.as_tensor(np.asarray(xs, dtype=np.uint64).astype(np.int64), device="cuda")
     out = torch.full((len(xs),), complex(float("nan"), 0), dtype=torch.complex64, device="cuda")
@@ -93,3 +94,45 @@ def test_cfg3_grid_6x6_depth12_sampled():
     assert _rel(got[:3], ref) <= TOL
     pt = float(np.mean(np.abs(got.astype(np.complex128)) ** 2) * 2.0 ** 36)
     assert 0.5 < pt < 1.6
+
+
+@pytest.mark.parametrize("maker,B,n,cap,route", [
+    (lambda: C.grid(3, 4, 8, 2), 4, 3, 5, "both"),            # 1 bitstring per pass, 3 sliced indices
+    (lambda: C.random_circuit(10, 120, 5), 4, 4, 7, "slice"),  # 5 sliced indices, output closures among them
+    (lambda: C.random_circuit(10, 120, 5), 1, 1, 6, "slice"),  # one bitstring per call
+    (lambda: C.grid(4, 4, 8, 11), 8, 7, 8, "chunk"),          # 1 bitstring per pass, no slicing
+    (lambda: C.qft(8, 77), 4, 4, 5, "slice"),
+])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_capped_contraction(maker, B, n, cap, route, precision):
+    """A cap below every order's peak: the planner contracts the bitstrings in smaller passes
+    and/or slices indices (each slice contracted, the slices' amplitudes summed in FP64).
+    Both are exact, so the bar is the same as for an uncapped plan; the largest intermediate
+    obeys the cap.  n < B leaves padded bitstrings in the last pass."""
+    from oracle.statevector import simulate_state
+    c = maker()
+    psi = simulate_state(c)
+    xs = C.random_bitstrings(c.n_qubits, n, 4000 + cap)
+    got, st = _amps(c, xs, B, precision, max_log2=cap)
+    assert st["net_max_log2"] <= cap
+    sliced, chunked = st["net_sliced"] > 0, (1 << st["net_batch_log2"]) < B
+    assert (sliced, chunked) == {"slice": (True, False), "chunk": (False, True), "both": (True, True)}[route]
+    assert _rel(got, psi[xs.astype(np.int64)]) <= TOL
+
+
+@pytest.mark.parametrize("cap", [14, 10])
+def test_capped_grid_5x5(cap):
+    """25 qubits, 16 bitstrings per call with 13 passed: cap 2^14 takes passes of 2 bitstrings
+    (the last one padded), cap 2^10 passes of one bitstring with 4 sliced indices; against the
+    oracle's FP64 sweep, and the same amplitudes as the uncapped plan."""
+    from oracle.tn import contract_amplitude_sweep
+    c = C.grid(5, 5, 10, 7)
+    xs = C.random_bitstrings(25, 13, 4100)
+    got, st = _amps(c, xs, 16, 1, max_log2=cap)
+    assert st["net_max_log2"] <= cap and st["net_batch_log2"] < 4
+    assert (st["net_sliced"] > 0) == (cap == 10)
+    ref = np.array([contract_amplitude_sweep(c, int(x)) for x in xs[:4]])
+    assert _rel(got[:4], ref) <= TOL
+    whole, st0 = _amps(c, xs, 16, 1)
+    assert st0["net_sliced"] == 0 and st0["net_batch_log2"] == 4
+    assert _rel(got, whole) <= TOL
