@@ -42,7 +42,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="state24",
                     choices=["state24", "state10", "grad20", "gemm_fp32", "gemm_3xtf32", "gemm_bf16x3",
-                             "serving512", "amps36", "permute28", "gemm_merge", "fig31"])
+                             "serving512", "amps36", "permute28", "gemm_merge", "fig31", "fig31amps"])
     ap.add_argument("--batch", type=int, default=0, help="gemm workloads: batch override (small profiling cases)")
     ap.add_argument("--legs", type=int, default=0, help="permute28: tensor legs override (small profiling cases)")
     ap.add_argument("--prec", type=int, default=1, help="amps36: GEMM precision (0 FP32, 1 3xTF32, 2 split BF16)")
@@ -170,7 +170,7 @@ import numpy as np
 from paper_2108_06831_gb300 import circuits as C
 from oracle.statevector import basis_state, apply_matrix, gate_matrix, simulate_state
 from oracle import observables as OB
-from oracle.tn import contract_amplitude_sweep
+from oracle.tn import contract_amplitude, contract_amplitude_sweep
 kind, budget = {kind!r}, {budget}
 t0 = time.perf_counter()
 if kind == "state":
@@ -228,10 +228,23 @@ elif kind == "sweep":
     dt = time.perf_counter() - t0
     out = dict(value=amps / dt, unit="amplitudes/s", seconds=dt,
                sample=f"FP64 state-vector oracle, the {{done}} smallest of the 98 Fig. 3.1 circuits ({{dt:.1f}} s)")
+elif kind == "sweep_amps":
+    pts = [(n, k) for n in range(2, 29, 2) for k in range(2, 15, 2)]
+    done = 0
+    for i, (n, k) in enumerate(pts):  # one bitstring per point, until the budget is spent
+        if done and time.perf_counter() - t0 > budget:
+            break
+        c = C.paper_fig31(n, k, {seed} + i)
+        contract_amplitude(c, int(C.random_bitstrings(n, 1, {seed} + 500 + i)[0]))
+        done += 1
+    dt = time.perf_counter() - t0
+    out = dict(value=done / dt, unit="amplitudes/s", seconds=dt,
+               sample=f"FP64 oracle greedy network contraction, one amplitude of each of the first {{done}} "
+                      f"of the 98 Fig. 3.1 circuits ({{dt:.1f}} s)")
 print(json.dumps(out))
 """
 
-ORACLE_KINDS = ("state", "grad", "amps", "serve", "sweep")
+ORACLE_KINDS = ("state", "grad", "amps", "serve", "sweep", "sweep_amps")
 
 
 def run_oracle_sample(kind: str, n: int, depth: int, seed: int, budget: float, threads: int = 1):
@@ -265,6 +278,9 @@ WORKLOADS = {
     # the paper's Fig. 3.1 test circuits: n in {2, 4, ..., 28} qubits, k in {2, 4, ..., 14} rounds,
     # full states; a step contracts all 98 of them
     "fig31": dict(kind="sweep", n=28, depth=14, seed=6000, batch=98),
+    # the same 98 circuits in amplitude mode: 64 seeded bitstrings each, by network contraction
+    # (3xTF32 merges, one plan per circuit sized for 64 bitstrings per call)
+    "fig31amps": dict(kind="sweep_amps", n=28, depth=14, seed=6000, batch=98, chunk=64, prec=1),
     "grad20": dict(kind="grad", n=20, depth=10, seed=4000, batch=64),
 }
 
@@ -435,6 +451,47 @@ def main():
             per_pass += n_slices + 1
         per_call = per_pass * (chunk >> nst["net_batch_log2"])
         launches_per_step = per_call * (batch // chunk)
+        kernel_only = None
+    elif wl["kind"] == "sweep_amps":
+        pts = [(n, k) for n in range(2, 29, 2) for k in range(2, 15, 2)]
+        chunk = wl["chunk"]
+        nplans, nws, nxs, nout, plan_s = {}, {}, {}, {}, {}
+        for i, (n, k) in enumerate(pts):
+            t0 = time.perf_counter()
+            nplans[(n, k)] = tn.Plan(tn.CircuitHandle(C.paper_fig31(n, k, wl["seed"] + i)),
+                                     target=tn.TARGET_AMPLITUDES, network_bitstrings=chunk, precision=1)
+            plan_s[(n, k)] = time.perf_counter() - t0
+            nws[(n, k)] = torch.empty(max(nplans[(n, k)].workspace_bytes, 16), dtype=torch.uint8, device=dev)
+            nxs[(n, k)] = torch.as_tensor(C.random_bitstrings(n, chunk, wl["seed"] + 1000 + i).astype(np.int64),
+                                          device=dev)
+            nout[(n, k)] = torch.empty(chunk, dtype=torch.complex64, device=dev)
+        batch = len(pts)
+        units_per_step = float(chunk * len(pts))
+        unit = "amplitudes/s"
+        ctr = None
+
+        def eager_step():
+            for key in pts:
+                tn.contract_amplitudes(nplans[key], None, nxs[key], nout[key], nws[key])
+        # the 98 calls (their closure kernels, merges and copies) captured once in a CUDA graph;
+        # a step replays it
+        eager_step()
+        torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        cap = torch.cuda.Stream(device=dev)
+        with torch.cuda.stream(cap):
+            with torch.cuda.graph(graph, stream=cap):
+                eager_step()
+        torch.cuda.synchronize()
+
+        def step():
+            graph.replay()
+        launches_per_step = 0
+        for key in pts:
+            st = nplans[key].stats()
+            sl = 1 << st["net_sliced"]
+            per_pass = sl * (1 + st["net_merges"] + st["net_tensor_merges"]) + (sl + 1 if sl > 1 else 0)
+            launches_per_step += per_pass * (chunk >> st["net_batch_log2"])
         kernel_only = None
     elif wl["kind"] == "sweep":
         pts = [(n, k) for n in range(2, 29, 2) for k in range(2, 15, 2)]
@@ -638,6 +695,21 @@ def main():
         ems = timed(e2e_step, args.steps)
         line["e2e"] = {"value": units_per_step * args.steps / (sum(ems) / 1000), "unit": unit,
                        "h2d_bytes_per_step": int(h_xs.numel() * 8), "d2h_bytes_per_step": int(h_amps.numel() * 8)}
+    if not args.no_e2e and wl["kind"] == "sweep_amps":
+        h_xs = {key: nxs[key].cpu().pin_memory() for key in pts}
+        h_amps = {key: torch.empty(chunk, dtype=torch.complex64).pin_memory() for key in pts}
+
+        def e2e_step():
+            for key in pts:
+                nxs[key].copy_(h_xs[key], non_blocking=True)
+                tn.contract_amplitudes(nplans[key], None, nxs[key], nout[key], nws[key])
+                h_amps[key].copy_(nout[key], non_blocking=True)
+        for _ in range(3):
+            e2e_step()
+        ems = timed(e2e_step, args.steps)
+        line["e2e"] = {"value": units_per_step * args.steps / (sum(ems) / 1000), "unit": unit,
+                       "h2d_bytes_per_step": int(sum(v.numel() for v in h_xs.values()) * 8),
+                       "d2h_bytes_per_step": int(sum(v.numel() for v in h_amps.values()) * 8)}
     if wl["kind"] == "amps":
         per_step_s = t_max / args.steps / 1000.0
         a = amps.cpu().numpy().astype(np.complex128)
@@ -724,6 +796,41 @@ def main():
                             "frac": tfl / FP32_ALU_PEAK_TFLOPS, "traffic": None,
                             "kernel": "tnq_p* (fused gate-apply), Fig. 3.1 circuit n=28 k=14",
                             "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 x 2070 MHz"}
+    if wl["kind"] == "sweep_amps":
+        # per point: amplitudes/s of its call timed on its own, planning time (host), plan shape;
+        # roofline: the algorithmic bytes of every launched merge of the step against HBM
+        per_point = {}
+        for key in pts:
+            pl = nplans[key]
+
+            def one():
+                tn.contract_amplitudes(pl, None, nxs[key], nout[key], nws[key])
+            for _ in range(2):
+                one()
+            pms = statistics.mean(timed(one, max(2, args.steps)))
+            st = pl.stats()
+            per_point[f"n{key[0]}_k{key[1]}"] = {
+                "amplitudes_per_s": round(chunk / (pms / 1000.0), 1), "plan_s": round(plan_s[key], 3),
+                "merges": st["net_merges"], "bitstrings_per_pass": 1 << st["net_batch_log2"],
+                "largest_intermediate_log2": st["net_max_log2"]}
+        per_step_s = t_max / args.steps / 1000.0
+        step_bytes = sum(nplans[key].stats()["net_bytes"] for key in pts)
+        ach = step_bytes / per_step_s / 1e9
+        for _ in range(2):
+            eager_step()
+        eager_ms = statistics.mean(timed(eager_step, max(2, args.steps)))
+        line["config"].update({"points": "n in 2..28 step 2, k in 2..14 step 2", "circuits_per_step": batch,
+                               "bitstrings_per_circuit": chunk, "precision": 1,
+                               "launch": "the step's 98 calls replayed as one CUDA graph",
+                               "planning_s_total": round(sum(plan_s.values()), 2)})
+        line["eager"] = {"value": units_per_step / (eager_ms / 1000.0), "unit": unit, "ms_per_step": eager_ms,
+                         "what": "the same 98 calls issued one by one (no graph)"}
+        line["per_point"] = per_point
+        line["roofline"] = {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
+                            "frac": ach / hbm_peak, "traffic": None,
+                            "kernel": "network merges (k_cgemm_fp32 / k_cgemm_tc*) of all 98 circuits",
+                            "algorithmic_bytes_per_step": step_bytes,
+                            "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})"}
     if wl["kind"] == "permute":
         per_step_s = t_max / args.steps / 1000.0
         ach = units_per_step / per_step_s

@@ -413,6 +413,8 @@ tn_status tn_plan_get_stats(const tn_plan *p, tn_plan_stats *st) {
     st->net_max_log2 = p->net->max_log2;
     st->net_sliced = (int)p->net->slices.size();
     st->net_batch_log2 = p->net->log2_batch;
+    st->net_cost = p->net->cost;
+    st->net_bytes = p->net->bytes;
     st->flops = p->net->flops;
     int tc = 0;
     for (const NetLaunch &L : p->net->launches) tc += L.precision != TN_PREC_FP32;

@@ -49,9 +49,10 @@ template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 template <int BM, int BN, int BK, int TM, int TN>
-__global__ void __launch_bounds__(kThreads, 2) k_cgemm_fp32(long long M, long long N, long long K,
+__global__ void __launch_bounds__(kThreads, 2) k_cgemm_fp32(long long M, long long N, long long K, long long k_len,
                                                          const float2 *__restrict__ A, const float2 *__restrict__ B,
-                                                         float2 *__restrict__ C, const __grid_constant__ StagedMap om) {
+                                                         float2 *__restrict__ C, float2 *__restrict__ P,
+                                                         const __grid_constant__ StagedMap om) {
   static_assert((BM / TM) * (BN / TN) == kThreads, "one thread per TM x TN block");
   // two K slices of both operands in flight (row-major, row stride BK + 1: a warp's reads across
   // rows fall in distinct banks); the C tile (row stride BN + 1) in the permuted epilogue
@@ -65,6 +66,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_cgemm_fp32(long long M, long lo
   const float2 *Ab = A + b * M * K;
   const float2 *Bb = B + b * N * K;
   float2 *Cb = C + b * M * N;
+  // split K (P != nullptr): this CTA sums k in [kb, ke) and stores its partial tile to P
+  const long long kb = (long long)blockIdx.y * k_len, ke = kb + k_len < K ? kb + k_len : K;
   constexpr int NX = BN / TN;  // threads along n
   const int tx = threadIdx.x % NX, ty = threadIdx.x / NX;
   float2 acc[TM][TN];
@@ -81,20 +84,20 @@ __global__ void __launch_bounds__(kThreads, 2) k_cgemm_fp32(long long M, long lo
       const long long gk = k0 + c;
       if (r < BM) {
         const long long gm = m0 + r;
-        if (gm < M && gk < K) cp_async8(as + r * kLd + c, Ab + gm * K + gk);
+        if (gm < M && gk < ke) cp_async8(as + r * kLd + c, Ab + gm * K + gk);
         else as[r * kLd + c] = make_float2(0.f, 0.f);
       } else {
         const long long gn = n0 + (r - BM);
-        if (gn < N && gk < K) cp_async8(bs + (r - BM) * kLd + c, Bb + gn * K + gk);
+        if (gn < N && gk < ke) cp_async8(bs + (r - BM) * kLd + c, Bb + gn * K + gk);
         else bs[(r - BM) * kLd + c] = make_float2(0.f, 0.f);
       }
     }
     cp_async_commit();
   };
   int sb = 0;
-  if (K > 0) load_slice(0, 0);
-  for (long long k0 = 0; k0 < K; k0 += BK) {
-    if (k0 + BK < K) {
+  if (ke > kb) load_slice(0, kb);
+  for (long long k0 = kb; k0 < ke; k0 += BK) {
+    if (k0 + BK < ke) {
       load_slice(sb ^ 1, k0 + BK);
       cp_async_wait<1>();  // the current slice has landed (the next may still be in flight)
     } else {
@@ -122,13 +125,14 @@ __global__ void __launch_bounds__(kThreads, 2) k_cgemm_fp32(long long M, long lo
     __syncthreads();  // the buffer is free for the slice after next
     sb ^= 1;
   }
-  if (om.map.identity) {
+  if (P != nullptr || om.map.identity) {
+    float2 *Ob = P != nullptr ? P + ((long long)blockIdx.y * gridDim.z + b) * M * N : Cb;
 #pragma unroll
     for (int i = 0; i < TM; ++i)
 #pragma unroll
       for (int j = 0; j < TN; ++j) {
         const long long gm = m0 + ty + (BM / TM) * i, gn = n0 + tx + NX * j;
-        if (gm < M && gn < N) Cb[gm * N + gn] = acc[i][j];
+        if (gm < M && gn < N) Ob[gm * N + gn] = acc[i][j];
       }
   } else {
     // Permuted output: the tile is staged in shared memory and written back in stored-index
@@ -163,6 +167,22 @@ __global__ void __launch_bounds__(kThreads, 2) k_cgemm_fp32(long long M, long lo
       for (int u = threadIdx.x; u < (1 << L); u += kThreads)
         C[gbase + g_lo[u & lo_mask] + g_hi[u >> nlo]] = smem[s_lo[u & lo_mask] + s_hi[u >> nlo]];
     }
+  }
+}
+
+// Sum of the split-K partials (in split order) of every output element, stored through the
+// output map: C[map(f)] = sum_s P[s][f], f the natural index (b M + m) N + n.
+__global__ void k_splitk_reduce(const float2 *__restrict__ P, int splits, long long total, float2 *__restrict__ C,
+                                const __grid_constant__ OutMap om) {
+  for (long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x; f < total;
+       f += (long long)gridDim.x * blockDim.x) {
+    float2 acc = P[f];
+    for (int s = 1; s < splits; ++s) {
+      const float2 v = P[(long long)s * total + f];
+      acc.x += v.x;
+      acc.y += v.y;
+    }
+    C[om.identity ? f : map_bits(om, f, 0)] = acc;
   }
 }
 
@@ -202,38 +222,70 @@ void build_staged(StagedMap &sm, const OutMap &om, long long M, long long N, int
   sm.pairs = L > 0 && spos(order[0]) == 0;
 }
 
-template <int BM, int BN, int BK, int TM, int TN>
-cudaError_t launch_shape(long long batch, long long M, long long N, long long K, const float2 *A, const float2 *B,
-                         float2 *C, const OutMap &om, cudaStream_t s) {
-  const long long tiles = ((N + BN - 1) / BN) * ((M + BM - 1) / BM);
-  if (tiles > 0x7fffffffll) return cudaErrorNotSupported;
-  dim3 grid((unsigned)tiles, 1u, (unsigned)batch);
-  StagedMap sm;
-  std::memset(&sm, 0, sizeof(sm));
-  sm.map = om;
-  if (!om.identity) build_staged(sm, om, M, N, BM, BN);
-  k_cgemm_fp32<BM, BN, BK, TM, TN><<<grid, kThreads, 0, s>>>(M, N, K, A, B, C, sm);
-  return cudaGetLastError();
-}
-
 // Tile shape (BM x BN) for an output of N columns.
 inline void tile_for(long long N, int *bm, int *bn) {
   *bn = N <= 8 ? 8 : N <= 16 ? 16 : N <= 32 ? 32 : 64;
   *bm = *bn == 64 ? 64 : 128;
 }
 
-template <int BK>
-cudaError_t launch_k(long long batch, long long M, long long N, long long K, const float2 *A, const float2 *B,
-                     float2 *C, const OutMap &om, cudaStream_t s) {
+// Split K: an output of few tiles with a long K (a merge that contracts most of two large
+// operands into a small result) would leave most SMs idle and one CTA looping over K; K is
+// then cut into ranges of at least 256 (a multiple of the K slice) so that about two CTAs
+// per SM (152 SMs) run, each storing a partial tile, and k_splitk_reduce adds the partials.
+constexpr long long kSplitTargetCtas = 2 * 152;
+int split_k(long long batch, long long M, long long N, long long K, long long *k_len) {
   int bm = 0, bn = 0;
   tile_for(N, &bm, &bn);
-  if (bn == 8) return launch_shape<128, 8, BK, 2, 2>(batch, M, N, K, A, B, C, om, s);
-  if (bn == 16) return launch_shape<128, 16, BK, 4, 2>(batch, M, N, K, A, B, C, om, s);
-  if (bn == 32) return launch_shape<128, 32, BK, 4, 4>(batch, M, N, K, A, B, C, om, s);
-  return launch_shape<64, 64, BK, 4, 4>(batch, M, N, K, A, B, C, om, s);
+  const long long tiles = batch * ((M + bm - 1) / bm) * ((N + bn - 1) / bn);
+  *k_len = K;
+  if (K < 512 || tiles >= kSplitTargetCtas) return 1;
+  long long S = std::min<long long>((kSplitTargetCtas + tiles - 1) / tiles, K / 256);
+  if (S <= 1) return 1;
+  const int bk = K <= 8 ? 8 : 16;
+  long long kl = (K + S - 1) / S;
+  kl = (kl + bk - 1) / bk * bk;
+  *k_len = kl;
+  return (int)((K + kl - 1) / kl);
+}
+
+template <int BM, int BN, int BK, int TM, int TN>
+cudaError_t launch_shape(long long batch, long long M, long long N, long long K, const float2 *A, const float2 *B,
+                         float2 *C, float2 *P, const OutMap &om, cudaStream_t s) {
+  const long long tiles = ((N + BN - 1) / BN) * ((M + BM - 1) / BM);
+  if (tiles > 0x7fffffffll) return cudaErrorNotSupported;
+  long long k_len = K;
+  const int splits = P != nullptr ? split_k(batch, M, N, K, &k_len) : 1;
+  dim3 grid((unsigned)tiles, (unsigned)splits, (unsigned)batch);
+  StagedMap sm;
+  std::memset(&sm, 0, sizeof(sm));
+  sm.map = om;
+  if (!om.identity && splits == 1) build_staged(sm, om, M, N, BM, BN);
+  k_cgemm_fp32<BM, BN, BK, TM, TN><<<grid, kThreads, 0, s>>>(M, N, K, k_len, A, B, C, splits > 1 ? P : nullptr, sm);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || splits == 1) return e;
+  const long long total = batch * M * N;
+  k_splitk_reduce<<<(unsigned)std::min<long long>((total + 255) / 256, 4096), 256, 0, s>>>(P, splits, total, C, om);
+  return cudaGetLastError();
+}
+
+template <int BK>
+cudaError_t launch_k(long long batch, long long M, long long N, long long K, const float2 *A, const float2 *B,
+                     float2 *C, float2 *P, const OutMap &om, cudaStream_t s) {
+  int bm = 0, bn = 0;
+  tile_for(N, &bm, &bn);
+  if (bn == 8) return launch_shape<128, 8, BK, 2, 2>(batch, M, N, K, A, B, C, P, om, s);
+  if (bn == 16) return launch_shape<128, 16, BK, 4, 2>(batch, M, N, K, A, B, C, P, om, s);
+  if (bn == 32) return launch_shape<128, 32, BK, 4, 4>(batch, M, N, K, A, B, C, P, om, s);
+  return launch_shape<64, 64, BK, 4, 4>(batch, M, N, K, A, B, C, P, om, s);
 }
 
 }  // namespace
+
+size_t cgemm_fp32_workspace(long long batch, long long M, long long N, long long K) {
+  long long k_len = 0;
+  const int splits = split_k(batch, M, N, K, &k_len);
+  return splits > 1 ? (size_t)splits * (size_t)(batch * M * N) * sizeof(float2) : 0;
+}
 
 double cgemm_fp32_tile_fill(long long M, long long N) {
   int bm = 0, bn = 0;
@@ -244,12 +296,15 @@ double cgemm_fp32_tile_fill(long long M, long long N) {
 }
 
 cudaError_t launch_cgemm_fp32(long long batch, long long M, long long N, long long K, const float2 *A, const float2 *B,
-                              float2 *C, cudaStream_t s, const OutMap *om) {
+                              float2 *C, void *ws, size_t ws_bytes, cudaStream_t s, const OutMap *om) {
   if (batch > 65535) return cudaErrorNotSupported;
+  const size_t need = cgemm_fp32_workspace(batch, M, N, K);
+  if (need > 0 && (ws == nullptr || ws_bytes < need)) return cudaErrorInvalidValue;
+  float2 *P = need > 0 ? static_cast<float2 *>(ws) : nullptr;
   const OutMap ident;
   const OutMap &m = om ? *om : ident;
-  if (K <= 8) return launch_k<8>(batch, M, N, K, A, B, C, m, s);
-  return launch_k<16>(batch, M, N, K, A, B, C, m, s);
+  if (K <= 8) return launch_k<8>(batch, M, N, K, A, B, C, P, m, s);
+  return launch_k<16>(batch, M, N, K, A, B, C, P, m, s);
 }
 
 }  // namespace tnq

@@ -37,7 +37,8 @@
 namespace tnq {
 
 cudaError_t launch_cgemm_fp32(long long batch, long long M, long long N, long long K, const float2 *A, const float2 *B,
-                              float2 *C, cudaStream_t s, const OutMap *om);
+                              float2 *C, void *ws, size_t ws_bytes, cudaStream_t s, const OutMap *om);
+size_t cgemm_fp32_workspace(long long batch, long long M, long long N, long long K);
 
 namespace {
 
@@ -886,7 +887,8 @@ cudaError_t run_tc(long long batch, long long M, long long N, long long K, const
 }  // namespace
 
 size_t cgemm_workspace(int precision, long long batch, long long M, long long N, long long K) {
-  if (precision == TN_PREC_FP32 || !tc_shape_ok(precision, M, N, K)) return 0;
+  if (precision == TN_PREC_FP32) return cgemm_fp32_workspace(batch, M, N, K);
+  if (!tc_shape_ok(precision, M, N, K)) return 0;
   const int parts = precision == TN_PREC_3XTF32 ? 2 : 3;
   // A split on chip: only B's parts are stored
   if (split_a_on_chip(precision, N, K)) return parts * align256(part_bytes(precision, 2 * N, 2 * K, batch));
@@ -895,7 +897,7 @@ size_t cgemm_workspace(int precision, long long batch, long long M, long long N,
 
 cudaError_t launch_cgemm(int precision, long long batch, long long M, long long N, long long K, const float2 *A,
                          const float2 *B, float2 *C, void *ws, size_t ws_bytes, cudaStream_t s, const OutMap *om) {
-  if (precision == TN_PREC_FP32) return launch_cgemm_fp32(batch, M, N, K, A, B, C, s, om);
+  if (precision == TN_PREC_FP32) return launch_cgemm_fp32(batch, M, N, K, A, B, C, ws, ws_bytes, s, om);
   const OutMap ident;
   const OutMap &m = om ? *om : ident;
   if (!tc_shape_ok(precision, M, N, K)) return cudaErrorNotSupported;

@@ -22,14 +22,17 @@
 //     index too).  Indices are picked greedily on the best order (the one shrinking the most
 //     largest intermediates, then the fewest flops), and the sliced network is planned again.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <complex>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <map>
+#include <queue>
 #include <set>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "network.h"
@@ -166,18 +169,18 @@ tn_status build_network(const tn_circuit &c, int log2_batch, NetPlan &net, std::
 
 namespace {
 
-// Arithmetic intensity (complex flops 8 M N K per byte) above which a launched merge is taken
-// to be bound by arithmetic rather than by HBM in the order cost.
-constexpr double kRidge = 32.0;
+// Orders tried: per pass size (coarse), and at the chosen pass size.
+constexpr int kCoarseTrials = 64;
+constexpr int kTrials = 256;
 
 struct Trial {
   std::vector<NetStep> steps;
   std::vector<std::vector<int>> legs;
   int max_log2 = 0;
-  double flops = 0;
-  // cost of the merges that depend on the bitstrings (their result carries the bitstring index,
-  // label 0; the rest is folded at plan time): per merge max(bytes read and written,
-  // flops / kRidge), summed
+  double flops = 0;      // of the merges that run on each call
+  double fold_work = 0;  // complex multiply-adds of the merges folded at plan time
+  // cost of the merges that run on each call (all but those folded at plan time): per merge
+  // kLaunchBytes + max(bytes read and written, flops / kRidge), summed
   double dyn_cost = 0;
   // slicing of an order whose peak exceeds the cap: the indices, and the cost of all slices
   bool sliceable = false;
@@ -190,7 +193,8 @@ struct Contractor {
   const NetPlan &net;
   std::vector<std::vector<int>> legs;
   std::vector<char> live;
-  std::map<int, std::vector<int>> where;  // label -> live tensors carrying it
+  std::vector<std::vector<int>> where;  // label -> live tensors carrying it
+  std::vector<char> stat;                 // tensor does not depend on the bitstrings
   Trial tr;
   explicit Contractor(const NetPlan &n) : net(n) {
     for (const NetNode &nd : net.nodes) {  // sliced indices are not part of any slice's network
@@ -200,12 +204,22 @@ struct Contractor {
       legs.push_back(l);
     }
     live.assign(legs.size(), 1);
+    where.resize(net.label_dim.size());
+    for (const NetNode &nd : net.nodes) stat.push_back(nd.kind == NODE_FIXED ? 1 : 0);
     for (size_t i = 0; i < legs.size(); ++i)
       for (int x : legs[i]) where[x].push_back((int)i);
   }
   int bits_of(const std::vector<int> &ls) const {
     int b = 0;
     for (int x : ls) b += net.label_dim[(size_t)x];
+    return b;
+  }
+  // bits the greedy scores a leg list with: the bitstring index may be weighted as if it were
+  // larger (a small batch otherwise makes merging the output closures early look cheap)
+  int score_bits0 = -1;
+  int score_bits(const std::vector<int> &ls) const {
+    int b = 0;
+    for (int x : ls) b += (x == 0 && score_bits0 >= 0) ? score_bits0 : net.label_dim[(size_t)x];
     return b;
   }
   void merged(int i, int j, std::vector<int> &res, std::vector<int> &batch, std::vector<int> &contr) {
@@ -244,11 +258,23 @@ struct Contractor {
       if (std::find(batch.begin(), batch.end(), x) == batch.end() && std::find(contr.begin(), contr.end(), x) == contr.end())
         nb += net.label_dim[(size_t)x];
     const double fl = 8.0 * std::ldexp(1.0, bits_of(batch) + mb + nb + bits_of(contr));
-    tr.flops += fl;
-    if (std::find(res.begin(), res.end(), 0) != res.end())
-      tr.dyn_cost += std::max(8.0 * (std::ldexp(1.0, bits_of(res)) + std::ldexp(1.0, bits_of(legs[(size_t)bi])) +
-                                     std::ldexp(1.0, bits_of(legs[(size_t)bj]))),
-                              fl / kRidge);
+    // a merge of two bitstring-independent tensors is folded at plan time when it fits the
+    // folding budget (the rule the lowering applies); every other merge runs on each call
+    bool folded = false;
+    if (stat[(size_t)bi] && stat[(size_t)bj]) {
+      const double work = std::ldexp(1.0, bits_of(res) + bits_of(contr));
+      if (bits_of(res) <= kFoldMaxLog2 && tr.fold_work + work <= kFoldMaxWork) {
+        tr.fold_work += work;
+        folded = true;
+      }
+    }
+    if (!folded) {
+      tr.flops += fl;
+      tr.dyn_cost += kLaunchBytes + std::max(8.0 * (std::ldexp(1.0, bits_of(res)) +
+                                                    std::ldexp(1.0, bits_of(legs[(size_t)bi])) +
+                                                    std::ldexp(1.0, bits_of(legs[(size_t)bj]))),
+                                             fl / kRidge);
+    }
     const int out = (int)legs.size();
     for (int x : legs[(size_t)bi]) {
       auto &w = where[x];
@@ -258,37 +284,118 @@ struct Contractor {
       auto &w = where[x];
       w.erase(std::remove(w.begin(), w.end(), bj), w.end());
     }
-    for (int x : contr) where.erase(x);
+    for (int x : contr) where[(size_t)x].clear();
     legs.push_back(res);
     live.push_back(1);
+    stat.push_back(folded ? 1 : 0);
     live[(size_t)bi] = live[(size_t)bj] = 0;
     for (int x : res) where[x].push_back(out);
     tr.steps.push_back(st);
     return out;
   }
-  // greedy by size reduction among live tensors whose flag is set in `allowed` (all if empty)
-  void greedy(double temperature, uint64_t seed, const std::vector<char> &allowed_in) {
+  // Greedy by size reduction among live tensors whose flag is set in `allowed` (all if empty):
+  // candidate pairs share an index other than the bitstring index; the pair minimising
+  // (size(result) - size(A) - size(B)) / max(size(A), size(B)), less Gumbel noise of the given
+  // temperature drawn when the pair is scored, is merged next.  Candidates live in a heap: a
+  // merge only adds the pairs of its result (the score of a pair not involving the result
+  // cannot change: an index's batch/contracted role changes only when two of its carriers
+  // merge).  With fold_cap >= 0 only pairs of bitstring-independent tensors whose result
+  // has at most 2^fold_cap entries are candidates (merges folded at plan time).
+  void greedy(double temperature, uint64_t seed, const std::vector<char> &allowed_in, int fold_cap = -1) {
     uint64_t rs = seed * 6364136223846793005ull + 1442695040888963407ull;
     auto uniform = [&]() {
       rs = rs * 6364136223846793005ull + 1442695040888963407ull;
       return ((rs >> 11) + 0.5) * (1.0 / 9007199254740992.0);
     };
+    struct Cand {
+      double score, base;  // base: without noise
+      int i, j;
+      bool operator>(const Cand &o) const {
+        return score > o.score || (score == o.score && (i > o.i || (i == o.i && j > o.j)));
+      }
+    };
+    std::priority_queue<Cand, std::vector<Cand>, std::greater<Cand>> heap;
     std::vector<char> allowed = allowed_in;
+    std::vector<int> res, batch, contr;
+    auto ok = [&](int i) {
+      return live[(size_t)i] && (allowed.empty() || allowed[(size_t)i]) && (fold_cap < 0 || stat[(size_t)i]);
+    };
+    auto push = [&](int i, int j) {
+      if (i > j) std::swap(i, j);
+      merged(i, j, res, batch, contr);
+      if (fold_cap >= 0 && bits_of(res) > fold_cap) return;
+      const double sr = std::ldexp(1.0, score_bits(res)), sa = std::ldexp(1.0, score_bits(legs[(size_t)i])),
+                   sb = std::ldexp(1.0, score_bits(legs[(size_t)j]));
+      const double base = (sr - sa - sb) / std::max(sa, sb);
+      const double score = temperature > 0 ? base - temperature * std::log(-std::log(uniform())) : base;
+      heap.push({score, base, i, j});
+    };
+    std::vector<std::pair<int, int>> init;
+    for (size_t x = 1; x < where.size(); ++x) {
+      const std::vector<int> &own = where[x];
+      for (size_t u = 0; u < own.size(); ++u)
+        for (size_t v = u + 1; v < own.size(); ++v)
+          if (ok(own[u]) && ok(own[v])) init.push_back({std::min(own[u], own[v]), std::max(own[u], own[v])});
+    }
+    std::sort(init.begin(), init.end());
+    init.erase(std::unique(init.begin(), init.end()), init.end());
+    for (const auto &pr : init) push(pr.first, pr.second);
+    std::vector<int> seen;
+    constexpr int kMaxRedraws = 64;
+    int redraws = 0;
+    while (!heap.empty()) {
+      const Cand c = heap.top();
+      heap.pop();
+      if (!live[(size_t)c.i] || !live[(size_t)c.j]) continue;
+      // the noise of the pair on top is drawn again (as if every pair's noise were drawn anew
+      // at every step); a pair that no longer wins goes back
+      if (temperature > 0 && !heap.empty() && redraws < kMaxRedraws) {
+        const double s2 = c.base - temperature * std::log(-std::log(uniform()));
+        if (s2 > heap.top().score) {
+          heap.push({s2, c.base, c.i, c.j});
+          ++redraws;
+          continue;
+        }
+      }
+      redraws = 0;
+      const int out = merge(c.i, c.j);
+      if (!allowed.empty()) {
+        allowed.resize(legs.size(), 0);
+        allowed[(size_t)out] = 1;
+      }
+      if (!ok(out)) continue;
+      seen.clear();
+      for (int x : legs[(size_t)out]) {
+        if (x == 0) continue;
+        for (int o : where[x])
+          if (o != out && ok(o) && std::find(seen.begin(), seen.end(), o) == seen.end()) {
+            seen.push_back(o);
+            push(out, o);
+          }
+      }
+    }
+  }
+  // The same greedy choice with the noise of every candidate pair drawn anew at every step
+  // (each step samples a pair with probability ~ exp(-score / temperature)); a full scan of the
+  // candidates per step.
+  void greedy_stepwise(double temperature, uint64_t seed) {
+    uint64_t rs = seed * 6364136223846793005ull + 1442695040888963407ull;
+    auto uniform = [&]() {
+      rs = rs * 6364136223846793005ull + 1442695040888963407ull;
+      return ((rs >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+    };
     std::vector<int> res, batch, contr;
     for (;;) {
       double best = 1e300;
       int bi = -1, bj = -1;
-      for (auto &kv : where) {
-        if (kv.first == 0) continue;
-        const std::vector<int> &own = kv.second;
-        if (own.size() < 2) continue;
+      for (size_t x = 1; x < where.size(); ++x) {
+        const std::vector<int> &own = where[x];
         for (size_t u = 0; u < own.size(); ++u)
           for (size_t v = u + 1; v < own.size(); ++v) {
             const int i = std::min(own[u], own[v]), j = std::max(own[u], own[v]);
-            if (!allowed.empty() && (!allowed[(size_t)i] || !allowed[(size_t)j])) continue;
             merged(i, j, res, batch, contr);
-            const double sr = std::ldexp(1.0, bits_of(res)), sa = std::ldexp(1.0, bits_of(legs[(size_t)i])),
-                         sb = std::ldexp(1.0, bits_of(legs[(size_t)j]));
+            const double sr = std::ldexp(1.0, score_bits(res)), sa = std::ldexp(1.0, score_bits(legs[(size_t)i])),
+                         sb = std::ldexp(1.0, score_bits(legs[(size_t)j]));
             double score = (sr - sa - sb) / std::max(sa, sb);
             if (temperature > 0) score -= temperature * std::log(-std::log(uniform()));
             if (score < best) {
@@ -299,11 +406,7 @@ struct Contractor {
           }
       }
       if (bi < 0) break;
-      const int out = merge(bi, bj);
-      if (!allowed.empty()) {
-        allowed.resize(legs.size(), 0);
-        allowed[(size_t)out] = 1;
-      }
+      merge(bi, bj);
     }
   }
   // join whatever is left (connected only through the bitstring index); in a sliced network
@@ -334,12 +437,33 @@ struct Contractor {
   }
 };
 
-// One greedy contraction path: candidates are pairs of live tensors sharing an index other
-// than the bitstring index; the pair minimising size(result) - size(A) - size(B) is merged
-// (with Gumbel noise of the given temperature for the randomised trials).
-void greedy_trial(const NetPlan &net, double temperature, uint64_t seed, Trial &tr) {
+// One greedy contraction path (Contractor::greedy over the whole network, with Gumbel noise
+// of the given temperature for the randomised trials).
+void greedy_trial(const NetPlan &net, double temperature, uint64_t seed, int score_bits0, Trial &tr) {
   Contractor ct(net);
+  ct.score_bits0 = score_bits0;
   ct.greedy(temperature, seed, {});
+  ct.finish();
+  tr = std::move(ct.tr);
+}
+
+// One greedy path with step-wise noise (Contractor::greedy_stepwise).
+void stepwise_trial(const NetPlan &net, double temperature, uint64_t seed, int score_bits0, Trial &tr) {
+  Contractor ct(net);
+  ct.score_bits0 = score_bits0;
+  ct.greedy_stepwise(temperature, seed);
+  ct.finish();
+  tr = std::move(ct.tr);
+}
+
+// Fold first: merges of bitstring-independent tensors (evaluated once at plan time) are made
+// greedily while their results stay within the folding size, then the greedy goes on over
+// the whole network.
+void fold_first_trial(const NetPlan &net, double temperature, uint64_t seed, int score_bits0, Trial &tr) {
+  Contractor ct(net);
+  ct.score_bits0 = score_bits0;
+  ct.greedy(temperature, seed, {}, kFoldMaxLog2);
+  ct.greedy(temperature, seed + 1, {});
   ct.finish();
   tr = std::move(ct.tr);
 }
@@ -471,16 +595,23 @@ void choose_slices(const NetPlan &net, Trial &order, int max_log2) {
       if (!in_s[(size_t)x]) b += net.label_dim[(size_t)x];
     return b;
   };
+  // per slice: merges of folded (bitstring-independent) tensors within the folding size are
+  // free (the work budget, spent once per slice copy, is not modelled here)
   double cost = 0, flops = 0;
+  std::vector<char> fst(nt, 0);
+  for (size_t i = 0; i < net.nodes.size() && i < nt; ++i) fst[i] = net.nodes[i].kind == NODE_FIXED;
   for (size_t k = 0; k < order.steps.size(); ++k) {
     const NetStep &st = order.steps[k];
+    const std::vector<int> &res = order.legs[(size_t)st.out];
+    if (fst[(size_t)st.a] && fst[(size_t)st.b] && bits(res) <= kFoldMaxLog2) {
+      fst[(size_t)st.out] = 1;
+      continue;
+    }
     const double fl = 8.0 * std::ldexp(1.0, ub[k]);
     flops += fl;
-    const std::vector<int> &res = order.legs[(size_t)st.out];
-    if (std::find(res.begin(), res.end(), 0) != res.end())
-      cost += std::max(8.0 * (std::ldexp(1.0, bits(res)) + std::ldexp(1.0, bits(order.legs[(size_t)st.a])) +
-                              std::ldexp(1.0, bits(order.legs[(size_t)st.b]))),
-                       fl / kRidge);
+    cost += kLaunchBytes + std::max(8.0 * (std::ldexp(1.0, bits(res)) + std::ldexp(1.0, bits(order.legs[(size_t)st.a])) +
+                                           std::ldexp(1.0, bits(order.legs[(size_t)st.b]))),
+                                    fl / kRidge);
   }
   order.sliced_cost = cost * n_slices;
   order.sliced_flops = flops * n_slices;
@@ -499,31 +630,47 @@ bool better_order(const Trial &tr, const Trial &best, int max_log2) {
   return tr.max_log2 < best.max_log2 || (tr.max_log2 == best.max_log2 && tr.flops < best.flops);
 }
 
-// The deterministic greedy plus randomised trials (greedy and qubit sweeps); the preferred one.
-// With `slice`, orders that exceed the cap are sliced to fit (choose_slices).  *min_peak (if
-// given) receives the smallest peak of any trial.
-Trial search_orders(const NetPlan &net, int max_log2, bool slice, int *min_peak = nullptr) {
-  Trial best;
-  bool have = false;
-  if (min_peak) *min_peak = 1 << 30;
-  const int trials = 128;
-  for (int t = 0; t < trials; ++t) {
-    Trial tr;
-    const double temp = (t % 64) == 0 ? 0.0 : 0.05 + 0.5 * (double)(t % 16) / 16.0;
-    const uint64_t seed = 0x9E3779B97F4A7C15ull * (uint64_t)(t + 1);
-    if (t < trials / 2) greedy_trial(net, temp, seed, tr);
-    else sweep_trial(net, temp, seed, tr);
-    if (min_peak) *min_peak = std::min(*min_peak, tr.max_log2);
+// Randomised trials, the preferred one: half greedy (the first deterministic; they score the
+// bitstring index at its size or 4, 8, 12 bits larger in turn; half of them with step-wise
+// noise), a quarter qubit sweeps, a quarter fold-first.  With `slice`, orders that exceed the cap are sliced to fit
+// (choose_slices).  Trials are independent and run on the host's cores; the choice among
+// them is made in trial order, so the result does not depend on the thread count.
+Trial search_orders(const NetPlan &net, int max_log2, bool slice, int trials) {
+  const int ng = trials / 2, ns = trials / 4;
+  std::vector<Trial> res((size_t)trials);
+  auto run = [&](int t) {
+    Trial &tr = res[(size_t)t];
+    // u: the trial's index within its kind's sequence (kinds offset by 64 and 128)
+    const int u = t < ng ? t : (t < ng + ns ? 64 + (t - ng) : 128 + (t - ng - ns));
+    const double temp = (u % 64) == 0 ? 0.0 : 0.05 + 0.5 * (double)(u % 16) / 16.0;
+    const uint64_t seed = 0x9E3779B97F4A7C15ull * (uint64_t)(u + 1);
+    const int w0 = (u & 3) ? net.label_dim[0] + 4 * (u & 3) : -1;
+    if (t < ng / 2) greedy_trial(net, temp, seed, w0, tr);
+    else if (t < ng) stepwise_trial(net, temp, seed, w0, tr);
+    else if (t < ng + ns) sweep_trial(net, (u % 64) == 0 ? 0.05 : temp, seed, tr);
+    else fold_first_trial(net, temp, seed, w0, tr);
     if (slice && tr.max_log2 > max_log2) choose_slices(net, tr, max_log2);
-    if (getenv("TNQ_DEBUG_NET"))
+  };
+  std::atomic<int> next{0};
+  auto worker = [&]() {
+    for (int t = next++; t < trials; t = next++) run(t);
+  };
+  const int nth = std::max(1, std::min(trials, (int)std::thread::hardware_concurrency()));
+  std::vector<std::thread> pool;
+  for (int i = 1; i < nth; ++i) pool.emplace_back(worker);
+  worker();
+  for (std::thread &th : pool) th.join();
+  const bool debug = getenv("TNQ_DEBUG_NET") != nullptr;
+  int best_t = 0;
+  for (int t = 0; t < trials; ++t) {
+    const Trial &tr = res[(size_t)t];
+    if (debug)
       fprintf(stderr, "trial %d: peak %d flops %.3e cost %.3e sliced %d (%zu) cost %.3e\n", t, tr.max_log2, tr.flops,
               tr.dyn_cost, (int)tr.sliceable, tr.slices.size(), tr.sliced_cost);
-    if (!have || better_order(tr, best, max_log2)) {
-      best = std::move(tr);
-      have = true;
-    }
+    if (t > 0 && better_order(tr, res[(size_t)best_t], max_log2)) best_t = t;
   }
-  return best;
+  if (debug) fprintf(stderr, "best trial %d of %d\n", best_t, trials);
+  return std::move(res[(size_t)best_t]);
 }
 
 // The merges of `order` (planned on the unsliced network) replayed on the sliced one.
@@ -544,24 +691,32 @@ tn_status plan_network(NetPlan &net, int max_log2, std::string &err) {
     net.log2_batch = bits;
     net.label_dim[0] = bits;
   };
-  set_batch(lb);
-  int min_peak = 0;
-  Trial best = search_orders(net, max_log2, true, &min_peak);
-  if (best.max_log2 > max_log2 && lb > 0) {
-    // Fewer bitstrings per pass: amplitudes of different bitstrings are independent, so a call
-    // may contract its bitstrings 2^j at a time (j passes' worth of launches, no extra flops in
-    // the merges that carry the bitstring index).  The j that brings the smallest peak within
-    // the cap is tried against slicing the whole batch; the cheaper over a full call is kept.
-    const int j = std::min(lb, min_peak - max_log2);
+  // Bitstrings per pass: amplitudes of different bitstrings are independent, so a call may
+  // contract its bitstrings 2^(lb - j) at a time in 2^j passes.  A smaller pass shrinks every
+  // tensor that carries the bitstring index (a cap may then be met without slicing) and
+  // lets the order treat the output closures differently, at the price of more launches.
+  // Every pass size is planned; the cheapest over a full call is kept.
+  auto usable = [&](const Trial &t) { return t.max_log2 <= max_log2 || t.sliceable; };
+  auto call_cost = [&](const Trial &t, int passes_log2) {
+    return std::ldexp(t.max_log2 <= max_log2 ? t.dyn_cost : t.sliced_cost, passes_log2);
+  };
+  // a coarse search per pass size, then the full search at the best one
+  Trial best;
+  int best_j = -1;
+  for (int j = 0; j <= lb; ++j) {
     set_batch(lb - j);
-    Trial fewer = search_orders(net, max_log2, true);
-    auto usable = [&](const Trial &t) { return t.max_log2 <= max_log2 || t.sliceable; };
-    auto call_cost = [&](const Trial &t, int passes_log2) {
-      return std::ldexp(t.max_log2 <= max_log2 ? t.dyn_cost : t.sliced_cost, passes_log2);
-    };
-    if (usable(fewer) && (!usable(best) || call_cost(fewer, j) < call_cost(best, 0))) best = std::move(fewer);
-    else set_batch(lb);
+    Trial t = search_orders(net, max_log2, true, kCoarseTrials);
+    if (getenv("TNQ_DEBUG_NET"))
+      fprintf(stderr, "pass 2^%d: peak %d, %zu sliced, usable %d, call cost %.4g\n", lb - j, t.max_log2,
+              t.slices.size(), (int)usable(t), call_cost(t, j));
+    if (best_j < 0 || (usable(t) && (!usable(best) || call_cost(t, j) < call_cost(best, best_j)))) {
+      best = std::move(t);
+      best_j = j;
+    }
   }
+  set_batch(lb - best_j);
+  Trial full = search_orders(net, max_log2, true, kTrials);
+  if (usable(full) && (!usable(best) || call_cost(full, best_j) < call_cost(best, best_j))) best = std::move(full);
   if (best.max_log2 > max_log2) {
     if (!best.sliceable) {
       err = "network contraction would create a 2^" + std::to_string(best.max_log2) + "-entry intermediate (cap 2^" +
@@ -574,13 +729,12 @@ tn_status plan_network(NetPlan &net, int max_log2, std::string &err) {
     // the order found above, on the sliced network, fits by construction; a search on the
     // sliced network itself may find a cheaper one
     Trial replay = replay_order(net, best);
-    Trial again = search_orders(net, max_log2, false);
+    Trial again = search_orders(net, max_log2, false, kTrials);
     best = better_order(again, replay, max_log2) ? std::move(again) : std::move(replay);
   }
   net.steps = best.steps;
   net.all_legs = best.legs;
   net.max_log2 = best.max_log2;
-  net.flops = std::ldexp(best.flops, (int)net.slices.size());
   if (net.max_log2 > max_log2) {
     err = "network contraction would create a 2^" + std::to_string(net.max_log2) + "-entry intermediate (cap 2^" +
           std::to_string(max_log2) + ")";

@@ -43,6 +43,12 @@ struct NetLaunch {
 constexpr int kFoldMaxLog2 = 20;       // largest folded result: 2^20 entries
 constexpr double kFoldMaxWork = 2e8;   // complex multiply-adds over all folded merges (all slices)
 
+// Order cost of a launched merge: kLaunchBytes (a launch and a short kernel, ~3 us of HBM time)
+// + max(bytes read and written, complex flops / kRidge): merges are HBM-bound unless their
+// arithmetic intensity exceeds kRidge.
+constexpr double kRidge = 32.0;
+constexpr double kLaunchBytes = 2e7;
+
 // Slicing: at most 2^16 slices; the constant table of all slices at most 2^27 entries.
 constexpr int kMaxSliceBits = 16;
 constexpr long long kMaxTableEntries = 1ll << 27;
@@ -56,7 +62,9 @@ struct NetPlan {
   std::vector<NetStep> steps;
   std::vector<std::vector<int>> all_legs;  // legs of every tensor id
   int max_log2 = 0;   // largest intermediate of one slice
-  double flops = 0;  // 8 M N K summed over merges and slices
+  double flops = 0;  // 8 batch M N K of the launched merges of one call (all slices and passes)
+  double cost = 0;   // the same merges' fixed launch cost + max(bytes moved, flops / 32) (the order cost)
+  double bytes = 0;  // the same merges' operands read and results written (complex64)
   // Slicing, when no order keeps every intermediate within the cap: the indices in `slices`
   // are fixed per slice (bit k of a slice number is the value of label slices[k]); a slice is
   // the network without those indices, and the amplitudes are the sum of all slices' results.

@@ -457,6 +457,20 @@ tn_status lower_network(NetPlan &net, int precision, std::string &err) {
     return TN_ERR_UNSUPPORTED;
   }
   net.final_off = net.tensor_off[(size_t)net.launches.back().out_id];
+  // algorithmic flops of one call of 2^call_log2 bitstrings: the launched merges, per slice
+  // and per pass of bitstrings (folded merges are plan-time work)
+  double fl = 0, cost = 0, by = 0;
+  for (const NetLaunch &L : net.launches) {
+    const double f = 8.0 * (double)L.batch * (double)L.M * (double)L.N * (double)L.K;
+    const double bytes = 8.0 * (double)L.batch * ((double)L.M * L.K + (double)L.N * L.K + (double)L.M * L.N);
+    fl += f;
+    by += bytes;
+    cost += kLaunchBytes + std::max(bytes, f / kRidge);
+  }
+  const int rep = (int)net.slices.size() + net.call_log2 - net.log2_batch;  // log2 (slices x passes)
+  net.flops = std::ldexp(fl, rep);
+  net.cost = std::ldexp(cost, rep);
+  net.bytes = std::ldexp(by, rep);
   net.off_acc = -1;
   if (!net.slices.empty()) {  // FP64 slice sum after the contraction's own workspace
     net.off_acc = (long long)((hw + 255) & ~(size_t)255);

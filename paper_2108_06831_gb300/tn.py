@@ -51,7 +51,8 @@ class TnPlanStats(C.Structure):
                 ("flops", C.c_double), ("n_bwd_passes", C.c_int32), ("specialized", C.c_int32),
                 ("net_merges", C.c_int32), ("net_max_log2", C.c_int32), ("net_tensor_merges", C.c_int32),
                 ("net_folded_merges", C.c_int32), ("bwd_flops", C.c_double),
-                ("net_sliced", C.c_int32), ("net_batch_log2", C.c_int32)]
+                ("net_sliced", C.c_int32), ("net_batch_log2", C.c_int32), ("net_cost", C.c_double),
+                ("net_bytes", C.c_double)]
 
 
 class TnTuneOpts(C.Structure):

@@ -131,3 +131,18 @@ def test_network_plan_capped_host_only():
     with pytest.raises(tn.TnError) as e:
         tn.Plan(ch, max_intermediate_log2=4, **kw)
     assert e.value.status == tn.ERR_UNSUPPORTED
+
+
+def test_network_plan_routes_host_only():
+    """The capped plans the GPU parity tests run take every route of the planner: slicing only,
+    smaller bitstring passes only, and both."""
+    from paper_2108_06831_gb300 import tn
+    cases = [(C.qft(8, 77), 4, 5), (C.brickwork(12, 10, 3)[0], 16, 8), (C.grid(3, 4, 8, 2), 4, 5),
+             (C.random_circuit(10, 120, 5), 4, 7), (C.grid(3, 4, 8, 2), 4, 4), (C.random_circuit(10, 120, 5), 1, 6)]
+    routes = set()
+    for c, B, cap in cases:
+        s = tn.Plan(tn.CircuitHandle(c), target=tn.TARGET_AMPLITUDES, host_only=True, network_bitstrings=B,
+                    max_intermediate_log2=cap).stats()
+        assert s["net_max_log2"] <= cap
+        routes.add((s["net_sliced"] > 0, (1 << s["net_batch_log2"]) < B))
+    assert {(True, False), (False, True), (True, True)} <= routes

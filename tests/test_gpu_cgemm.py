@@ -84,3 +84,13 @@ def test_cgemm_fp32_more_than_65535_row_tiles():
     """A tall, narrow product (8.4M rows, 3 columns, K 5: more than 65535 row tiles of 128 rows,
     ragged in every dimension), as operand exchange in network merges produces."""
     assert _run(0, 1, (1 << 23) + 200, 3, 5, seed=11) <= TOL
+
+
+@pytest.mark.parametrize("shape", [(1, 1, 1, 65536), (3, 5, 7, 3000), (2, 130, 9, 1024), (1, 64, 64, 8192)])
+def test_cgemm_fp32_split_k(shape):
+    """Few output tiles and a long K (a merge contracting two large operands into a small
+    result): K is split over CTAs and the partials summed in a second kernel."""
+    tn = _tn()
+    batch, M, N, K = shape
+    assert tn.cgemm_workspace_bytes(0, batch, M, N, K) > 0  # the split path is taken
+    assert _run(0, batch, M, N, K, seed=sum(shape)) <= TOL
