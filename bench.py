@@ -42,7 +42,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="state24",
                     choices=["state24", "state10", "grad20", "gemm_fp32", "gemm_3xtf32", "gemm_bf16x3",
-                             "serving512", "amps36", "permute28", "gemm_merge", "fig31", "fig31amps"])
+                             "serving512", "amps36", "permute28", "gemm_merge", "fig31", "fig31amps", "plan31"])
     ap.add_argument("--batch", type=int, default=0, help="gemm workloads: batch override (small profiling cases)")
     ap.add_argument("--legs", type=int, default=0, help="permute28: tensor legs override (small profiling cases)")
     ap.add_argument("--prec", type=int, default=1, help="amps36: GEMM precision (0 FP32, 1 3xTF32, 2 split BF16)")
@@ -282,7 +282,45 @@ WORKLOADS = {
     # (3xTF32 merges, one plan per circuit sized for 64 bitstrings per call)
     "fig31amps": dict(kind="sweep_amps", n=28, depth=14, seed=6000, batch=98, chunk=64, prec=1),
     "grad20": dict(kind="grad", n=20, depth=10, seed=4000, batch=64),
+    # contraction-path search on the host (the paper's E1 grid): the 98 Fig. 3.1 circuits planned
+    # for 64 bitstrings per call, the deterministic greedy alone against the randomised search
+    "plan31": dict(kind="plan", n=28, depth=14, seed=6000, batch=98, chunk=64),
 }
+
+
+def plan_search_line(args, wl):
+    """Host-only measurement: planning time and planned cost per Fig. 3.1 circuit, greedy alone
+    (order_trials = 1) against the default search; no GPU work."""
+    from paper_2108_06831_gb300 import circuits as C
+    from paper_2108_06831_gb300 import tn
+    pts = [(n, k) for n in range(2, 29, 2) for k in range(2, 15, 2)]
+    per_point, tot = {}, {"greedy": [0.0, 0.0], "search": [0.0, 0.0]}
+    for i, (n, k) in enumerate(pts):
+        ch = tn.CircuitHandle(C.paper_fig31(n, k, wl["seed"] + i))
+        row = {}
+        for name, trials in (("greedy", 1), ("search", 0)):
+            t0 = time.perf_counter()
+            st = tn.Plan(ch, target=tn.TARGET_AMPLITUDES, host_only=True, network_bitstrings=wl["chunk"],
+                         precision=1, order_trials=trials).stats()
+            dt = time.perf_counter() - t0
+            row[name] = {"plan_s": round(dt, 4), "cost_bytes": st["net_cost"], "largest_intermediate_log2":
+                         st["net_max_log2"], "merges": st["net_merges"]}
+            tot[name][0] += dt
+            tot[name][1] += st["net_cost"]
+        per_point[f"n{n}_k{k}"] = row
+    ratios = sorted(r["greedy"]["cost_bytes"] / r["search"]["cost_bytes"] for r in per_point.values())
+    return {"metric": "contraction-path search time (host), Fig. 3.1 grid", "value": tot["search"][0], "unit": "s",
+            "n_gpus": 0, "steps": 1, "warmup": 0, "ms_per_step": 1000.0 * tot["search"][0],
+            "higher_is_better": False, "scaling": None, "vs_baseline": None, "dtype": "f64 (host planning)",
+            "data": "synthetic", "gpu_launches": 0, "roofline": None,
+            "config": {"workload": args.workload, "points": "n in 2..28 step 2, k in 2..14 step 2",
+                       "bitstrings_per_call": wl["chunk"], "host_cores": os.cpu_count(),
+                       "search": "256 orders per search (greedy, step-wise greedy, qubit sweep, fold-first), "
+                                 "every bitstring pass size"},
+            "greedy": {"seconds": tot["greedy"][0], "cost_bytes_total": tot["greedy"][1]},
+            "search": {"seconds": tot["search"][0], "cost_bytes_total": tot["search"][1]},
+            "greedy_over_search_cost": {"median": ratios[len(ratios) // 2], "max": ratios[-1], "min": ratios[0]},
+            "per_point": per_point}
 
 
 def reference_arm(args):
@@ -324,6 +362,10 @@ def main():
     if args.impl == "reference":
         return reference_arm(args)
     wl = WORKLOADS[args.workload]
+    if wl["kind"] == "plan":
+        if int(os.environ.get("RANK", "0")) == 0:
+            print(json.dumps(plan_search_line(args, wl)))
+        return 0
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))

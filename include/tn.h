@@ -123,7 +123,10 @@ typedef struct {
   int32_t flags;                 /* TN_PLAN_* bits */
   uint64_t seed;                 /* planner tie-break seed */
   int64_t amp_batch;             /* TN_PLAN_NETWORK: bitstrings per call (power of two), else 0 */
-  int64_t reserved[5];           /* must be zero */
+  int64_t order_trials;          /* TN_PLAN_NETWORK: contraction orders tried per search: 0 = 256 (randomised
+                                  * greedy, qubit-sweep and fold-first trials); 1 = the deterministic greedy
+                                  * alone; otherwise 4..4096 */
+  int64_t reserved[4];           /* must be zero */
 } tn_plan_opts;
 
 /* Plan summary (for measurement and tests). */

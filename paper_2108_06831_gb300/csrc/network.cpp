@@ -645,7 +645,8 @@ Trial search_orders(const NetPlan &net, int max_log2, bool slice, int trials) {
     const double temp = (u % 64) == 0 ? 0.0 : 0.05 + 0.5 * (double)(u % 16) / 16.0;
     const uint64_t seed = 0x9E3779B97F4A7C15ull * (uint64_t)(u + 1);
     const int w0 = (u & 3) ? net.label_dim[0] + 4 * (u & 3) : -1;
-    if (t < ng / 2) greedy_trial(net, temp, seed, w0, tr);
+    if (trials == 1) greedy_trial(net, 0.0, seed, -1, tr);  // the deterministic greedy alone
+    else if (t < ng / 2) greedy_trial(net, temp, seed, w0, tr);
     else if (t < ng) stepwise_trial(net, temp, seed, w0, tr);
     else if (t < ng + ns) sweep_trial(net, (u % 64) == 0 ? 0.05 : temp, seed, tr);
     else fold_first_trial(net, temp, seed, w0, tr);
@@ -683,7 +684,9 @@ Trial replay_order(const NetPlan &net, const Trial &order) {
 
 }  // namespace
 
-tn_status plan_network(NetPlan &net, int max_log2, std::string &err) {
+tn_status plan_network(NetPlan &net, int max_log2, int order_trials, std::string &err) {
+  const int trials = order_trials > 0 ? order_trials : kTrials;
+  const int coarse = std::min(trials, kCoarseTrials);
   net.slices.clear();
   net.sliced.assign(net.label_dim.size(), 0);
   const int lb = net.call_log2;
@@ -705,7 +708,7 @@ tn_status plan_network(NetPlan &net, int max_log2, std::string &err) {
   int best_j = -1;
   for (int j = 0; j <= lb; ++j) {
     set_batch(lb - j);
-    Trial t = search_orders(net, max_log2, true, kCoarseTrials);
+    Trial t = search_orders(net, max_log2, true, coarse);
     if (getenv("TNQ_DEBUG_NET"))
       fprintf(stderr, "pass 2^%d: peak %d, %zu sliced, usable %d, call cost %.4g\n", lb - j, t.max_log2,
               t.slices.size(), (int)usable(t), call_cost(t, j));
@@ -715,7 +718,7 @@ tn_status plan_network(NetPlan &net, int max_log2, std::string &err) {
     }
   }
   set_batch(lb - best_j);
-  Trial full = search_orders(net, max_log2, true, kTrials);
+  Trial full = search_orders(net, max_log2, true, trials);
   if (usable(full) && (!usable(best) || call_cost(full, best_j) < call_cost(best, best_j))) best = std::move(full);
   if (best.max_log2 > max_log2) {
     if (!best.sliceable) {
@@ -729,7 +732,7 @@ tn_status plan_network(NetPlan &net, int max_log2, std::string &err) {
     // the order found above, on the sliced network, fits by construction; a search on the
     // sliced network itself may find a cheaper one
     Trial replay = replay_order(net, best);
-    Trial again = search_orders(net, max_log2, false, kTrials);
+    Trial again = search_orders(net, max_log2, false, trials);
     best = better_order(again, replay, max_log2) ? std::move(again) : std::move(replay);
   }
   net.steps = best.steps;

@@ -146,3 +146,20 @@ def test_network_plan_routes_host_only():
         assert s["net_max_log2"] <= cap
         routes.add((s["net_sliced"] > 0, (1 << s["net_batch_log2"]) < B))
     assert {(True, False), (False, True), (True, True)} <= routes
+
+
+def test_network_order_search_never_worse_than_greedy():
+    """The randomised search includes the deterministic greedy at every bitstring pass size, so
+    its planned cost is never above the greedy's alone (order_trials = 1); other trial counts
+    outside 4..4096 are rejected."""
+    from paper_2108_06831_gb300 import tn
+    for c in (C.paper_fig31(12, 6, 1), C.grid(4, 4, 8, 2), C.qft(9, 5), C.random_circuit(10, 80, 3)):
+        ch = tn.CircuitHandle(c)
+        kw = dict(target=tn.TARGET_AMPLITUDES, host_only=True, network_bitstrings=16)
+        greedy = tn.Plan(ch, order_trials=1, **kw).stats()["net_cost"]
+        search = tn.Plan(ch, **kw).stats()["net_cost"]
+        few = tn.Plan(ch, order_trials=8, **kw).stats()["net_cost"]
+        assert search <= greedy and few <= greedy
+    for bad in (2, 3, 5000, -1):
+        with pytest.raises(tn.TnError):
+            tn.Plan(tn.CircuitHandle(C.ghz(4)), order_trials=bad, **kw)
