@@ -186,6 +186,35 @@ __global__ void k_splitk_reduce(const float2 *__restrict__ P, int splits, long l
   }
 }
 
+// The same sum for few outputs: one block of 128 threads per output element strides over the
+// splits, then a fixed tree (warp shuffles, then the four warp sums in order).
+__global__ void k_splitk_reduce_few(const float2 *__restrict__ P, int splits, long long total, float2 *__restrict__ C,
+                                    const __grid_constant__ OutMap om) {
+  const long long f = blockIdx.x;
+  float2 acc = make_float2(0.f, 0.f);
+  for (int s = threadIdx.x; s < splits; s += blockDim.x) {
+    const float2 v = P[(long long)s * total + f];
+    acc.x += v.x;
+    acc.y += v.y;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    acc.x += __shfl_down_sync(0xffffffffu, acc.x, o);
+    acc.y += __shfl_down_sync(0xffffffffu, acc.y, o);
+  }
+  __shared__ float2 warp_sum[4];
+  if ((threadIdx.x & 31) == 0) warp_sum[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float2 r = warp_sum[0];
+    for (int w = 1; w < 4; ++w) {
+      r.x += warp_sum[w].x;
+      r.y += warp_sum[w].y;
+    }
+    C[om.identity ? f : map_bits(om, f, 0)] = r;
+  }
+}
+
 // Tables of the permuted epilogue for one tile shape (built on the host once per launch).
 // The tile's valid local bits (vc column bits, then vr row bits) are enumerated by increasing
 // stored position; u's low nlo bits and high L - nlo bits index the tables.
@@ -264,7 +293,10 @@ cudaError_t launch_shape(long long batch, long long M, long long N, long long K,
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || splits == 1) return e;
   const long long total = batch * M * N;
-  k_splitk_reduce<<<(unsigned)std::min<long long>((total + 255) / 256, 4096), 256, 0, s>>>(P, splits, total, C, om);
+  if (total <= 4096)
+    k_splitk_reduce_few<<<(unsigned)total, 128, 0, s>>>(P, splits, total, C, om);
+  else
+    k_splitk_reduce<<<(unsigned)std::min<long long>((total + 255) / 256, 4096), 256, 0, s>>>(P, splits, total, C, om);
   return cudaGetLastError();
 }
 

@@ -86,7 +86,8 @@ def test_cgemm_fp32_more_than_65535_row_tiles():
     assert _run(0, 1, (1 << 23) + 200, 3, 5, seed=11) <= TOL
 
 
-@pytest.mark.parametrize("shape", [(1, 1, 1, 65536), (3, 5, 7, 3000), (2, 130, 9, 1024), (1, 64, 64, 8192)])
+@pytest.mark.parametrize("shape", [(1, 1, 1, 65536), (3, 5, 7, 3000), (2, 130, 9, 1024), (1, 64, 64, 8192),
+                                   (1, 128, 64, 4096)])
 def test_cgemm_fp32_split_k(shape):
     """Few output tiles and a long K (a merge contracting two large operands into a small
     result): K is split over CTAs and the partials summed in a second kernel."""
