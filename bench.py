@@ -42,7 +42,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="state24",
                     choices=["state24", "state10", "grad20", "gemm_fp32", "gemm_3xtf32", "gemm_bf16x3",
-                             "serving512", "amps36", "permute28", "gemm_merge", "fig31", "fig31amps", "plan31"])
+                             "serving512", "amps36", "permute28", "gemm_merge", "fig31", "fig31amps", "plan31", "q428_24"])
     ap.add_argument("--batch", type=int, default=0, help="gemm workloads: batch override (small profiling cases)")
     ap.add_argument("--legs", type=int, default=0, help="permute28: tensor legs override (small profiling cases)")
     ap.add_argument("--prec", type=int, default=1, help="amps36: GEMM precision (0 FP32, 1 3xTF32, 2 split BF16)")
@@ -228,6 +228,23 @@ elif kind == "sweep":
     dt = time.perf_counter() - t0
     out = dict(value=amps / dt, unit="amplitudes/s", seconds=dt,
                sample=f"FP64 state-vector oracle, the {{done}} smallest of the 98 Fig. 3.1 circuits ({{dt:.1f}} s)")
+elif kind == "q428":
+    from oracle.fixedpoint import apply_gate_q, quantize_matrix, ONE
+    c, _ = C.brickwork({n}, {depth}, {seed})
+    re = np.zeros(1 << c.n_qubits, dtype=np.int64)
+    im = np.zeros(1 << c.n_qubits, dtype=np.int64)
+    re[0] = ONE
+    done = 0
+    for g in c.gates:
+        Ur, Ui = quantize_matrix(gate_matrix(c, g, None))
+        re, im = apply_gate_q(re, im, c.n_qubits, Ur, Ui, g.qubits)
+        done += 1
+        if time.perf_counter() - t0 > budget:
+            break
+    dt = time.perf_counter() - t0
+    out = dict(value=(1 << c.n_qubits) / (dt * len(c.gates) / done), unit="amplitudes/s", seconds=dt,
+               sample=f"Q4.28 fixed-point oracle (numpy int64), first {{done}} of {{len(c.gates)}} gates "
+                      f"({{dt:.1f}} s), scaled to the whole circuit")
 elif kind == "sweep_amps":
     pts = [(n, k) for n in range(2, 29, 2) for k in range(2, 15, 2)]
     done = 0
@@ -244,7 +261,7 @@ elif kind == "sweep_amps":
 print(json.dumps(out))
 """
 
-ORACLE_KINDS = ("state", "grad", "amps", "serve", "sweep", "sweep_amps")
+ORACLE_KINDS = ("state", "grad", "amps", "serve", "sweep", "sweep_amps", "q428")
 
 
 def run_oracle_sample(kind: str, n: int, depth: int, seed: int, budget: float, threads: int = 1):
@@ -282,6 +299,9 @@ WORKLOADS = {
     # (3xTF32 merges, one plan per circuit sized for 64 bitstrings per call)
     "fig31amps": dict(kind="sweep_amps", n=28, depth=14, seed=6000, batch=98, chunk=64, prec=1),
     "grad20": dict(kind="grad", n=20, depth=10, seed=4000, batch=64),
+    # the 24-qubit brickwork (depth 20, fixed angles) in the paper's Q4.28 fixed-point arithmetic:
+    # one HBM-bound launch per gate on int32 pairs
+    "q428_24": dict(kind="q428", n=24, depth=20, seed=1001, batch=1),
     # contraction-path search on the host (the paper's E1 grid): the 98 Fig. 3.1 circuits planned
     # for 64 bitstrings per call, the deterministic greedy alone against the randomised search
     "plan31": dict(kind="plan", n=28, depth=14, seed=6000, batch=98, chunk=64),
@@ -494,6 +514,19 @@ def main():
         per_call = per_pass * (chunk >> nst["net_batch_log2"])
         launches_per_step = per_call * (batch // chunk)
         kernel_only = None
+    elif wl["kind"] == "q428":
+        circ, _ = C.brickwork(wl["n"], wl["depth"], wl["seed"])
+        qplan = tn.Plan(tn.CircuitHandle(circ), q428=True)
+        qst = torch.empty((1 << wl["n"], 2), dtype=torch.int32, device=dev)
+        batch = 1
+        units_per_step = float(1 << wl["n"])
+        unit = "amplitudes/s"
+        ctr = None
+
+        def step():
+            tn.contract_state_q428(qplan, qst)
+        launches_per_step = 1 + len(circ.gates)  # basis state, then one launch per gate
+        kernel_only = None
     elif wl["kind"] == "sweep_amps":
         pts = [(n, k) for n in range(2, 29, 2) for k in range(2, 15, 2)]
         chunk = wl["chunk"]
@@ -634,6 +667,8 @@ def main():
     dtype = {0: "f32", 1: "3xtf32 (f32 accumulate)", 2: "bf16x3 (f32 accumulate)"}[prec_used]
     if wl["kind"] == "permute":
         dtype = "c64 (data movement)"
+    if wl["kind"] == "q428":
+        dtype = "q4.28 (int32 pairs, int64 sums)"
     t_max = max_over_ranks(sum(ms), world, dev)
     value = whole_job_value(units_per_step, args.steps, world, t_max)
     assert tn.sync_status() == tn.OK
@@ -873,6 +908,35 @@ def main():
                             "kernel": "network merges (k_cgemm_fp32 / k_cgemm_tc*) of all 98 circuits",
                             "algorithmic_bytes_per_step": step_bytes,
                             "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})"}
+    if wl["kind"] == "q428":
+        # algorithmic bytes of the step: the basis state written, then every amplitude read and
+        # written once per gate (int32 pairs); all launches of the step are of this kind
+        per_step_s = t_max / args.steps / 1000.0
+        qb = qplan.stats()["hbm_bytes"]
+        ach = qb / per_step_s / 1e9
+        # the same circuit through the FP32 path: relative 2-norm difference of the two states
+        fctr = tn.Contractor(circ, device=dev)
+        f32 = fctr.state(None)[0].to(torch.complex128)
+        qv = (qst[:, 0].to(torch.float64) + 1j * qst[:, 1].to(torch.float64)) / float(1 << 28)
+        diff = (torch.linalg.vector_norm(qv - f32) / torch.linalg.vector_norm(f32)).item()
+        line["config"].update({"circuit": "brickwork, fixed angles", "arithmetic": "Q4.28: int32 values q/2^28, "
+                               "exact 64-bit sums, round half up, saturating", "gates": len(circ.gates)})
+        line["rel_l2_vs_fp32_path"] = diff
+        line["roofline"] = {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
+                            "frac": ach / hbm_peak, "traffic": None, "kernel": "k_q428_g1 / k_q428_g2",
+                            "algorithmic_bytes_per_step": qb, "avg_launch_ms": 1000.0 * per_step_s / launches_per_step,
+                            "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})"}
+    if not args.no_e2e and wl["kind"] == "q428":
+        h_q = torch.empty((1 << wl["n"], 2), dtype=torch.int32).pin_memory()
+
+        def e2e_step():
+            tn.contract_state_q428(qplan, qst)
+            h_q.copy_(qst, non_blocking=True)
+        for _ in range(3):
+            e2e_step()
+        ems = timed(e2e_step, args.steps)
+        line["e2e"] = {"value": units_per_step * args.steps / (sum(ems) / 1000), "unit": unit,
+                       "h2d_bytes_per_step": 0, "d2h_bytes_per_step": int(h_q.numel() * 4)}
     if wl["kind"] == "permute":
         per_step_s = t_max / args.steps / 1000.0
         ach = units_per_step / per_step_s

@@ -110,6 +110,9 @@ typedef enum { TN_PREC_FP32 = 0, TN_PREC_3XTF32 = 1, TN_PREC_SPLIT_BF16 = 2 } tn
                             * (each fixed to 0 and 1 in turn, the slices' amplitudes summed in FP64),
                             * whichever costs less, at most 2^16 slices; beyond that
                             * TN_ERR_UNSUPPORTED. */
+#define TN_PLAN_Q428 8 /* a fixed-point plan for tn_contract_state_q428 (Sec. 3: the FPGA datapath's
+                         * complex arithmetic in 32-bit fixed point, 28 fractional bits); fixed-angle
+                         * circuits, batch 1, target TN_TARGET_STATE, at most 34 qubits */
 #define TN_PLAN_NO_SPECIALIZE 2 /* run the interpreting gate-apply kernel instead of plan-specialised
                                  * kernels (those are generated as CUDA C++ and compiled with NVRTC
                                  * when the plan is built; compiled code is cached on disk) */
@@ -210,6 +213,17 @@ void tn_free_observable(tn_observable *o);
  *   workspace_dev  >= tn_plan_workspace_bytes device bytes, or NULL when that is 0 */
 tn_status tn_contract_state(const tn_plan *p, const double *params_dev, void *state_dev,
                             void *workspace_dev, tn_stream_t s);
+
+/* Fixed-point emulation of the paper's datapath (Sec. 3: complex arithmetic in 32-bit fixed point
+ * with 28 bits behind the binary point).  p: a plan built with TN_PLAN_Q428.  state_dev: int32
+ * [2^N][2] (re, im), device memory owned by the caller; on return (stream-ordered) it holds the
+ * circuit applied to |init_basis>, every value q meaning q / 2^28.  Arithmetic: each gate matrix
+ * is quantised once, Uq = floor(U 2^28 + 1/2) (FP64, then saturated to int32); each gate is applied
+ * once, every output component being the exact integer sum of Uq[i][k] psi[k] (64-bit) rounded
+ * half up to Q4.28 ((acc + 2^27) >> 28) and saturated to int32.  Exact for unitary gates on states
+ * of norm <= 1 (every sum below 2^60).  Returns TN_ERR_INVALID_ARG for a NULL pointer or a plan
+ * not built with TN_PLAN_Q428; needs no workspace. */
+tn_status tn_contract_state_q428(const tn_plan *p, int32_t *state_dev, tn_stream_t s);
 
 /* Single amplitudes <x_i| C |init_basis> (Sec. 2.2.3: output legs closed by basis states).
  *   bitstrings_dev uint64 [n_bitstrings] device (bit N-1-q = qubit q), each < 2^N

@@ -151,6 +151,7 @@ tn_status call_mats(const tn_plan *p, const double *params, void *ws, cudaStream
 tn_status common_checks(const tn_plan *p) {
   TN_CHECK_ARG(p != nullptr, "plan is NULL");
   TN_CHECK_ARG(!p->host_only, "plan was built with TN_PLAN_HOST_ONLY and cannot run");
+  TN_CHECK_ARG(p->q428 == nullptr, "a TN_PLAN_Q428 plan runs through tn_contract_state_q428 only");
   return check_device(p->device);
 }
 
@@ -232,6 +233,12 @@ tn_status tn_plan_contraction(const tn_circuit *c, const tn_plan_opts *opts, tn_
   for (int i = 0; i < 4; ++i) TN_CHECK_ARG(o.reserved[i] == 0, "reserved fields must be zero");
   TN_CHECK_ARG(o.order_trials == 0 || o.order_trials == 1 || (o.order_trials >= 4 && o.order_trials <= 4096),
                "order_trials must be 0, 1 or 4..4096 (got %lld)", (long long)o.order_trials);
+  if (o.flags & TN_PLAN_Q428) {
+    TN_CHECK_ARG(!(o.flags & TN_PLAN_NETWORK), "TN_PLAN_Q428 and TN_PLAN_NETWORK exclude each other");
+    TN_CHECK_ARG(o.target == TN_TARGET_STATE && o.batch == 1, "TN_PLAN_Q428 contracts one state (batch 1)");
+    TN_CHECK_ARG(c->n_params == 0, "TN_PLAN_Q428 takes fixed-angle circuits");
+    TN_CHECK_ARG(c->n <= kMaxQubits, "TN_PLAN_Q428 holds at most %d qubits", kMaxQubits);
+  }
   if (o.flags & TN_PLAN_NETWORK) {
     TN_CHECK_ARG(o.target == TN_TARGET_AMPLITUDES, "TN_PLAN_NETWORK needs TN_TARGET_AMPLITUDES");
     TN_CHECK_ARG(o.batch == 1, "TN_PLAN_NETWORK takes one parameter set (batch 1)");
@@ -260,6 +267,14 @@ tn_status tn_plan_contraction(const tn_circuit *c, const tn_plan_opts *opts, tn_
   p->T = T;
   p->K = K;
   std::string err;
+  if (o.flags & TN_PLAN_Q428) {
+    p->q428 = new std::vector<Q428Gate>();
+    q428_build(*c, *p->q428);
+    if (!p->host_only) TN_CUDA(cudaGetDevice(&p->device), "cudaGetDevice");
+    p->ws_bytes = 0;
+    *out = p;
+    return TN_OK;
+  }
   if (o.flags & TN_PLAN_NETWORK) {
     p->net = new NetPlan();
     int lb = 0;
@@ -399,6 +414,11 @@ tn_status tn_plan_get_stats(const tn_plan *p, tn_plan_stats *st) {
   st->n_passes = (int)p->fwd.passes.size();
   st->n_phases = (int)p->fwd.phases.size();
   st->n_ops = (long long)p->fwd.ops.size();
+  if (p->q428) {  // one launch per gate, each reading and writing every amplitude (int32 pairs)
+    st->n_passes = (int)p->q428->size();
+    st->hbm_bytes = 8.0 * std::ldexp(1.0, p->n) * (1.0 + 2.0 * (double)p->q428->size());
+    return TN_OK;
+  }
   st->tile_qubits = p->T;
   st->reg_qubits = p->K;
   st->flops = p->fwd.flops;
@@ -427,6 +447,8 @@ tn_status tn_plan_get_stats(const tn_plan *p, tn_plan_stats *st) {
 
 void tn_free_plan(tn_plan *p) {
   if (!p) return;
+  delete p->q428;
+  p->q428 = nullptr;
   if (p->net) {
     if (!p->host_only) free_network(*p->net);
     delete p->net;
@@ -608,6 +630,18 @@ tn_status tn_contract_amplitudes(const tn_plan *p, const double *params_dev, con
   TN_CUDA(launch_forward(p, mats, mstride, psi, cs), "gate-apply kernel");
   TN_CUDA(launch_gather(psi, p->n, p->batch, bitstrings_dev, n_bitstrings, static_cast<float2 *>(amps_dev), cs),
           "gather kernel");
+  return TN_OK;
+}
+
+tn_status tn_contract_state_q428(const tn_plan *p, int32_t *state_dev, tn_stream_t s) {
+  TN_CHECK_ARG(p != nullptr, "plan is NULL");
+  TN_CHECK_ARG(p->q428 != nullptr, "the plan was not built with TN_PLAN_Q428");
+  TN_CHECK_ARG(!p->host_only, "plan was built with TN_PLAN_HOST_ONLY and cannot run");
+  TN_CHECK_ARG(state_dev != nullptr, "state_dev is NULL");
+  TN_CHECK_ARG(((uintptr_t)state_dev & 7) == 0, "state_dev must be 8-byte aligned");
+  tn_status st = check_device(p->device);
+  if (st != TN_OK) return st;
+  TN_CUDA(launch_q428(*p->q428, p->n, p->init, state_dev, reinterpret_cast<cudaStream_t>(s)), "fixed-point kernels");
   return TN_OK;
 }
 

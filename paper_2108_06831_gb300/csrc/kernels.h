@@ -49,6 +49,11 @@ struct OutMap {
   uint8_t pos[64] = {};
 };
 size_t cgemm_workspace(int precision, long long batch, long long M, long long N, long long K);
+// Fixed-point (Q4.28) state contraction: basis state, then every gate once (k_q428.cu).
+int32_t q428_quantize(double x);
+void q428_build(const tn_circuit &c, std::vector<Q428Gate> &out);
+cudaError_t launch_q428(const std::vector<Q428Gate> &gates, int n, unsigned long long init, int32_t *state,
+                        cudaStream_t s);
 // Fraction of the FP32 GEMM's tile work that falls inside an M x N output (its tile choice).
 double cgemm_fp32_tile_fill(long long M, long long N);
 cudaError_t launch_cgemm(int precision, long long batch, long long M, long long N, long long K, const float2 *A,

@@ -268,8 +268,19 @@ namespace tnq {
 struct NetPlan;
 }
 
+namespace tnq {
+// A gate of a fixed-point plan: the matrix rounded to Q4.28 (value q / 2^28), row-major,
+// (re, im) interleaved; pos: state bits of the gate's qubits (first qubit first).
+struct Q428Gate {
+  int nq;
+  int pos[2];
+  int32_t u[32];
+};
+}  // namespace tnq
+
 struct tn_plan {
   tnq::NetPlan *net = nullptr;  // TN_PLAN_NETWORK plans: pairwise network contraction
+  std::vector<tnq::Q428Gate> *q428 = nullptr;  // TN_PLAN_Q428 plans: quantised gate list
   int n;
   long long n_gates;
   int batch;

@@ -26,6 +26,7 @@ PREC_FP32, PREC_3XTF32, PREC_SPLIT_BF16 = 0, 1, 2
 PLAN_HOST_ONLY = 1
 PLAN_NO_SPECIALIZE = 2
 PLAN_NETWORK = 4
+PLAN_Q428 = 8
 
 GATE_KINDS = {name: i for i, name in enumerate(
     ["H", "X", "Y", "Z", "S", "SDG", "T", "TDG", "SX", "SY", "SW", "RX", "RY", "RZ", "U3",
@@ -77,6 +78,7 @@ _sigs = {
     "tn_build_observable": [C.c_int32, C.POINTER(TnPauliSum), C.POINTER(_vp)],
     "tn_free_observable": [_vp],
     "tn_contract_state": [_vp, _vp, _vp, _vp, _vp],
+    "tn_contract_state_q428": [_vp, _vp, _vp],
     "tn_contract_amplitudes": [_vp, _vp, _vp, C.c_int64, _vp, _vp, _vp],
     "tn_expectation": [_vp, _vp, _vp, _vp, _vp, _vp],
     "tn_expectation_backward": [_vp, _vp, _vp, _vp, _vp, _vp, _vp],
@@ -178,12 +180,13 @@ class CircuitHandle:
 class Plan:
     def __init__(self, ch: CircuitHandle, target: int = TARGET_STATE, precision: int = PREC_FP32, batch: int = 1,
                  tile_qubits: int = 0, host_only: bool = False, specialize: bool = True, network_bitstrings: int = 0,
-                 max_intermediate_log2: int = 0, order_trials: int = 0):
+                 max_intermediate_log2: int = 0, order_trials: int = 0, q428: bool = False):
         o = TnPlanOpts()
         o.order_trials = order_trials
         o.target, o.precision, o.batch, o.tile_qubits = target, precision, batch, tile_qubits
         o.max_intermediate_log2 = max_intermediate_log2
-        o.flags = (PLAN_HOST_ONLY if host_only else 0) | (0 if specialize else PLAN_NO_SPECIALIZE)
+        o.flags = (PLAN_HOST_ONLY if host_only else 0) | (0 if specialize else PLAN_NO_SPECIALIZE) | \
+            (PLAN_Q428 if q428 else 0)
         if network_bitstrings:
             o.flags |= PLAN_NETWORK
             o.amp_batch = network_bitstrings
@@ -243,6 +246,11 @@ def build_observable(H: PauliSum) -> Observable:
 def contract_state(plan: Plan, params, state, workspace, stream=None) -> None:
     _check(_lib.tn_contract_state(plan._h, _ptr(params), _ptr(state), _ptr(workspace), _stream(stream)),
            "tn_contract_state")
+
+
+def contract_state_q428(plan: Plan, state, stream=None) -> None:
+    """Fixed-point (Q4.28) contraction of a plan built with q428=True; state: int32 [2^N, 2] on the device."""
+    _check(_lib.tn_contract_state_q428(plan._h, _ptr(state), _stream(stream)), "tn_contract_state_q428")
 
 
 def contract_amplitudes(plan: Plan, params, bitstrings, amps, workspace, stream=None) -> None:

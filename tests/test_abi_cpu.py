@@ -163,3 +163,20 @@ def test_network_order_search_never_worse_than_greedy():
     for bad in (2, 3, 5000, -1):
         with pytest.raises(tn.TnError):
             tn.Plan(tn.CircuitHandle(C.ghz(4)), order_trials=bad, **kw)
+
+
+def test_q428_plan_host_only():
+    """A fixed-point plan: one launch per gate, each reading and writing every amplitude (int32
+    pairs) after the basis state is written; fixed-angle circuits with batch 1 only, and not
+    together with network planning."""
+    from paper_2108_06831_gb300 import tn
+    c = C.brickwork(12, 6, 4)[0]
+    s = tn.Plan(tn.CircuitHandle(c), q428=True, host_only=True).stats()
+    assert s["n_passes"] == len(c.gates)
+    assert s["hbm_bytes"] == 8.0 * (1 << 12) * (1 + 2 * len(c.gates))
+    with pytest.raises(tn.TnError):
+        tn.Plan(tn.CircuitHandle(C.brickwork(6, 2, 1, parameterized=True)[0]), q428=True, host_only=True)
+    with pytest.raises(tn.TnError):
+        tn.Plan(tn.CircuitHandle(c), q428=True, batch=2, host_only=True)
+    with pytest.raises(tn.TnError):
+        tn.Plan(tn.CircuitHandle(c), q428=True, network_bitstrings=4, target=tn.TARGET_AMPLITUDES, host_only=True)

@@ -275,3 +275,53 @@ def test_sweep_amplitudes_equal_state_entries(maker):
     xs = C.random_bitstrings(c.n_qubits, 6, 12)
     for x in xs:
         assert abs(TN.contract_amplitude_sweep(c, int(x), p) - psi[int(x)]) < 1e-12
+
+
+# --- Q4.28 fixed-point oracle (Sec. 3: 32-bit fixed point, 28 fractional bits) -------------
+
+def test_q428_quantize_rounding_and_saturation():
+    """floor(x 2^28 + 1/2): halves round up, values beyond the int32 range saturate."""
+    from oracle import fixedpoint as F
+    assert F.quantize(1.0) == 1 << 28 and F.quantize(-1.0) == -(1 << 28)
+    assert F.quantize(2.0 ** -29) == 1 and F.quantize(-(2.0 ** -29)) == 0  # ties toward +inf
+    assert F.quantize(3 * 2.0 ** -30) == 1 and F.quantize(-3 * 2.0 ** -30) == -1
+    assert F.quantize(2.0 ** -30) == 0
+    assert F.quantize(8.0) == 2 ** 31 - 1 and F.quantize(-9.0) == -(2 ** 31)
+    assert F.quantize(-8.0) == -(2 ** 31)  # -8 is representable
+
+
+def test_q428_exact_permutations_and_signs():
+    """X, CNOT, SWAP and CZ have entries 0 and +-1: in Q4.28 they permute and negate exactly."""
+    from oracle import fixedpoint as F
+    c = C.Circuit(3, [C.Gate("X", (0,)), C.Gate("CNOT", (0, 2)), C.Gate("SWAP", (1, 2)), C.Gate("CZ", (0, 1))],
+                  init_basis=0)
+    re, im = F.simulate_state_q428(c)
+    # |000> -X0-> |100> -CNOT(0,2)-> |101> -SWAP(1,2)-> |110> -CZ(0,1)-> -|110>
+    expect = np.zeros(8, dtype=np.int64)
+    expect[0b110] = -(1 << 28)
+    assert np.array_equal(re, expect) and not im.any()
+
+
+def test_q428_hadamard_on_basis_is_the_quantised_entry():
+    """H|0>: each output is Uq[i][0] * 2^28 rounded back, i.e. exactly quantize(1/sqrt 2)."""
+    from oracle import fixedpoint as F
+    re, im = F.simulate_state_q428(C.Circuit(1, [C.Gate("H", (0,))]))
+    q = F.quantize(1.0 / np.sqrt(2.0))
+    assert re.tolist() == [q, q] and not im.any()
+
+
+@pytest.mark.parametrize("n,seed", [(1, 1), (3, 2), (6, 3), (9, 4)])
+def test_q428_within_rounding_bound_of_fp64(n, seed):
+    """Error bound: one gate adds at most 2^-29 per output component from rounding (2^-28.5 per
+    complex amplitude) plus the matrix quantisation error (each entry within 2^-29 per part, so
+    the operator error is at most d 2^-28.5 for a d x d gate, d <= 4); unitaries do not grow
+    errors in the 2-norm.  So ||psi_q - psi|| <= G (2^(n/2) 2^-28.5 + 4 2^-28.5).  A dropped term,
+    wrong sign or transposed operand gives an O(1) error."""
+    from oracle import fixedpoint as F
+    from oracle.statevector import simulate_state
+    c = C.random_circuit(n, 15 * n + 5, 900 + seed)
+    re, im = F.simulate_state_q428(c)
+    err = np.linalg.norm(F.to_complex(re, im) - simulate_state(c))
+    bound = len(c.gates) * (2.0 ** (n / 2) + 4.0) * 2.0 ** -28.5
+    assert err <= bound, (err, bound)
+    assert err > 0 or n == 1  # rounding does happen
