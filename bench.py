@@ -56,18 +56,25 @@ def parse():
     return ap.parse_args()
 
 
-def recorded_traffic(kernel_hash):
-    """DRAM bytes per launch of the gate-apply pass kernels from the committed ncu summary, or
-    None unless the generated kernel sources hash to the value recorded with that capture."""
+def recorded_traffic(kernel_hash, profile="fused_gate_apply_state24.md"):
+    """DRAM bytes per launch of the profiled kernel from the committed ncu summary, or None
+    unless the kernel sources hash to the value recorded with that capture."""
     import re
     try:
-        with open(os.path.join(ROOT, "profiles", "fused_gate_apply_state24.md")) as fh:
+        with open(os.path.join(ROOT, "profiles", profile)) as fh:
             m = re.search(r"traffic_bytes_per_launch=(\d+) kernel_hash=([0-9a-f]+)", fh.read())
         if m and m.group(2) == kernel_hash:
             return float(m.group(1))
     except OSError:
         pass
     return None
+
+
+def file_hash(path):
+    """sha256 (16 hex digits) of one source file."""
+    import hashlib
+    with open(path, "rb") as fh:
+        return hashlib.sha256(fh.read()).hexdigest()[:16]
 
 
 def jit_source_hash(dump_dir):
@@ -922,8 +929,11 @@ def main():
         line["config"].update({"circuit": "brickwork, fixed angles", "arithmetic": "Q4.28: int32 values q/2^28, "
                                "exact 64-bit sums, round half up, saturating", "gates": len(circ.gates)})
         line["rel_l2_vs_fp32_path"] = diff
+        qhash = file_hash(os.path.join(ROOT, "paper_2108_06831_gb300", "csrc", "k_q428.cu"))
         line["roofline"] = {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
-                            "frac": ach / hbm_peak, "traffic": None, "kernel": "k_q428_g1 / k_q428_g2",
+                            "frac": ach / hbm_peak, "traffic": recorded_traffic(qhash, "q428_state24.md"),
+                            "traffic_kernel": "k_q428_g1", "kernel_source_hash": qhash,
+                            "kernel": "k_q428_g1 / k_q428_g2",
                             "algorithmic_bytes_per_step": qb, "avg_launch_ms": 1000.0 * per_step_s / launches_per_step,
                             "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})"}
     if not args.no_e2e and wl["kind"] == "q428":
