@@ -355,6 +355,10 @@ def reference_arm(args):
     if rank != 0:
         return 0
     wl = WORKLOADS[args.workload]
+    if wl["kind"] == "plan":
+        print(json.dumps({"impl": "reference", "unavailable": "host-only planning workload: the oracle contracts "
+                          "in its own fixed order and has no order search to time"}))
+        return 0
     if wl["kind"] not in ORACLE_KINDS:
         print(json.dumps({"impl": "reference", "unavailable": "kernel-level workload with no oracle counterpart "
                           "(the oracle computes states, amplitudes and expectations, not bare GEMMs or permutes)"}))
@@ -376,7 +380,8 @@ def reference_arm(args):
     sample = info["sample"] + ", 1 thread"
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": unit, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * wall / max(args.steps, 1),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "q4.28 (int64 sums)" if wl["kind"] == "q428" else "f64", "data": "synthetic",
             "config": {"workload": args.workload, **{k: wl[k] for k in ("n", "depth", "batch")}},
             "cpu_baseline": {"value": v, "unit": unit, "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
