@@ -95,3 +95,25 @@ def test_cgemm_fp32_split_k(shape):
     batch, M, N, K = shape
     assert tn.cgemm_workspace_bytes(0, batch, M, N, K) > 0  # the split path is taken
     assert _run(0, batch, M, N, K, seed=sum(shape)) <= TOL
+
+
+def test_block_diagonal_matricisation_is_the_batched_gemm():
+    """Sec. 3 lays an order-(p, q) tensor out as one matrix: block_diag of its trailing d x d slices
+    t[idx] over the leading indices.  Multiplying that block-diagonal matrix by a stacked operand
+    is the batched GEMM with the leading indices as the batch (the form every network merge
+    takes), with no zero block stored or multiplied."""
+    scipy_linalg = pytest.importorskip("scipy.linalg")
+    tn = _tn()
+    rng = np.random.default_rng(31)
+    t = rng.normal(size=(2, 2, 2, 4, 4)) + 1j * rng.normal(size=(2, 2, 2, 4, 4))
+    mats = [t[idx] for idx in np.ndindex(t.shape[:-2])]
+    X = rng.normal(size=(8 * 4, 6)) + 1j * rng.normal(size=(8 * 4, 6))
+    ref = (scipy_linalg.block_diag(*mats) @ X).reshape(8, 4, 6)  # [block][row][column]
+    a = torch.as_tensor(np.stack(mats).astype(np.complex64), device="cuda")                    # [b][m][k]
+    b = torch.as_tensor(X.reshape(8, 4, 6).transpose(0, 2, 1).copy().astype(np.complex64), device="cuda")  # [b][n][k]
+    c = torch.empty((8, 4, 6), dtype=torch.complex64, device="cuda")
+    ws = torch.empty(16, dtype=torch.uint8, device="cuda")
+    tn.cgemm_batched(0, 8, 4, 6, 4, a, b, c, ws, tn.cgemm_workspace_bytes(0, 8, 4, 6, 4))
+    torch.cuda.synchronize()
+    got = c.cpu().numpy().astype(np.complex128)
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= TOL

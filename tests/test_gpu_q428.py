@@ -92,3 +92,34 @@ def test_wrong_plan_kinds_rejected():
                           torch.empty(16, dtype=torch.uint8, device="cuda"))
     with pytest.raises(tn.TnError):
         tn.Plan(tn.CircuitHandle(C.brickwork(6, 2, 1, parameterized=True)[0]), q428=True)
+
+
+def test_30_qubits_closed_form():
+    """30 qubits (an 8 GiB int32-pair state): H on every qubit, CZ on every neighbour pair, X on
+    qubit 0.  Each H meets a qubit still in |0>, so it maps every amplitude a to
+    round(quantize(1/sqrt 2) a / 2^28) on both branches; CZ (entries +-1) negates exactly and X
+    permutes exactly.  Every entry is then +-a_30 (real), the sign (-1)^(sum_q x_q x_{q+1}) of the
+    index before the X."""
+    from oracle import fixedpoint as F
+    from paper_2108_06831_gb300 import tn
+    n = 30
+    gates = [C.Gate("H", (q,)) for q in range(n)] + [C.Gate("CZ", (q, q + 1)) for q in range(n - 1)]
+    gates.append(C.Gate("X", (0,)))
+    p = tn.Plan(tn.CircuitHandle(C.Circuit(n, gates)), q428=True)
+    st = torch.empty((1 << n, 2), dtype=torch.int32, device="cuda")
+    tn.contract_state_q428(p, st)
+    torch.cuda.synchronize()
+    assert tn.sync_status() == tn.OK
+    qh = F.quantize(1.0 / np.sqrt(2.0))
+    a = F.ONE
+    for _ in range(n):
+        a = int(F.round_q(np.array([qh * a], dtype=np.int64))[0])
+    assert not bool((st[:, 1] != 0).any())
+    assert bool((st[:, 0].abs() == a).all())
+    rng = np.random.default_rng(30)
+    xs = rng.integers(0, 1 << n, size=4096, dtype=np.int64)
+    got = st[torch.as_tensor(xs, device="cuda"), 0].cpu().numpy().astype(np.int64)
+    pre = xs ^ (1 << (n - 1))  # undo the X on qubit 0 (the most significant bit)
+    bits = (pre[:, None] >> (n - 1 - np.arange(n))[None, :]) & 1
+    sign = 1 - 2 * (np.sum(bits[:, :-1] * bits[:, 1:], axis=1) & 1)
+    assert np.array_equal(got, sign * a)
