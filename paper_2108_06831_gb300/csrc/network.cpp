@@ -11,16 +11,20 @@
 //   - every output leg is closed by u_q^b = <x_q^b| M_q (M_q the qubit's trailing one-qubit
 //     product), a [B x 2] tensor sharing the bitstring index b (a hyperedge over all outputs)
 //     -- built on the device from the bitstrings at call time;
-//   - pairs of nodes sharing an index are merged greedily by size reduction (randomised
-//     trials, the best kept); an index carried by more than the two merged tensors (a
-//     hyperedge, e.g. the bitstring index) is a batch index of the merge;
+//   - the order is searched over seeded trials run on all host cores (greedy merging by size
+//     reduction with Gumbel noise, qubit sweeps, fold-first), the cheapest kept by the cost
+//     of one call (launches, bytes, flops; merges of bitstring-independent tensors are folded
+//     at plan time and cost nothing per call); an index carried by more than the two merged
+//     tensors (a hyperedge, e.g. the bitstring index) is a batch index of the merge;
 //   - each merge is lowered to one batched complex GEMM (kernel c) whose operands are laid
 //     out as it reads them;
-//   - when no order found keeps every intermediate within the cap, indices are sliced: each
-//     chosen index is fixed to 0 and to 1 in turn, every slice is the network without it, and
-//     the amplitudes are the sum over all slices (exact: the full contraction sums over that
-//     index too).  Indices are picked greedily on the best order (the one shrinking the most
-//     largest intermediates, then the fewest flops), and the sliced network is planned again.
+//   - a call's bitstrings may be contracted in smaller passes (every pass size is searched);
+//   - when no order keeps every intermediate within the cap, indices are sliced: each chosen
+//     index is fixed to 0 and to 1 in turn, every slice is the network without it, and the
+//     amplitudes are the sum over all slices (exact: the full contraction sums over that
+//     index too).  Indices are picked greedily on every trial that exceeds the cap (the one
+//     shrinking the most largest intermediates, then the most flops), and the sliced network
+//     is planned again.
 #include <algorithm>
 #include <atomic>
 #include <cmath>
