@@ -170,6 +170,33 @@ __global__ void __launch_bounds__(kThreads, 2) k_cgemm_fp32(long long M, long lo
   }
 }
 
+// Small merges (at most 2^18 complex multiply-adds, K <= 64; most merges of small circuits):
+// one thread per output element reads its K-contiguous rows of A and B straight from global
+// memory (cache-resident at this size) and stores through the output map, without tile
+// staging.  The accumulation over k is the tiled kernel's (same order, same fused
+// multiply-adds), so both give the same bits.
+__global__ void __launch_bounds__(256) k_cgemm_small(long long M, long long N, long long K, long long total,
+                                                     const float2 *__restrict__ A, const float2 *__restrict__ B,
+                                                     float2 *__restrict__ C, const __grid_constant__ OutMap om) {
+  for (long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x; f < total;
+       f += (long long)gridDim.x * blockDim.x) {
+    const long long n = f % N, bm = f / N;  // bm = b M + m
+    const long long b = bm / M;
+    const float2 *a = A + bm * K;
+    const float2 *w = B + (b * N + n) * K;
+    float2 acc = make_float2(0.f, 0.f);
+    for (long long k = 0; k < K; ++k) {
+      const float2 x = a[k], y = w[k];
+      acc.x = fmaf(x.x, y.x, acc.x);
+      acc.x = fmaf(-x.y, y.y, acc.x);
+      acc.y = fmaf(x.x, y.y, acc.y);
+      acc.y = fmaf(x.y, y.x, acc.y);
+    }
+    C[om.identity ? f : map_bits(om, f, 0)] = acc;
+  }
+}
+constexpr long long kSmallWork = 1ll << 18;
+
 // Sum of the split-K partials (in split order) of every output element, stored through the
 // output map: C[map(f)] = sum_s P[s][f], f the natural index (b M + m) N + n.
 __global__ void k_splitk_reduce(const float2 *__restrict__ P, int splits, long long total, float2 *__restrict__ C,
@@ -335,6 +362,11 @@ cudaError_t launch_cgemm_fp32(long long batch, long long M, long long N, long lo
   float2 *P = need > 0 ? static_cast<float2 *>(ws) : nullptr;
   const OutMap ident;
   const OutMap &m = om ? *om : ident;
+  const long long total = batch * M * N;
+  if (K <= 64 && (double)total * (double)K <= (double)kSmallWork) {
+    k_cgemm_small<<<(unsigned)std::min<long long>((total + 255) / 256, 1024), 256, 0, s>>>(M, N, K, total, A, B, C, m);
+    return cudaGetLastError();
+  }
   if (K <= 8) return launch_k<8>(batch, M, N, K, A, B, C, P, m, s);
   return launch_k<16>(batch, M, N, K, A, B, C, P, m, s);
 }

@@ -60,7 +60,10 @@ def test_cgemm_deep_contraction(prec):
 
 
 def test_cgemm_fp32_ragged_shapes():
-    for shape in [(1, 5, 7, 3), (2, 65, 33, 17), (1, 1, 1, 1), (3, 130, 70, 9)]:
+    # the first four take the one-thread-per-output kernel (at most 2^18 multiply-adds), the last
+    # three the tiled kernel with ragged edges in M, N and K
+    for shape in [(1, 5, 7, 3), (2, 65, 33, 17), (1, 1, 1, 1), (3, 130, 70, 9),
+                  (2, 300, 70, 20), (1, 1000, 9, 40), (1, 77, 200, 100)]:
         assert _run(0, *shape, seed=7) <= TOL
 
 
