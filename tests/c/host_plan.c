@@ -1,5 +1,7 @@
 /* Uses the C ABI from plain C99 (no C++, no Python): builds a circuit, plans it on the host
- * only (no device needed), reads the plan statistics, checks argument errors, frees it. */
+ * only (no device needed) as a state contraction, as a network contraction under an
+ * intermediate cap and as a fixed-point (Q4.28) plan, reads the plan statistics, checks
+ * argument errors, frees everything. */
 #include <stdio.h>
 #include <string.h>
 
@@ -56,7 +58,44 @@ int main(void) {
     printf("expected TN_ERR_INVALID_ARG\n");
     return 1;
   }
-  printf("ok %s passes=%d phases=%d flops=%.0f\n", tn_version(), st.n_passes, st.n_phases, st.flops);
+  /* amplitudes by network contraction, 16 bitstrings per call, intermediates capped at 2^8 */
+  tn_plan_opts on;
+  memset(&on, 0, sizeof(on));
+  on.target = TN_TARGET_AMPLITUDES;
+  on.batch = 1;
+  on.precision = TN_PREC_3XTF32;
+  on.flags = TN_PLAN_HOST_ONLY | TN_PLAN_NETWORK;
+  on.amp_batch = 16;
+  on.max_intermediate_log2 = 8;
+  tn_plan *pn = NULL;
+  tn_plan_stats sn;
+  memset(&sn, 0, sizeof(sn));
+  if (tn_plan_contraction(c, &on, &pn) != TN_OK || tn_plan_get_stats(pn, &sn) != TN_OK ||
+      sn.net_max_log2 > 8 || sn.net_merges < 1 || sn.net_cost <= 0.0 || sn.net_bytes <= 0.0) {
+    printf("network plan failed: %s\n", tn_last_error());
+    return 1;
+  }
+  on.order_trials = 2; /* neither 1 nor 4..4096 */
+  tn_plan *pbad = NULL;
+  if (tn_plan_contraction(c, &on, &pbad) != TN_ERR_INVALID_ARG || pbad != NULL) {
+    printf("expected TN_ERR_INVALID_ARG for order_trials = 2\n");
+    return 1;
+  }
+  /* the fixed-point plan: one launch per gate */
+  tn_plan_opts oq = o;
+  oq.flags = TN_PLAN_HOST_ONLY | TN_PLAN_Q428;
+  tn_plan *pq = NULL;
+  tn_plan_stats sq;
+  memset(&sq, 0, sizeof(sq));
+  if (tn_plan_contraction(c, &oq, &pq) != TN_OK || tn_plan_get_stats(pq, &sq) != TN_OK || sq.n_passes != ng) {
+    printf("fixed-point plan failed: %s\n", tn_last_error());
+    return 1;
+  }
+  printf("ok %s passes=%d phases=%d flops=%.0f; network merges=%d sliced=%d pass=2^%d; q428 launches=%d\n",
+         tn_version(), st.n_passes, st.n_phases, st.flops, sn.net_merges, sn.net_sliced, sn.net_batch_log2,
+         sq.n_passes);
+  tn_free_plan(pq);
+  tn_free_plan(pn);
   tn_free_plan(p);
   tn_free_circuit(c);
   return 0;
