@@ -37,6 +37,7 @@
 #include <set>
 #include <string>
 #include <thread>
+#include <unordered_map>
 #include <vector>
 
 #include "network.h"
@@ -381,7 +382,8 @@ struct Contractor {
   }
   // The same greedy choice with the noise of every candidate pair drawn anew at every step
   // (each step samples a pair with probability ~ exp(-score / temperature)); a full scan of the
-  // candidates per step.
+  // candidates per step.  A pair's score without noise is computed once: it cannot change while
+  // both tensors live (as in greedy()).
   void greedy_stepwise(double temperature, uint64_t seed) {
     uint64_t rs = seed * 6364136223846793005ull + 1442695040888963407ull;
     auto uniform = [&]() {
@@ -389,6 +391,7 @@ struct Contractor {
       return ((rs >> 11) + 0.5) * (1.0 / 9007199254740992.0);
     };
     std::vector<int> res, batch, contr;
+    std::unordered_map<uint64_t, double> base_of;  // (i, j) -> score without noise
     for (;;) {
       double best = 1e300;
       int bi = -1, bj = -1;
@@ -397,10 +400,15 @@ struct Contractor {
         for (size_t u = 0; u < own.size(); ++u)
           for (size_t v = u + 1; v < own.size(); ++v) {
             const int i = std::min(own[u], own[v]), j = std::max(own[u], own[v]);
-            merged(i, j, res, batch, contr);
-            const double sr = std::ldexp(1.0, score_bits(res)), sa = std::ldexp(1.0, score_bits(legs[(size_t)i])),
-                         sb = std::ldexp(1.0, score_bits(legs[(size_t)j]));
-            double score = (sr - sa - sb) / std::max(sa, sb);
+            const uint64_t key = ((uint64_t)(uint32_t)i << 32) | (uint32_t)j;
+            auto it = base_of.find(key);
+            if (it == base_of.end()) {
+              merged(i, j, res, batch, contr);
+              const double sr = std::ldexp(1.0, score_bits(res)), sa = std::ldexp(1.0, score_bits(legs[(size_t)i])),
+                           sb = std::ldexp(1.0, score_bits(legs[(size_t)j]));
+              it = base_of.emplace(key, (sr - sa - sb) / std::max(sa, sb)).first;
+            }
+            double score = it->second;
             if (temperature > 0) score -= temperature * std::log(-std::log(uniform()));
             if (score < best) {
               best = score;
