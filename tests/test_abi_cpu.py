@@ -3,6 +3,7 @@ include/tn.h declares, validates arguments and plans (host-only) without touchin
 import os
 import re
 
+import numpy as np
 import pytest
 
 from paper_2108_06831_gb300 import circuits as C
@@ -180,3 +181,29 @@ def test_q428_plan_host_only():
         tn.Plan(tn.CircuitHandle(c), q428=True, batch=2, host_only=True)
     with pytest.raises(tn.TnError):
         tn.Plan(tn.CircuitHandle(c), q428=True, network_bitstrings=4, target=tn.TARGET_AMPLITUDES, host_only=True)
+
+
+def test_network_planner_invariants_random_circuits():
+    """Over seeded random circuits, bitstring batches and caps: the largest intermediate obeys the
+    cap; passes never hold more bitstrings than a call; at most 16 indices are sliced; the planned
+    cost covers the algorithmic bytes (it adds launch costs to max(bytes, flops / 32)); the same
+    inputs give the same plan; a larger search is never worse than the greedy alone."""
+    from paper_2108_06831_gb300 import tn
+    rng = np.random.default_rng(2024)
+    for trial in range(12):
+        n = int(rng.integers(4, 12))
+        c = C.random_circuit(n, int(rng.integers(2 * n, 10 * n)), 5000 + trial)
+        B = 1 << int(rng.integers(0, 5))
+        cap = int(rng.choice([0, 6, 8, 10]))
+        ch = tn.CircuitHandle(c)
+        kw = dict(target=tn.TARGET_AMPLITUDES, host_only=True, network_bitstrings=B, max_intermediate_log2=cap)
+        try:
+            s = tn.Plan(ch, **kw).stats()
+        except tn.TnError as e:  # a cap no slicing within 2^16 slices reaches
+            assert e.status == tn.ERR_UNSUPPORTED and cap
+            continue
+        assert s["net_max_log2"] <= (cap or 28)
+        assert (1 << s["net_batch_log2"]) <= B and 0 <= s["net_sliced"] <= 16
+        assert s["net_cost"] >= s["net_bytes"] > 0
+        assert tn.Plan(ch, **kw).stats() == s
+        assert s["net_cost"] <= tn.Plan(ch, order_trials=1, **kw).stats()["net_cost"]
