@@ -317,18 +317,18 @@ WORKLOADS = {
 
 def plan_search_line(args, wl):
     """Host-only measurement: planning time and planned cost per Fig. 3.1 circuit, greedy alone
-    (order_trials = 1) against the default search; no GPU work."""
+    (order_trials = 1) against the default search and the adaptive search; no GPU work."""
     from paper_2108_06831_gb300 import circuits as C
     from paper_2108_06831_gb300 import tn
     pts = [(n, k) for n in range(2, 29, 2) for k in range(2, 15, 2)]
-    per_point, tot = {}, {"greedy": [0.0, 0.0], "search": [0.0, 0.0]}
+    per_point, tot = {}, {"greedy": [0.0, 0.0], "search": [0.0, 0.0], "adaptive": [0.0, 0.0]}
     for i, (n, k) in enumerate(pts):
         ch = tn.CircuitHandle(C.paper_fig31(n, k, wl["seed"] + i))
         row = {}
-        for name, trials in (("greedy", 1), ("search", 0)):
+        for name, trials, adaptive in (("greedy", 1, 0), ("search", 0, 0), ("adaptive", 0, 1)):
             t0 = time.perf_counter()
             st = tn.Plan(ch, target=tn.TARGET_AMPLITUDES, host_only=True, network_bitstrings=wl["chunk"],
-                         precision=1, order_trials=trials).stats()
+                         precision=1, order_trials=trials, order_search=adaptive).stats()
             dt = time.perf_counter() - t0
             row[name] = {"plan_s": round(dt, 4), "cost_bytes": st["net_cost"], "largest_intermediate_log2":
                          st["net_max_log2"], "merges": st["net_merges"]}
@@ -346,6 +346,9 @@ def plan_search_line(args, wl):
                                  "every bitstring pass size"},
             "greedy": {"seconds": tot["greedy"][0], "cost_bytes_total": tot["greedy"][1]},
             "search": {"seconds": tot["search"][0], "cost_bytes_total": tot["search"][1]},
+            "adaptive": {"seconds": tot["adaptive"][0], "cost_bytes_total": tot["adaptive"][1],
+                         "what": "order_search = 1: cross-entropy search over trial kind, temperature and "
+                                 "bitstring-index weight, 256 orders in 4 rounds"},
             "greedy_over_search_cost": {"median": ratios[len(ratios) // 2], "max": ratios[-1], "min": ratios[0]},
             "per_point": per_point}
 

@@ -129,7 +129,10 @@ typedef struct {
   int64_t order_trials;          /* TN_PLAN_NETWORK: contraction orders tried per search: 0 = 256 (randomised
                                   * greedy, qubit-sweep and fold-first trials); 1 = the deterministic greedy
                                   * alone; otherwise 4..4096 */
-  int64_t reserved[4];           /* must be zero */
+  int64_t order_search;          /* TN_PLAN_NETWORK: 0 = the fixed mix of trials above; 1 = adaptive search
+                                  * (a cross-entropy hyper-optimiser over the trial kind, noise temperature and
+                                  * bitstring-index weight, refitted each round to the best quarter so far) */
+  int64_t reserved[3];           /* must be zero */
 } tn_plan_opts;
 
 /* Plan summary (for measurement and tests). */

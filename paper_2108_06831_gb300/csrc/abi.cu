@@ -230,7 +230,9 @@ tn_status tn_plan_contraction(const tn_circuit *c, const tn_plan_opts *opts, tn_
   TN_CHECK_ARG(o.precision >= TN_PREC_FP32 && o.precision <= TN_PREC_SPLIT_BF16, "bad precision %d", o.precision);
   TN_CHECK_ARG(o.tile_qubits == 0 || (o.tile_qubits >= kLowBits + 2 && o.tile_qubits <= kMaxTile), "tile_qubits=%d not in {0, 6..%d}",
                o.tile_qubits, kMaxTile);
-  for (int i = 0; i < 4; ++i) TN_CHECK_ARG(o.reserved[i] == 0, "reserved fields must be zero");
+  for (int i = 0; i < 3; ++i) TN_CHECK_ARG(o.reserved[i] == 0, "reserved fields must be zero");
+  TN_CHECK_ARG(o.order_search == 0 || o.order_search == 1, "order_search must be 0 or 1 (got %lld)",
+               (long long)o.order_search);
   TN_CHECK_ARG(o.order_trials == 0 || o.order_trials == 1 || (o.order_trials >= 4 && o.order_trials <= 4096),
                "order_trials must be 0, 1 or 4..4096 (got %lld)", (long long)o.order_trials);
   if (o.flags & TN_PLAN_Q428) {
@@ -280,7 +282,7 @@ tn_status tn_plan_contraction(const tn_circuit *c, const tn_plan_opts *opts, tn_
     int lb = 0;
     while ((1ll << lb) < o.amp_batch) ++lb;
     tn_status s2 = build_network(*c, lb, *p->net, err);
-    if (s2 == TN_OK) s2 = plan_network(*p->net, o.max_intermediate_log2, (int)o.order_trials, err);
+    if (s2 == TN_OK) s2 = plan_network(*p->net, o.max_intermediate_log2, (int)o.order_trials, (int)o.order_search, err);
     if (s2 == TN_OK) s2 = lower_network(*p->net, o.precision, err);
     if (s2 == TN_OK && !p->host_only) {
       TN_CUDA(cudaGetDevice(&p->device), "cudaGetDevice");

@@ -686,6 +686,109 @@ Trial search_orders(const NetPlan &net, int max_log2, bool slice, int trials) {
   return std::move(res[(size_t)best_t]);
 }
 
+// Adaptive search (a cross-entropy hyper-optimiser over the order generator): the settings of
+// a trial are its kind (greedy, step-wise greedy, qubit sweep, fold-first), its noise
+// temperature and the extra weight the greedy kinds give the bitstring index (0, 4, 8 or 12
+// bits).  The first round draws them uniformly (and includes the deterministic greedy); after
+// every round the distribution is refitted to the best quarter of all orders so far (kind and
+// weight frequencies with add-one smoothing, temperature mean and spread), so later rounds
+// spend their trials where good orders came from.  Settings come from one seeded generator and
+// the choice is made in generation order: the result is deterministic.
+Trial adaptive_search(const NetPlan &net, int max_log2, bool slice, int trials) {
+  struct Spec {
+    int kind;
+    double temp;
+    int extra;  // -1: the bitstring index at its size
+    uint64_t seed;
+  };
+  uint64_t rs = 0x2545F4914F6CDD1Dull;
+  auto next_u64 = [&]() {  // splitmix64
+    uint64_t z = (rs += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+  };
+  auto uniform = [&]() { return ((next_u64() >> 11) + 0.5) * (1.0 / 9007199254740992.0); };
+  auto pick = [&](const double *p, int n) {
+    double r = uniform(), acc = 0;
+    for (int i = 0; i < n - 1; ++i) {
+      acc += p[i];
+      if (r < acc) return i;
+    }
+    return n - 1;
+  };
+  double p_kind[4] = {0.25, 0.25, 0.25, 0.25}, p_extra[4] = {0.25, 0.25, 0.25, 0.25};
+  double t_mean = 0.3, t_sd = 0.25;
+  const int rounds = 4, per_round = std::max(8, trials / rounds);
+  std::vector<Spec> specs;
+  std::vector<Trial> res;
+  for (int r = 0; r < rounds; ++r) {
+    const size_t first = specs.size();
+    for (int i = 0; i < per_round; ++i) {
+      Spec sp;
+      if (r == 0 && i == 0) {
+        sp = Spec{0, 0.0, -1, 0x9E3779B97F4A7C15ull};  // the deterministic greedy
+      } else {
+        sp.kind = pick(p_kind, 4);
+        // temperature: normal around the elite mean (Box-Muller), kept within [0, 2]
+        const double g = std::sqrt(-2.0 * std::log(uniform())) * std::cos(6.283185307179586 * uniform());
+        sp.temp = std::min(2.0, std::max(0.0, t_mean + t_sd * g));
+        const int e = pick(p_extra, 4);
+        sp.extra = e == 0 ? -1 : 4 * e;
+        sp.seed = next_u64();
+      }
+      specs.push_back(sp);
+    }
+    res.resize(specs.size());
+    std::atomic<size_t> next{first};
+    auto worker = [&]() {
+      for (size_t t = next++; t < specs.size(); t = next++) {
+        const Spec &sp = specs[t];
+        Trial &tr = res[t];
+        const int w0 = sp.extra < 0 ? -1 : net.label_dim[0] + sp.extra;
+        if (sp.kind == 0) greedy_trial(net, sp.temp, sp.seed, w0, tr);
+        else if (sp.kind == 1) stepwise_trial(net, sp.temp, sp.seed, w0, tr);
+        else if (sp.kind == 2) sweep_trial(net, std::max(sp.temp, 0.05), sp.seed, tr);
+        else fold_first_trial(net, sp.temp, sp.seed, w0, tr);
+        if (slice && tr.max_log2 > max_log2) choose_slices(net, tr, max_log2);
+      }
+    };
+    const int nth = std::max(1, std::min(per_round, (int)std::thread::hardware_concurrency()));
+    std::vector<std::thread> pool;
+    for (int i = 1; i < nth; ++i) pool.emplace_back(worker);
+    worker();
+    for (std::thread &th : pool) th.join();
+    // refit to the best quarter of everything so far
+    std::vector<size_t> order(res.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](size_t a, size_t b) { return better_order(res[a], res[b], max_log2); });
+    const size_t elite = std::max<size_t>(4, order.size() / 4);
+    double ck[4] = {1, 1, 1, 1}, ce[4] = {1, 1, 1, 1}, sum = 0, sum2 = 0;
+    for (size_t k = 0; k < elite && k < order.size(); ++k) {
+      const Spec &sp = specs[order[k]];
+      ck[sp.kind] += 1;
+      ce[sp.extra < 0 ? 0 : sp.extra / 4] += 1;
+      sum += sp.temp;
+      sum2 += sp.temp * sp.temp;
+    }
+    const double ne = (double)std::min(elite, order.size());
+    for (int i = 0; i < 4; ++i) {
+      p_kind[i] = ck[i] / (ne + 4.0);
+      p_extra[i] = ce[i] / (ne + 4.0);
+    }
+    t_mean = sum / ne;
+    t_sd = std::max(0.02, std::sqrt(std::max(0.0, sum2 / ne - t_mean * t_mean)));
+  }
+  int best_t = 0;
+  for (size_t t = 1; t < res.size(); ++t)
+    if (better_order(res[t], res[(size_t)best_t], max_log2)) best_t = (int)t;
+  if (getenv("TNQ_DEBUG_NET"))
+    fprintf(stderr, "adaptive: best trial %d of %zu (kind %d, temperature %.3f, extra %d)\n", best_t, res.size(),
+            specs[(size_t)best_t].kind, specs[(size_t)best_t].temp, specs[(size_t)best_t].extra);
+  return std::move(res[(size_t)best_t]);
+}
+
 // The merges of `order` (planned on the unsliced network) replayed on the sliced one.
 Trial replay_order(const NetPlan &net, const Trial &order) {
   Contractor ct(net);
@@ -696,9 +799,14 @@ Trial replay_order(const NetPlan &net, const Trial &order) {
 
 }  // namespace
 
-tn_status plan_network(NetPlan &net, int max_log2, int order_trials, std::string &err) {
+tn_status plan_network(NetPlan &net, int max_log2, int order_trials, int order_search, std::string &err) {
   const int trials = order_trials > 0 ? order_trials : kTrials;
   const int coarse = std::min(trials, kCoarseTrials);
+  // the full searches: the fixed trial mix, or the adaptive search (order_search = 1)
+  auto full_search = [&](bool slice) {
+    return order_search == 1 && trials > 1 ? adaptive_search(net, max_log2, slice, trials)
+                                           : search_orders(net, max_log2, slice, trials);
+  };
   net.slices.clear();
   net.sliced.assign(net.label_dim.size(), 0);
   const int lb = net.call_log2;
@@ -730,7 +838,7 @@ tn_status plan_network(NetPlan &net, int max_log2, int order_trials, std::string
     }
   }
   set_batch(lb - best_j);
-  Trial full = search_orders(net, max_log2, true, trials);
+  Trial full = full_search(true);
   if (usable(full) && (!usable(best) || call_cost(full, best_j) < call_cost(best, best_j))) best = std::move(full);
   if (best.max_log2 > max_log2) {
     if (!best.sliceable) {
@@ -744,7 +852,7 @@ tn_status plan_network(NetPlan &net, int max_log2, int order_trials, std::string
     // the order found above, on the sliced network, fits by construction; a search on the
     // sliced network itself may find a cheaper one
     Trial replay = replay_order(net, best);
-    Trial again = search_orders(net, max_log2, false, trials);
+    Trial again = full_search(false);
     best = better_order(again, replay, max_log2) ? std::move(again) : std::move(replay);
   }
   net.steps = best.steps;

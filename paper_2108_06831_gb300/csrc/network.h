@@ -90,7 +90,7 @@ struct NetPlan {
 };
 
 tn_status build_network(const tn_circuit &c, int log2_batch, NetPlan &net, std::string &err);
-tn_status plan_network(NetPlan &net, int max_log2, int order_trials, std::string &err);
+tn_status plan_network(NetPlan &net, int max_log2, int order_trials, int order_search, std::string &err);
 tn_status lower_network(NetPlan &net, int precision, std::string &err);
 tn_status upload_network(NetPlan &net, std::string &err);
 cudaError_t run_network(const NetPlan &net, const uint64_t *bitstrings, long long n_bits, float2 *amps, void *ws,

@@ -43,7 +43,7 @@ class TnPlanOpts(C.Structure):
     _fields_ = [("target", C.c_int32), ("precision", C.c_int32), ("batch", C.c_int32),
                 ("tile_qubits", C.c_int32), ("max_intermediate_log2", C.c_int32), ("flags", C.c_int32),
                 ("seed", C.c_uint64), ("amp_batch", C.c_int64), ("order_trials", C.c_int64),
-                ("reserved", C.c_int64 * 4)]
+                ("order_search", C.c_int64), ("reserved", C.c_int64 * 3)]
 
 
 class TnPlanStats(C.Structure):
@@ -180,9 +180,10 @@ class CircuitHandle:
 class Plan:
     def __init__(self, ch: CircuitHandle, target: int = TARGET_STATE, precision: int = PREC_FP32, batch: int = 1,
                  tile_qubits: int = 0, host_only: bool = False, specialize: bool = True, network_bitstrings: int = 0,
-                 max_intermediate_log2: int = 0, order_trials: int = 0, q428: bool = False):
+                 max_intermediate_log2: int = 0, order_trials: int = 0, q428: bool = False, order_search: int = 0):
         o = TnPlanOpts()
         o.order_trials = order_trials
+        o.order_search = order_search
         o.target, o.precision, o.batch, o.tile_qubits = target, precision, batch, tile_qubits
         o.max_intermediate_log2 = max_intermediate_log2
         o.flags = (PLAN_HOST_ONLY if host_only else 0) | (0 if specialize else PLAN_NO_SPECIALIZE) | \

@@ -207,3 +207,18 @@ def test_network_planner_invariants_random_circuits():
         assert s["net_cost"] >= s["net_bytes"] > 0
         assert tn.Plan(ch, **kw).stats() == s
         assert s["net_cost"] <= tn.Plan(ch, order_trials=1, **kw).stats()["net_cost"]
+
+
+def test_network_adaptive_search():
+    """order_search = 1 (the adaptive hyper-optimiser over the order generator): deterministic,
+    never worse than the greedy alone, within the cap; other values are rejected."""
+    from paper_2108_06831_gb300 import tn
+    kw = dict(target=tn.TARGET_AMPLITUDES, host_only=True, network_bitstrings=16)
+    for c, cap in ((C.paper_fig31(14, 8, 2), 0), (C.grid(4, 4, 8, 11), 9), (C.random_circuit(10, 90, 6), 0)):
+        ch = tn.CircuitHandle(c)
+        a = tn.Plan(ch, order_search=1, max_intermediate_log2=cap, **kw).stats()
+        assert tn.Plan(ch, order_search=1, max_intermediate_log2=cap, **kw).stats() == a
+        greedy = tn.Plan(ch, order_trials=1, max_intermediate_log2=cap, **kw).stats()
+        assert a["net_cost"] <= greedy["net_cost"] and a["net_max_log2"] <= (cap or 28)
+    with pytest.raises(tn.TnError):
+        tn.Plan(tn.CircuitHandle(C.ghz(4)), order_search=2, **kw)
