@@ -642,6 +642,22 @@ bool better_order(const Trial &tr, const Trial &best, int max_log2) {
   return tr.max_log2 < best.max_log2 || (tr.max_log2 == best.max_log2 && tr.flops < best.flops);
 }
 
+// fn(t) for t in [begin, end) on the host's cores (each t on one thread; fn writes only its own
+// slot of a result array, so the outcome does not depend on the thread count).
+template <typename F>
+void parallel_for(size_t begin, size_t end, F &&fn) {
+  std::atomic<size_t> next{begin};
+  auto worker = [&]() {
+    for (size_t t = next++; t < end; t = next++) fn(t);
+  };
+  const size_t n = end > begin ? end - begin : 0;
+  const int nth = (int)std::max<size_t>(1, std::min<size_t>(n, std::thread::hardware_concurrency()));
+  std::vector<std::thread> pool;
+  for (int i = 1; i < nth; ++i) pool.emplace_back(worker);
+  worker();
+  for (std::thread &th : pool) th.join();
+}
+
 // Randomised trials, the preferred one: half greedy (the first deterministic; they score the
 // bitstring index at its size or 4, 8, 12 bits larger in turn; half of them with step-wise
 // noise), a quarter qubit sweeps, a quarter fold-first.  With `slice`, orders that exceed the cap are sliced to fit
@@ -650,8 +666,9 @@ bool better_order(const Trial &tr, const Trial &best, int max_log2) {
 Trial search_orders(const NetPlan &net, int max_log2, bool slice, int trials) {
   const int ng = trials / 2, ns = trials / 4;
   std::vector<Trial> res((size_t)trials);
-  auto run = [&](int t) {
-    Trial &tr = res[(size_t)t];
+  parallel_for(0, (size_t)trials, [&](size_t ti) {
+    const int t = (int)ti;
+    Trial &tr = res[ti];
     // u: the trial's index within its kind's sequence (kinds offset by 64 and 128)
     const int u = t < ng ? t : (t < ng + ns ? 64 + (t - ng) : 128 + (t - ng - ns));
     const double temp = (u % 64) == 0 ? 0.0 : 0.05 + 0.5 * (double)(u % 16) / 16.0;
@@ -663,16 +680,7 @@ Trial search_orders(const NetPlan &net, int max_log2, bool slice, int trials) {
     else if (t < ng + ns) sweep_trial(net, (u % 64) == 0 ? 0.05 : temp, seed, tr);
     else fold_first_trial(net, temp, seed, w0, tr);
     if (slice && tr.max_log2 > max_log2) choose_slices(net, tr, max_log2);
-  };
-  std::atomic<int> next{0};
-  auto worker = [&]() {
-    for (int t = next++; t < trials; t = next++) run(t);
-  };
-  const int nth = std::max(1, std::min(trials, (int)std::thread::hardware_concurrency()));
-  std::vector<std::thread> pool;
-  for (int i = 1; i < nth; ++i) pool.emplace_back(worker);
-  worker();
-  for (std::thread &th : pool) th.join();
+  });
   const bool debug = getenv("TNQ_DEBUG_NET") != nullptr;
   int best_t = 0;
   for (int t = 0; t < trials; ++t) {
@@ -740,24 +748,16 @@ Trial adaptive_search(const NetPlan &net, int max_log2, bool slice, int trials) 
       specs.push_back(sp);
     }
     res.resize(specs.size());
-    std::atomic<size_t> next{first};
-    auto worker = [&]() {
-      for (size_t t = next++; t < specs.size(); t = next++) {
-        const Spec &sp = specs[t];
-        Trial &tr = res[t];
-        const int w0 = sp.extra < 0 ? -1 : net.label_dim[0] + sp.extra;
-        if (sp.kind == 0) greedy_trial(net, sp.temp, sp.seed, w0, tr);
-        else if (sp.kind == 1) stepwise_trial(net, sp.temp, sp.seed, w0, tr);
-        else if (sp.kind == 2) sweep_trial(net, std::max(sp.temp, 0.05), sp.seed, tr);
-        else fold_first_trial(net, sp.temp, sp.seed, w0, tr);
-        if (slice && tr.max_log2 > max_log2) choose_slices(net, tr, max_log2);
-      }
-    };
-    const int nth = std::max(1, std::min(per_round, (int)std::thread::hardware_concurrency()));
-    std::vector<std::thread> pool;
-    for (int i = 1; i < nth; ++i) pool.emplace_back(worker);
-    worker();
-    for (std::thread &th : pool) th.join();
+    parallel_for(first, specs.size(), [&](size_t t) {
+      const Spec &sp = specs[t];
+      Trial &tr = res[t];
+      const int w0 = sp.extra < 0 ? -1 : net.label_dim[0] + sp.extra;
+      if (sp.kind == 0) greedy_trial(net, sp.temp, sp.seed, w0, tr);
+      else if (sp.kind == 1) stepwise_trial(net, sp.temp, sp.seed, w0, tr);
+      else if (sp.kind == 2) sweep_trial(net, std::max(sp.temp, 0.05), sp.seed, tr);
+      else fold_first_trial(net, sp.temp, sp.seed, w0, tr);
+      if (slice && tr.max_log2 > max_log2) choose_slices(net, tr, max_log2);
+    });
     // refit to the best quarter of everything so far
     std::vector<size_t> order(res.size());
     for (size_t i = 0; i < order.size(); ++i) order[i] = i;
