@@ -320,7 +320,7 @@ def plan_search_line(args, wl):
     (order_trials = 1) against the default search and the adaptive search; no GPU work."""
     from paper_2108_06831_gb300 import circuits as C
     from paper_2108_06831_gb300 import tn
-    pts = [(n, k) for n in range(2, 29, 2) for k in range(2, 15, 2)]
+    pts = wl.get("points") or [(n, k) for n in range(2, 29, 2) for k in range(2, 15, 2)]
     per_point, tot = {}, {"greedy": [0.0, 0.0], "search": [0.0, 0.0], "adaptive": [0.0, 0.0]}
     for i, (n, k) in enumerate(pts):
         ch = tn.CircuitHandle(C.paper_fig31(n, k, wl["seed"] + i))
