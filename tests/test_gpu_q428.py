@@ -100,7 +100,6 @@ def test_30_qubits_closed_form():
     round(quantize(1/sqrt 2) a / 2^28) on both branches; CZ (entries +-1) negates exactly and X
     permutes exactly.  Every entry is then +-a_30 (real), the sign (-1)^(sum_q x_q x_{q+1}) of the
     index before the X."""
-    from oracle import fixedpoint as F
     from paper_2108_06831_gb300 import tn
     n = 30
     gates = [C.Gate("H", (q,)) for q in range(n)] + [C.Gate("CZ", (q, q + 1)) for q in range(n - 1)]
@@ -110,10 +109,14 @@ def test_30_qubits_closed_form():
     tn.contract_state_q428(p, st)
     torch.cuda.synchronize()
     assert tn.sync_status() == tn.OK
-    qh = F.quantize(1.0 / np.sqrt(2.0))
-    a = F.ONE
+    # quantize(1/sqrt 2) = floor(2^28 / sqrt 2 + 1/2) = 189812531 (2^28 / sqrt 2 = 189812531.25)
+    qh = 189812531
+    assert abs(qh - (1 << 28) / np.sqrt(2.0)) < 0.5
+    # each H: a <- floor((qh a + 2^27) / 2^28), the reading's round half up written out in
+    # Python integers (exact); a stays positive, far from the int32 limits
+    a = 1 << 28
     for _ in range(n):
-        a = int(F.round_q(np.array([qh * a], dtype=np.int64))[0])
+        a = (qh * a + (1 << 27)) // (1 << 28)
     assert not bool((st[:, 1] != 0).any())
     assert bool((st[:, 0].abs() == a).all())
     rng = np.random.default_rng(30)

@@ -290,6 +290,49 @@ def test_q428_quantize_rounding_and_saturation():
     assert F.quantize(-8.0) == -(2 ** 31)  # -8 is representable
 
 
+def test_q428_output_rounding_on_hand_computed_sums():
+    """One gate on a hand-built Q4.28 state whose exact integer sums fall on the rounding
+    boundaries.  With U = diag(u0, u1) (imaginary parts 0) the output components are
+    round(u_l psi_l / 2^28); the reading fixes round half up, floor((acc + 2^27) / 2^28), and
+    saturation to int32.  Expected values are literals worked out by hand:
+      acc = +2^27        -> 1  (a tie rounds up)      acc = -2^27     -> 0  (toward +inf)
+      acc = 2^27 - 1     -> 0                         acc = 3 2^27    -> 2
+      acc = -3 2^27      -> -1                        acc = 2^27 + 1  -> 1
+    and, on a two-qubit gate with rows (2^29, 2^29, 2^29, 2^29) and -(same) applied to the
+    state (2^29, 2^29, 2^29, 2^29): acc = +-2^60, i.e. +-2^32 after the shift, saturated to
+    2^31 - 1 and -2^31.
+    A floor (no half added), a truncation toward zero or a missing clip fails at least one."""
+    from oracle import fixedpoint as F
+    z = np.zeros((2, 2), dtype=np.int64)
+    cases = [  # (u0, psi0, u1, psi1, out0, out1)
+        (1 << 13, 1 << 14, -(1 << 13), 1 << 14, 1, 0),
+        ((1 << 27) - 1, 1, 3, 1 << 27, 0, 2),
+        (-3, 1 << 27, (1 << 27) + 1, 1, -1, 1),
+    ]
+    for u0, p0, u1, p1, o0, o1 in cases:
+        Ur = np.array([[u0, 0], [0, u1]], dtype=np.int64)
+        re = np.array([p0, p1], dtype=np.int64)
+        # the imaginary parts mirror the real ones: acc_im = u_l im_l, same boundaries
+        out_r, out_i = F.apply_gate_q(re.copy(), re.copy(), 1, Ur, z, [0])
+        assert out_r.tolist() == [o0, o1], (u0, p0, u1, p1, out_r)
+        assert out_i.tolist() == [o0, o1]
+    U4 = np.zeros((4, 4), dtype=np.int64)
+    U4[0, :] = 1 << 29
+    U4[1, :] = -(1 << 29)
+    big = np.full(4, 1 << 29, dtype=np.int64)
+    out_r, out_i = F.apply_gate_q(big.copy(), big.copy(), 2, U4, np.zeros((4, 4), dtype=np.int64), [0, 1])
+    assert out_r.tolist() == [(1 << 31) - 1, -(1 << 31), 0, 0]
+    assert out_i.tolist() == [(1 << 31) - 1, -(1 << 31), 0, 0]
+    # a complex entry mixes the parts: (u_r + i u_i)(p_r + i p_i) with u = (2^13, 2^13),
+    # psi = (2^14, -2^14 + 1): re acc = 2^27 + 2^27 - 2^13 = 2^28 - 2^13 -> 1 (rounded up from
+    # 0.99997), im acc = 2^13 (-2^14 + 1) + 2^27 = 2^13 -> 0
+    Ur = np.array([[1 << 13, 0], [0, 0]], dtype=np.int64)
+    Ui = np.array([[1 << 13, 0], [0, 0]], dtype=np.int64)
+    out_r, out_i = F.apply_gate_q(np.array([1 << 14, 0], dtype=np.int64),
+                                  np.array([-(1 << 14) + 1, 0], dtype=np.int64), 1, Ur, Ui, [0])
+    assert out_r.tolist() == [1, 0] and out_i.tolist() == [0, 0]
+
+
 def test_q428_exact_permutations_and_signs():
     """X, CNOT, SWAP and CZ have entries 0 and +-1: in Q4.28 they permute and negate exactly."""
     from oracle import fixedpoint as F
