@@ -278,8 +278,10 @@ tn_status tn_state_expectation(const tn_observable *H, int32_t batch, const void
  *     with TN_ERR_INVALID_ARG, and nothing is enqueued;
  *   - all calls on a device share the array; each clears the slots it uses, but calls that
  *     overlap on the GPU (unordered streams) race on it;
- *   - the first call on a device looks up the array's address (cudaGetSymbolAddress) with
- *     that device current; make that first call before any stream capture begins.
+ *   - every call looks up the array's address on the current device (cudaGetSymbolAddress;
+ *     nothing is cached across calls, so it stays valid after cudaDeviceReset); the first
+ *     lookup on a device loads the library's module there, so make the first call on each
+ *     device before any stream capture begins.
  * Allocates no device memory.  Other arguments and results as tn_state_expectation. */
 tn_status tn_state_expectation_noalloc(const tn_observable *H, int32_t batch, const void *state_dev,
                                        double *out_dev, tn_stream_t s);

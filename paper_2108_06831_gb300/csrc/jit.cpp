@@ -8,9 +8,9 @@
 // FFMA code.  Gate matrices still come from the per-call table (so parameterised circuits
 // share the compiled code); they are staged in shared memory once per batch element.
 //
-// Compiled cubins are cached in-process by a 64-bit hash of the source, and on disk in
-// $TNQ_CACHE_DIR (default ~/.cache/tnq) so repeated plans of the same circuit structure
-// skip compilation.
+// Compiled cubins are cached in-process by a 64-bit hash of the source, the NVRTC options and
+// the NVRTC version, and on disk in $TNQ_CACHE_DIR (default ~/.cache/tnq) under the same key,
+// so repeated plans of the same circuit structure skip compilation.
 #include <nvrtc.h>
 #include <sys/stat.h>
 #include <sys/types.h>
@@ -767,8 +767,27 @@ void write_file(const std::string &dir, const std::string &path, const std::stri
   rename(tmp.c_str(), path.c_str());
 }
 
+// NVRTC options of every generated kernel; they are part of the cache key.
+const char *const kNvrtcOpts[] = {"-arch=sm_103a", "-std=c++17", "-default-device", "-lineinfo"};
+constexpr int kNvrtcNumOpts = (int)(sizeof(kNvrtcOpts) / sizeof(kNvrtcOpts[0]));
+
+// Cache key of a generated source: the source, the compile options and the NVRTC version,
+// so that a cubin cached by another toolkit or with other options is never reused.
+uint64_t cubin_key(const std::string &src) {
+  int major = 0, minor = 0;
+  nvrtcVersion(&major, &minor);
+  std::string key = src;
+  key += "\n// nvrtc ";
+  key += std::to_string(major) + "." + std::to_string(minor);
+  for (int i = 0; i < kNvrtcNumOpts; ++i) {
+    key += ' ';
+    key += kNvrtcOpts[i];
+  }
+  return fnv1a(key);
+}
+
 tn_status compile_cubin(const std::string &src, std::string &cubin, std::string &err) {
-  const uint64_t h = fnv1a(src);
+  const uint64_t h = cubin_key(src);
   {
     std::lock_guard<std::mutex> lk(g_cache_mu);
     auto it = g_cubins.find(h);
@@ -787,8 +806,7 @@ tn_status compile_cubin(const std::string &src, std::string &cubin, std::string 
       err = "nvrtcCreateProgram failed";
       return TN_ERR_UNSUPPORTED;
     }
-    const char *opts[] = {"-arch=sm_103a", "-std=c++17", "-default-device", "-lineinfo"};
-    nvrtcResult r = nvrtcCompileProgram(prog, 4, opts);
+    nvrtcResult r = nvrtcCompileProgram(prog, kNvrtcNumOpts, kNvrtcOpts);
     if (r != NVRTC_SUCCESS) {
       size_t n = 0;
       nvrtcGetProgramLogSize(prog, &n);

@@ -227,8 +227,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_cgemm_tc(const __grid_constant_
   // 1024-byte alignment of every tile (required by the 128-byte swizzle pattern)
   unsigned char *smem = reinterpret_cast<unsigned char *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   __shared__ __align__(8) uint64_t full[S], conv[S], empty[S], done;
+  __shared__ __align__(8) uint64_t drain;  // abort path: completion of the MMAs already issued
   __shared__ uint32_t tmem_base;
   __shared__ int abort_flag;
+  __shared__ int issued_parity[S];  // parity of the last TMA phase issued per stage, -1 if none
   __shared__ long long ctab[BN / 2];
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -240,8 +242,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_cgemm_tc(const __grid_constant_
       mbar_init(&full[s], 1);
       mbar_init(&conv[s], kConvThreads);
       mbar_init(&empty[s], 1);
+      issued_parity[s] = -1;
     }
     mbar_init(&done, 1);
+    mbar_init(&drain, 1);
     abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -254,6 +258,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_cgemm_tc(const __grid_constant_
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem_d = tmem_base;
+  bool mma_issued = false;  // warp 5 lane 0: at least one MMA was issued
 
   if (warp == 4) {
     if (lane == 0) {  // TMA producer
@@ -264,6 +269,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_cgemm_tc(const __grid_constant_
           break;
         }
         mbar_expect_tx(&full[s], tx_bytes);
+        issued_parity[s] = (kt / S) & 1;
         unsigned char *st = smem + (size_t)s * stage_bytes;
         const int kc = kt * (KBYTES / CF::kElem);
         const int a_loads = SPLIT_A ? 1 : CF::kParts;
@@ -301,6 +307,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_cgemm_tc(const __grid_constant_
             mma<PREC>(dst, smem_desc(a_base + off), smem_desc(b_base + off), acc ? 1u : 0u);
           }
         }
+        mma_issued = true;
         mma_commit(&empty[s]);  // frees the stage once these MMAs have read it
       }
       if (ok) mma_commit(&done);
@@ -365,9 +372,19 @@ __global__ void __launch_bounds__(kThreads, 1) k_cgemm_tc(const __grid_constant_
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  if (abort_flag && threadIdx.x == 0) {
-    // let copies already in flight land before the CTA's shared memory is released
-    for (int s = 0; s < S; ++s) mbar_wait(&full[s], 0, nullptr);
+  if (abort_flag) {  // uniform: nothing writes the flag after the barrier above
+    // let copies already in flight land (the last phase issued into each stage), and let the
+    // MMAs already issued finish reading shared memory and writing TMEM, before the CTA
+    // releases either
+    if (threadIdx.x == 0)
+      for (int s = 0; s < S; ++s)
+        if (issued_parity[s] >= 0) mbar_wait(&full[s], (uint32_t)issued_parity[s], nullptr);
+    if (warp == 5 && lane == 0 && mma_issued) {
+      mma_commit(&drain);
+      mbar_wait(&drain, 0, nullptr);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
   }
   if (warp == 5) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -446,7 +463,7 @@ __global__ void __launch_bounds__(kStreamThreads, 1)
   constexpr uint32_t tx_bytes = a_boxes * kTileA + CF::kParts * kTileB;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char *smem = reinterpret_cast<unsigned char *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  __shared__ __align__(8) uint64_t full[S], conv[S], empty[S], acc_full[2], acc_empty[2];
+  __shared__ __align__(8) uint64_t full[S], conv[S], empty[S], acc_full[2], acc_empty[2], drain;
   __shared__ uint32_t tmem_base;
   __shared__ int abort_flag;
   __shared__ int issued_parity[S];  // parity of the last TMA phase issued per stage, -1 if none
@@ -511,6 +528,7 @@ __global__ void __launch_bounds__(kStreamThreads, 1)
       mbar_init(&acc_full[b], 1);
       mbar_init(&acc_empty[b], 128);
     }
+    mbar_init(&drain, 1);
     abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -523,6 +541,7 @@ __global__ void __launch_bounds__(kStreamThreads, 1)
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem_d = tmem_base;
+  bool mma_issued = false;  // warp 5 lane 0: at least one MMA was issued
 
   auto aborted = [&]() { return *reinterpret_cast<volatile int *>(&abort_flag) != 0; };
   auto decode = [&](long long t, int &nt, int &mt, int &bz) {
@@ -586,6 +605,7 @@ __global__ void __launch_bounds__(kStreamThreads, 1)
               mma<PREC>(dst, smem_desc(a_base + off), smem_desc(b_base + off), acc ? 1u : 0u);
             }
           }
+          mma_issued = true;
           mma_commit(&empty[s]);
         }
         if (!ok) {
@@ -698,10 +718,18 @@ __global__ void __launch_bounds__(kStreamThreads, 1)
   __syncwarp();
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  if (abort_flag && threadIdx.x == 0) {
-    // let copies already in flight land before the CTA's shared memory is released
-    for (int s = 0; s < S; ++s)
-      if (issued_parity[s] >= 0) mbar_wait(&full[s], (uint32_t)issued_parity[s], nullptr);
+  if (abort_flag) {  // uniform: nothing writes the flag after the barrier above
+    // let copies already in flight land, and the MMAs already issued finish, before the CTA
+    // releases its shared memory and tensor memory
+    if (threadIdx.x == 0)
+      for (int s = 0; s < S; ++s)
+        if (issued_parity[s] >= 0) mbar_wait(&full[s], (uint32_t)issued_parity[s], nullptr);
+    if (warp == 5 && lane == 0 && mma_issued) {
+      mma_commit(&drain);
+      mbar_wait(&drain, 0, nullptr);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
   }
   if (warp == 5) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");

@@ -15,10 +15,10 @@
 //   - every call on a device uses the same array, and it keeps the previous call's contents:
 //     the reduction clears the slots it reads before writing them, but two calls that overlap
 //     on the GPU (different streams, no ordering between them) race on the array;
-//   - the first call on each device looks up the array's device address with
-//     cudaGetSymbolAddress while that device is current; make that first call before any
-//     stream capture begins.
-#include <mutex>
+//   - every call looks up the array's device address with cudaGetSymbolAddress on the
+//     current device (a host-side lookup; nothing is cached, so an address stays right after
+//     cudaDeviceReset rebuilds the context).  The first lookup on a device loads the module
+//     there, so make the first call on each device before any stream capture begins.
 
 #include "kernels.h"
 #include "tnq_internal.h"
@@ -30,27 +30,13 @@ constexpr size_t kNoAllocPartials = 131072;  // doubles: 1 MiB of device memory 
 static __device__ __align__(256) double g_noalloc_partials[kNoAllocPartials];
 
 namespace {
-constexpr int kMaxDevices = 64;
-std::mutex g_noalloc_mu;
-double *g_noalloc_ptr[kMaxDevices] = {nullptr};
-
-// Device address of g_noalloc_partials on the current device (looked up once per device).
+// Device address of g_noalloc_partials in the current device's context.  In host code the
+// symbol's name stands for a host-side shadow, so the address must come from the runtime.
 tn_status noalloc_scratch(double **out) {
-  int dev = -1;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
-  if (dev < 0 || dev >= kMaxDevices) {
-    set_error("device %d beyond the %d devices this entry point tracks", dev, kMaxDevices);
-    return TN_ERR_UNSUPPORTED;
-  }
-  std::lock_guard<std::mutex> lk(g_noalloc_mu);
-  if (g_noalloc_ptr[dev] == nullptr) {
-    double *p = nullptr;
-    e = cudaGetSymbolAddress((void **)&p, g_noalloc_partials);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress of the built-in scratch array");
-    g_noalloc_ptr[dev] = p;
-  }
-  *out = g_noalloc_ptr[dev];
+  double *p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress((void **)&p, g_noalloc_partials);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress of the built-in scratch array");
+  *out = p;
   return TN_OK;
 }
 }  // namespace

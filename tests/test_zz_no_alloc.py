@@ -40,10 +40,18 @@ def test_noalloc_matches_workspace_entry_point_twice():
     obs1 = tn.Observable(C.tfim(n))
     got, ref = _expect_both(tn, obs1, 3, states)
     assert np.all(np.abs(got - ref) <= 1e-4 * np.maximum(1.0, np.abs(ref)))
+    # and against the FP64 oracle (state-vector simulation, explicit Pauli application)
+    from oracle import observables as OB
+    H1 = C.tfim(n)
+    exact = np.array([OB.expectation(c, H1, params[b]) for b in range(3)])
+    assert np.all(np.abs(got - exact) <= 1e-4 * np.maximum(1.0, np.abs(exact)))
     # second call right after: another observable and fewer states over the same scratch
     obs2 = tn.Observable(C.random_pauli_sum(n, 17, 5))
     got2, ref2 = _expect_both(tn, obs2, 2, states)
     assert np.all(np.abs(got2 - ref2) <= 1e-4 * np.maximum(1.0, np.abs(ref2)))
+    H2 = C.random_pauli_sum(n, 17, 5)
+    exact2 = np.array([OB.expectation(c, H2, params[b]) for b in range(2)])
+    assert np.all(np.abs(got2 - exact2) <= 1e-4 * np.maximum(1.0, np.abs(exact2)))
 
 
 def test_noalloc_rejects_requests_beyond_its_scratch():
