@@ -31,7 +31,30 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "amplitudes/s, grads/s & % roofline; split-prec+batched vs plain FP32 at ≤1e-5 err"
-FP32_ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x (FMA = 2 flops) x max SM clock
+# FP32 multiply-add roofline of the kernels bound by FP32 arithmetic: measured on the GPU at start-up
+# (set_fp32_peak); the nominal rate from the device's SM count and maximum clock is reported beside it
+FP32_ALU_PEAK_TFLOPS = None
+FP32_ALU_PEAK_SRC = None
+
+
+def set_fp32_peak(tn, torch, dev):
+    """The FP32 multiply-add rate measured on this GPU by the library's probe (packed FP32x2 FMA
+    chains on every SM at full occupancy, CUDA events), and the nominal rate (SM count from the
+    device, 128 FP32 lanes per SM, maximum SM clock from nvidia-smi) for context."""
+    global FP32_ALU_PEAK_TFLOPS, FP32_ALU_PEAK_SRC
+    rate, secs = tn.probe_fma_rate()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    try:
+        mhz = float(subprocess.run(["nvidia-smi", "-i", str(dev.index or 0), "--query-gpu=clocks.max.sm",
+                                    "--format=csv,noheader,nounits"], capture_output=True, text=True,
+                                   timeout=20).stdout.strip().splitlines()[0])
+    except Exception:
+        mhz = float("nan")
+    nominal = sms * 128 * 2 * mhz * 1e6 / 1e12
+    FP32_ALU_PEAK_TFLOPS = rate
+    FP32_ALU_PEAK_SRC = (f"measured FP32 FMA rate {rate:.1f} TFLOP/s (tn_probe_fma_rate: packed FP32x2 FMA chains on "
+                         f"every SM, {secs * 1e3:.0f} ms launch); nominal {sms} SMs x 128 lanes x 2 flops x "
+                         f"{mhz:.0f} MHz = {nominal:.1f} TFLOP/s")
 
 
 def parse():
@@ -181,18 +204,23 @@ from oracle.tn import contract_amplitude, contract_amplitude_sweep
 kind, budget = {kind!r}, {budget}
 t0 = time.perf_counter()
 if kind == "state":
-    c, p = C.brickwork({n}, {depth}, {seed}, parameterized=True)
-    psi = basis_state(c.n_qubits, 0)
-    done = 0
-    for g in c.gates:
-        psi = apply_matrix(psi, c.n_qubits, gate_matrix(c, g, p), g.qubits)
-        done += 1
-        if time.perf_counter() - t0 > budget:
+    # whole circuits of the same family (brickwork, depth {depth}, seed {seed}), growing the width
+    # while the next one (about twice the work) still fits the budget; nothing is extrapolated
+    m = min(12, {n})
+    while True:
+        c, p = C.brickwork(m, {depth}, {seed}, parameterized=True)
+        t1 = time.perf_counter()
+        psi = basis_state(c.n_qubits, 0)
+        for g in c.gates:
+            psi = apply_matrix(psi, c.n_qubits, gate_matrix(c, g, p), g.qubits)
+        dt = time.perf_counter() - t1
+        if m >= {n} or time.perf_counter() - t0 + 2.2 * dt > budget:
             break
-    dt = time.perf_counter() - t0
-    out = dict(value=(1 << c.n_qubits) / (dt * len(c.gates) / done), unit="amplitudes/s", seconds=dt,
-               sample=f"FP64 state-vector oracle, first {{done}} of {{len(c.gates)}} gates of the circuit "
-                      f"({{dt:.1f}} s), scaled to the whole circuit")
+        m += 1
+    out = dict(value=(1 << m) / dt, unit="amplitudes/s", seconds=dt,
+               sample=f"FP64 state-vector oracle, the whole {{m}}-qubit brickwork of depth {depth} "
+                      f"({{len(c.gates)}} gates, {{dt:.1f}} s; the widest that fits the time budget, "
+                      f"not scaled)")
 elif kind == "grad":
     c = C.hea({n}, 10)
     e = OB.expectation(c, C.tfim({n}), C.hea_params(c.n_params, 1, 4000)[0])
@@ -237,21 +265,24 @@ elif kind == "sweep":
                sample=f"FP64 state-vector oracle, the {{done}} smallest of the 98 Fig. 3.1 circuits ({{dt:.1f}} s)")
 elif kind == "q428":
     from oracle.fixedpoint import apply_gate_q, quantize_matrix, ONE
-    c, _ = C.brickwork({n}, {depth}, {seed})
-    re = np.zeros(1 << c.n_qubits, dtype=np.int64)
-    im = np.zeros(1 << c.n_qubits, dtype=np.int64)
-    re[0] = ONE
-    done = 0
-    for g in c.gates:
-        Ur, Ui = quantize_matrix(gate_matrix(c, g, None))
-        re, im = apply_gate_q(re, im, c.n_qubits, Ur, Ui, g.qubits)
-        done += 1
-        if time.perf_counter() - t0 > budget:
+    m = min(12, {n})
+    while True:
+        c, _ = C.brickwork(m, {depth}, {seed})
+        t1 = time.perf_counter()
+        re = np.zeros(1 << c.n_qubits, dtype=np.int64)
+        im = np.zeros(1 << c.n_qubits, dtype=np.int64)
+        re[0] = ONE
+        for g in c.gates:
+            Ur, Ui = quantize_matrix(gate_matrix(c, g, None))
+            re, im = apply_gate_q(re, im, c.n_qubits, Ur, Ui, g.qubits)
+        dt = time.perf_counter() - t1
+        if m >= {n} or time.perf_counter() - t0 + 2.2 * dt > budget:
             break
-    dt = time.perf_counter() - t0
-    out = dict(value=(1 << c.n_qubits) / (dt * len(c.gates) / done), unit="amplitudes/s", seconds=dt,
-               sample=f"Q4.28 fixed-point oracle (numpy int64), first {{done}} of {{len(c.gates)}} gates "
-                      f"({{dt:.1f}} s), scaled to the whole circuit")
+        m += 1
+    out = dict(value=(1 << m) / dt, unit="amplitudes/s", seconds=dt,
+               sample=f"Q4.28 fixed-point oracle (numpy int64), the whole {{m}}-qubit brickwork of depth "
+                      f"{depth} ({{len(c.gates)}} gates, {{dt:.1f}} s; the widest that fits the time budget, "
+                      f"not scaled)")
 elif kind == "sweep_amps":
     pts = [(n, k) for n in range(2, 29, 2) for k in range(2, 15, 2)]
     done = 0
@@ -408,7 +439,7 @@ def main():
     # the CPU baseline runs first, in a fresh process, before this process touches the GPU
     cpu = cpu_all = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and wl["kind"] in ORACLE_KINDS:
-        info, err = run_oracle_sample(wl["kind"], wl["n"], wl["depth"], wl["seed"], 12.0)
+        info, err = run_oracle_sample(wl["kind"], wl["n"], wl["depth"], wl["seed"], 20.0)
         if info is not None:
             cpu = {"value": info["value"], "unit": info["unit"], "cores": 1, "kind": "oracle",
                    "sample": info["sample"] + ", 1 thread"}
@@ -416,7 +447,7 @@ def main():
             cpu = {"value": None, "unit": None, "cores": 1, "kind": "oracle", "sample": f"failed: {err}"}
         # the same sample with the BLAS threads on every host core (numpy tensordot / einsum)
         ncores = os.cpu_count() or 1
-        info_all, _ = run_oracle_sample(wl["kind"], wl["n"], wl["depth"], wl["seed"], 12.0, threads=ncores)
+        info_all, _ = run_oracle_sample(wl["kind"], wl["n"], wl["depth"], wl["seed"], 20.0, threads=ncores)
         if info_all is not None:
             cpu_all = {"value": info_all["value"], "unit": info_all["unit"], "cores": ncores, "kind": "oracle",
                        "sample": info_all["sample"] + f", {ncores} BLAS threads"}
@@ -435,6 +466,7 @@ def main():
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # 256 MiB > L2
 
     hbm_peak, peak_kind = load_peaks()
+    set_fp32_peak(tn, torch, dev)
     if wl["kind"] == "state":
         circ_p, params0 = C.brickwork(wl["n"], wl["depth"], wl["seed"], parameterized=True)
         circ_f, _ = C.brickwork(wl["n"], wl["depth"], wl["seed"])
@@ -465,6 +497,9 @@ def main():
         kernel_launches = fst["n_passes"]
         alg_bytes = fst["hbm_bytes"] * batch
         alg_flops = fst["flops"] * batch
+        # the circuit's own count: every one-qubit gate as a general 2x2 complex product, 14 real
+        # flops per amplitude (2 complex multiplies, 1 complex add); CZ (a sign) none
+        plain_flops = 14.0 * (1 << wl["n"]) * batch * sum(1 for g in circ_f.gates if len(g.qubits) == 1)
     elif wl["kind"] == "serve":
         circs = C.serving_mix(wl["batch"], wl["seed"])
         handles = [tn.CircuitHandle(c) for c in circs]
@@ -716,7 +751,7 @@ def main():
             line["roofline"] = {"bound": "alu", "achieved": tfl, "peak": FP32_ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
                                 "frac": alu_frac, "traffic": None,
                                 "kernel": "tnq_p* (fused gate-apply pass kernels)",
-                                "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 x 2070 MHz",
+                                "peak_source": FP32_ALU_PEAK_SRC,
                                 "also": {"hbm_gbs": gbs, "hbm_frac": hbm_frac, "hbm_peak": hbm_peak,
                                          "hbm_peak_source": peak_kind}}
         else:
@@ -729,6 +764,14 @@ def main():
             line["roofline"]["kernel_source_hash"] = kernel_hash
         line["roofline"]["launches_per_step"] = kernel_launches
         line["roofline"]["avg_launch_ms"] = avg_launch_ms
+        if wl["kind"] == "state":
+            ptf = plain_flops / kernel_launches / (avg_launch_ms / 1000) / 1e12
+            line["roofline"]["executed_flops_per_step"] = alg_flops
+            line["roofline"]["plain_2x2_count"] = {
+                "flops_per_step": plain_flops, "tflops": ptf, "frac_of_fp32_peak": ptf / FP32_ALU_PEAK_TFLOPS,
+                "note": "14 real flops per amplitude per one-qubit gate (general 2x2 complex product), "
+                        "CZ none; 'achieved' counts the flops the kernels execute after the planner's "
+                        "rewrites"}
 
     if args.workload == "state10":
         # the configuration is latency-bound: one circuit (batch 1) per call, microseconds per call
@@ -847,7 +890,7 @@ def main():
                             "frac": tfl / FP32_ALU_PEAK_TFLOPS, "traffic": None,
                             "kernel": "tn_expectation_value_and_grad (tnq_p* forward + tnq_b* adjoint sweep)",
                             "algorithmic_flops_per_call": bwd_alg_flops,
-                            "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 x 2070 MHz"}
+                            "peak_source": FP32_ALU_PEAK_SRC}
     if wl["kind"] == "serve":
         for _ in range(2):
             seq_step()
@@ -865,7 +908,7 @@ def main():
         tfl = alg / (t_max / args.steps / 1000.0) / 1e12
         line["roofline"] = {"bound": "alu", "achieved": tfl, "peak": FP32_ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
                             "frac": tfl / FP32_ALU_PEAK_TFLOPS, "traffic": None, "kernel": "k_batch_exec",
-                            "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 x 2070 MHz"}
+                            "peak_source": FP32_ALU_PEAK_SRC}
     if wl["kind"] == "sweep":
         # amplitudes/s of every (n, k) point, each timed on its own; the roofline is the largest
         # point's (n = 28, k = 14: 2 GiB state) gate work against the FP32 ALU peak
@@ -887,7 +930,7 @@ def main():
         line["roofline"] = {"bound": "alu", "achieved": tfl, "peak": FP32_ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
                             "frac": tfl / FP32_ALU_PEAK_TFLOPS, "traffic": None,
                             "kernel": "tnq_p* (fused gate-apply), Fig. 3.1 circuit n=28 k=14",
-                            "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 x 2070 MHz"}
+                            "peak_source": FP32_ALU_PEAK_SRC}
     if wl["kind"] == "sweep_amps":
         # per point: amplitudes/s of its call timed on its own, planning time (host), plan shape;
         # roofline: the algorithmic bytes of every launched merge of the step against HBM
@@ -983,7 +1026,7 @@ def main():
         if wl["prec"] == 0:
             comp = {"bound": "alu", "achieved": alg / per_step_s / 1e12, "peak": FP32_ALU_PEAK_TFLOPS,
                     "unit": "TFLOP/s", "frac": alg / per_step_s / 1e12 / FP32_ALU_PEAK_TFLOPS,
-                    "traffic": None, "kernel": "k_cgemm_fp32"}
+                    "traffic": None, "kernel": "k_cgemm_fp32", "peak_source": FP32_ALU_PEAK_SRC}
         else:
             products = 3 if wl["prec"] == 1 else 6
             executed = products * alg  # real tensor flops: products x (2M)(2N)(2K)/... = products x 8MNK

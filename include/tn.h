@@ -324,6 +324,15 @@ tn_status tn_batch_state_offsets(const tn_batch *b, int64_t *offsets);
  * runs out (about 2 s) is reported by tn_sync_status as TN_ERR_TIMEOUT. */
 tn_status tn_batch_run(const tn_batch *b, void *states_dev, void *workspace_dev, tn_stream_t s);
 void tn_free_batch(tn_batch *b);
+/* Testing aid for the failure path (the paper has no counterpart).  Makes the tiles of work-list
+ * pass `pass` (1 <= pass < that circuit's passes in the batch; a circuit that fits one tile has
+ * one) of circuit `circ` wait for one more completed tile of the previous pass than exists, and
+ * bounds every dependency wait of later runs by wait_limit_ns (in [1e6, 1e10]).  The next
+ * tn_batch_run then gives up after that bound: the kernel returns, the states are incomplete, and
+ * tn_sync_status reports TN_ERR_TIMEOUT.  circ = -1 restores the table and the default bound
+ * (about 2 s).  Blocking (one small host-to-device copy); not to be called while a run of this
+ * batch is in flight. */
+tn_status tn_batch_test_stall(tn_batch *b, int32_t circ, int32_t pass, int64_t wait_limit_ns);
 
 /* Tile autotuner (the paper fixes the contraction order ahead of evaluation, Sec. 2.2.3 /
  * Sec. 3; how a plan is cut into tiles is left to the implementation and chosen here by
@@ -352,6 +361,13 @@ tn_status tn_batch_build_tuned(const tn_circuit *const *circuits, int32_t n_circ
  * first device-side failure recorded since the last call (TN_ERR_TIMEOUT / TN_ERR_NUMERIC),
  * or TN_ERR_CUDA if the synchronisation itself failed. */
 tn_status tn_sync_status(tn_stream_t s);
+/* Measured FP32 multiply-add rate of the current device (the paper has no counterpart; the
+ * roofline denominator of the kernels bound by FP32 arithmetic): a kernel of independent packed
+ * FP32x2 multiply-add chains (fma.rn.f32x2, 4 flops per instruction and thread) on every SM at
+ * full occupancy, timed with CUDA events over a few launches of tens of milliseconds each (on a
+ * stream of its own, synchronised).  *tflops receives the best rate in TFLOP/s, *seconds
+ * (optional) that launch's duration.  Blocking; allocates no device memory. */
+tn_status tn_probe_fma_rate(double *tflops, double *seconds);
 /* Message of the last failed call on this thread ("" if none).  Valid until the next call. */
 const char *tn_last_error(void);
 const char *tn_version(void);

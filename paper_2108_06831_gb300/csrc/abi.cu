@@ -864,6 +864,18 @@ tn_status tn_batch_build_tuned(const tn_circuit *const *circuits, int32_t n_circ
 
 void tn_free_batch(tn_batch *b) { batch_free(b); }
 
+tn_status tn_probe_fma_rate(double *tflops, double *seconds) {
+  TN_CHECK_ARG(tflops != nullptr, "NULL argument");
+  return probe_fma_rate(tflops, seconds);
+}
+
+tn_status tn_batch_test_stall(tn_batch *b, int32_t circ, int32_t pass, int64_t wait_limit_ns) {
+  TN_CHECK_ARG(b != nullptr, "NULL argument");
+  tn_status st = check_device(batch_device(b));
+  if (st != TN_OK) return st;
+  return batch_test_stall(b, circ, pass, (long long)wait_limit_ns);
+}
+
 tn_status tn_sync_status(tn_stream_t s) {
   int v = 0;
   cudaError_t e = read_and_clear_status(&v, reinterpret_cast<cudaStream_t>(s));

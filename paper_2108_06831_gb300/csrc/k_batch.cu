@@ -35,6 +35,7 @@ struct alignas(16) BatchTask {
   int pass;  // index into the batch's PassDesc array
   int prev;  // task that must complete first, -1 if none
   int n_tiles;
+  int need_extra;  // tiles of prev awaited beyond its count: 0 (1 only under tn_batch_test_stall)
 };
 
 namespace {
@@ -42,7 +43,7 @@ namespace {
 constexpr int kBatchThreads = 256;  // 2^(12 - 4): the largest tile (12 qubits) with 4 register qubits
 constexpr int kBatchT = 12;
 constexpr size_t kBatchStageMax = 32 * 1024;  // shared memory for a pass's staged records
-constexpr unsigned long long kWaitNs = 2000000000ull;
+constexpr unsigned long long kWaitNs = 2000000000ull;  // default bound of a dependency wait
 
 __device__ __forceinline__ unsigned long long now_ns() {
   unsigned long long t;
@@ -62,7 +63,8 @@ __global__ void __launch_bounds__(kBatchThreads, 3) k_batch_exec(const BatchTask
                                                               const PassDesc *__restrict__ passes,
                                                               float2 *__restrict__ states, int *done,
                                                               unsigned long long *next_item, int *abort_flag,
-                                                              long long total_items, int *status, int stage_cap) {
+                                                              long long total_items, int *status, int stage_cap,
+                                                              unsigned long long wait_ns) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ PassDesc pd;
   __shared__ long long s_item;
@@ -90,12 +92,12 @@ __global__ void __launch_bounds__(kBatchThreads, 3) k_batch_exec(const BatchTask
         s_task = lo;
         const int prev = tasks[lo].prev;
         if (prev >= 0) {
-          const int need = tasks[prev].n_tiles;
+          const int need = tasks[prev].n_tiles + tasks[lo].need_extra;
           if (ld_acquire(done + prev) < need) {
             const unsigned long long t0 = now_ns();
             for (;;) {
               if (ld_acquire(done + prev) >= need) break;
-              if (ld_acquire(abort_flag) != 0 || now_ns() - t0 > kWaitNs) {
+              if (ld_acquire(abort_flag) != 0 || now_ns() - t0 > wait_ns) {
                 atomicCAS(status, 0, (int)TN_ERR_TIMEOUT);
                 atomicExch(abort_flag, 1);
                 s_go = 0;
@@ -239,6 +241,10 @@ struct tn_batch {
   size_t ws_bytes = 0;
   int stage_cap = 0;             // shared-memory bytes for a pass's records (largest pass, capped)
   std::vector<tn_plan *> owned;  // plans made for this batch (tile autotuner)
+  std::vector<tnq::BatchTask> h_tasks;            // host copy of the task list
+  std::vector<std::vector<int>> circ_tasks;       // tasks of each circuit, pass order
+  unsigned long long wait_ns = 2000000000ull;     // dependency-wait bound passed to the kernel
+  int stalled_task = -1;                          // task altered by tn_batch_test_stall, -1 if none
 };
 
 namespace tnq {
@@ -322,6 +328,9 @@ tn_status batch_build(const tn_plan *const *plans, int n, tn_batch **out) {
       last_task[(size_t)i] = (int)tasks.size();
       tasks.push_back(t);
     }
+  b->circ_tasks.assign((size_t)n, {});
+  for (size_t k = 0; k < tasks.size(); ++k) b->circ_tasks[(size_t)tasks[k].circ].push_back((int)k);
+  b->h_tasks = tasks;
   b->total_items = items;
   b->n_tasks = (int)tasks.size();
   b->ws_bytes = ((size_t)b->n_tasks * sizeof(int) + 255) / 256 * 256 + 256;
@@ -368,7 +377,8 @@ cudaError_t batch_run(const tn_batch *b, float2 *states, void *ws, cudaStream_t 
   if (grid < 1) return cudaSuccess;
   k_batch_exec<<<(unsigned)grid, kBatchThreads, smem, s>>>(b->d_tasks, b->n_tasks, b->d_circs, b->d_passes, states,
                                                            done, next, abort_flag, b->total_items,
-                                                           static_cast<int *>(status_word_ptr()), b->stage_cap);
+                                                           static_cast<int *>(status_word_ptr()), b->stage_cap,
+                                                           b->wait_ns);
   return cudaGetLastError();
 }
 
@@ -384,6 +394,42 @@ tn_status batch_offsets(const tn_batch *b, long long *offsets) {
 }
 
 int batch_device(const tn_batch *b) { return b->device; }
+
+tn_status batch_test_stall(tn_batch *b, int circ, int pass, long long wait_ns) {
+  auto upload = [&](int k) -> cudaError_t {
+    return cudaMemcpy(b->d_tasks + k, &b->h_tasks[(size_t)k], sizeof(BatchTask), cudaMemcpyHostToDevice);
+  };
+  // restore the table and the default bound first
+  if (b->stalled_task >= 0) {
+    b->h_tasks[(size_t)b->stalled_task].need_extra = 0;
+    const cudaError_t e = upload(b->stalled_task);
+    if (e != cudaSuccess) return cuda_fail(e, "batch task table");
+    b->stalled_task = -1;
+  }
+  b->wait_ns = kWaitNs;
+  if (circ < 0) return TN_OK;
+  if (circ >= b->n) {
+    set_error("circuit %d out of range (batch of %d)", circ, b->n);
+    return TN_ERR_INVALID_ARG;
+  }
+  const std::vector<int> &ts = b->circ_tasks[(size_t)circ];
+  if (pass < 1 || pass >= (int)ts.size()) {
+    set_error("circuit %d has %d work-list passes; a stall needs 1 <= pass < %d", circ, (int)ts.size(),
+              (int)ts.size());
+    return TN_ERR_INVALID_ARG;
+  }
+  if (wait_ns < 1000000ll || wait_ns > 10000000000ll) {
+    set_error("wait_limit_ns must be within [1e6, 1e10]");
+    return TN_ERR_INVALID_ARG;
+  }
+  const int k = ts[(size_t)pass];
+  b->h_tasks[(size_t)k].need_extra = 1;
+  const cudaError_t e = upload(k);
+  if (e != cudaSuccess) return cuda_fail(e, "batch task table");
+  b->stalled_task = k;
+  b->wait_ns = (unsigned long long)wait_ns;
+  return TN_OK;
+}
 
 void batch_free(tn_batch *b) {
   if (!b) return;

@@ -67,6 +67,8 @@ void batch_free(tn_batch *b);
 tn_status batch_sizes(const tn_batch *b, long long *elems, size_t *ws);
 tn_status batch_offsets(const tn_batch *b, long long *offsets);
 int batch_device(const tn_batch *b);
+tn_status batch_test_stall(tn_batch *b, int circ, int pass, long long wait_ns);
+tn_status probe_fma_rate(double *tflops, double *seconds);
 // The batch takes ownership of plans (freed with it).
 void batch_adopt_plans(tn_batch *b, const std::vector<tn_plan *> &plans);
 // Tile autotuner: plans every circuit at measured-best tile sizes and batches them.

@@ -94,6 +94,8 @@ _sigs = {
     "tn_batch_state_offsets": [_vp, C.POINTER(C.c_int64)],
     "tn_batch_run": [_vp, _vp, _vp, _vp],
     "tn_free_batch": [_vp],
+    "tn_batch_test_stall": [_vp, C.c_int32, C.c_int32, C.c_int64],
+    "tn_probe_fma_rate": [C.POINTER(C.c_double), C.POINTER(C.c_double)],
     "tn_batch_build_tuned": [C.POINTER(_vp), C.c_int32, C.POINTER(TnTuneOpts), _vp, C.POINTER(_vp),
                              C.POINTER(C.c_int32)],
     "tn_sync_status": [_vp],
@@ -358,6 +360,20 @@ class Batch:
 
 def batch_run(batch: Batch, states, workspace, stream=None) -> None:
     _check(_lib.tn_batch_run(batch._h, _ptr(states), _ptr(workspace), _stream(stream)), "tn_batch_run")
+
+
+def batch_test_stall(batch: Batch, circ: int, pass_index: int = 1, wait_limit_ns: int = 0) -> None:
+    """Failure-path testing aid (tn_batch_test_stall): the next runs stop at a dependency wait
+    that can never be met, after wait_limit_ns; circ = -1 restores the batch."""
+    _check(_lib.tn_batch_test_stall(batch._h, int(circ), int(pass_index), int(wait_limit_ns)),
+           "tn_batch_test_stall")
+
+
+def probe_fma_rate() -> tuple:
+    """(TFLOP/s, seconds): the measured FP32 multiply-add rate of the current device."""
+    r, t = C.c_double(), C.c_double()
+    _check(_lib.tn_probe_fma_rate(C.byref(r), C.byref(t)), "tn_probe_fma_rate")
+    return r.value, t.value
 
 
 def sync_status(stream=None) -> int:

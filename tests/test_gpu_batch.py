@@ -119,3 +119,35 @@ def test_tuned_batch_rejects_bad_options():
     hp = [tn.CircuitHandle(C.brickwork(8, 3, 1, parameterized=True)[0])]
     with pytest.raises(tn.TnError):
         tn.Batch.tuned(hp)
+
+
+# The 512-circuit serving mix at its own sizes: a subset of serving_mix(512, 5000) that reaches
+# 22 qubits and depth 28-30 (both halves, brickwork and QFT, including the largest circuit of
+# each), through the tile autotuner and one launch, every state against the oracle.
+SERVING_SUBSET = [i * 31 for i in range(16)] + [494, 441]
+
+
+def test_serving_mix_subset_tuned_matches_oracle():
+    import multiprocessing as mp
+    import os
+    from oracle.statevector import simulate_state
+    from paper_2108_06831_gb300 import tn
+    mix = C.serving_mix(512, 5000)
+    circs = [mix[i] for i in SERVING_SUBSET]
+    assert max(c.n_qubits for c in circs) == 22
+    # the oracle runs in spawned worker processes while the GPU works
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(max(1, min(8, os.cpu_count() or 1))) as pool:
+        pending = pool.map_async(simulate_state, circs, chunksize=1)
+        handles = [tn.CircuitHandle(c) for c in circs]
+        b = tn.Batch.tuned(handles, reps=1)
+        states = torch.full((b.state_elems,), complex(float("nan"), 0), dtype=torch.complex64, device="cuda")
+        ws = torch.empty(b.workspace_bytes, dtype=torch.uint8, device="cuda")
+        tn.batch_run(b, states, ws)
+        torch.cuda.synchronize()
+        assert tn.sync_status() == tn.OK
+        got = states.cpu().numpy()
+        refs = pending.get(timeout=1800)
+    for c, off, ref in zip(circs, b.offsets, refs):
+        s = got[off:off + (1 << c.n_qubits)]
+        assert np.linalg.norm(s - ref) / np.linalg.norm(ref) <= TOL, c.name

@@ -81,17 +81,40 @@ def test_grid_5x5_depth12(precision):
     assert _rel(got[:6], ref) <= TOL
 
 
-def test_cfg3_grid_6x6_depth12_sampled():
-    """The 36-qubit configuration in the bench's launch configuration (64 bitstrings per call,
-    3xTF32 merges): three amplitudes against the oracle's own network sweep (FP64), and the
-    Porter-Thomas statistic over the 64 (mean |a|^2 2^36 near 1)."""
-    from oracle.tn import contract_amplitude_sweep
+def read_golden_amplitudes(name):
+    """(bitstrings, amplitudes) stored by tests/golden/make_oracle_amplitudes.py (FP64 oracle)."""
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", name)
+    xs, amps = [], []
+    with open(path) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            x, re, im = line.split()
+            xs.append(int(x))
+            amps.append(complex(float(re), float(im)))
+    return np.array(xs, dtype=np.uint64), np.array(amps)
+
+
+@pytest.mark.parametrize("precision", [0, 1, 2])
+def test_cfg3_grid_6x6_depth12_against_stored_oracle(precision):
+    """The 36-qubit configuration in the bench's launch configuration (64 bitstrings per call)
+    in each merge precision (FP32, 3xTF32, split BF16): all 64 amplitudes of the call against
+    the oracle's FP64 sweep contraction (stored; the oracle needs ~10 s per amplitude), element
+    by element within the relative L2 bar, and the Porter-Thomas statistic (mean |a|^2 2^36
+    near 1)."""
     c = C.grid(6, 6, 12, 3003)
     xs = C.random_bitstrings(36, 64, 3004)
-    got, st = _amps(c, xs, 64, 1)
+    gx, ref = read_golden_amplitudes("oracle_grid6x6_d12_s3003.txt")
+    assert np.array_equal(gx, xs)  # the generator still makes the stored bitstrings
+    got, st = _amps(c, xs, 64, precision)
     assert st["net_max_log2"] <= 28
-    ref = np.array([contract_amplitude_sweep(c, int(x)) for x in xs[:3]])
-    assert _rel(got[:3], ref) <= TOL
+    err = _rel(got, ref)
+    assert err <= TOL, err
+    # element by element: no amplitude is off by more than the bar times the vector's RMS
+    rms = np.linalg.norm(ref) / np.sqrt(len(ref))
+    assert np.max(np.abs(got - ref)) <= TOL * rms * 4, np.max(np.abs(got - ref)) / rms
+    print(f"cfg3 precision {precision}: rel L2 error vs FP64 {err:.2e}")
     pt = float(np.mean(np.abs(got.astype(np.complex128)) ** 2) * 2.0 ** 36)
     assert 0.5 < pt < 1.6
 

@@ -160,22 +160,29 @@ def test_fig31_sweep_points(n, k):
     assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= 1e-5
 
 
-def test_fig31_largest_point_norm_and_tiles():
-    """n = 28, k = 14 (2 GiB state): no full-state oracle fits the test budget; the norm is 1 and
-    two different tilings (different pass structures) agree."""
+def test_fig31_largest_point_against_stored_oracle():
+    """n = 28, k = 14 (2 GiB state), the largest point of the Fig. 3.1 grid, in the bench's
+    launch configuration: 8 amplitudes against the oracle's FP64 greedy network contraction
+    (stored: ~1 min and 9 GB of host memory per amplitude), plus the norm."""
+    import os
     from paper_2108_06831_gb300 import tn
     c = C.paper_fig31(28, 14, 6042)
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "oracle_fig31_n28_k14_s6042.txt")
+    rows = [l.split() for l in open(path) if l.strip() and not l.startswith("#")]
+    xs = np.array([int(r[0]) for r in rows], dtype=np.int64)
+    ref = np.array([complex(float(r[1]), float(r[2])) for r in rows])
+    assert np.array_equal(xs.astype(np.uint64), C.random_bitstrings(28, 8, 6242))
     a = tn.Contractor(c)
-    b = tn.Contractor(c, tile_qubits=10)
     x = torch.empty(1 << 28, dtype=torch.complex64, device="cuda")
     tn.contract_state(a.plan, None, x, a.workspace)
-    y = torch.empty_like(x)
-    tn.contract_state(b.plan, None, y, b.workspace)
     torch.cuda.synchronize()
     assert tn.sync_status() == tn.OK
     nx = torch.linalg.vector_norm(x.to(torch.complex128)).item()
     assert abs(nx - 1.0) <= 1e-5
-    assert (torch.linalg.vector_norm((x - y).to(torch.complex128)) / nx).item() <= 1e-5
+    got = x[torch.as_tensor(xs, device="cuda")].cpu().numpy()
+    # amplitudes of a 2^28-entry state are ~2^-14: judge them against the state's RMS scale
+    err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+    assert err <= 1e-5, err
 
 
 def test_max_size_32_qubits_closed_form():
