@@ -76,6 +76,11 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-specialize", action="store_true", help="run the interpreting gate-apply kernel")
+    ap.add_argument("--blocks", type=int, default=0,
+                    help="state workloads: contract by uniform 2^k x 2^k blocks of k = 6 or 7 qubits, each "
+                         "applied by the batched complex GEMM in --prec (0 FP32, 1 3xTF32, 2 split BF16)")
+    ap.add_argument("--no-fuse", action="store_true",
+                    help="state workloads: apply the gates one by one (no precontracted two-qubit blocks)")
     return ap.parse_args()
 
 
@@ -473,7 +478,9 @@ def main():
         batch = wl["batch"]
         params = np.tile(params0, (batch, 1))
         spec = not args.no_specialize
-        ctr = tn.Contractor(circ_p, batch=batch, tile_qubits=args.tile, device=dev, specialize=spec)
+        bprec = args.prec if args.blocks else 0
+        ctr = tn.Contractor(circ_p, batch=batch, tile_qubits=args.tile, device=dev, specialize=spec,
+                            fuse=not args.no_fuse, block_qubits=args.blocks, precision=bprec)
         p_dev = torch.as_tensor(params, device=dev)
         out = torch.empty((batch, 1 << wl["n"]), dtype=torch.complex64, device=dev)
         units_per_step = batch * (1 << wl["n"])
@@ -482,10 +489,13 @@ def main():
         def step():
             tn.contract_state(ctr.plan, p_dev, out, ctr.workspace)
         launches_per_step = 1 + ctr.plan.stats()["n_passes"]
+        if args.blocks:  # block build + first block; per GEMM the B operand's split (tensor cores) + the GEMM
+            launches_per_step = 2 + ctr.plan.stats()["n_passes"] * (2 if bprec else 1)
         import tempfile
         dump = tempfile.mkdtemp(prefix="tnq_src_")
         os.environ["TNQ_JIT_DUMP_DIR"] = dump  # the timed plan's generated sources, hashed below
-        fixed = tn.Contractor(circ_f, batch=batch, tile_qubits=args.tile, device=dev, specialize=spec)
+        fixed = tn.Contractor(circ_f, batch=batch, tile_qubits=args.tile, device=dev, specialize=spec,
+                              fuse=not args.no_fuse, block_qubits=args.blocks, precision=bprec)
         del os.environ["TNQ_JIT_DUMP_DIR"]
         kernel_hash = jit_source_hash(dump)
         import shutil
@@ -713,7 +723,7 @@ def main():
     if world > 1:
         dist.barrier()
     # the arithmetic the step computes in: FP32 (complex64 states), or the tensor-core split forms
-    prec_used = args.prec if wl["kind"] == "amps" else wl.get("prec", 0)
+    prec_used = args.prec if (wl["kind"] == "amps" or (wl["kind"] == "state" and args.blocks)) else wl.get("prec", 0)
     dtype = {0: "f32", 1: "3xtf32 (f32 accumulate)", 2: "bf16x3 (f32 accumulate)"}[prec_used]
     if wl["kind"] == "permute":
         dtype = "c64 (data movement)"
@@ -729,6 +739,10 @@ def main():
             "config": {"workload": args.workload, "n_qubits": wl["n"], "depth": wl["depth"], "batch": batch,
                        "tile_qubits": ctr.plan.stats()["tile_qubits"] if ctr is not None else None,
                        "specialized_kernels": bool(ctr.plan.stats()["specialized"]) if ctr is not None else None,
+                       "fused_2q_blocks": ctr.plan.stats()["n_fused"] if ctr is not None and not args.blocks else None,
+                       "uniform_blocks": ({"block_qubits": args.blocks, "blocks": ctr.plan.stats()["n_fused"],
+                                           "gemm_launches": ctr.plan.stats()["n_passes"]}
+                                          if args.blocks and ctr is not None else None),
                        "l2": "256 MiB buffer written between timed steps (untimed)",
                        "parallelism": f"replicas x{world}"},
             "clocks": clk.summary()}
@@ -747,7 +761,35 @@ def main():
         tfl = flops_per_launch / (avg_launch_ms / 1000) / 1e12
         hbm_frac = gbs / hbm_peak
         alu_frac = tfl / FP32_ALU_PEAK_TFLOPS
-        if alu_frac >= hbm_frac:
+        if wl["kind"] == "state" and args.blocks:
+            # uniform blocks: the dominant kernel is the batched complex GEMM (one launch per block);
+            # the whole call (block build, clear, first block, GEMMs) is charged to the GEMMs
+            if bprec == 0:
+                tpk, tsrc, tk = alu_frac, FP32_ALU_PEAK_SRC, "alu"
+                tpeak, tach = FP32_ALU_PEAK_TFLOPS, tfl
+            else:
+                bf16 = 1886.8
+                try:
+                    with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+                        bf16 = float(json.load(f)["bf16_tflops"])
+                except Exception:
+                    pass
+                products = 3 if bprec == 1 else 6
+                tpeak = bf16 * (1.1 / 2.25) if bprec == 1 else bf16
+                tach = products * tfl
+                tpk, tk = tach / tpeak, "tensor"
+                tsrc = "MEASURED_PEAKS.json bf16_tflops" + (" x 1.1/2.25 (TF32 nominal ratio)" if bprec == 1 else "")
+            kname = ("k_cgemm_tc_stream (batched complex GEMM, tcgen05)" if bprec else "k_cgemm_fp32 (batched complex GEMM)")
+            if tpk >= hbm_frac:
+                line["roofline"] = {"bound": tk, "achieved": tach, "peak": tpeak, "unit": "TFLOP/s", "frac": tpk,
+                                    "traffic": None, "kernel": kname, "peak_source": tsrc,
+                                    "also": {"hbm_gbs": gbs, "hbm_frac": hbm_frac, "hbm_peak": hbm_peak}}
+            else:
+                line["roofline"] = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
+                                    "frac": hbm_frac, "traffic": None, "kernel": kname,
+                                    "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})",
+                                    "also": {"tflops_executed": tach, "compute_frac": tpk, "compute_bound": tk}}
+        elif alu_frac >= hbm_frac:
             line["roofline"] = {"bound": "alu", "achieved": tfl, "peak": FP32_ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
                                 "frac": alu_frac, "traffic": None,
                                 "kernel": "tnq_p* (fused gate-apply pass kernels)",
@@ -759,7 +801,7 @@ def main():
                                 "traffic": None, "kernel": "tnq_p* (fused gate-apply pass kernels)",
                                 "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})",
                                 "also": {"tflops": tfl, "alu_frac": alu_frac}}
-        if args.workload == "state24" and not args.tile and not args.no_specialize:
+        if args.workload == "state24" and not args.tile and not args.no_specialize and not args.no_fuse:
             line["roofline"]["traffic"] = recorded_traffic(kernel_hash)
             line["roofline"]["kernel_source_hash"] = kernel_hash
         line["roofline"]["launches_per_step"] = kernel_launches

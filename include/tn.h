@@ -113,6 +113,18 @@ typedef enum { TN_PREC_FP32 = 0, TN_PREC_3XTF32 = 1, TN_PREC_SPLIT_BF16 = 2 } tn
 #define TN_PLAN_Q428 8 /* a fixed-point plan for tn_contract_state_q428 (Sec. 3: the FPGA datapath's
                          * complex arithmetic in 32-bit fixed point, 28 fractional bits); fixed-angle
                          * circuits, batch 1, target TN_TARGET_STATE, at most 34 qubits */
+#define TN_PLAN_NO_FUSION 16 /* apply the gates of the forward passes one by one: no precontraction of
+                              * runs of gates on two qubits into dense 4x4 blocks (by default a run whose
+                              * gates cost the pass kernels more than one dense 4x4 is precontracted,
+                              * per call, in FP64 -- Sec. 3's precomputed small contractions) */
+#define TN_PLAN_BLOCKS 32 /* TN_TARGET_STATE by uniform square blocks (Sec. 3: the contraction deployed as
+                           * square matrices of one size): the circuit is cut into blocks of gates on
+                           * opts->block_qubits = k qubits (6 or 7; windows of k qubits at alternating
+                           * offsets, each taking its light cone), every block is precontracted per
+                           * call into one 2^k x 2^k unitary (FP64, from the parameters), and applied
+                           * to the state viewed as [2^(N-k)] x [2^k] by the batched complex GEMM in
+                           * opts->precision (FP32 on the CUDA cores, 3XTF32 or SPLIT_BF16 on the
+                           * tensor cores).  Needs k + 7 <= n_qubits and a power-of-two batch. */
 #define TN_PLAN_NO_SPECIALIZE 2 /* run the interpreting gate-apply kernel instead of plan-specialised
                                  * kernels (those are generated as CUDA C++ and compiled with NVRTC
                                  * when the plan is built; compiled code is cached on disk) */
@@ -132,7 +144,8 @@ typedef struct {
   int64_t order_search;          /* TN_PLAN_NETWORK: 0 = the fixed mix of trials above; 1 = adaptive search
                                   * (a cross-entropy hyper-optimiser over the trial kind, noise temperature and
                                   * bitstring-index weight, refitted each round to the best quarter so far) */
-  int64_t reserved[3];           /* must be zero */
+  int64_t block_qubits;          /* TN_PLAN_BLOCKS: qubits per block k (6 or 7); 0 = 6 */
+  int64_t reserved[2];           /* must be zero */
 } tn_plan_opts;
 
 /* Plan summary (for measurement and tests). */
@@ -165,6 +178,9 @@ typedef struct {
                            max(bytes read and written, complex flops / 32) */
   double net_bytes;     /* TN_PLAN_NETWORK: algorithmic HBM bytes of one call of amp_batch bitstrings: every
                            launched merge's operands read and result written once (complex64) */
+  int32_t n_fused;      /* dense 4x4 blocks (precontracted runs of gates on two qubits) in the forward passes;
+                           TN_PLAN_BLOCKS: the 2^k x 2^k blocks (n_passes = GEMM launches = blocks - 1) */
+  int32_t reserved_stats;
 } tn_plan_stats;
 
 /* Pauli sum H = sum_t coef[t] * P_t (host memory, read during tn_build_observable only).

@@ -11,6 +11,7 @@
 
 #include "jit.h"
 #include "network.h"
+#include "blocks.h"
 #include "kernels.h"
 #include "tnq_internal.h"
 
@@ -110,6 +111,7 @@ tn_status upload(const std::vector<T> &v, T **dst) {
 
 void free_plan_device(tn_plan *p) {
   cudaFree(p->d_slots);
+  cudaFree(p->d_fused);
   cudaFree(p->d_fwd_pass);
   cudaFree(p->d_bwd_pass);
   cudaFree(p->d_fwd_phase);
@@ -141,7 +143,8 @@ tn_status call_mats(const tn_plan *p, const double *params, void *ws, cudaStream
   TN_CHECK_ARG(params != nullptr, "this circuit reads %d parameters: params_dev must not be NULL", p->n_params);
   TN_CHECK_ARG(ws != nullptr, "workspace_dev must not be NULL (plan needs %zu bytes)", p->ws_bytes);
   float2 *m = reinterpret_cast<float2 *>(static_cast<char *>(ws) + p->ws_mats);
-  TN_CUDA(launch_materialize(p->d_slots, (int)p->slots.size(), params, p->n_params, p->batch, p->mstride, m, s),
+  TN_CUDA(launch_materialize(p->d_slots, (int)p->slots.size(), p->d_fused, params, p->n_params, p->batch, p->mstride,
+                             m, s),
           "gate table kernel");
   *mats = m;
   *mstride = p->mstride;
@@ -230,7 +233,16 @@ tn_status tn_plan_contraction(const tn_circuit *c, const tn_plan_opts *opts, tn_
   TN_CHECK_ARG(o.precision >= TN_PREC_FP32 && o.precision <= TN_PREC_SPLIT_BF16, "bad precision %d", o.precision);
   TN_CHECK_ARG(o.tile_qubits == 0 || (o.tile_qubits >= kLowBits + 2 && o.tile_qubits <= kMaxTile), "tile_qubits=%d not in {0, 6..%d}",
                o.tile_qubits, kMaxTile);
-  for (int i = 0; i < 3; ++i) TN_CHECK_ARG(o.reserved[i] == 0, "reserved fields must be zero");
+  for (int i = 0; i < 2; ++i) TN_CHECK_ARG(o.reserved[i] == 0, "reserved fields must be zero");
+  if (o.flags & TN_PLAN_BLOCKS) {
+    TN_CHECK_ARG(!(o.flags & (TN_PLAN_NETWORK | TN_PLAN_Q428)), "TN_PLAN_BLOCKS excludes TN_PLAN_NETWORK and TN_PLAN_Q428");
+    TN_CHECK_ARG(o.target == TN_TARGET_STATE, "TN_PLAN_BLOCKS contracts states (TN_TARGET_STATE)");
+    if (o.block_qubits == 0) o.block_qubits = 6;
+    TN_CHECK_ARG(o.block_qubits == 6 || o.block_qubits == 7, "block_qubits must be 6 or 7 (got %lld)",
+                 (long long)o.block_qubits);
+  } else {
+    TN_CHECK_ARG(o.block_qubits == 0, "block_qubits is for TN_PLAN_BLOCKS plans");
+  }
   TN_CHECK_ARG(o.order_search == 0 || o.order_search == 1, "order_search must be 0 or 1 (got %lld)",
                (long long)o.order_search);
   TN_CHECK_ARG(o.order_trials == 0 || o.order_trials == 1 || (o.order_trials >= 4 && o.order_trials <= 4096),
@@ -277,6 +289,28 @@ tn_status tn_plan_contraction(const tn_circuit *c, const tn_plan_opts *opts, tn_
     *out = p;
     return TN_OK;
   }
+  if (o.flags & TN_PLAN_BLOCKS) {
+    p->blocks = new BlockPlan();
+    tn_status s2 = plan_blocks(*c, (int)o.block_qubits, o.batch, o.precision, *p->blocks, err);
+    if (s2 == TN_OK && !p->host_only) {
+      cudaError_t ce = cudaGetDevice(&p->device);
+      if (ce != cudaSuccess) {
+        err = cudaGetErrorString(ce);
+        s2 = TN_ERR_CUDA;
+      }
+    }
+    if (s2 == TN_OK) s2 = upload_blocks(*p->blocks, p->host_only, err);
+    if (s2 != TN_OK) {
+      set_error("block plan: %s", err.c_str());
+      delete p->blocks;
+      delete p;
+      return s2;
+    }
+    p->param_dependent = c->n_params > 0;
+    p->ws_bytes = p->blocks->ws_bytes;
+    *out = p;
+    return TN_OK;
+  }
   if (o.flags & TN_PLAN_NETWORK) {
     p->net = new NetPlan();
     int lb = 0;
@@ -299,7 +333,9 @@ tn_status tn_plan_contraction(const tn_circuit *c, const tn_plan_opts *opts, tn_
     *out = p;
     return TN_OK;
   }
-  const tn_circuit fwd_circ = push_phases(*c);
+  const bool fuse = !(o.flags & TN_PLAN_NO_FUSION);
+  const tn_circuit fwd_circ = push_phases(fuse ? fuse_pairs(*c, p->fused) : *c, p->fused);
+  for (const TnGate &g : fwd_circ.gates) p->n_fused += g.kind == KIND_F2 ? 1 : 0;
   tn_status st = build_pass_plan(fwd_circ, T, K, false, p->slots, p->fwd, err);
   // the adjoint sweep stages two tiles (psi, lambda), double-buffered: at most 2^11 amplitudes each
   const int T_bwd = std::min(T, 11);
@@ -313,8 +349,7 @@ tn_status tn_plan_contraction(const tn_circuit *c, const tn_plan_opts *opts, tn_
   p->mstride = 0;
   if (!p->slots.empty()) {
     const MatSlot &l = p->slots.back();
-    int ent = l.shape == SHAPE_M2 ? 4 : l.shape == SHAPE_M4 ? 16 : 2;
-    p->mstride = l.offset + ent;
+    p->mstride = l.offset + shape_units(l.shape);
   }
   p->mstride = (p->mstride + 1) & ~1;
   p->param_dependent = c->n_params > 0;
@@ -359,6 +394,7 @@ tn_status tn_plan_contraction(const tn_circuit *c, const tn_plan_opts *opts, tn_
     TN_CUDA(cudaGetDevice(&p->device), "cudaGetDevice");
     tn_status u = TN_OK;
     if (u == TN_OK) u = upload(p->slots, &p->d_slots);
+    if (u == TN_OK && !p->fused.empty()) u = upload(p->fused, &p->d_fused);
     if (u == TN_OK) u = upload(p->fwd.passes, &p->d_fwd_pass);
     if (u == TN_OK) u = upload(p->fwd.phases, &p->d_fwd_phase);
     if (u == TN_OK) u = upload(p->fwd.ops, &p->d_fwd_ops);
@@ -372,7 +408,7 @@ tn_status tn_plan_contraction(const tn_circuit *c, const tn_plan_opts *opts, tn_
         set_error("cudaMalloc of the fixed gate table: %s", cudaGetErrorString(e));
         u = TN_ERR_OOM;
       } else {
-        e = launch_materialize(p->d_slots, (int)p->slots.size(), nullptr, 0, 1, p->mstride,
+        e = launch_materialize(p->d_slots, (int)p->slots.size(), p->d_fused, nullptr, 0, 1, p->mstride,
                                reinterpret_cast<float2 *>(p->d_fixed_mats), 0);
         if (e == cudaSuccess) e = cudaDeviceSynchronize();
         if (e != cudaSuccess) u = cuda_fail(e, "fixed gate table");
@@ -416,6 +452,7 @@ tn_status tn_plan_get_stats(const tn_plan *p, tn_plan_stats *st) {
   st->n_passes = (int)p->fwd.passes.size();
   st->n_phases = (int)p->fwd.phases.size();
   st->n_ops = (long long)p->fwd.ops.size();
+  st->n_fused = p->n_fused;
   if (p->q428) {  // one launch per gate, each reading and writing every amplitude (int32 pairs)
     st->n_passes = (int)p->q428->size();
     st->hbm_bytes = 8.0 * std::ldexp(1.0, p->n) * (1.0 + 2.0 * (double)p->q428->size());
@@ -430,6 +467,18 @@ tn_status tn_plan_get_stats(const tn_plan *p, tn_plan_stats *st) {
   st->n_bwd_passes = (int)p->bwd.passes.size();
   st->bwd_flops = 2.0 * p->bwd.flops + p->bwd.grad_flops;
   st->specialized = p->jit_kernels.empty() ? 0 : 1;
+  if (p->blocks) {
+    const BlockPlan &bp = *p->blocks;
+    st->n_passes = (int)bp.qubits.size() - 1;
+    st->n_phases = 0;
+    st->n_ops = (long long)bp.gates.size();
+    st->n_fused = (int)bp.qubits.size();
+    st->tile_qubits = bp.k;
+    st->reg_qubits = 0;
+    st->flops = bp.flops;
+    st->hbm_bytes = bp.bytes;
+    st->specialized = 0;
+  }
   if (p->net) {
     st->n_passes = 0;
     st->net_merges = (int)p->net->launches.size();
@@ -451,6 +500,12 @@ void tn_free_plan(tn_plan *p) {
   if (!p) return;
   delete p->q428;
   p->q428 = nullptr;
+  if (p->blocks) {
+    if (!p->host_only) free_blocks(*p->blocks);
+    delete p->blocks;
+    delete p;
+    return;
+  }
   if (p->net) {
     if (!p->host_only) free_network(*p->net);
     delete p->net;
@@ -599,6 +654,14 @@ tn_status tn_contract_state(const tn_plan *p, const double *params_dev, void *st
   TN_CHECK_ARG(state_dev != nullptr, "state_dev is NULL");
   TN_CHECK_ARG(((uintptr_t)state_dev & 15) == 0, "state_dev must be 16-byte aligned");
   cudaStream_t cs = reinterpret_cast<cudaStream_t>(s);
+  if (p->blocks) {
+    TN_CHECK_ARG(p->n_params == 0 || params_dev != nullptr,
+                 "this circuit reads %d parameters: params_dev must not be NULL", p->n_params);
+    TN_CHECK_ARG(workspace_dev != nullptr, "workspace_dev is NULL (plan needs %zu bytes)", p->ws_bytes);
+    TN_CUDA(run_blocks(*p->blocks, params_dev, p->n_params, static_cast<float2 *>(state_dev), workspace_dev, cs),
+            "block contraction");
+    return TN_OK;
+  }
   const float2 *mats = nullptr;
   long long mstride = 0;
   st = call_mats(p, params_dev, workspace_dev, cs, &mats, &mstride);

@@ -139,14 +139,22 @@ __device__ __forceinline__ void reg_g2_b(float2 (&a)[1 << K], int rb, const floa
 }
 
 template <int K>
-__device__ __forceinline__ void reg_g2_dispatch(float2 (&a)[1 << K], int ra, int rb, const float2 *m) {
+__device__ __forceinline__ void reg_g2_dispatch(float2 (&a)[1 << K], int ra, int rb, const float2 *m, bool packed) {
   if constexpr (K >= 2) {
     float2 u[16];
+    if (packed) {  // SHAPE_M4X: entry k is (re, re, -im, im)
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      const float4 v = ld4(m + 2 * k);
-      u[2 * k] = make_float2(v.x, v.y);
-      u[2 * k + 1] = make_float2(v.z, v.w);
+      for (int k = 0; k < 16; ++k) {
+        const float4 v = ld4(m + 2 * k);
+        u[k] = make_float2(v.x, v.w);
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const float4 v = ld4(m + 2 * k);
+        u[2 * k] = make_float2(v.x, v.y);
+        u[2 * k + 1] = make_float2(v.z, v.w);
+      }
     }
     switch (ra) {
       case 0: reg_g2_b<K, 0>(a, rb, u); break;
@@ -205,7 +213,7 @@ __device__ __forceinline__ void apply_op(float2 (&a)[1 << K], const OpDesc &op, 
         if (neg) reg_flush_sign<K>(a, neg);
         neg = 0;
       }
-      reg_g2_dispatch<K>(a, op.a_pos, op.b_pos, mats + op.mat);
+      reg_g2_dispatch<K>(a, op.a_pos, op.b_pos, mats + op.mat, (op.flags & OPF_PACKED) != 0);
       break;
     case OP_D1: {
       const float4 d = ld4(mats + op.mat);

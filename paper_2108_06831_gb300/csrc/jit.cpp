@@ -183,6 +183,41 @@ void emit_op(Emitter &E, const OpDesc &op, int kind) {
           }
         return;
       }
+      if (op.flags & OPF_PACKED) {
+        // fused block: entries in the packed layout (re, re, -im, im); every output is a chain of
+        // 8 packed multiply-adds, each input is swapped once for its 4 uses
+        E.line("{");
+        for (int k = 0; k < 16; ++k) {
+          snprintf(buf, sizeof buf, "  const float4 e%d = M4[%d];", k, (op.mat >> 1) + k);
+          E.line(buf);
+        }
+        for (int j = 0; j < R; ++j) {
+          if (j & ((1 << ra) | (1 << rb))) continue;
+          const int idx[4] = {j, j | (1 << rb), j | (1 << ra), j | (1 << ra) | (1 << rb)};
+          E.line("  {");
+          for (int m = 0; m < 4; ++m) {
+            snprintf(buf, sizeof buf, "    const float2 v%d = a[%d]; const u64 p%d = pk(v%d.x, v%d.y), s%d = pk(v%d.y, v%d.x);", m,
+                     idx[m], m, m, m, m, m, m);
+            E.line(buf);
+          }
+          for (int k = 0; k < 4; ++k) {
+            std::string t = "    { u64 t = mul2(pk(e" + std::to_string(4 * k) + ".x, e" + std::to_string(4 * k) + ".y), p0);";
+            snprintf(buf, sizeof buf, " t = fma2(pk(e%d.z, e%d.w), s0, t);", 4 * k, 4 * k);
+            t += buf;
+            for (int m = 1; m < 4; ++m) {
+              snprintf(buf, sizeof buf, " t = fma2(pk(e%d.x, e%d.y), p%d, t); t = fma2(pk(e%d.z, e%d.w), s%d, t);", 4 * k + m,
+                       4 * k + m, m, 4 * k + m, 4 * k + m, m);
+              t += buf;
+            }
+            snprintf(buf, sizeof buf, " a[%d] = up(t); }", idx[k]);
+            t += buf;
+            E.line(t);
+          }
+          E.line("  }");
+        }
+        E.line("}");
+        return;
+      }
       E.line("{ float2 u[16];");
       for (int k = 0; k < 16; ++k) E.line("  u[" + std::to_string(k) + "] = " + mat(k) + ";");
       for (int j = 0; j < R; ++j) {

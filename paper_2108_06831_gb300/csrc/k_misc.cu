@@ -6,14 +6,25 @@
 namespace tnq {
 
 // Gate tensors are built once per call from the parameters (one thread per slot and
-// batch element; angles in FP64, entries stored as complex64).
-__global__ void k_materialize(const MatSlot *__restrict__ slots, int n_slots, const double *__restrict__ params,
-                              int n_params, int batch, long long mstride, float2 *__restrict__ out) {
+// batch element; angles in FP64, entries stored as complex64).  A fused block (KIND_F2) is the
+// FP64 product of its member gates, stored in the packed layout (SHAPE_M4X).
+__global__ void k_materialize(const MatSlot *__restrict__ slots, int n_slots, const FusedMember *__restrict__ fused,
+                              const double *__restrict__ params, int n_params, int batch, long long mstride,
+                              float2 *__restrict__ out) {
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (long long)n_slots * batch) return;
   const int b = (int)(idx / n_slots);
   const int k = (int)(idx % n_slots);
   const MatSlot &s = slots[k];
+  float2 *dst = out + (long long)b * mstride + s.offset;
+  if (s.kind == KIND_F2) {
+    double m[32];
+    float ent[64];
+    fused_matrix(fused + s.fuse_begin, s.fuse_count, params ? params + (long long)b * n_params : nullptr, m);
+    packed_m4x(m, ent);
+    for (int i = 0; i < 32; ++i) dst[i] = make_float2(ent[2 * i], ent[2 * i + 1]);
+    return;
+  }
   double ang[3] = {s.angle[0], s.angle[1], s.angle[2]};
   for (int a = 0; a < 3; ++a)
     for (int k = 0; k < 2; ++k)
@@ -21,17 +32,16 @@ __global__ void k_materialize(const MatSlot *__restrict__ slots, int n_slots, co
   double tmp[32];
   float ent[32];
   const int n = slot_entries(s, ang, tmp, ent);
-  float2 *dst = out + (long long)b * mstride + s.offset;
   for (int i = 0; i < n; ++i) dst[i] = make_float2(ent[2 * i], ent[2 * i + 1]);
 }
 
-cudaError_t launch_materialize(const MatSlot *d_slots, int n_slots, const double *params, int n_params, int batch,
-                               long long mstride, float2 *out, cudaStream_t s) {
+cudaError_t launch_materialize(const MatSlot *d_slots, int n_slots, const FusedMember *d_fused, const double *params,
+                               int n_params, int batch, long long mstride, float2 *out, cudaStream_t s) {
   const long long total = (long long)n_slots * batch;
   if (total == 0) return cudaSuccess;
   const int threads = 128;
-  k_materialize<<<(unsigned)((total + threads - 1) / threads), threads, 0, s>>>(d_slots, n_slots, params, n_params,
-                                                                               batch, mstride, out);
+  k_materialize<<<(unsigned)((total + threads - 1) / threads), threads, 0, s>>>(d_slots, n_slots, d_fused, params,
+                                                                               n_params, batch, mstride, out);
   return cudaGetLastError();
 }
 

@@ -54,6 +54,8 @@ GateCls classify(const TnGate &g) {
     case TN_GATE_CNOT: c.type = OP_C1; c.qb = g.q[1]; c.need_b = true; c.shape = SHAPE_M2; break;
     case TN_GATE_SWAP: case TN_GATE_MAT2:
       c.type = OP_G2; c.qb = g.q[1]; c.need_a = c.need_b = true; c.shape = SHAPE_M4; break;
+    case KIND_F2:
+      c.type = OP_G2; c.qb = g.q[1]; c.need_a = c.need_b = true; c.shape = SHAPE_M4X; break;
     default:  // H X Y SX SY SW RX RY U3
       c.type = OP_G1; c.need_a = true; c.shape = SHAPE_M2; break;
   }
@@ -101,15 +103,7 @@ int op_code_cost(int type, int kind, bool adjoint, bool has_grad, int n_grad) {
 }
 constexpr int kPassCodeBudget = 7000;
 
-int shape_entries(int shape) {
-  switch (shape) {
-    case SHAPE_M2: return 4;
-    case SHAPE_M4: return 16;
-    case SHAPE_DIAG2: return 2;
-    case SHAPE_PHASE: return 1;
-  }
-  return 0;
-}
+int shape_entries(int shape) { return shape_units(shape); }
 
 struct Planner {
   int N, T, K;
@@ -147,7 +141,151 @@ bool is_diagonal_kind(const TnGate &g) {
   }
 }
 
+// Cost of a gate in the forward pass kernels, in packed FP32x2 multiply-add instructions per
+// amplitude (the FMA pipe's work): U3 3 (after the phase-pushing rewrite below), a real or
+// imaginary-off-diagonal rotation 2, a general 2x2 4, a one-sided phase 1, a general diagonal 2,
+// permutations (X, CNOT, SWAP) none, a sign (Z, CZ) a quarter; a dense 4x4 costs 8.
+double fuse_cost(const TnGate &g) {
+  switch (g.kind) {
+    case TN_GATE_U3: return 3.0;
+    case TN_GATE_RX: case TN_GATE_RY: case TN_GATE_H: case TN_GATE_SX: case TN_GATE_SY: return 2.0;
+    case TN_GATE_X: case TN_GATE_CNOT: case TN_GATE_SWAP: return 0.0;
+    case TN_GATE_Z: case TN_GATE_CZ: return 0.25;
+    case TN_GATE_S: case TN_GATE_SDG: case TN_GATE_T: case TN_GATE_TDG: return 1.0;
+    case TN_GATE_CP: return 0.5;
+    case TN_GATE_RZ: return 2.0;
+    case TN_GATE_MAT1: return mat1_is_diagonal(g) ? 2.0 : 4.0;
+    case TN_GATE_MAT2: return 8.0;
+    default: return 4.0;  // Y, SW: general 2x2
+  }
+}
+constexpr double kFusedCost = 8.0;
+constexpr double kFuseMargin = 0.5;  // fuse only when it saves more than this
+
 }  // namespace
+
+// Precontracts runs of gates on two qubits into dense 4x4 blocks (KIND_F2), the GPU form of
+// the paper's precomputation of small contractions so that what is deployed are square
+// matrices of one size (Sec. 3).  Gates are scanned in time order; each qubit has at most one
+// open block (one qubit or two).  A one-qubit gate joins its qubit's block.  A two-qubit gate
+// joins the block of its pair, or merges two one-qubit blocks into a pair block; otherwise the
+// blocks of its qubits are closed, and it is emitted on its own if diagonal (it would only
+// couple two blocks) or starts a pair block.  A closed pair block becomes one KIND_F2 when its
+// gates cost more than a dense 4x4 (fuse_cost), else its gates are emitted as they are.
+// Emitting a block when it closes only moves gates past gates on other qubits, so the result
+// applies the same operator.
+tn_circuit fuse_pairs(const tn_circuit &c, std::vector<FusedMember> &fused) {
+  tn_circuit o;
+  o.n = c.n;
+  o.init = c.init;
+  o.n_params = c.n_params;
+  struct Block {
+    int qa = -1, qb = -1;  // qb < 0: one-qubit block
+    std::vector<int> gates;
+    double cost = 0.0;
+  };
+  std::vector<Block> blocks;
+  std::vector<int> open((size_t)c.n, -1);
+  auto member_of = [&](const TnGate &g, int qa) {
+    FusedMember m;
+    std::memset(&m, 0, sizeof(m));
+    m.kind = g.kind;
+    if (gate_nqubits(g.kind) == 1) m.role = g.q[0] == qa ? ROLE_A : ROLE_B;
+    else m.role = g.q[0] == qa ? ROLE_AB : ROLE_BA;
+    for (int a = 0; a < 3; ++a) {
+      m.angle[a] = g.angle[a];
+      m.pidx[a][0] = g.pidx[a][0];
+      m.pidx[a][1] = g.pidx[a][1];
+    }
+    for (int a = 0; a < 32; ++a) m.mat[a] = g.mat[a];
+    return m;
+  };
+  auto close = [&](int q) {
+    const int bi = open[(size_t)q];
+    if (bi < 0) return;
+    Block &b = blocks[(size_t)bi];
+    open[(size_t)b.qa] = -1;
+    if (b.qb >= 0) open[(size_t)b.qb] = -1;
+    if (b.qb >= 0 && b.cost > kFusedCost + kFuseMargin) {
+      TnGate f;
+      std::memset(&f, 0, sizeof(f));
+      f.kind = KIND_F2;
+      f.q[0] = b.qa;
+      f.q[1] = b.qb;
+      f.param_idx = -1;
+      for (int a = 0; a < 3; ++a) f.pidx[a][0] = f.pidx[a][1] = -1;
+      f.fuse_begin = (int)fused.size();
+      for (int gi : b.gates) fused.push_back(member_of(c.gates[(size_t)gi], b.qa));
+      f.fuse_count = (int)b.gates.size();
+      o.gates.push_back(f);
+    } else {
+      for (int gi : b.gates) o.gates.push_back(c.gates[(size_t)gi]);
+    }
+    b.gates.clear();
+  };
+  auto add = [&](int bi, int gi) {
+    blocks[(size_t)bi].gates.push_back(gi);
+    blocks[(size_t)bi].cost += fuse_cost(c.gates[(size_t)gi]);
+  };
+  for (int gi = 0; gi < (int)c.gates.size(); ++gi) {
+    const TnGate &g = c.gates[(size_t)gi];
+    if (gate_nqubits(g.kind) == 1) {
+      const int q = g.q[0];
+      int bi = open[(size_t)q];
+      if (bi >= 0 && (int)blocks[(size_t)bi].gates.size() >= kMaxFusedMembers) {
+        close(q);
+        bi = -1;
+      }
+      if (bi < 0) {
+        blocks.emplace_back();
+        bi = (int)blocks.size() - 1;
+        blocks[(size_t)bi].qa = q;
+        open[(size_t)q] = bi;
+      }
+      add(bi, gi);
+      continue;
+    }
+    const int a = g.q[0], b = g.q[1];
+    const int A = open[(size_t)a], B = open[(size_t)b];
+    if (A >= 0 && A == B && (int)blocks[(size_t)A].gates.size() < kMaxFusedMembers) {
+      add(A, gi);
+      continue;
+    }
+    const bool a_free = A < 0 || blocks[(size_t)A].qb < 0;
+    const bool b_free = B < 0 || blocks[(size_t)B].qb < 0;
+    const size_t na = A >= 0 ? blocks[(size_t)A].gates.size() : 0, nb = B >= 0 ? blocks[(size_t)B].gates.size() : 0;
+    if (A != B && a_free && b_free && (int)(na + nb) < kMaxFusedMembers) {
+      Block nbk;
+      nbk.qa = a;
+      nbk.qb = b;
+      for (int k : {A, B}) {
+        if (k < 0) continue;
+        for (int x : blocks[(size_t)k].gates) nbk.gates.push_back(x);
+        nbk.cost += blocks[(size_t)k].cost;
+        blocks[(size_t)k].gates.clear();
+      }
+      blocks.push_back(std::move(nbk));
+      const int bi = (int)blocks.size() - 1;
+      open[(size_t)a] = open[(size_t)b] = bi;
+      add(bi, gi);
+      continue;
+    }
+    close(a);
+    close(b);
+    if (is_diagonal_kind(g)) {
+      o.gates.push_back(g);
+      continue;
+    }
+    blocks.emplace_back();
+    const int bi = (int)blocks.size() - 1;
+    blocks[(size_t)bi].qa = a;
+    blocks[(size_t)bi].qb = b;
+    open[(size_t)a] = open[(size_t)b] = bi;
+    add(bi, gi);
+  }
+  for (int q = 0; q < c.n; ++q) close(q);
+  return o;
+}
 
 // Rewrites every U3(t, p, l) as P(p) V(t, l) (exact: U3 = P(p) RY(t) P(l)) and carries each
 // pending P(p) forward along its qubit while it commutes with what follows (diagonal gates,
@@ -155,7 +293,7 @@ bool is_diagonal_kind(const TnGate &g) {
 // V(t', l' + p).  A pending phase that meets anything else is emitted as a gate P(p) first;
 // the remaining ones are emitted at the end.  V costs 12 real multiply-adds per amplitude
 // pair instead of 16 for a general 2x2 matrix, because its first column is real.
-tn_circuit push_phases(const tn_circuit &c) {
+tn_circuit push_phases(const tn_circuit &c, std::vector<FusedMember> &fused) {
   tn_circuit o;
   o.n = c.n;
   o.init = c.init;
@@ -216,6 +354,28 @@ tn_circuit push_phases(const tn_circuit &c) {
       o.gates.push_back(g);
       continue;
     }
+    if (g.kind == KIND_F2 && (pend[(size_t)g.q[0]].on || pend[(size_t)g.q[1]].on)) {
+      // a fused block is a dense 4x4 anyway: the pending phases become its first members
+      TnGate f = g;
+      f.fuse_begin = (int)fused.size();
+      for (int r = 0; r < 2; ++r) {
+        Pending &pp = pend[(size_t)g.q[r]];
+        if (!pp.on) continue;
+        FusedMember m;
+        std::memset(&m, 0, sizeof(m));
+        m.kind = KIND_P;
+        m.role = r == 0 ? ROLE_A : ROLE_B;
+        for (int a = 0; a < 3; ++a) m.pidx[a][0] = m.pidx[a][1] = -1;
+        m.angle[0] = pp.val;
+        m.pidx[0][0] = pp.idx;
+        fused.push_back(m);
+        pp = Pending();
+      }
+      for (int k = 0; k < g.fuse_count; ++k) fused.push_back(fused[(size_t)(g.fuse_begin + k)]);
+      f.fuse_count = (int)fused.size() - f.fuse_begin;
+      o.gates.push_back(f);
+      continue;
+    }
     emit_p(g.q[0]);
     if (gate_nqubits(g.kind) == 2) emit_p(g.q[1]);
     o.gates.push_back(g);
@@ -255,6 +415,8 @@ tn_status build_pass_plan(const tn_circuit &c, int T, int K, bool adjoint, std::
       s.pidx[a][1] = g.pidx[a][1];
     }
     for (int a = 0; a < 32; ++a) s.fixed[a] = g.mat[a];
+    s.fuse_begin = g.fuse_begin;
+    s.fuse_count = g.fuse_count;
     int off = 0;
     if (!slots.empty()) {
       const MatSlot &l = slots.back();
@@ -425,6 +587,7 @@ tn_status build_pass_plan(const tn_circuit &c, int T, int K, bool adjoint, std::
         OpDesc op;
         std::memset(&op, 0, sizeof(op));
         op.type = (uint8_t)gc.type;
+        if (gc.shape == SHAPE_M4X) op.flags |= OPF_PACKED;
         src_of(gc.qa, op.a_kind, op.a_pos);
         if (gc.qb >= 0) src_of(gc.qb, op.b_kind, op.b_pos);
         op.mat = gc.shape >= 0 ? add_slot(g, adjoint ? FORM_ADJ : FORM_U, gc.shape) : 0;

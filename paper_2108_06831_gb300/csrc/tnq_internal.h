@@ -45,7 +45,10 @@ enum OpType : uint8_t {
   OP_DP = 6,  // phase e where bits a and b are both 1                  (1 entry)
 };
 enum SrcKind : uint8_t { SRC_REG = 0, SRC_TILE = 1, SRC_GLOB = 2 };
-enum OpFlags : uint8_t { OPF_FLUSH = 1 };
+enum OpFlags : uint8_t {
+  OPF_FLUSH = 1,   // apply the pending CZ signs first
+  OPF_PACKED = 2,  // OP_G2 entries in the packed layout of SHAPE_M4X
+};
 
 struct alignas(16) OpDesc {
   uint8_t type;
@@ -88,27 +91,60 @@ struct alignas(16) PassDesc {
 
 // How one entry range of a batch's matrix table is produced from the parameters.
 enum MatForm : int32_t { FORM_U = 0, FORM_ADJ = 1, FORM_D0 = 2, FORM_D1 = 3, FORM_D2 = 4 };
-// Entry layouts per op type: G1/C1 2x2 row-major, G2 4x4, D1 (d0, d1), DP (phase).
-enum MatShape : int32_t { SHAPE_M2 = 0, SHAPE_M4 = 1, SHAPE_DIAG2 = 2, SHAPE_PHASE = 3 };
+// Entry layouts per op type: G1/C1 2x2 row-major, G2 4x4, D1 (d0, d1), DP (phase).  SHAPE_M4X is
+// the 4x4 of a fused block laid out for packed FP32x2 arithmetic: entry k = (re, im) becomes the
+// four floats (re, re, -im, im), so that u * v = (re, re) * (v.re, v.im) + (-im, im) * (v.im, v.re)
+// reads both packed factors straight from one 16-byte load.
+enum MatShape : int32_t { SHAPE_M2 = 0, SHAPE_M4 = 1, SHAPE_DIAG2 = 2, SHAPE_PHASE = 3, SHAPE_M4X = 4 };
+
+// complex64 units a slot of the given shape occupies
+TNQ_HD int shape_units(int shape) {
+  switch (shape) {
+    case SHAPE_M2: return 4;
+    case SHAPE_M4: return 16;
+    case SHAPE_DIAG2: return 2;
+    case SHAPE_PHASE: return 1;
+    case SHAPE_M4X: return 32;
+  }
+  return 0;
+}
 
 struct alignas(16) MatSlot {
-  int32_t kind;       // tn_gate_kind or an internal kind (KIND_V, KIND_P)
+  int32_t kind;       // tn_gate_kind or an internal kind (KIND_V, KIND_P, KIND_F2)
   int32_t form;       // MatForm
   int32_t shape;      // MatShape
   int32_t offset;     // destination offset (complex64 units)
   int32_t pidx[3][2]; // angle a = angle[a] + sum of params[pidx[a][k]] over pidx >= 0
-  int32_t pad[2];
+  int32_t fuse_begin, fuse_count;  // KIND_F2: its member gates in the plan's FusedMember table
   double angle[3];
   double pad2;
   double fixed[32];   // MAT1/MAT2 entries (re, im)
 };
 
-// Internal gate kinds produced by the planner's phase-pushing rewrite (never in the ABI):
+// Internal gate kinds produced by the planner (never in the ABI):
 //   V(t, a) = RY(t) P(a) = [[cos t/2, -sin t/2 e^{ia}], [sin t/2, cos t/2 e^{ia}]]
 //   P(a)    = diag(1, e^{ia})
-// so that U3(t, p, l) = P(p) V(t, l).
+// so that U3(t, p, l) = P(p) V(t, l) (the phase-pushing rewrite); and
+//   F2      = the product of a run of gates on two qubits (a, b), precontracted into one 4x4
+//             matrix indexed 2 bit(a) + bit(b) (Sec. 3: small contractions computed ahead so
+//             that the tensors applied are square matrices of one size).  Its members are
+//             listed in the plan's FusedMember table; the product is formed per call from
+//             the parameters, in FP64.
 constexpr int KIND_V = 64;
 constexpr int KIND_P = 65;
+constexpr int KIND_F2 = 66;
+constexpr int kMaxFusedMembers = 24;  // gates precontracted into one F2 at most
+
+// One gate of a fused block: its kind, which of the block's qubits it acts on, its angles.
+enum FuseRole : int32_t { ROLE_A = 0, ROLE_B = 1, ROLE_AB = 2, ROLE_BA = 3 };
+struct alignas(16) FusedMember {
+  int32_t kind;        // tn_gate_kind, KIND_V or KIND_P
+  int32_t role;        // FuseRole: one-qubit on a / on b, two-qubit on (a, b) / on (b, a)
+  int32_t pidx[3][2];  // angle a = angle[a] + sum of params[pidx[a][k]] over pidx >= 0
+  double angle[3];
+  double pad;
+  double mat[32];      // MAT1 / MAT2 entries (re, im)
+};
 
 // ---------------------------------------------------------------------------------------
 // Gate matrices in double precision (shared by the plan-time host path and the per-call
@@ -120,7 +156,7 @@ TNQ_HD void cset(double *o, int i, double re, double im) { o[2 * i] = re; o[2 * 
 // (FORM_D0 + a).  Returns the dimension (2 or 4); 0 for an unknown kind.
 TNQ_HD int gate_nqubits(int kind) {
   return (kind == TN_GATE_CZ || kind == TN_GATE_CNOT || kind == TN_GATE_CP || kind == TN_GATE_SWAP ||
-          kind == TN_GATE_MAT2) ? 2 : 1;
+          kind == TN_GATE_MAT2 || kind == KIND_F2) ? 2 : 1;
 }
 
 TNQ_HD int gate_matrix(int kind, int form, const double *ang, const double *fixed, double *o) {
@@ -231,6 +267,67 @@ TNQ_HD int slot_entries(const MatSlot &s, const double *ang, double *tmp /*32*/,
   return 0;
 }
 
+
+// The 4x4 of a fused block (KIND_F2): the product of its member gates in order, FP64,
+// indexed 2 bit(a) + bit(b).  param_row: this batch element's parameters (may be NULL when
+// no member reads one).  Writes 16 (re, im) pairs to out.
+TNQ_HD void fused_matrix(const FusedMember *mem, int count, const double *param_row, double *out /*32*/) {
+  for (int i = 0; i < 32; ++i) out[i] = 0.0;
+  for (int i = 0; i < 4; ++i) out[2 * (5 * i)] = 1.0;
+  double g[32], e[32], r[32];
+  for (int m = 0; m < count; ++m) {
+    const FusedMember &f = mem[m];
+    double ang[3] = {f.angle[0], f.angle[1], f.angle[2]};
+    for (int a = 0; a < 3; ++a)
+      for (int k = 0; k < 2; ++k)
+        if (f.pidx[a][k] >= 0 && param_row) ang[a] += param_row[f.pidx[a][k]];
+    const int dim = gate_matrix(f.kind, FORM_U, ang, f.mat, g);
+    // embed the member as a 4x4 on (a, b)
+    for (int i = 0; i < 32; ++i) e[i] = 0.0;
+    for (int i = 0; i < 4; ++i)
+      for (int j = 0; j < 4; ++j) {
+        const int ia = i >> 1, ib = i & 1, ja = j >> 1, jb = j & 1;
+        double re = 0.0, im = 0.0;
+        if (dim == 2) {
+          if (f.role == ROLE_A && ib == jb) { re = g[2 * (2 * ia + ja)]; im = g[2 * (2 * ia + ja) + 1]; }
+          if (f.role == ROLE_B && ia == ja) { re = g[2 * (2 * ib + jb)]; im = g[2 * (2 * ib + jb) + 1]; }
+        } else {
+          // ROLE_BA: the member's first qubit is b, so its index is 2 bit(b) + bit(a)
+          const int ii = f.role == ROLE_AB ? i : 2 * ib + ia, jj = f.role == ROLE_AB ? j : 2 * jb + ja;
+          re = g[2 * (4 * ii + jj)];
+          im = g[2 * (4 * ii + jj) + 1];
+        }
+        e[2 * (4 * i + j)] = re;
+        e[2 * (4 * i + j) + 1] = im;
+      }
+    // out <- e * out
+    for (int i = 0; i < 4; ++i)
+      for (int j = 0; j < 4; ++j) {
+        double re = 0.0, im = 0.0;
+        for (int k = 0; k < 4; ++k) {
+          const double xr = e[2 * (4 * i + k)], xi = e[2 * (4 * i + k) + 1];
+          const double yr = out[2 * (4 * k + j)], yi = out[2 * (4 * k + j) + 1];
+          re += xr * yr - xi * yi;
+          im += xr * yi + xi * yr;
+        }
+        r[2 * (4 * i + j)] = re;
+        r[2 * (4 * i + j) + 1] = im;
+      }
+    for (int i = 0; i < 32; ++i) out[i] = r[i];
+  }
+}
+
+// The SHAPE_M4X entries of a fused 4x4 m (16 (re, im) pairs): (re, re, -im, im) per entry.
+TNQ_HD void packed_m4x(const double *m, float *dst /*64 floats*/) {
+  for (int k = 0; k < 16; ++k) {
+    const float re = (float)m[2 * k], im = (float)m[2 * k + 1];
+    dst[4 * k] = re;
+    dst[4 * k + 1] = re;
+    dst[4 * k + 2] = -im;
+    dst[4 * k + 3] = im;
+  }
+}
+
 }  // namespace tnq
 
 // ---------------------------------------------------------------------------------------
@@ -243,6 +340,7 @@ struct TnGate {
   int pidx[3][2];  // angle a = angle[a] + sum of params[pidx[a][k]] over pidx >= 0
   double angle[3];
   double mat[32];
+  int fuse_begin, fuse_count;  // KIND_F2: members in the plan's FusedMember table (else 0, 0)
 };
 
 struct tn_circuit {
@@ -278,8 +376,13 @@ struct Q428Gate {
 };
 }  // namespace tnq
 
+namespace tnq {
+struct BlockPlan;
+}
+
 struct tn_plan {
   tnq::NetPlan *net = nullptr;  // TN_PLAN_NETWORK plans: pairwise network contraction
+  tnq::BlockPlan *blocks = nullptr;  // TN_PLAN_BLOCKS plans: uniform square blocks
   std::vector<tnq::Q428Gate> *q428 = nullptr;  // TN_PLAN_Q428 plans: quantised gate list
   int n;
   long long n_gates;
@@ -291,11 +394,14 @@ struct tn_plan {
   bool host_only;
   int device;
   std::vector<tnq::MatSlot> slots;  // forward + adjoint + derivative entries
+  std::vector<tnq::FusedMember> fused;  // members of the forward plan's F2 gates
+  int n_fused = 0;                      // F2 gates in the forward plan
   int mstride;                      // complex64 entries per batch element's matrix table
   bool param_dependent;
   PassPlan fwd, bwd;
   // device copies (NULL when host_only)
   tnq::MatSlot *d_slots = nullptr;
+  tnq::FusedMember *d_fused = nullptr;
   tnq::PassDesc *d_fwd_pass = nullptr, *d_bwd_pass = nullptr;
   tnq::PhaseDesc *d_fwd_phase = nullptr, *d_bwd_phase = nullptr;
   tnq::OpDesc *d_fwd_ops = nullptr, *d_bwd_ops = nullptr;
@@ -352,5 +458,6 @@ void set_error(const char *fmt, ...);
 tn_status cuda_fail(cudaError_t e, const char *what);
 tn_status build_pass_plan(const tn_circuit &c, int T, int K, bool adjoint, std::vector<MatSlot> &slots,
                           PassPlan &out, std::string &err);
-tn_circuit push_phases(const tn_circuit &c);
+tn_circuit push_phases(const tn_circuit &c, std::vector<FusedMember> &fused);
+tn_circuit fuse_pairs(const tn_circuit &c, std::vector<FusedMember> &fused);
 }  // namespace tnq

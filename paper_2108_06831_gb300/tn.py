@@ -27,6 +27,8 @@ PLAN_HOST_ONLY = 1
 PLAN_NO_SPECIALIZE = 2
 PLAN_NETWORK = 4
 PLAN_Q428 = 8
+PLAN_NO_FUSION = 16
+PLAN_BLOCKS = 32
 
 GATE_KINDS = {name: i for i, name in enumerate(
     ["H", "X", "Y", "Z", "S", "SDG", "T", "TDG", "SX", "SY", "SW", "RX", "RY", "RZ", "U3",
@@ -43,7 +45,8 @@ class TnPlanOpts(C.Structure):
     _fields_ = [("target", C.c_int32), ("precision", C.c_int32), ("batch", C.c_int32),
                 ("tile_qubits", C.c_int32), ("max_intermediate_log2", C.c_int32), ("flags", C.c_int32),
                 ("seed", C.c_uint64), ("amp_batch", C.c_int64), ("order_trials", C.c_int64),
-                ("order_search", C.c_int64), ("reserved", C.c_int64 * 3)]
+                ("order_search", C.c_int64), ("block_qubits", C.c_int64),
+                ("reserved", C.c_int64 * 2)]
 
 
 class TnPlanStats(C.Structure):
@@ -54,7 +57,7 @@ class TnPlanStats(C.Structure):
                 ("net_merges", C.c_int32), ("net_max_log2", C.c_int32), ("net_tensor_merges", C.c_int32),
                 ("net_folded_merges", C.c_int32), ("bwd_flops", C.c_double),
                 ("net_sliced", C.c_int32), ("net_batch_log2", C.c_int32), ("net_cost", C.c_double),
-                ("net_bytes", C.c_double)]
+                ("net_bytes", C.c_double), ("n_fused", C.c_int32), ("reserved_stats", C.c_int32)]
 
 
 class TnTuneOpts(C.Structure):
@@ -182,14 +185,16 @@ class CircuitHandle:
 class Plan:
     def __init__(self, ch: CircuitHandle, target: int = TARGET_STATE, precision: int = PREC_FP32, batch: int = 1,
                  tile_qubits: int = 0, host_only: bool = False, specialize: bool = True, network_bitstrings: int = 0,
-                 max_intermediate_log2: int = 0, order_trials: int = 0, q428: bool = False, order_search: int = 0):
+                 max_intermediate_log2: int = 0, order_trials: int = 0, q428: bool = False, order_search: int = 0,
+                 fuse: bool = True, block_qubits: int = 0):
         o = TnPlanOpts()
         o.order_trials = order_trials
         o.order_search = order_search
         o.target, o.precision, o.batch, o.tile_qubits = target, precision, batch, tile_qubits
         o.max_intermediate_log2 = max_intermediate_log2
         o.flags = (PLAN_HOST_ONLY if host_only else 0) | (0 if specialize else PLAN_NO_SPECIALIZE) | \
-            (PLAN_Q428 if q428 else 0)
+            (PLAN_Q428 if q428 else 0) | (0 if fuse else PLAN_NO_FUSION) | (PLAN_BLOCKS if block_qubits else 0)
+        o.block_qubits = block_qubits
         if network_bitstrings:
             o.flags |= PLAN_NETWORK
             o.amp_batch = network_bitstrings
@@ -205,7 +210,7 @@ class Plan:
     def stats(self) -> dict:
         s = TnPlanStats()
         _check(_lib.tn_plan_get_stats(self._h, C.byref(s)), "tn_plan_get_stats")
-        return {f: getattr(s, f) for f, _ in TnPlanStats._fields_ if f != "reserved"}
+        return {f: getattr(s, f) for f, _ in TnPlanStats._fields_ if not f.startswith("reserved")}
 
     def __del__(self):
         if getattr(self, "_h", None):
@@ -391,13 +396,15 @@ class Contractor:
     """Plan + workspace for repeated contractions of one circuit (device memory from torch)."""
 
     def __init__(self, circ: Circuit, target: int = TARGET_STATE, batch: int = 1, tile_qubits: int = 0,
-                 precision: int = PREC_FP32, device=None, specialize: bool = True):
+                 precision: int = PREC_FP32, device=None, specialize: bool = True, fuse: bool = True,
+                 block_qubits: int = 0):
         torch = _torch()
         self.device = torch.device(device or "cuda")
         with torch.cuda.device(self.device):
             self.circuit_handle = CircuitHandle(circ)
             self.plan = Plan(self.circuit_handle, target=target, precision=precision, batch=batch,
-                             tile_qubits=tile_qubits, specialize=specialize)
+                             tile_qubits=tile_qubits, specialize=specialize, fuse=fuse,
+                             block_qubits=block_qubits)
         self.n_qubits, self.batch, self.n_params = circ.n_qubits, batch, self.plan.n_params
         nb = max(self.plan.workspace_bytes, 16)
         self.workspace = torch.empty(nb, dtype=torch.uint8, device=self.device)

@@ -50,16 +50,24 @@ def test_host_only_plans():
     tn = _tn()
     c, _ = C.brickwork(24, 20, 1001)
     ch = tn.CircuitHandle(c)
+    n_u3 = sum(1 for g in c.gates if g.kind == "U3")
+    n_cz = sum(1 for g in c.gates if g.kind == "CZ")
     for T in (8, 10, 12, 13):
-        s = tn.Plan(ch, tile_qubits=T, host_only=True).stats()
+        s = tn.Plan(ch, tile_qubits=T, host_only=True, fuse=False).stats()
         # every U3 becomes V = RY P (the pushed phase P(phi) merges into the qubit's next V),
         # so the plan holds every gate once plus one final phase gate per qubit
-        assert s["n_ops"] == len(c.gates) + 24
+        assert s["n_ops"] == len(c.gates) + 24 and s["n_fused"] == 0
         assert s["tile_qubits"] == T and s["reg_qubits"] == 4
         assert s["n_passes"] >= 2
         # flops as executed: V costs 10 real flops per amplitude, a final phase 3, CZ none
-        n_u3 = sum(1 for g in c.gates if g.kind == "U3")
         assert s["flops"] == pytest.approx((10.0 * n_u3 + 3.0 * 24) * (1 << 24))
+        # precontracted: each even-layer CZ pair with the U3s of its two qubits in that layer and
+        # the next becomes one dense 4x4 (12 per two layers); the odd-layer CZs stay
+        f = tn.Plan(ch, tile_qubits=T, host_only=True).stats()
+        assert f["n_fused"] == 12 * 10
+        assert f["n_ops"] == 120 + (n_cz - 120)
+        assert f["flops"] == pytest.approx(30.0 * 120 * (1 << 24))
+        assert f["n_phases"] < s["n_phases"]
     small = tn.Plan(tn.CircuitHandle(C.brickwork(10, 8, 1000)[0]), host_only=True).stats()
     assert small["tile_qubits"] == 10 and small["n_passes"] <= 2  # one tile; code budget may split it
 
@@ -75,6 +83,28 @@ def test_plan_option_validation():
         tn.Plan(ch, batch=-1, host_only=True)
     p = tn.Plan(ch, target=tn.TARGET_EXPECTATION, batch=4, host_only=True)
     assert p.workspace_bytes >= 2 * 4 * 8 * 32
+
+
+def test_block_plans_host_only():
+    """Uniform square blocks (TN_PLAN_BLOCKS): the 24-qubit brickwork cut into blocks of 6 and 7
+    qubits (windows at alternating offsets take their light cones), one GEMM launch per block
+    after the first, and the options the mode rejects."""
+    tn = _tn()
+    ch = tn.CircuitHandle(C.brickwork(24, 20, 1001, parameterized=True)[0])
+    for k, most in ((6, 30), (7, 26)):
+        s = tn.Plan(ch, host_only=True, block_qubits=k, precision=tn.PREC_3XTF32).stats()
+        assert s["tile_qubits"] == k and 2 <= s["n_fused"] <= most
+        assert s["n_passes"] == s["n_fused"] - 1
+        assert s["flops"] == pytest.approx(8.0 * (1 << (24 - k)) * (1 << k) ** 2 * s["n_passes"])
+    small = tn.CircuitHandle(C.brickwork(12, 4, 1)[0])
+    with pytest.raises(tn.TnError):  # fewer than k + 7 qubits
+        tn.Plan(small, host_only=True, block_qubits=6)
+    with pytest.raises(tn.TnError):
+        tn.Plan(ch, host_only=True, block_qubits=5)
+    with pytest.raises(tn.TnError):
+        tn.Plan(ch, host_only=True, block_qubits=6, batch=3)
+    with pytest.raises(tn.TnError):
+        tn.Plan(ch, host_only=True, block_qubits=6, target=tn.TARGET_EXPECTATION)
 
 
 def test_network_plan_6x6_grid_host_only():
