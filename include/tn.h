@@ -174,7 +174,7 @@ typedef struct {
                              bitstrings runs in passes of 2^net_batch_log2 (fewer than amp_batch when that
                              is the cheaper way to keep intermediates within max_intermediate_log2) */
   double net_cost;      /* TN_PLAN_NETWORK: the planner's cost of one call of amp_batch bitstrings, in bytes:
-                           sum over launched merges (all slices and passes) of a fixed 2e7 per launch plus
+                           sum over launched merges (all slices and passes) of a fixed 6e7 per launch plus
                            max(bytes read and written, complex flops / 32) */
   double net_bytes;     /* TN_PLAN_NETWORK: algorithmic HBM bytes of one call of amp_batch bitstrings: every
                            launched merge's operands read and result written once (complex64) */

@@ -299,7 +299,7 @@ tn_status tn_plan_contraction(const tn_circuit *c, const tn_plan_opts *opts, tn_
         s2 = TN_ERR_CUDA;
       }
     }
-    if (s2 == TN_OK) s2 = upload_blocks(*p->blocks, p->host_only, err);
+    if (s2 == TN_OK) s2 = upload_blocks(*p->blocks, p->host_only, c->n_params > 0, err);
     if (s2 != TN_OK) {
       set_error("block plan: %s", err.c_str());
       delete p->blocks;

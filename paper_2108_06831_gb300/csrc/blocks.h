@@ -53,11 +53,14 @@ struct BlockPlan {
   BlockGate *d_gates = nullptr;
   int *d_meta = nullptr;                 // per block: gate_begin, gate_count
   long long *d_init_pos = nullptr;
+  float2 *d_fixed_mats = nullptr;        // fixed-angle circuits: the block matrices, built once
 };
 
 tn_status plan_blocks(const tn_circuit &c, int k, int batch, int precision, BlockPlan &bp, std::string &err);
-// Workspace layout; device tables unless host_only.
-tn_status upload_blocks(BlockPlan &bp, bool host_only, std::string &err);
+// Workspace layout; device tables unless host_only (and, for fixed angles, the block matrices).
+tn_status upload_blocks(BlockPlan &bp, bool host_only, bool param_dependent, std::string &err);
+// The block matrices for every batch element (FP64 product of each block's gates, stored complex64).
+cudaError_t build_block_mats(const BlockPlan &bp, const double *params, int n_params, float2 *mats, cudaStream_t s);
 // state <- the circuit applied to |init> (batch elements back to back, canonical layout).
 cudaError_t run_blocks(const BlockPlan &bp, const double *params, int n_params, float2 *state, void *ws,
                        cudaStream_t s);

@@ -43,11 +43,12 @@ struct NetLaunch {
 constexpr int kFoldMaxLog2 = 20;       // largest folded result: 2^20 entries
 constexpr double kFoldMaxWork = 2e8;   // complex multiply-adds over all folded merges (all slices)
 
-// Order cost of a launched merge: kLaunchBytes (a launch and a short kernel, ~3 us of HBM time)
+// Order cost of a launched merge: kLaunchBytes (a launch and a short kernel: ~9 us measured per
+// launch on sliced and small-merge plans, i.e. 6e7 bytes of HBM time at ~6.7 TB/s)
 // + max(bytes read and written, complex flops / kRidge): merges are HBM-bound unless their
 // arithmetic intensity exceeds kRidge.
 constexpr double kRidge = 32.0;
-constexpr double kLaunchBytes = 2e7;
+constexpr double kLaunchBytes = 6e7;
 
 // Slicing: at most 2^16 slices; the constant table of all slices at most 2^27 entries.
 constexpr int kMaxSliceBits = 16;
