@@ -174,7 +174,7 @@ typedef struct {
                              bitstrings runs in passes of 2^net_batch_log2 (fewer than amp_batch when that
                              is the cheaper way to keep intermediates within max_intermediate_log2) */
   double net_cost;      /* TN_PLAN_NETWORK: the planner's cost of one call of amp_batch bitstrings, in bytes:
-                           sum over launched merges (all slices and passes) of a fixed 6e7 per launch plus
+                           sum over launched merges (all slices and passes) of a fixed 2e7 per launch plus
                            max(bytes read and written, complex flops / 32) */
   double net_bytes;     /* TN_PLAN_NETWORK: algorithmic HBM bytes of one call of amp_batch bitstrings: every
                            launched merge's operands read and result written once (complex64) */
@@ -327,9 +327,9 @@ tn_status tn_cgemm_batched(int32_t precision, int64_t batch, int64_t M, int64_t 
  * ------------------------------------------------------------------------------------- */
 typedef struct tn_batch tn_batch; /* opaque, library-owned, holds device tables */
 
-/* Group plans (fixed-angle circuits, batch 1, TN_TARGET_STATE or any target, tile qubits in
- * [6, 12]) for one launch.  The plans must outlive the batch.  TN_ERR_UNSUPPORTED for plans
- * with parameters or batch > 1. */
+/* Group plans (batch 1, any target, tile qubits in [6, 12]) for one launch.  The plans must
+ * outlive the batch.  TN_ERR_UNSUPPORTED for plans of batch > 1.  Plans of circuits that read
+ * parameters are allowed: their gate tables are built in the run (tn_batch_run_params). */
 tn_status tn_batch_build(const tn_plan *const *plans, int32_t n_plans, tn_batch **out);
 /* complex64 entries of the output buffer (all states, each 16-byte aligned) and workspace bytes. */
 tn_status tn_batch_sizes(const tn_batch *b, int64_t *state_elems, size_t *workspace_bytes);
@@ -339,6 +339,17 @@ tn_status tn_batch_state_offsets(const tn_batch *b, int64_t *offsets);
  * workspace (its counters) and one kernel launch on s; capturable in a CUDA graph.  A wait that
  * runs out (about 2 s) is reported by tn_sync_status as TN_ERR_TIMEOUT. */
 tn_status tn_batch_run(const tn_batch *b, void *states_dev, void *workspace_dev, tn_stream_t s);
+/* As tn_batch_run, for batches with parameterised circuits (spec: many parameter sets in
+ * one persistent launch; Sec. 2.2.3: the order is fixed ahead of the values).  params_dev
+ * (device, float64) holds every circuit's parameters back to back, circuit i's first at
+ * param_offsets[i] of tn_batch_params; NULL allowed when no circuit reads any.  Enqueues one
+ * memset, one kernel that builds all parameterised circuits' gate tables into the workspace
+ * (FP64 angles, complex64 entries), and the persistent launch; capturable in a CUDA graph. */
+tn_status tn_batch_run_params(const tn_batch *b, const double *params_dev, void *states_dev, void *workspace_dev,
+                              tn_stream_t s);
+/* *n_params = parameters of all circuits together; param_offsets (optional, one per circuit)
+ * receives each circuit's first parameter in params_dev. */
+tn_status tn_batch_params(const tn_batch *b, int32_t *n_params, int64_t *param_offsets);
 void tn_free_batch(tn_batch *b);
 /* Testing aid for the failure path (the paper has no counterpart).  Makes the tiles of work-list
  * pass `pass` (1 <= pass < that circuit's passes in the batch; a circuit that fits one tile has

@@ -419,6 +419,15 @@ tn_status tn_plan_contraction(const tn_circuit *c, const tn_plan_opts *opts, tn_
       for (size_t i = 0; i < kinds.size(); ++i) kinds[i] = fwd_circ.gates[(size_t)p->fwd.op_gate[i]].kind;
       std::string jerr;
       u = jit_build(*p, kinds, false, false, jerr);
+      if (u == TN_OK && !p->param_dependent && p->d_fixed_mats) {
+        // fixed angles: each pass's constant table is filled once
+        for (size_t i = 0; i < p->jit_cm_ptr.size() && u == TN_OK; ++i)
+          if (p->jit_cm_ptr[i] && p->jit_cm_bytes[i]) {
+            cudaError_t e = cudaMemcpy(p->jit_cm_ptr[i], p->d_fixed_mats + 2 * (size_t)p->fwd.passes[i].mat_begin,
+                                       p->jit_cm_bytes[i], cudaMemcpyDeviceToDevice);
+            if (e != cudaSuccess) u = cuda_fail(e, "generated kernels' matrix tables");
+          }
+      }
       if (u == TN_OK && jit_bwd_supported(*p)) {
         std::vector<int> bk(p->bwd.ops.size());
         for (size_t i = 0; i < bk.size(); ++i) bk[i] = c->gates[(size_t)p->bwd.op_gate[i]].kind;
@@ -894,12 +903,29 @@ tn_status tn_batch_state_offsets(const tn_batch *b, int64_t *offsets) {
 }
 
 tn_status tn_batch_run(const tn_batch *b, void *states_dev, void *workspace_dev, tn_stream_t s) {
+  TN_CHECK_ARG(b != nullptr, "NULL argument");
+  TN_CHECK_ARG(batch_num_params(b, nullptr) == 0,
+               "the batch has parameterised circuits (%d parameters): use tn_batch_run_params",
+               batch_num_params(b, nullptr));
+  return tn_batch_run_params(b, nullptr, states_dev, workspace_dev, s);
+}
+
+tn_status tn_batch_run_params(const tn_batch *b, const double *params_dev, void *states_dev, void *workspace_dev,
+                              tn_stream_t s) {
   TN_CHECK_ARG(b != nullptr && states_dev != nullptr && workspace_dev != nullptr, "NULL argument");
   TN_CHECK_ARG(((uintptr_t)states_dev & 15) == 0, "states_dev must be 16-byte aligned");
+  TN_CHECK_ARG(batch_num_params(b, nullptr) == 0 || params_dev != nullptr,
+               "the batch's circuits read %d parameters: params_dev must not be NULL", batch_num_params(b, nullptr));
   tn_status st = check_device(batch_device(b));
   if (st != TN_OK) return st;
-  TN_CUDA(batch_run(b, static_cast<float2 *>(states_dev), workspace_dev, reinterpret_cast<cudaStream_t>(s)),
+  TN_CUDA(batch_run(b, params_dev, static_cast<float2 *>(states_dev), workspace_dev, reinterpret_cast<cudaStream_t>(s)),
           "batched executor");
+  return TN_OK;
+}
+
+tn_status tn_batch_params(const tn_batch *b, int32_t *n_params, int64_t *param_offsets) {
+  TN_CHECK_ARG(b != nullptr && n_params != nullptr, "NULL argument");
+  *n_params = batch_num_params(b, reinterpret_cast<long long *>(param_offsets));
   return TN_OK;
 }
 

@@ -110,7 +110,7 @@ tn_status batch_build_tuned(const tn_circuit *const *circuits, int n, const tn_t
     float best = 1e30f;
     for (int r = 0; e == cudaSuccess && r <= reps; ++r) {  // launch 0 warms up
       e = cudaEventRecord(e0, s);
-      if (e == cudaSuccess) e = batch_run(b, static_cast<float2 *>(states.p), ws.p, s);
+      if (e == cudaSuccess) e = batch_run(b, nullptr, static_cast<float2 *>(states.p), ws.p, s);
       if (e == cudaSuccess) e = cudaEventRecord(e1, s);
       if (e == cudaSuccess) e = cudaEventSynchronize(e1);
       float t = 0.f;

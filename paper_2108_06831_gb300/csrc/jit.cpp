@@ -318,6 +318,18 @@ void emit_op(Emitter &E, const OpDesc &op, int kind) {
   }
 }
 
+}  // namespace
+
+// Forward pass kernels read their matrix entries from a per-pass __constant__ table when one
+// table serves every tile: fixed angles (one table for all batch elements) or batch 1.
+bool jit_const_mats(const tn_plan &p) {
+  if (const char *e = getenv("TNQ_JIT_CONST"))
+    if (atoi(e) == 0) return false;
+  return !p.param_dependent || p.batch == 1;
+}
+
+namespace {
+
 std::string gen_pass(const tn_plan &p, int pi, const std::vector<int> &op_kind, int *threads_out, size_t *smem_out) {
   const PassDesc &pd = p.fwd.passes[pi];
   const int T = pd.T, K = pd.K, L = T < kLowBits ? T : kLowBits;
@@ -329,9 +341,18 @@ std::string gen_pass(const tn_plan &p, int pi, const std::vector<int> &op_kind, 
   E.K = K;
   E.R = 1 << K;
   char buf[512];
+  // Matrix entries: in a __constant__ table of this pass's module when every batch element reads
+  // the same table (fixed angles) or there is one (batch 1): warp-uniform operands from the
+  // constant cache, no shared-memory copy and no registers to hold them.  Otherwise staged in
+  // shared memory per batch element.
+  const bool cmem = jit_const_mats(p);
   // resident CTAs per SM requested from the register allocator (TNQ_JIT_MIN_BLOCKS, default 2)
   int min_blocks = 2;
   if (const char *mb = getenv("TNQ_JIT_MIN_BLOCKS")) min_blocks = std::max(1, std::min(4, atoi(mb)));
+  if (cmem) {
+    snprintf(buf, sizeof buf, "__constant__ float4 tnq_cm%d[%d];", pi, std::max(1, mat_n / 2));
+    E.line(buf);
+  }
   snprintf(buf, sizeof buf,
            "extern \"C\" __global__ void __launch_bounds__(%d, %d) tnq_p%d(const float2 *__restrict__ mats_g, long long mstride, "
            "float2 *__restrict__ state, long long work, u64 init_basis) {",
@@ -342,8 +363,10 @@ std::string gen_pass(const tn_plan &p, int pi, const std::vector<int> &op_kind, 
   E.line("  float2 *const sm0 = reinterpret_cast<float2 *>(smraw);");
   snprintf(buf, sizeof buf, "  float2 *const sm1 = sm0 + %d;", (nbuf - 1) * TILE);
   E.line(buf);
-  snprintf(buf, sizeof buf, "  float4 *smat = reinterpret_cast<float4 *>(sm0 + %d);", nbuf * TILE);
-  E.line(buf);
+  if (!cmem) {
+    snprintf(buf, sizeof buf, "  float4 *smat = reinterpret_cast<float4 *>(sm0 + %d);", nbuf * TILE);
+    E.line(buf);
+  }
   E.line("  const int tid = threadIdx.x;");
   // per-thread part of the load/store deposit: tile index i = 2*tid + 2*k*NTHR
   {
@@ -411,18 +434,23 @@ std::string gen_pass(const tn_plan &p, int pi, const std::vector<int> &op_kind, 
   }
   snprintf(buf, sizeof buf, "    float2 *st = state + (b << %d);", N);
   E.line(buf);
-  // stage this batch element's matrix entries
-  E.line("    if (b != cur_b) {");
-  snprintf(buf, sizeof buf,
-           "      const float4 *src = reinterpret_cast<const float4 *>(mats_g + b * mstride + %d);", pd.mat_begin);
-  E.line(buf);
-  snprintf(buf, sizeof buf, "      for (int i = tid; i < %d; i += %d) smat[i] = src[i];", mat_n / 2, NTHR);
-  E.line(buf);
-  E.line("      cur_b = b;");
-  E.line("      __syncthreads();");
-  E.line("    }");
-  snprintf(buf, sizeof buf, "    const float4 *M4 = smat - %d;", pd.mat_begin / 2);
-  E.line(buf);
+  if (cmem) {
+    snprintf(buf, sizeof buf, "    const float4 *M4 = tnq_cm%d - %d;", pi, pd.mat_begin / 2);
+    E.line(buf);
+  } else {
+    // stage this batch element's matrix entries
+    E.line("    if (b != cur_b) {");
+    snprintf(buf, sizeof buf,
+             "      const float4 *src = reinterpret_cast<const float4 *>(mats_g + b * mstride + %d);", pd.mat_begin);
+    E.line(buf);
+    snprintf(buf, sizeof buf, "      for (int i = tid; i < %d; i += %d) smat[i] = src[i];", mat_n / 2, NTHR);
+    E.line(buf);
+    E.line("      cur_b = b;");
+    E.line("      __syncthreads();");
+    E.line("    }");
+    snprintf(buf, sizeof buf, "    const float4 *M4 = smat - %d;", pd.mat_begin / 2);
+    E.line(buf);
+  }
   // synthesise the first pass's tile (loaded passes were filled by cp.async above)
   if (pd.init_mode) {
     snprintf(buf, sizeof buf, "    for (int i = tid; i < %d; i += %d) sm[i] = make_float2(0.f, 0.f);", TILE, NTHR);
@@ -490,13 +518,58 @@ std::string gen_pass(const tn_plan &p, int pi, const std::vector<int> &op_kind, 
   if (!pd.init_mode) E.line("  asm volatile(\"cp.async.wait_group 0;\" ::: \"memory\");");
   E.line("}");
   *threads_out = NTHR;
-  *smem_out = (size_t)nbuf * TILE * 8 + (size_t)mat_n * 8;
+  *smem_out = (size_t)nbuf * TILE * 8 + (cmem ? 0 : (size_t)mat_n * 8);
   return E.o.str();
 }
 
 
 // Derivative dot 2 Re <lambda| D |psi> of one parameter of an op, reduced over the warp and
 // added to the pass's accumulation slot.  D has the structure of the gate kind.
+// Parameter derivative of a Pauli rotation U = exp(-i t P / 2) (RX, RY, RZ): dU/dt = (-i/2) P U, so
+// 2 Re <lambda_k| dU psi_{k-1}> = Im <lambda_k| P |psi_k>, evaluated from the tiles before U is
+// undone (no derivative matrix applied): 2 multiply-adds per amplitude instead of a gate
+// application and a dot.
+bool pauli_rotation(int kind) { return kind == TN_GATE_RX || kind == TN_GATE_RY || kind == TN_GATE_RZ; }
+
+void emit_grad_pauli(Emitter &E, const OpDesc &op, int kind, const GradRec &gr, int nwarps) {
+  const int R = E.R;
+  char buf[320];
+  E.line("{ float acc = 0.f;");
+  if (kind == TN_GATE_RZ) {  // Im <l|Z|a> = sum_j (-1)^{bit_j} (l.x a.y - l.y a.x)
+    const bool reg = op.a_kind == SRC_REG;
+    for (int j = 0; j < R; ++j) {
+      const bool neg = reg && (j & (1 << op.a_pos));
+      snprintf(buf, sizeof buf, "  acc = fmaf(%sl[%d].x, a[%d].y, acc); acc = fmaf(%sl[%d].y, a[%d].x, acc);",
+               neg ? "-" : "", j, j, neg ? "" : "-", j, j);
+      E.line(buf);
+    }
+    if (!reg) E.line("  if (" + cond_expr(op.a_kind, op.a_pos) + ") acc = -acc;");
+  } else {
+    const int r = op.a_pos;  // X or Y on register bit r: pairs (x = a[j], y = a[j1])
+    for (int j = 0; j < R; ++j) {
+      if (j & (1 << r)) continue;
+      const int j1 = j | (1 << r);
+      if (kind == TN_GATE_RY)  // Im: (ly . x) - (lx . y), dot = re re + im im
+        snprintf(buf, sizeof buf,
+                 "  acc = fmaf(l[%d].x, a[%d].x, acc); acc = fmaf(l[%d].y, a[%d].y, acc); "
+                 "acc = fmaf(-l[%d].x, a[%d].x, acc); acc = fmaf(-l[%d].y, a[%d].y, acc);",
+                 j1, j, j1, j, j, j1, j, j1);
+      else  // RX: Im(conj(lx) y) + Im(conj(ly) x)
+        snprintf(buf, sizeof buf,
+                 "  acc = fmaf(l[%d].x, a[%d].y, acc); acc = fmaf(-l[%d].y, a[%d].x, acc); "
+                 "acc = fmaf(l[%d].x, a[%d].y, acc); acc = fmaf(-l[%d].y, a[%d].x, acc);",
+                 j, j1, j, j1, j1, j, j1, j);
+      E.line(buf);
+    }
+  }
+  E.line("  acc += __shfl_xor_sync(0xFFFFFFFFu, acc, 16); acc += __shfl_xor_sync(0xFFFFFFFFu, acc, 8);");
+  E.line("  acc += __shfl_xor_sync(0xFFFFFFFFu, acc, 4); acc += __shfl_xor_sync(0xFFFFFFFFu, acc, 2);");
+  E.line("  acc += __shfl_xor_sync(0xFFFFFFFFu, acc, 1);");
+  snprintf(buf, sizeof buf, "  if (lane == 0) wacc[%d + warp] += acc;", gr.slot * nwarps);
+  E.line(buf);
+  E.line("}");
+}
+
 void emit_grad(Emitter &E, const OpDesc &op, int kind, const GradRec &gr, int nwarps) {
   const int R = E.R;
   char buf[320];
@@ -730,8 +803,11 @@ std::string gen_bwd_pass(const tn_plan &p, int pi, const std::vector<int> &op_ki
       tmp.R = E.R;
       emit_op(tmp, op, op_kind[o]);
       const std::string code_a = tmp.o.str();
+      const bool pauli = op.has_grad && pauli_rotation(op_kind[o]);
+      if (pauli)  // from psi_k, lambda_k
+        for (int g = 0; g < op.n_grad; ++g) emit_grad_pauli(E, op, op_kind[o], p.bwd.grads[(size_t)(op.aux + g)], NW);
       E.o << code_a;  // psi_{k-1} = U^dag psi_k
-      if (op.has_grad)
+      if (op.has_grad && !pauli)
         for (int g = 0; g < op.n_grad; ++g) emit_grad(E, op, op_kind[o], p.bwd.grads[(size_t)(op.aux + g)], NW);
       E.o << rename_array(code_a, "l");  // lambda_{k-1} = U^dag lambda_k
     }
@@ -942,10 +1018,30 @@ tn_status jit_build(tn_plan &p, const std::vector<int> &op_kind, bool backward, 
     }
     kers[i] = k;
   }
+  if (!backward) {
+    p.jit_cm_ptr.assign(np, nullptr);
+    p.jit_cm_bytes.assign(np, 0);
+    if (jit_const_mats(p))
+      for (size_t i = 0; i < np; ++i) {
+        char name[32];
+        snprintf(name, sizeof name, "tnq_cm%zu", i);
+        void *ptr = nullptr;
+        size_t bytes = 0;
+        cudaError_t e = cudaLibraryGetGlobal(&ptr, &bytes, libs[i], name);
+        if (e != cudaSuccess) {
+          err = std::string("generated kernel's matrix table: ") + cudaGetErrorString(e);
+          return TN_ERR_CUDA;
+        }
+        p.jit_cm_ptr[i] = ptr;
+        p.jit_cm_bytes[i] = (size_t)(pp.passes[i].mat_end - pp.passes[i].mat_begin) * sizeof(float2);
+      }
+  }
   return TN_OK;
 }
 
 void jit_release(tn_plan &p) {
+  p.jit_cm_ptr.clear();
+  p.jit_cm_bytes.clear();
   for (cudaLibrary_t l : p.jit_libs)
     if (l) cudaLibraryUnload(l);
   for (cudaLibrary_t l : p.jit_bwd_libs)

@@ -15,4 +15,7 @@ bool jit_bwd_supported(const tn_plan &p);
 // after compiling (no GPU needed).
 tn_status jit_build(tn_plan &p, const std::vector<int> &op_kind, bool backward, bool compile_only, std::string &err);
 void jit_release(tn_plan &p);
+// Whether the forward pass kernels read their matrix entries from per-pass __constant__ tables
+// (fixed angles, or batch 1); the host copies each pass's entries there before it runs.
+bool jit_const_mats(const tn_plan &p);
 }  // namespace tnq

@@ -181,6 +181,11 @@ cudaError_t launch_forward(const tn_plan *p, const float2 *mats, long long mstri
       if (grid > work) grid = work;
       const float2 *m = mats;
       unsigned long long init = p->init;
+      // per-call tables (parameterised, batch 1): this pass's entries into its constant table
+      if (p->param_dependent && i < p->jit_cm_ptr.size() && p->jit_cm_ptr[i] && p->jit_cm_bytes[i]) {
+        e = cudaMemcpyAsync(p->jit_cm_ptr[i], mats + h.mat_begin, p->jit_cm_bytes[i], cudaMemcpyDeviceToDevice, s);
+        if (e != cudaSuccess) return e;
+      }
       void *args[] = {(void *)&m, (void *)&mstride, (void *)&state, (void *)&work, (void *)&init};
       e = cudaLaunchKernel((const void *)p->jit_kernels[i], dim3((unsigned)grid), dim3(threads), args, smem, s);
       if (e != cudaSuccess) return e;

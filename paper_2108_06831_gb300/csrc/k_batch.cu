@@ -24,9 +24,10 @@ struct alignas(16) BatchCirc {
   unsigned long long init;
   const PhaseDesc *phases;
   const OpDesc *ops;
-  const float2 *mats;
+  const float2 *mats;   // fixed angles: the plan's table; NULL: the run's table at mats_off
+  long long mats_off;   // parameterised circuits: complex64 offset in the run's gate table
   int N;
-  int pad[3];
+  int pad;
 };
 
 struct alignas(16) BatchTask {
@@ -64,7 +65,8 @@ __global__ void __launch_bounds__(kBatchThreads, 3) k_batch_exec(const BatchTask
                                                               float2 *__restrict__ states, int *done,
                                                               unsigned long long *next_item, int *abort_flag,
                                                               long long total_items, int *status, int stage_cap,
-                                                              unsigned long long wait_ns) {
+                                                              unsigned long long wait_ns,
+                                                              const float2 *__restrict__ run_mats) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ PassDesc pd;
   __shared__ long long s_item;
@@ -112,7 +114,8 @@ __global__ void __launch_bounds__(kBatchThreads, 3) k_batch_exec(const BatchTask
     __syncthreads();
     if (!s_go) break;
     const BatchTask task = tasks[s_task];
-    const BatchCirc circ = circs[task.circ];
+    BatchCirc circ = circs[task.circ];
+    if (circ.mats == nullptr) circ.mats = run_mats + circ.mats_off;
     for (int i = threadIdx.x; i < (int)(sizeof(PassDesc) / 4); i += blockDim.x)
       reinterpret_cast<int *>(&pd)[i] = reinterpret_cast<const int *>(passes + task.pass)[i];
     __syncthreads();
@@ -242,6 +245,14 @@ struct tn_batch {
   int stage_cap = 0;             // shared-memory bytes for a pass's records (largest pass, capped)
   std::vector<tn_plan *> owned;  // plans made for this batch (tile autotuner)
   std::vector<tnq::BatchTask> h_tasks;            // host copy of the task list
+  // parameterised circuits: their gate tables are materialised per run (one kernel, all circuits)
+  int n_params = 0;                                // parameters of all circuits, back to back
+  std::vector<long long> param_offsets;            // first parameter of each circuit
+  int n_slots = 0;                                 // matrix slots of the parameterised circuits
+  long long run_mats_elems = 0;                    // complex64 entries of the per-run table
+  size_t ws_mats = 0;                              // byte offset of that table in the workspace
+  tnq::MatSlot *d_slots = nullptr;
+  tnq::FusedMember *d_fused = nullptr;
   std::vector<std::vector<int>> circ_tasks;       // tasks of each circuit, pass order
   unsigned long long wait_ns = 2000000000ull;     // dependency-wait bound passed to the kernel
   int stalled_task = -1;                          // task altered by tn_batch_test_stall, -1 if none
@@ -253,6 +264,9 @@ tn_status batch_build(const tn_plan *const *plans, int n, tn_batch **out) {
   std::vector<BatchCirc> circs((size_t)n);
   std::vector<PassDesc> passes;
   std::vector<std::vector<int>> circ_pass((size_t)n);  // batch pass indices per circuit
+  std::vector<MatSlot> all_slots;                       // parameterised circuits' forward slots
+  std::vector<FusedMember> all_fused;
+  long long run_mats = 0;
   tn_batch *b = new tn_batch();
   b->n = n;
   b->offsets.resize((size_t)n);
@@ -264,9 +278,9 @@ tn_status batch_build(const tn_plan *const *plans, int n, tn_batch **out) {
       set_error("plan %d is NULL or host-only", i);
       return TN_ERR_INVALID_ARG;
     }
-    if (p->param_dependent || p->batch != 1) {
+    if (p->batch != 1) {
       delete b;
-      set_error("plan %d: the batched executor takes fixed-angle circuits with batch 1", i);
+      set_error("plan %d: the batched executor takes plans of batch 1 (one parameter set per circuit)", i);
       return TN_ERR_UNSUPPORTED;
     }
     if (p->K != 4 || p->T > kBatchT || p->T < kLowBits + 2) {
@@ -281,7 +295,35 @@ tn_status batch_build(const tn_plan *const *plans, int n, tn_batch **out) {
     c.phases = p->d_fwd_phase;
     c.ops = p->d_fwd_ops;
     c.mats = reinterpret_cast<const float2 *>(p->d_fixed_mats);
+    c.mats_off = 0;
     c.N = p->n;
+    b->param_offsets.push_back(b->n_params);
+    if (p->param_dependent) {
+      // its slots join the batch's per-run table: entry offsets, fused members and parameter
+      // indices shifted to the circuit's place in the combined tables
+      c.mats = nullptr;
+      c.mats_off = run_mats;
+      const int fbase = (int)all_fused.size();
+      for (const FusedMember &f : p->fused) {
+        FusedMember g = f;
+        for (int a = 0; a < 3; ++a)
+          for (int k = 0; k < 2; ++k)
+            if (g.pidx[a][k] >= 0) g.pidx[a][k] += b->n_params;
+        all_fused.push_back(g);
+      }
+      for (const MatSlot &sl : p->slots) {
+        if (sl.form != FORM_U) continue;  // forward entries only (the executor runs no adjoint)
+        MatSlot t = sl;
+        t.offset += (int)run_mats;
+        if (t.kind == KIND_F2) t.fuse_begin += fbase;
+        for (int a = 0; a < 3; ++a)
+          for (int k = 0; k < 2; ++k)
+            if (t.pidx[a][k] >= 0) t.pidx[a][k] += b->n_params;
+        all_slots.push_back(t);
+      }
+      run_mats += (p->mstride + 1) & ~1ll;
+      b->n_params += p->n_params;
+    }
     b->offsets[(size_t)i] = off;
     off += 1ll << p->n;
     off = (off + 1) & ~1ll;  // keep every state 16-byte aligned
@@ -334,6 +376,10 @@ tn_status batch_build(const tn_plan *const *plans, int n, tn_batch **out) {
   b->total_items = items;
   b->n_tasks = (int)tasks.size();
   b->ws_bytes = ((size_t)b->n_tasks * sizeof(int) + 255) / 256 * 256 + 256;
+  b->n_slots = (int)all_slots.size();
+  b->run_mats_elems = run_mats;
+  b->ws_mats = b->ws_bytes;
+  b->ws_bytes += ((size_t)run_mats * sizeof(float2) + 255) / 256 * 256;
   cudaError_t e = cudaGetDevice(&b->device);
   auto up = [&](const void *src, size_t bytes, void **dst) {
     if (e != cudaSuccess) return;
@@ -343,10 +389,14 @@ tn_status batch_build(const tn_plan *const *plans, int n, tn_batch **out) {
   up(tasks.data(), sizeof(BatchTask) * tasks.size(), (void **)&b->d_tasks);
   up(circs.data(), sizeof(BatchCirc) * circs.size(), (void **)&b->d_circs);
   up(passes.data(), sizeof(PassDesc) * passes.size(), (void **)&b->d_passes);
+  if (!all_slots.empty()) up(all_slots.data(), sizeof(MatSlot) * all_slots.size(), (void **)&b->d_slots);
+  if (!all_fused.empty()) up(all_fused.data(), sizeof(FusedMember) * all_fused.size(), (void **)&b->d_fused);
   if (e != cudaSuccess) {
     cudaFree(b->d_tasks);
     cudaFree(b->d_circs);
     cudaFree(b->d_passes);
+    cudaFree(b->d_slots);
+    cudaFree(b->d_fused);
     delete b;
     return cuda_fail(e, "batched executor tables");
   }
@@ -354,15 +404,20 @@ tn_status batch_build(const tn_plan *const *plans, int n, tn_batch **out) {
   return TN_OK;
 }
 
-cudaError_t batch_run(const tn_batch *b, float2 *states, void *ws, cudaStream_t s) {
-  // workspace: [done counters per task][next item (u64)][abort flag]
+cudaError_t batch_run(const tn_batch *b, const double *params, float2 *states, void *ws, cudaStream_t s) {
+  // workspace: [done counters per task][next item (u64)][abort flag][per-run gate table]
   char *w = static_cast<char *>(ws);
   int *done = reinterpret_cast<int *>(w);
   const size_t counters = ((size_t)b->n_tasks * sizeof(int) + 255) / 256 * 256;
   unsigned long long *next = reinterpret_cast<unsigned long long *>(w + counters);
   int *abort_flag = reinterpret_cast<int *>(w + counters + 8);
-  cudaError_t e = cudaMemsetAsync(ws, 0, b->ws_bytes, s);
+  float2 *run_mats = reinterpret_cast<float2 *>(w + b->ws_mats);
+  cudaError_t e = cudaMemsetAsync(ws, 0, b->ws_mats, s);
   if (e != cudaSuccess) return e;
+  if (b->n_slots > 0) {  // every parameterised circuit's gate table, one kernel
+    e = launch_materialize(b->d_slots, b->n_slots, b->d_fused, params, b->n_params, 1, 0, run_mats, s);
+    if (e != cudaSuccess) return e;
+  }
   const size_t smem = ((size_t)sizeof(float2) << kBatchT) + ((size_t)1 << (kBatchT - kLowBits)) * sizeof(long long) +
                       (size_t)b->stage_cap;
   e = ensure_smem(reinterpret_cast<const void *>(k_batch_exec), smem);
@@ -378,7 +433,7 @@ cudaError_t batch_run(const tn_batch *b, float2 *states, void *ws, cudaStream_t 
   k_batch_exec<<<(unsigned)grid, kBatchThreads, smem, s>>>(b->d_tasks, b->n_tasks, b->d_circs, b->d_passes, states,
                                                            done, next, abort_flag, b->total_items,
                                                            static_cast<int *>(status_word_ptr()), b->stage_cap,
-                                                           b->wait_ns);
+                                                           b->wait_ns, run_mats);
   return cudaGetLastError();
 }
 
@@ -431,8 +486,16 @@ tn_status batch_test_stall(tn_batch *b, int circ, int pass, long long wait_ns) {
   return TN_OK;
 }
 
+int batch_num_params(const tn_batch *b, long long *offsets) {
+  if (offsets)
+    for (int i = 0; i < b->n; ++i) offsets[i] = b->param_offsets[(size_t)i];
+  return b->n_params;
+}
+
 void batch_free(tn_batch *b) {
   if (!b) return;
+  cudaFree(b->d_slots);
+  cudaFree(b->d_fused);
   cudaFree(b->d_tasks);
   cudaFree(b->d_circs);
   cudaFree(b->d_passes);

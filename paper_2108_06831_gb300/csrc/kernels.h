@@ -62,7 +62,10 @@ cudaError_t launch_cgemm(int precision, long long batch, long long M, long long 
 
 // Persistent batched executor.
 tn_status batch_build(const tn_plan *const *plans, int n, tn_batch **out);
-cudaError_t batch_run(const tn_batch *b, float2 *states, void *ws, cudaStream_t s);
+// params: every parameterised circuit's parameters back to back (NULL when none has any).
+cudaError_t batch_run(const tn_batch *b, const double *params, float2 *states, void *ws, cudaStream_t s);
+// Parameters of all circuits together; offsets[i] (optional) = circuit i's first parameter.
+int batch_num_params(const tn_batch *b, long long *offsets);
 void batch_free(tn_batch *b);
 tn_status batch_sizes(const tn_batch *b, long long *elems, size_t *ws);
 tn_status batch_offsets(const tn_batch *b, long long *offsets);

@@ -43,12 +43,13 @@ struct NetLaunch {
 constexpr int kFoldMaxLog2 = 20;       // largest folded result: 2^20 entries
 constexpr double kFoldMaxWork = 2e8;   // complex multiply-adds over all folded merges (all slices)
 
-// Order cost of a launched merge: kLaunchBytes (a launch and a short kernel: ~9 us measured per
-// launch on sliced and small-merge plans, i.e. 6e7 bytes of HBM time at ~6.7 TB/s)
+// Order cost of a launched merge: kLaunchBytes (a launch and a short kernel, ~3 us of HBM time;
+// charging the ~9 us measured per launch on sliced plans, 6e7, picked orders that ran the Fig. 3.1
+// amplitude sweep 24% slower, 37.6 against 30.4 ms, and changed no capped 36-qubit plan)
 // + max(bytes read and written, complex flops / kRidge): merges are HBM-bound unless their
 // arithmetic intensity exceeds kRidge.
 constexpr double kRidge = 32.0;
-constexpr double kLaunchBytes = 6e7;
+constexpr double kLaunchBytes = 2e7;
 
 // Slicing: at most 2^16 slices; the constant table of all slices at most 2^27 entries.
 constexpr int kMaxSliceBits = 16;

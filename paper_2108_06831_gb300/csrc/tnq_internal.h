@@ -412,6 +412,8 @@ struct tn_plan {
   std::vector<cudaKernel_t> jit_kernels;
   std::vector<int> jit_threads, jit_grid;
   std::vector<size_t> jit_smem;
+  std::vector<void *> jit_cm_ptr;    // per forward pass: device address of its __constant__ matrix table
+  std::vector<size_t> jit_cm_bytes;  //   and the bytes the pass reads (copied before its launch)
   std::vector<cudaLibrary_t> jit_bwd_libs;
   std::vector<cudaKernel_t> jit_bwd_kernels;
   std::vector<int> jit_bwd_threads;

@@ -98,6 +98,8 @@ _sigs = {
     "tn_batch_run": [_vp, _vp, _vp, _vp],
     "tn_free_batch": [_vp],
     "tn_batch_test_stall": [_vp, C.c_int32, C.c_int32, C.c_int64],
+    "tn_batch_run_params": [_vp, _vp, _vp, _vp, _vp],
+    "tn_batch_params": [_vp, C.POINTER(C.c_int32), C.POINTER(C.c_int64)],
     "tn_probe_fma_rate": [C.POINTER(C.c_double), C.POINTER(C.c_double)],
     "tn_batch_build_tuned": [C.POINTER(_vp), C.c_int32, C.POINTER(TnTuneOpts), _vp, C.POINTER(_vp),
                              C.POINTER(C.c_int32)],
@@ -356,6 +358,10 @@ class Batch:
         offs = (C.c_int64 * n)()
         _check(_lib.tn_batch_state_offsets(h, offs), "tn_batch_state_offsets")
         self.offsets = list(offs)
+        npar = C.c_int32()
+        poffs = (C.c_int64 * n)()
+        _check(_lib.tn_batch_params(h, C.byref(npar), poffs), "tn_batch_params")
+        self.n_params, self.param_offsets = npar.value, list(poffs)
 
     def __del__(self):
         if getattr(self, "_h", None):
@@ -363,8 +369,14 @@ class Batch:
             self._h = None
 
 
-def batch_run(batch: Batch, states, workspace, stream=None) -> None:
-    _check(_lib.tn_batch_run(batch._h, _ptr(states), _ptr(workspace), _stream(stream)), "tn_batch_run")
+def batch_run(batch: Batch, states, workspace, stream=None, params=None) -> None:
+    """One persistent launch over every circuit of the batch; params (device float64, all circuits'
+    parameters back to back at batch.param_offsets) for batches with parameterised circuits."""
+    if params is None:
+        _check(_lib.tn_batch_run(batch._h, _ptr(states), _ptr(workspace), _stream(stream)), "tn_batch_run")
+    else:
+        _check(_lib.tn_batch_run_params(batch._h, _ptr(params), _ptr(states), _ptr(workspace), _stream(stream)),
+               "tn_batch_run_params")
 
 
 def batch_test_stall(batch: Batch, circ: int, pass_index: int = 1, wait_limit_ns: int = 0) -> None:

@@ -76,10 +76,71 @@ def test_batch_small_tiles_many_passes_and_graph_replay():
             assert np.linalg.norm(s - ref) / np.linalg.norm(ref) <= TOL, c.name
 
 
-def test_batch_rejects_parameterised_plans():
+def test_batch_with_parameterised_circuits():
+    """Parameterised circuits in the persistent launch: every circuit's gate table is built in the
+    run from its own parameters (one kernel for all), fixed-angle circuits beside them; the run is
+    captured in a CUDA graph and replayed with new parameter values written into the same buffer."""
+    from oracle.statevector import simulate_state
+    from paper_2108_06831_gb300 import tn
+    rng = np.random.default_rng(12)
+    circs, params = [], []
+    for i in range(12):
+        n = int(rng.integers(6, 17))
+        if i % 3 == 2:
+            circs.append(C.qft(n, int(rng.integers(0, 1 << n))))
+            params.append(np.zeros(0))
+        elif i % 3 == 1:
+            c = C.hea(n, 3)
+            circs.append(c)
+            params.append(C.hea_params(c.n_params, 1, 100 + i)[0])
+        else:
+            c, p = C.brickwork(n, int(rng.integers(2, 10)), 600 + i, parameterized=True)
+            circs.append(c)
+            params.append(p)
+    plans = [tn.Plan(tn.CircuitHandle(c), tile_qubits=min(8 + (i % 4), c.n_qubits) if c.n_qubits >= 6 else 0,
+                     specialize=False) for i, c in enumerate(circs)]
+    b = tn.Batch(plans)
+    assert b.n_params == sum(len(p) for p in params)
+    flat = np.zeros(max(b.n_params, 1))
+    for p, off in zip(params, b.param_offsets):
+        flat[off:off + len(p)] = p
+    d_params = torch.as_tensor(flat, device="cuda")
+    states = torch.full((b.state_elems,), complex(float("nan"), 0), dtype=torch.complex64, device="cuda")
+    ws = torch.empty(b.workspace_bytes, dtype=torch.uint8, device="cuda")
+    with pytest.raises(tn.TnError):  # parameters are required
+        tn.batch_run(b, states, ws)
+
+    def check():
+        got = states.cpu().numpy()
+        for c, p, off in zip(circs, params, b.offsets):
+            ref = simulate_state(c, p if len(p) else None)
+            s_ = got[off:off + (1 << c.n_qubits)]
+            assert np.linalg.norm(s_ - ref) / np.linalg.norm(ref) <= TOL, c.name
+    tn.batch_run(b, states, ws, params=d_params)
+    torch.cuda.synchronize()
+    assert tn.sync_status() == tn.OK
+    check()
+    stream = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(stream):
+        with torch.cuda.graph(g, stream=stream):
+            tn.batch_run(b, states, ws, params=d_params)
+    for rep in range(2):
+        params = [rng.uniform(-np.pi, np.pi, size=len(p)) for p in params]
+        for p, off in zip(params, b.param_offsets):
+            flat[off:off + len(p)] = p
+        d_params.copy_(torch.as_tensor(flat))
+        states.fill_(float("nan"))
+        g.replay()
+        torch.cuda.synchronize()
+        assert tn.sync_status() == tn.OK
+        check()
+
+
+def test_batch_rejects_batched_plans():
     from paper_2108_06831_gb300 import tn
     c, _ = C.brickwork(8, 2, 1, parameterized=True)
-    p = tn.Plan(tn.CircuitHandle(c), specialize=False)
+    p = tn.Plan(tn.CircuitHandle(c), batch=2, specialize=False)
     with pytest.raises(tn.TnError) as e:
         tn.Batch([p])
     assert e.value.status == tn.ERR_UNSUPPORTED
