@@ -65,7 +65,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="state24",
                     choices=["state24", "state10", "grad20", "gemm_fp32", "gemm_3xtf32", "gemm_bf16x3",
-                             "serving512", "amps36", "permute28", "gemm_merge", "fig31", "fig31amps", "plan31", "q428_24"])
+                             "serving512", "serving512p", "amps36", "permute28", "gemm_merge", "fig31", "fig31amps", "plan31", "q428_24"])
     ap.add_argument("--batch", type=int, default=0, help="gemm workloads: batch override (small profiling cases)")
     ap.add_argument("--legs", type=int, default=0, help="permute28: tensor legs override (small profiling cases)")
     ap.add_argument("--prec", type=int, default=1, help="amps36: GEMM precision (0 FP32, 1 3xTF32, 2 split BF16)")
@@ -326,6 +326,8 @@ WORKLOADS = {
     "amps36": dict(kind="amps", n=36, depth=12, seed=3003, batch=4096, chunk=64),
     # batched serving mix: 512 circuits, n ~ U[8, 22], depth ~ U[4, 30], half brickwork, half QFT
     "serving512": dict(kind="serve", n=0, depth=0, seed=5000, batch=512),
+    # the same mix with the brickwork halves' U3 angles as parameters (gate tables built in the run)
+    "serving512p": dict(kind="serve", n=0, depth=0, seed=5000, batch=512, params=True),
     "gemm_fp32": dict(kind="gemm", prec=0, M=4096, N=4096, K=4096, batch=1, n=0, depth=0, seed=7),
     "gemm_3xtf32": dict(kind="gemm", prec=1, M=4096, N=4096, K=4096, batch=1, n=0, depth=0, seed=7),
     "gemm_bf16x3": dict(kind="gemm", prec=2, M=4096, N=4096, K=4096, batch=1, n=0, depth=0, seed=7),
@@ -525,18 +527,31 @@ def main():
         batch = len(circs)
         units_per_step = float(sum(1 << c.n_qubits for c in circs))
         unit = "amplitudes/s"
-        tn.batch_run(bat, states, bws)
+        run_params = None
+        if wl.get("params"):
+            # the brickwork halves' U3 angles as per-run parameters: plans at the tiles the autotuner
+            # picked for the same circuits with fixed angles, gate tables built inside each run
+            circs_p, params_p = C.serving_mix_params(wl["batch"], wl["seed"])
+            pplans = [tn.Plan(tn.CircuitHandle(c), tile_qubits=t, specialize=False)
+                      for c, t in zip(circs_p, bat.tiles)]
+            bat = tn.Batch(pplans)
+            flat = np.zeros(max(bat.n_params, 1))
+            for pv, off in zip(params_p, bat.param_offsets):
+                flat[off:off + len(pv)] = pv
+            run_params = torch.as_tensor(flat, device=dev)
+            bws = torch.empty(bat.workspace_bytes, dtype=torch.uint8, device=dev)
+        tn.batch_run(bat, states, bws, params=run_params)
         torch.cuda.synchronize()
         graph = torch.cuda.CUDAGraph()
         cap = torch.cuda.Stream(device=dev)
         with torch.cuda.stream(cap):
             with torch.cuda.graph(graph, stream=cap):
-                tn.batch_run(bat, states, bws)
+                tn.batch_run(bat, states, bws, params=run_params)
         torch.cuda.synchronize()
 
         def step():
             graph.replay()
-        launches_per_step = 1
+        launches_per_step = 2 if run_params is not None else 1  # (gate tables +) the persistent kernel
         kernel_only = None
         ctr = None
         # the comparison: every circuit contracted on its own, one after another
@@ -608,15 +623,23 @@ def main():
         def eager_step():
             for key in pts:
                 tn.contract_amplitudes(nplans[key], None, nxs[key], nout[key], nws[key])
-        # the 98 calls (their closure kernels, merges and copies) captured once in a CUDA graph;
-        # a step replays it
+        # the 98 calls (their closure kernels, merges and copies) captured once in a CUDA graph, as
+        # independent chains on 8 streams (circuit i on stream i mod 8): the small merges of different
+        # circuits run side by side instead of one launch after another; a step replays the graph
         eager_step()
         torch.cuda.synchronize()
         graph = torch.cuda.CUDAGraph()
         cap = torch.cuda.Stream(device=dev)
+        lanes = [torch.cuda.Stream(device=dev) for _ in range(8)]
         with torch.cuda.stream(cap):
             with torch.cuda.graph(graph, stream=cap):
-                eager_step()
+                for ln in lanes:
+                    ln.wait_stream(cap)
+                for i, key in enumerate(pts):
+                    with torch.cuda.stream(lanes[i % len(lanes)]):
+                        tn.contract_amplitudes(nplans[key], None, nxs[key], nout[key], nws[key])
+                for ln in lanes:
+                    cap.wait_stream(ln)
         torch.cuda.synchronize()
 
         def step():
@@ -941,6 +964,9 @@ def main():
                                "launch": "one persistent kernel in a CUDA graph",
                                "tiles_by_qubits": {str(k): sorted(v) for k, v in sorted(tiles_by_n.items())},
                                "autotune_seconds": round(t_tune, 1)})
+        if run_params is not None:
+            line["config"]["parameters"] = (f"{bat.n_params} float64 parameters (the brickwork halves' U3 angles) "
+                                            f"read per run: gate tables built by one kernel inside each run")
         line["sequential"] = {"value": units_per_step / (statistics.mean(sms) / 1000.0), "unit": unit,
                               "ms_per_step": statistics.mean(sms),
                               "what": "the same circuits contracted one after another (tn_contract_state each)"}

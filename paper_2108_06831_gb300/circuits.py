@@ -272,6 +272,26 @@ def serving_mix(n_circuits: int, seed: int, n_min: int = 8, n_max: int = 22,
     return out
 
 
+def serving_mix_params(n_circuits: int, seed: int, n_min: int = 8, n_max: int = 22,
+                       d_min: int = 4, d_max: int = 30) -> Tuple[List[Circuit], List[np.ndarray]]:
+    """serving_mix with the brickwork halves' U3 angles as parameters: (circuits, per-circuit
+    parameter vectors; empty for the QFT halves).  The parameter values equal the angles
+    serving_mix(n_circuits, seed) draws, so the states are the same."""
+    rng = _rng(seed)
+    circs: List[Circuit] = []
+    params: List[np.ndarray] = []
+    for i in range(n_circuits):
+        n = int(rng.integers(n_min, n_max + 1))
+        if i % 2 == 0:
+            d = int(rng.integers(d_min, d_max + 1))
+            c, p = brickwork(n, d, seed * 100003 + i, parameterized=True)
+        else:
+            c, p = qft(n, random_basis(n, seed * 100003 + i)), np.zeros(0)
+        circs.append(c)
+        params.append(p)
+    return circs, params
+
+
 # ----------------------------------------------------------------------------
 # observables
 # ----------------------------------------------------------------------------

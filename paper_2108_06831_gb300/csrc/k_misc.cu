@@ -5,30 +5,61 @@
 
 namespace tnq {
 
-// Gate tensors are built once per call from the parameters (one thread per slot and
-// batch element; angles in FP64, entries stored as complex64).  A fused block (KIND_F2) is the
-// FP64 product of its member gates, stored in the packed layout (SHAPE_M4X).
-__global__ void k_materialize(const MatSlot *__restrict__ slots, int n_slots, const FusedMember *__restrict__ fused,
-                              const double *__restrict__ params, int n_params, int batch, long long mstride,
-                              float2 *__restrict__ out) {
-  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (long long)n_slots * batch) return;
+// Gate tensors are built once per call from the parameters: one warp per slot and batch element
+// (angles in FP64, entries stored as complex64).  A regular slot is one gate's matrix (lane 0).
+// A fused block (KIND_F2) is the FP64 product of its member gates, stored in the packed layout
+// (SHAPE_M4X): lane m evaluates member m's matrix embedded as a 4x4, then lanes 0..15 form the
+// product one entry each, member by member.
+constexpr int kMatWarps = 4;
+
+__global__ void __launch_bounds__(32 * kMatWarps) k_materialize(const MatSlot *__restrict__ slots, int n_slots,
+                                                               const FusedMember *__restrict__ fused,
+                                                               const double *__restrict__ params, int n_params,
+                                                               int batch, long long mstride, float2 *__restrict__ out) {
+  __shared__ double emb[kMatWarps][kMaxFusedMembers][32];
+  __shared__ double acc[kMatWarps][2][32];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long idx = (long long)blockIdx.x * kMatWarps + w;
+  if (idx >= (long long)n_slots * batch) return;  // whole warps leave together
   const int b = (int)(idx / n_slots);
   const int k = (int)(idx % n_slots);
   const MatSlot &s = slots[k];
   float2 *dst = out + (long long)b * mstride + s.offset;
+  const double *prow = params ? params + (long long)b * n_params : nullptr;
   if (s.kind == KIND_F2) {
-    double m[32];
-    float ent[64];
-    fused_matrix(fused + s.fuse_begin, s.fuse_count, params ? params + (long long)b * n_params : nullptr, m);
-    packed_m4x(m, ent);
-    for (int i = 0; i < 32; ++i) dst[i] = make_float2(ent[2 * i], ent[2 * i + 1]);
+    const int cnt = s.fuse_count;
+    if (lane < cnt) fused_embed(fused[s.fuse_begin + lane], prow, emb[w][lane]);
+    if (lane < 32) acc[w][0][lane] = (lane & 1) == 0 && ((lane >> 1) % 5) == 0 ? 1.0 : 0.0;  // identity
+    __syncwarp();
+    int cur = 0;
+    for (int m = 0; m < cnt; ++m) {  // acc <- emb[m] * acc
+      if (lane < 16) {
+        const int i = lane >> 2, j = lane & 3;
+        double re = 0.0, im = 0.0;
+        for (int q = 0; q < 4; ++q) {
+          const double xr = emb[w][m][2 * (4 * i + q)], xi = emb[w][m][2 * (4 * i + q) + 1];
+          const double yr = acc[w][cur][2 * (4 * q + j)], yi = acc[w][cur][2 * (4 * q + j) + 1];
+          re += xr * yr - xi * yi;
+          im += xr * yi + xi * yr;
+        }
+        acc[w][cur ^ 1][2 * lane] = re;
+        acc[w][cur ^ 1][2 * lane + 1] = im;
+      }
+      __syncwarp();
+      cur ^= 1;
+    }
+    if (lane < 16) {  // packed entry (re, re, -im, im)
+      const float re = (float)acc[w][cur][2 * lane], im = (float)acc[w][cur][2 * lane + 1];
+      dst[2 * lane] = make_float2(re, re);
+      dst[2 * lane + 1] = make_float2(-im, im);
+    }
     return;
   }
+  if (lane != 0) return;
   double ang[3] = {s.angle[0], s.angle[1], s.angle[2]};
   for (int a = 0; a < 3; ++a)
-    for (int k = 0; k < 2; ++k)
-      if (s.pidx[a][k] >= 0) ang[a] += params[(long long)b * n_params + s.pidx[a][k]];
+    for (int q = 0; q < 2; ++q)
+      if (s.pidx[a][q] >= 0) ang[a] += prow[s.pidx[a][q]];
   double tmp[32];
   float ent[32];
   const int n = slot_entries(s, ang, tmp, ent);
@@ -39,9 +70,8 @@ cudaError_t launch_materialize(const MatSlot *d_slots, int n_slots, const FusedM
                                int n_params, int batch, long long mstride, float2 *out, cudaStream_t s) {
   const long long total = (long long)n_slots * batch;
   if (total == 0) return cudaSuccess;
-  const int threads = 128;
-  k_materialize<<<(unsigned)((total + threads - 1) / threads), threads, 0, s>>>(d_slots, n_slots, d_fused, params,
-                                                                               n_params, batch, mstride, out);
+  k_materialize<<<(unsigned)((total + kMatWarps - 1) / kMatWarps), 32 * kMatWarps, 0, s>>>(
+      d_slots, n_slots, d_fused, params, n_params, batch, mstride, out);
   return cudaGetLastError();
 }
 

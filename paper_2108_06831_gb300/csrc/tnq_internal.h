@@ -268,65 +268,32 @@ TNQ_HD int slot_entries(const MatSlot &s, const double *ang, double *tmp /*32*/,
 }
 
 
-// The 4x4 of a fused block (KIND_F2): the product of its member gates in order, FP64,
-// indexed 2 bit(a) + bit(b).  param_row: this batch element's parameters (may be NULL when
-// no member reads one).  Writes 16 (re, im) pairs to out.
-TNQ_HD void fused_matrix(const FusedMember *mem, int count, const double *param_row, double *out /*32*/) {
-  for (int i = 0; i < 32; ++i) out[i] = 0.0;
-  for (int i = 0; i < 4; ++i) out[2 * (5 * i)] = 1.0;
-  double g[32], e[32], r[32];
-  for (int m = 0; m < count; ++m) {
-    const FusedMember &f = mem[m];
-    double ang[3] = {f.angle[0], f.angle[1], f.angle[2]};
-    for (int a = 0; a < 3; ++a)
-      for (int k = 0; k < 2; ++k)
-        if (f.pidx[a][k] >= 0 && param_row) ang[a] += param_row[f.pidx[a][k]];
-    const int dim = gate_matrix(f.kind, FORM_U, ang, f.mat, g);
-    // embed the member as a 4x4 on (a, b)
-    for (int i = 0; i < 32; ++i) e[i] = 0.0;
-    for (int i = 0; i < 4; ++i)
-      for (int j = 0; j < 4; ++j) {
-        const int ia = i >> 1, ib = i & 1, ja = j >> 1, jb = j & 1;
-        double re = 0.0, im = 0.0;
-        if (dim == 2) {
-          if (f.role == ROLE_A && ib == jb) { re = g[2 * (2 * ia + ja)]; im = g[2 * (2 * ia + ja) + 1]; }
-          if (f.role == ROLE_B && ia == ja) { re = g[2 * (2 * ib + jb)]; im = g[2 * (2 * ib + jb) + 1]; }
-        } else {
-          // ROLE_BA: the member's first qubit is b, so its index is 2 bit(b) + bit(a)
-          const int ii = f.role == ROLE_AB ? i : 2 * ib + ia, jj = f.role == ROLE_AB ? j : 2 * jb + ja;
-          re = g[2 * (4 * ii + jj)];
-          im = g[2 * (4 * ii + jj) + 1];
-        }
-        e[2 * (4 * i + j)] = re;
-        e[2 * (4 * i + j) + 1] = im;
+// One member of a fused block as a 4x4 on (a, b), indexed 2 bit(a) + bit(b), FP64 (re, im) pairs.
+TNQ_HD void fused_embed(const FusedMember &f, const double *param_row, double *e /*32*/) {
+  double ang[3] = {f.angle[0], f.angle[1], f.angle[2]};
+  for (int a = 0; a < 3; ++a)
+    for (int k = 0; k < 2; ++k)
+      if (f.pidx[a][k] >= 0 && param_row) ang[a] += param_row[f.pidx[a][k]];
+  double g[32];
+  const int dim = gate_matrix(f.kind, FORM_U, ang, f.mat, g);
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) {
+      const int ia = i >> 1, ib = i & 1, ja = j >> 1, jb = j & 1;
+      double re = 0.0, im = 0.0;
+      if (dim == 2) {
+        if (f.role == ROLE_A && ib == jb) { re = g[2 * (2 * ia + ja)]; im = g[2 * (2 * ia + ja) + 1]; }
+        if (f.role == ROLE_B && ia == ja) { re = g[2 * (2 * ib + jb)]; im = g[2 * (2 * ib + jb) + 1]; }
+      } else {
+        // ROLE_BA: the member's first qubit is b, so its index is 2 bit(b) + bit(a)
+        const int ii = f.role == ROLE_AB ? i : 2 * ib + ia, jj = f.role == ROLE_AB ? j : 2 * jb + ja;
+        re = g[2 * (4 * ii + jj)];
+        im = g[2 * (4 * ii + jj) + 1];
       }
-    // out <- e * out
-    for (int i = 0; i < 4; ++i)
-      for (int j = 0; j < 4; ++j) {
-        double re = 0.0, im = 0.0;
-        for (int k = 0; k < 4; ++k) {
-          const double xr = e[2 * (4 * i + k)], xi = e[2 * (4 * i + k) + 1];
-          const double yr = out[2 * (4 * k + j)], yi = out[2 * (4 * k + j) + 1];
-          re += xr * yr - xi * yi;
-          im += xr * yi + xi * yr;
-        }
-        r[2 * (4 * i + j)] = re;
-        r[2 * (4 * i + j) + 1] = im;
-      }
-    for (int i = 0; i < 32; ++i) out[i] = r[i];
-  }
+      e[2 * (4 * i + j)] = re;
+      e[2 * (4 * i + j) + 1] = im;
+    }
 }
 
-// The SHAPE_M4X entries of a fused 4x4 m (16 (re, im) pairs): (re, re, -im, im) per entry.
-TNQ_HD void packed_m4x(const double *m, float *dst /*64 floats*/) {
-  for (int k = 0; k < 16; ++k) {
-    const float re = (float)m[2 * k], im = (float)m[2 * k + 1];
-    dst[4 * k] = re;
-    dst[4 * k + 1] = re;
-    dst[4 * k + 2] = -im;
-    dst[4 * k + 3] = im;
-  }
-}
 
 }  // namespace tnq
 
