@@ -75,6 +75,8 @@ def parse():
     ap.add_argument("--tile", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="state24: skip the short runs of the other configurations after the headline")
     ap.add_argument("--no-specialize", action="store_true", help="run the interpreting gate-apply kernel")
     ap.add_argument("--blocks", type=int, default=0,
                     help="state workloads: contract by uniform 2^k x 2^k blocks of k = 6 or 7 qubits, each "
@@ -1114,11 +1116,52 @@ def main():
         line["cpu_baseline"] = cpu
     if cpu_all is not None:
         line["cpu_baseline_all_cores"] = cpu_all
+    if rank == 0 and world == 1 and args.workload == "state24" and not args.no_configs and not args.blocks \
+            and not args.no_fuse and not args.tile and not args.no_specialize:
+        # the other configurations, each measured in its own process after this one's timed region
+        # (short runs: 3 warm-up and 5 timed steps, no CPU baseline); the headline above is config 2
+        torch.cuda.synchronize()
+        line["other_configs"] = other_configs()
     if rank == 0:
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+OTHER_CONFIGS = [
+    ("config 1: 10-qubit brickwork depth 8, 512 parameter sets per call", ["--workload", "state10"]),
+    ("config 2, split precision on: uniform 2^6 x 2^6 blocks, 3xTF32 tensor-core GEMMs",
+     ["--blocks", "6", "--prec", "1"]),
+    ("config 2, split precision on: uniform 2^6 x 2^6 blocks, split-BF16 tensor-core GEMMs",
+     ["--blocks", "6", "--prec", "2"]),
+    ("config 3: 6x6 grid depth 12, 4096 amplitudes, 3xTF32 merges", ["--workload", "amps36", "--prec", "1"]),
+    ("config 3, plain FP32 merges", ["--workload", "amps36", "--prec", "0"]),
+    ("config 4: 20-qubit HEA, TFIM energy + adjoint gradient, 64 parameter sets", ["--workload", "grad20"]),
+    ("config 5: 512-circuit serving mix, one persistent launch in a CUDA graph", ["--workload", "serving512"]),
+]
+
+
+def other_configs():
+    """Short runs of the other configurations in fresh processes: value, unit, time per step,
+    roofline fraction and bound of each (or the failure)."""
+    out = {}
+    for name, extra in OTHER_CONFIGS:
+        cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--steps", "5", "--warmup", "3",
+               "--no-cpu-baseline", "--no-e2e"] + extra
+        try:
+            r = subprocess.run(cmd, capture_output=True, text=True, timeout=600)
+            d = json.loads(r.stdout.strip().splitlines()[-1])
+            rf = d.get("roofline") or {}
+            out[name] = {"value": d["value"], "unit": d["unit"], "ms_per_step": round(d["ms_per_step"], 4),
+                         "dtype": d.get("dtype"), "roofline_bound": rf.get("bound"),
+                         "roofline_frac": rf.get("frac"), "clocks": d.get("clocks"),
+                         "args": " ".join(extra)}
+            if "sequential" in d:
+                out[name]["sequential_ms_per_step"] = round(d["sequential"]["ms_per_step"], 3)
+        except Exception as e:  # reported, never fatal for the headline
+            out[name] = {"error": f"{type(e).__name__}: {str(e)[:200]}", "args": " ".join(extra)}
+    return out
 
 
 if __name__ == "__main__":
