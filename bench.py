@@ -75,6 +75,10 @@ def parse():
     ap.add_argument("--tile", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--order-search", type=int, default=0,
+                    help="network workloads: 1 = adaptive (cross-entropy) contraction-order search")
+    ap.add_argument("--lanes", type=int, default=8,
+                    help="fig31amps: streams the captured graph spreads the 98 calls over")
     ap.add_argument("--no-configs", action="store_true",
                     help="state24: skip the short runs of the other configurations after the headline")
     ap.add_argument("--no-specialize", action="store_true", help="run the interpreting gate-apply kernel")
@@ -568,7 +572,7 @@ def main():
         chunk = wl["chunk"]
         ctr = None
         plan = tn.Plan(tn.CircuitHandle(circ), target=tn.TARGET_AMPLITUDES, network_bitstrings=chunk,
-                       precision=args.prec, max_intermediate_log2=args.max_log2)
+                       precision=args.prec, max_intermediate_log2=args.max_log2, order_search=args.order_search)
         nst = plan.stats()
         aws = torch.empty(plan.workspace_bytes, dtype=torch.uint8, device=dev)
         xs_h = C.random_bitstrings(36, wl["batch"], wl["seed"] + 1)
@@ -611,7 +615,8 @@ def main():
         for i, (n, k) in enumerate(pts):
             t0 = time.perf_counter()
             nplans[(n, k)] = tn.Plan(tn.CircuitHandle(C.paper_fig31(n, k, wl["seed"] + i)),
-                                     target=tn.TARGET_AMPLITUDES, network_bitstrings=chunk, precision=1)
+                                     target=tn.TARGET_AMPLITUDES, network_bitstrings=chunk, precision=1,
+                                     order_search=args.order_search)
             plan_s[(n, k)] = time.perf_counter() - t0
             nws[(n, k)] = torch.empty(max(nplans[(n, k)].workspace_bytes, 16), dtype=torch.uint8, device=dev)
             nxs[(n, k)] = torch.as_tensor(C.random_bitstrings(n, chunk, wl["seed"] + 1000 + i).astype(np.int64),
@@ -626,13 +631,13 @@ def main():
             for key in pts:
                 tn.contract_amplitudes(nplans[key], None, nxs[key], nout[key], nws[key])
         # the 98 calls (their closure kernels, merges and copies) captured once in a CUDA graph, as
-        # independent chains on 8 streams (circuit i on stream i mod 8): the small merges of different
+        # independent chains on --lanes streams (circuit i on stream i mod lanes): the small merges of different
         # circuits run side by side instead of one launch after another; a step replays the graph
         eager_step()
         torch.cuda.synchronize()
         graph = torch.cuda.CUDAGraph()
         cap = torch.cuda.Stream(device=dev)
-        lanes = [torch.cuda.Stream(device=dev) for _ in range(8)]
+        lanes = [torch.cuda.Stream(device=dev) for _ in range(args.lanes)]
         with torch.cuda.stream(cap):
             with torch.cuda.graph(graph, stream=cap):
                 for ln in lanes:
@@ -765,6 +770,8 @@ def main():
                        "tile_qubits": ctr.plan.stats()["tile_qubits"] if ctr is not None else None,
                        "specialized_kernels": bool(ctr.plan.stats()["specialized"]) if ctr is not None else None,
                        "fused_2q_blocks": ctr.plan.stats()["n_fused"] if ctr is not None and not args.blocks else None,
+                       "order_search": ("adaptive" if args.order_search else "fixed mix")
+                       if wl["kind"] in ("amps", "sweep_amps") else None,
                        "uniform_blocks": ({"block_qubits": args.blocks, "blocks": ctr.plan.stats()["n_fused"],
                                            "gemm_launches": ctr.plan.stats()["n_passes"]}
                                           if args.blocks and ctr is not None else None),

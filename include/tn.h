@@ -212,6 +212,19 @@ void tn_free_circuit(tn_circuit *c);
  * Allocates and uploads the plan's device tables on the current CUDA device unless
  * opts->flags has TN_PLAN_HOST_ONLY.  opts may be NULL (defaults). */
 tn_status tn_plan_contraction(const tn_circuit *c, const tn_plan_opts *opts, tn_plan **out);
+/* Tile autotuner of one plan (the paper fixes the contraction order before evaluation, Sec.
+ * 2.2.3; the tile size -- qubits per on-chip tile, which decides passes, phases and the generated
+ * kernels -- is left to the implementation and chosen here by measurement).  Plans the circuit
+ * with opts at every candidate tile size (tune->candidates, 0-terminated, each in [6, 13]; all
+ * zero = {10, 11, 12, 13}; opts->tile_qubits must be 0; not for network, Q4.28, block or host-only
+ * plans), times each plan's tn_contract_state on s (one warm-up call, the fastest of tune->reps
+ * calls, 0 = 3; CUDA events; all parameters zero) and returns the fastest plan in *out (the others
+ * are freed) and its tile size in *tile_out (optional).  Blocking: allocates and frees its own
+ * scratch device memory (a state, a workspace, zero parameters), synchronises s.  tune may be
+ * NULL; tune->flags and reserved must be zero. */
+typedef struct tn_tune_opts tn_tune_opts;
+tn_status tn_plan_contraction_tuned(const tn_circuit *c, const tn_plan_opts *opts, const tn_tune_opts *tune,
+                                   tn_stream_t s, tn_plan **out, int32_t *tile_out);
 /* Device workspace (bytes) that every contraction call of this plan needs. */
 tn_status tn_plan_workspace_bytes(const tn_plan *p, size_t *bytes);
 tn_status tn_plan_get_stats(const tn_plan *p, tn_plan_stats *stats);
@@ -370,13 +383,13 @@ tn_status tn_batch_test_stall(tn_batch *b, int32_t circ, int32_t pass, int64_t w
  * fastest kept).  Blocking: allocates and frees its own scratch device memory, synchronises s.
  * *out receives a batch that owns its plans (tn_free_batch frees them); tiles_out (optional,
  * n_circuits entries) receives the chosen tile sizes.  A circuit of n <= 12 qubits may also run
- * as one tile (T = n). */
-typedef struct {
-  int32_t candidates[8]; /* tile sizes in [6, 12], 0-terminated; all zero = {8, 9, 10, 11, 12} */
+ * as one tile (T = n).  Candidates here: tile sizes in [6, 12]; all zero = {8, 9, 10, 11, 12}. */
+struct tn_tune_opts {
+  int32_t candidates[8]; /* tile sizes, 0-terminated; all zero = the tuner's default set */
   int32_t reps;          /* timed launches per candidate; 0 = 3 */
   int32_t flags;         /* must be 0 */
   int64_t reserved[4];   /* must be 0 */
-} tn_tune_opts;
+};
 tn_status tn_batch_build_tuned(const tn_circuit *const *circuits, int32_t n_circuits, const tn_tune_opts *opts,
                                tn_stream_t s, tn_batch **out, int32_t *tiles_out);
 

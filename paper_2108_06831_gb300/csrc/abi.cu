@@ -446,6 +446,32 @@ tn_status tn_plan_contraction(const tn_circuit *c, const tn_plan_opts *opts, tn_
   return TN_OK;
 }
 
+tn_status tn_plan_contraction_tuned(const tn_circuit *c, const tn_plan_opts *opts, const tn_tune_opts *tune,
+                                   tn_stream_t s, tn_plan **out, int32_t *tile_out) {
+  TN_CHECK_ARG(c != nullptr && out != nullptr, "NULL argument");
+  *out = nullptr;
+  tn_plan_opts o;
+  std::memset(&o, 0, sizeof(o));
+  if (opts) o = *opts;
+  TN_CHECK_ARG(!(o.flags & (TN_PLAN_NETWORK | TN_PLAN_Q428 | TN_PLAN_BLOCKS | TN_PLAN_HOST_ONLY)),
+               "the tile autotuner takes state / expectation plans that run on the GPU");
+  TN_CHECK_ARG(o.tile_qubits == 0, "tile_qubits is what the autotuner chooses: leave it 0");
+  tn_tune_opts t;
+  std::memset(&t, 0, sizeof(t));
+  if (tune) t = *tune;
+  std::vector<int> cands;
+  for (int i = 0; i < 8 && t.candidates[i] != 0; ++i) {
+    TN_CHECK_ARG(t.candidates[i] >= kLowBits + 2 && t.candidates[i] <= kMaxTile, "candidate tile %d not in [6, %d]",
+                 t.candidates[i], kMaxTile);
+    cands.push_back(t.candidates[i]);
+  }
+  if (cands.empty()) cands = {10, 11, 12, 13};
+  TN_CHECK_ARG(t.reps >= 0 && t.reps <= 100, "reps=%d out of range", t.reps);
+  TN_CHECK_ARG(t.flags == 0, "flags must be zero");
+  for (int i = 0; i < 4; ++i) TN_CHECK_ARG(t.reserved[i] == 0, "reserved fields must be zero");
+  return plan_tuned(c, o, cands, t.reps > 0 ? t.reps : 3, reinterpret_cast<cudaStream_t>(s), out, tile_out);
+}
+
 tn_status tn_plan_workspace_bytes(const tn_plan *p, size_t *bytes) {
   TN_CHECK_ARG(p != nullptr && bytes != nullptr, "NULL argument");
   *bytes = p->ws_bytes;

@@ -194,3 +194,82 @@ tn_status batch_build_tuned(const tn_circuit *const *circuits, int n, const tn_t
 }
 
 }  // namespace tnq
+
+namespace tnq {
+
+// Tile autotuner of one state / expectation plan: the circuit is planned at every candidate tile
+// size (qubits per on-chip tile: passes, phases and generated kernels all change with it), each
+// plan's forward contraction is timed on the caller's stream (CUDA events, one warm-up call, the
+// fastest of reps calls; parameters all zero: the kernels' work does not depend on their values),
+// and the fastest plan is returned; the others are freed.
+tn_status plan_tuned(const tn_circuit *c, const tn_plan_opts &base, const std::vector<int> &cands, int reps,
+                     cudaStream_t s, tn_plan **out, int32_t *tile_out) {
+  DevBuf state, ws, params;
+  cudaEvent_t t0 = nullptr, t1 = nullptr;
+  cudaError_t e = cudaEventCreate(&t0);
+  if (e == cudaSuccess) e = cudaEventCreate(&t1);
+  if (e != cudaSuccess) return cuda_fail(e, "autotuner events");
+  tn_plan *best = nullptr;
+  float best_ms = 0.f;
+  int best_T = 0;
+  tn_status st = TN_OK;
+  for (int T : cands) {
+    if (T > c->n && T != cands.front()) continue;  // larger tiles than the register are all the same plan
+    tn_plan_opts po = base;
+    po.tile_qubits = std::min(T, c->n) >= kLowBits + 2 ? std::min(T, c->n) : 0;
+    tn_plan *p = nullptr;
+    st = tn_plan_contraction(c, &po, &p);
+    if (st != TN_OK) break;
+    const size_t sbytes = ((size_t)sizeof(float2) << c->n) * (size_t)po.batch;
+    e = state.reserve(sbytes);
+    if (e == cudaSuccess) e = ws.reserve(std::max<size_t>(p->ws_bytes, 16));
+    if (e == cudaSuccess && c->n_params > 0) {
+      e = params.reserve((size_t)c->n_params * (size_t)po.batch * sizeof(double));
+      if (e == cudaSuccess) e = cudaMemsetAsync(params.p, 0, (size_t)c->n_params * po.batch * sizeof(double), s);
+    }
+    if (e != cudaSuccess) {
+      tn_free_plan(p);
+      st = cuda_fail(e, "autotuner scratch");
+      break;
+    }
+    float ms_min = 0.f;
+    for (int r = 0; r <= reps && st == TN_OK; ++r) {
+      if (r > 0) e = cudaEventRecord(t0, s);
+      if (e == cudaSuccess)
+        st = tn_contract_state(p, c->n_params > 0 ? static_cast<const double *>(params.p) : nullptr, state.p, ws.p,
+                               reinterpret_cast<tn_stream_t>(s));
+      if (st != TN_OK) break;
+      if (r > 0) {
+        e = cudaEventRecord(t1, s);
+        if (e == cudaSuccess) e = cudaEventSynchronize(t1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
+        if (e == cudaSuccess && (r == 1 || ms < ms_min)) ms_min = ms;
+      }
+      if (e != cudaSuccess) st = cuda_fail(e, "autotuner timing");
+    }
+    if (st != TN_OK) {
+      tn_free_plan(p);
+      break;
+    }
+    if (best == nullptr || ms_min < best_ms) {
+      if (best) tn_free_plan(best);
+      best = p;
+      best_ms = ms_min;
+      best_T = p->T;
+    } else {
+      tn_free_plan(p);
+    }
+  }
+  cudaEventDestroy(t0);
+  cudaEventDestroy(t1);
+  if (st != TN_OK) {
+    if (best) tn_free_plan(best);
+    return st;
+  }
+  *out = best;
+  if (tile_out) *tile_out = best_T;
+  return TN_OK;
+}
+
+}  // namespace tnq

@@ -78,6 +78,11 @@ void batch_adopt_plans(tn_batch *b, const std::vector<tn_plan *> &plans);
 tn_status batch_build_tuned(const tn_circuit *const *circuits, int n, const tn_tune_opts &o, cudaStream_t s,
                             tn_batch **out, int32_t *tiles_out);
 
+// Tile autotuner of one plan: plans at each candidate tile size, times the forward contraction,
+// returns the fastest plan (the others freed).
+tn_status plan_tuned(const tn_circuit *c, const tn_plan_opts &base, const std::vector<int> &cands, int reps,
+                     cudaStream_t s, tn_plan **out, int32_t *tile_out);
+
 // Raise a kernel's dynamic shared-memory limit on the current device if `bytes` needs it.
 cudaError_t ensure_smem(const void *func, size_t bytes);
 

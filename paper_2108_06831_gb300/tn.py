@@ -99,6 +99,8 @@ _sigs = {
     "tn_free_batch": [_vp],
     "tn_batch_test_stall": [_vp, C.c_int32, C.c_int32, C.c_int64],
     "tn_batch_run_params": [_vp, _vp, _vp, _vp, _vp],
+    "tn_plan_contraction_tuned": [_vp, C.POINTER(TnPlanOpts), C.POINTER(TnTuneOpts), _vp, C.POINTER(_vp),
+                                  C.POINTER(C.c_int32)],
     "tn_batch_params": [_vp, C.POINTER(C.c_int32), C.POINTER(C.c_int64)],
     "tn_probe_fma_rate": [C.POINTER(C.c_double), C.POINTER(C.c_double)],
     "tn_batch_build_tuned": [C.POINTER(_vp), C.c_int32, C.POINTER(TnTuneOpts), _vp, C.POINTER(_vp),
@@ -188,7 +190,7 @@ class Plan:
     def __init__(self, ch: CircuitHandle, target: int = TARGET_STATE, precision: int = PREC_FP32, batch: int = 1,
                  tile_qubits: int = 0, host_only: bool = False, specialize: bool = True, network_bitstrings: int = 0,
                  max_intermediate_log2: int = 0, order_trials: int = 0, q428: bool = False, order_search: int = 0,
-                 fuse: bool = True, block_qubits: int = 0):
+                 fuse: bool = True, block_qubits: int = 0, tune: Optional[dict] = None):
         o = TnPlanOpts()
         o.order_trials = order_trials
         o.order_search = order_search
@@ -201,7 +203,18 @@ class Plan:
             o.flags |= PLAN_NETWORK
             o.amp_batch = network_bitstrings
         h = _vp()
-        _check(_lib.tn_plan_contraction(ch._h, C.byref(o), C.byref(h)), "tn_plan_contraction")
+        self.tuned_tile = None
+        if tune is not None:  # tile size picked by measurement (tn_plan_contraction_tuned)
+            t = TnTuneOpts()
+            for i, cnd in enumerate(list(tune.get("candidates", ()))[:8]):
+                t.candidates[i] = int(cnd)
+            t.reps = int(tune.get("reps", 0))
+            tile = C.c_int32()
+            _check(_lib.tn_plan_contraction_tuned(ch._h, C.byref(o), C.byref(t), _stream(tune.get("stream")),
+                                                  C.byref(h), C.byref(tile)), "tn_plan_contraction_tuned")
+            self.tuned_tile = tile.value
+        else:
+            _check(_lib.tn_plan_contraction(ch._h, C.byref(o), C.byref(h)), "tn_plan_contraction")
         self._h = h
         self.circuit = ch
         self.n_qubits, self.n_params, self.batch, self.target = ch.n_qubits, ch.n_params, batch, target
@@ -409,14 +422,14 @@ class Contractor:
 
     def __init__(self, circ: Circuit, target: int = TARGET_STATE, batch: int = 1, tile_qubits: int = 0,
                  precision: int = PREC_FP32, device=None, specialize: bool = True, fuse: bool = True,
-                 block_qubits: int = 0):
+                 block_qubits: int = 0, tune: Optional[dict] = None):
         torch = _torch()
         self.device = torch.device(device or "cuda")
         with torch.cuda.device(self.device):
             self.circuit_handle = CircuitHandle(circ)
             self.plan = Plan(self.circuit_handle, target=target, precision=precision, batch=batch,
                              tile_qubits=tile_qubits, specialize=specialize, fuse=fuse,
-                             block_qubits=block_qubits)
+                             block_qubits=block_qubits, tune=tune)
         self.n_qubits, self.batch, self.n_params = circ.n_qubits, batch, self.plan.n_params
         nb = max(self.plan.workspace_bytes, 16)
         self.workspace = torch.empty(nb, dtype=torch.uint8, device=self.device)

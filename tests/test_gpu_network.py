@@ -11,11 +11,11 @@ torch = pytest.importorskip("torch")
 TOL = 1e-5
 
 
-def _amps(circ, xs, B, precision, max_log2=0):
+def _amps(circ, xs, B, precision, max_log2=0, order_search=0):
     from paper_2108_06831_gb300 import tn
     ch = tn.CircuitHandle(circ)
     p = tn.Plan(ch, target=tn.TARGET_AMPLITUDES, network_bitstrings=B, precision=precision,
-                max_intermediate_log2=max_log2)
+                max_intermediate_log2=max_log2, order_search=order_search)
     ws = torch.empty(max(p.workspace_bytes, 16), dtype=torch.uint8, device="cuda")
     x = torch.as_tensor(np.asarray(xs, dtype=np.uint64).astype(np.int64), device="cuda")
     out = torch.full((len(xs),), complex(float("nan"), 0), dtype=torch.complex64, device="cuda")
@@ -189,3 +189,17 @@ def test_fig31_amplitude_mode_28_qubits():
     assert st["net_max_log2"] <= 28
     ref = np.array([contract_amplitude(c, int(x)) for x in xs[:4]])
     assert _rel(got[:4], ref) <= TOL
+
+
+@pytest.mark.parametrize("maker,B", [(lambda: C.grid(4, 5, 10, 81), 64), (lambda: C.paper_fig31(20, 8, 82), 64),
+                                     (lambda: C.random_circuit(16, 200, 83), 16)])
+def test_adaptive_order_search_plans(maker, B):
+    """Orders from the adaptive search (order_search = 1, the cross-entropy hyper-optimiser) run on
+    the GPU and give the same amplitudes as the state vector."""
+    from oracle.statevector import simulate_state
+    c = maker()
+    psi = simulate_state(c)
+    xs = C.random_bitstrings(c.n_qubits, B, 84)
+    got, st = _amps(c, xs, B, 1, order_search=1)
+    assert st["net_merges"] > 0
+    assert _rel(got, psi[xs.astype(np.int64)]) <= TOL

@@ -209,3 +209,23 @@ def test_max_size_32_qubits_closed_form():
     ref = np.prod(col[np.arange(n)[None, :], bits], axis=1)
     ref = ref * (-1.0) ** np.sum(bits[:, :-1] * bits[:, 1:], axis=1)
     assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= STATE_TOL
+
+
+def test_tile_autotuner_single_plan():
+    """tn_plan_contraction_tuned: the circuit planned at each candidate tile size, each plan's
+    contraction timed, the fastest returned; its tile is a candidate and its state matches the
+    oracle (parameterised circuit, batch of 2)."""
+    from oracle.statevector import simulate_state
+    tn = _tn()
+    c, p0 = C.brickwork(16, 10, 91, parameterized=True)
+    params = np.stack([p0, np.random.default_rng(92).uniform(0, 2 * np.pi, size=p0.shape)])
+    ctr = tn.Contractor(c, batch=2, tune={"candidates": (8, 10, 12), "reps": 2})
+    assert ctr.plan.tuned_tile in (8, 10, 12)
+    assert ctr.plan.stats()["tile_qubits"] == ctr.plan.tuned_tile
+    got = ctr.state(torch.as_tensor(params, device="cuda")).cpu().numpy()
+    torch.cuda.synchronize()
+    assert tn.sync_status() == tn.OK
+    for b in range(2):
+        assert rel_l2(got[b], simulate_state(c, params[b])) <= STATE_TOL
+    with pytest.raises(tn.TnError):  # tile_qubits is the tuner's choice
+        tn.Plan(tn.CircuitHandle(c), tile_qubits=10, tune={})
