@@ -152,6 +152,17 @@ struct alignas(16) FusedMember {
 // ---------------------------------------------------------------------------------------
 TNQ_HD void cset(double *o, int i, double re, double im) { o[2 * i] = re; o[2 * i + 1] = im; }
 
+// sin and cos of one angle with one shared argument reduction on the device (FP64 is slow on this
+// GPU, and every gate table is built per call from the parameters).
+TNQ_HD void sincos2(double x, double *s, double *c) {
+#if defined(__CUDA_ARCH__)
+  sincos(x, s, c);
+#else
+  *s = std::sin(x);
+  *c = std::cos(x);
+#endif
+}
+
 // Full 2x2 / 4x4 matrix of a gate kind (form FORM_U), or its derivative w.r.t. angle a
 // (FORM_D0 + a).  Returns the dimension (2 or 4); 0 for an unknown kind.
 TNQ_HD int gate_nqubits(int kind) {
@@ -181,27 +192,32 @@ TNQ_HD int gate_matrix(int kind, int form, const double *ang, const double *fixe
     case TN_GATE_SW:  // cos(pi/4) I - i sin(pi/4) (X+Y)/sqrt2
       cset(o, 0, r2, 0); cset(o, 1, -0.5, -0.5); cset(o, 2, 0.5, -0.5); cset(o, 3, r2, 0); break;
     case TN_GATE_RX: {
-      double c = cos(ang[0] * 0.5), s = sin(ang[0] * 0.5);
+      double c, s;
+      sincos2(ang[0] * 0.5, &s, &c);
       if (!deriv) { cset(o, 0, c, 0); cset(o, 1, 0, -s); cset(o, 2, 0, -s); cset(o, 3, c, 0); }
       else { cset(o, 0, -0.5 * s, 0); cset(o, 1, 0, -0.5 * c); cset(o, 2, 0, -0.5 * c); cset(o, 3, -0.5 * s, 0); }
       break;
     }
     case TN_GATE_RY: {
-      double c = cos(ang[0] * 0.5), s = sin(ang[0] * 0.5);
+      double c, s;
+      sincos2(ang[0] * 0.5, &s, &c);
       if (!deriv) { cset(o, 0, c, 0); cset(o, 1, -s, 0); cset(o, 2, s, 0); cset(o, 3, c, 0); }
       else { cset(o, 0, -0.5 * s, 0); cset(o, 1, -0.5 * c, 0); cset(o, 2, 0.5 * c, 0); cset(o, 3, -0.5 * s, 0); }
       break;
     }
     case TN_GATE_RZ: {
-      double c = cos(ang[0] * 0.5), s = sin(ang[0] * 0.5);
+      double c, s;
+      sincos2(ang[0] * 0.5, &s, &c);
       if (!deriv) { cset(o, 0, c, -s); cset(o, 3, c, s); }
       else { cset(o, 0, -0.5 * s, -0.5 * c); cset(o, 3, -0.5 * s, 0.5 * c); }
       break;
     }
     case TN_GATE_U3: {
-      double c = cos(ang[0] * 0.5), s = sin(ang[0] * 0.5);
-      double cp = cos(ang[1]), sp = sin(ang[1]), cl = cos(ang[2]), sl = sin(ang[2]);
-      double cpl = cos(ang[1] + ang[2]), spl = sin(ang[1] + ang[2]);
+      double c, s, cp, sp, cl, sl;
+      sincos2(ang[0] * 0.5, &s, &c);
+      sincos2(ang[1], &sp, &cp);
+      sincos2(ang[2], &sl, &cl);
+      const double cpl = cp * cl - sp * sl, spl = sp * cl + cp * sl;  // e^{i(p+l)}
       if (!deriv) {
         cset(o, 0, c, 0); cset(o, 1, -cl * s, -sl * s); cset(o, 2, cp * s, sp * s); cset(o, 3, cpl * c, spl * c);
       } else if (a == 0) {
@@ -217,7 +233,8 @@ TNQ_HD int gate_matrix(int kind, int form, const double *ang, const double *fixe
     case TN_GATE_CZ: cset(o, 0, 1, 0); cset(o, 5, 1, 0); cset(o, 10, 1, 0); cset(o, 15, -1, 0); break;
     case TN_GATE_CNOT: cset(o, 0, 1, 0); cset(o, 5, 1, 0); cset(o, 11, 1, 0); cset(o, 14, 1, 0); break;
     case TN_GATE_CP: {
-      double c = cos(ang[0]), s = sin(ang[0]);
+      double c, s;
+      sincos2(ang[0], &s, &c);
       if (!deriv) { cset(o, 0, 1, 0); cset(o, 5, 1, 0); cset(o, 10, 1, 0); cset(o, 15, c, s); }
       else { cset(o, 15, -s, c); }
       break;
@@ -225,11 +242,19 @@ TNQ_HD int gate_matrix(int kind, int form, const double *ang, const double *fixe
     case TN_GATE_SWAP: cset(o, 0, 1, 0); cset(o, 6, 1, 0); cset(o, 9, 1, 0); cset(o, 15, 1, 0); break;
     case TN_GATE_MAT1: for (int i = 0; i < 8; ++i) o[i] = fixed[i]; break;
     case KIND_V: {
-      double c = cos(ang[0] * 0.5), s = sin(ang[0] * 0.5), ca = cos(ang[1]), sa = sin(ang[1]);
+      double c, s, ca, sa;
+      sincos2(ang[0] * 0.5, &s, &c);
+      sincos2(ang[1], &sa, &ca);
       cset(o, 0, c, 0); cset(o, 1, -s * ca, -s * sa); cset(o, 2, s, 0); cset(o, 3, c * ca, c * sa);
       break;
     }
-    case KIND_P: cset(o, 0, 1, 0); cset(o, 3, cos(ang[0]), sin(ang[0])); break;
+    case KIND_P: {
+      double c, s;
+      sincos2(ang[0], &s, &c);
+      cset(o, 0, 1, 0);
+      cset(o, 3, c, s);
+      break;
+    }
     case TN_GATE_MAT2: for (int i = 0; i < 32; ++i) o[i] = fixed[i]; break;
     default: return 0;
   }
