@@ -1018,6 +1018,20 @@ tn_status jit_build(tn_plan &p, const std::vector<int> &op_kind, bool backward, 
     }
     kers[i] = k;
   }
+  {
+    // resident CTAs per SM of each pass kernel, queried once here (not per launch)
+    std::vector<int> &grid = backward ? p.jit_bwd_grid : p.jit_grid;
+    grid.assign(np, 1);
+    for (size_t i = 0; i < np; ++i) {
+      int per_sm = 0;
+      cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)kers[i], threads[i], smem[i]);
+      if (e != cudaSuccess) {
+        err = std::string("occupancy of a generated kernel: ") + cudaGetErrorString(e);
+        return TN_ERR_CUDA;
+      }
+      grid[i] = per_sm < 1 ? 1 : per_sm;
+    }
+  }
   if (!backward) {
     p.jit_cm_ptr.assign(np, nullptr);
     p.jit_cm_bytes.assign(np, 0);
@@ -1040,6 +1054,8 @@ tn_status jit_build(tn_plan &p, const std::vector<int> &op_kind, bool backward, 
 }
 
 void jit_release(tn_plan &p) {
+  p.jit_grid.clear();
+  p.jit_bwd_grid.clear();
   p.jit_cm_ptr.clear();
   p.jit_cm_bytes.clear();
   for (cudaLibrary_t l : p.jit_libs)

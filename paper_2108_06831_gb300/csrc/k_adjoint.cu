@@ -237,11 +237,8 @@ cudaError_t launch_backward(const tn_plan *p, const float2 *mats, long long mstr
       const PassDesc &h = p->bwd.passes[i];
       const int threads = p->jit_bwd_threads[i];
       const size_t smem = p->jit_bwd_smem[i];
-      int per_sm = 0;
-      cudaError_t e =
-          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)p->jit_bwd_kernels[i], threads, smem);
-      if (e != cudaSuccess) return e;
-      if (per_sm < 1) per_sm = 1;
+      const int per_sm = i < p->jit_bwd_grid.size() ? p->jit_bwd_grid[i] : 1;  // queried at load time
+      cudaError_t e = cudaSuccess;
       const long long n_tiles = 1ll << h.n_outer;
       long long gx = ((long long)num_sms() * per_sm + p->batch - 1) / p->batch;
       if (gx > n_tiles) gx = n_tiles;

@@ -172,10 +172,8 @@ cudaError_t launch_forward(const tn_plan *p, const float2 *mats, long long mstri
       const PassDesc &h = p->fwd.passes[i];
       const int threads = p->jit_threads[i];
       const size_t smem = p->jit_smem[i];
-      int per_sm = 0;
-      cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)p->jit_kernels[i], threads, smem);
-      if (e != cudaSuccess) return e;
-      if (per_sm < 1) per_sm = 1;
+      const int per_sm = i < p->jit_grid.size() ? p->jit_grid[i] : 1;  // resident CTAs per SM (load time)
+      cudaError_t e = cudaSuccess;
       long long work = (long long)p->batch << h.n_outer;
       long long grid = (long long)num_sms() * per_sm;
       if (grid > work) grid = work;

@@ -408,7 +408,7 @@ struct tn_plan {
   std::vector<size_t> jit_cm_bytes;  //   and the bytes the pass reads (copied before its launch)
   std::vector<cudaLibrary_t> jit_bwd_libs;
   std::vector<cudaKernel_t> jit_bwd_kernels;
-  std::vector<int> jit_bwd_threads;
+  std::vector<int> jit_bwd_threads, jit_bwd_grid;
   std::vector<size_t> jit_bwd_smem;
   size_t ws_bytes = 0;
   // workspace layout (byte offsets)
