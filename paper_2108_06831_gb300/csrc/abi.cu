@@ -143,7 +143,8 @@ tn_status call_mats(const tn_plan *p, const double *params, void *ws, cudaStream
   TN_CHECK_ARG(params != nullptr, "this circuit reads %d parameters: params_dev must not be NULL", p->n_params);
   TN_CHECK_ARG(ws != nullptr, "workspace_dev must not be NULL (plan needs %zu bytes)", p->ws_bytes);
   float2 *m = reinterpret_cast<float2 *>(static_cast<char *>(ws) + p->ws_mats);
-  TN_CUDA(launch_materialize(p->d_slots, (int)p->slots.size(), p->d_fused, params, p->n_params, p->batch, p->mstride,
+  TN_CUDA(launch_materialize(p->d_slots, (int)p->slots.size(), p->n_fused_slots, p->d_fused, params, p->n_params,
+                             p->batch, p->mstride,
                              m, s),
           "gate table kernel");
   *mats = m;
@@ -393,7 +394,11 @@ tn_status tn_plan_contraction(const tn_circuit *c, const tn_plan_opts *opts, tn_
   if (!p->host_only) {
     TN_CUDA(cudaGetDevice(&p->device), "cudaGetDevice");
     tn_status u = TN_OK;
-    if (u == TN_OK) u = upload(p->slots, &p->d_slots);
+    if (u == TN_OK) {  // device copy in the order the materialisation kernel reads (fused blocks first)
+      std::vector<MatSlot> ordered = p->slots;
+      p->n_fused_slots = order_slots_fused_first(ordered);
+      u = upload(ordered, &p->d_slots);
+    }
     if (u == TN_OK && !p->fused.empty()) u = upload(p->fused, &p->d_fused);
     if (u == TN_OK) u = upload(p->fwd.passes, &p->d_fwd_pass);
     if (u == TN_OK) u = upload(p->fwd.phases, &p->d_fwd_phase);
@@ -408,7 +413,7 @@ tn_status tn_plan_contraction(const tn_circuit *c, const tn_plan_opts *opts, tn_
         set_error("cudaMalloc of the fixed gate table: %s", cudaGetErrorString(e));
         u = TN_ERR_OOM;
       } else {
-        e = launch_materialize(p->d_slots, (int)p->slots.size(), p->d_fused, nullptr, 0, 1, p->mstride,
+        e = launch_materialize(p->d_slots, (int)p->slots.size(), p->n_fused_slots, p->d_fused, nullptr, 0, 1, p->mstride,
                                reinterpret_cast<float2 *>(p->d_fixed_mats), 0);
         if (e == cudaSuccess) e = cudaDeviceSynchronize();
         if (e != cudaSuccess) u = cuda_fail(e, "fixed gate table");

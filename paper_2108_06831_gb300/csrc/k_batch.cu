@@ -249,6 +249,7 @@ struct tn_batch {
   int n_params = 0;                                // parameters of all circuits, back to back
   std::vector<long long> param_offsets;            // first parameter of each circuit
   int n_slots = 0;                                 // matrix slots of the parameterised circuits
+  int n_fused_slots = 0;                           //   of which fused blocks (listed first)
   long long run_mats_elems = 0;                    // complex64 entries of the per-run table
   size_t ws_mats = 0;                              // byte offset of that table in the workspace
   tnq::MatSlot *d_slots = nullptr;
@@ -389,6 +390,7 @@ tn_status batch_build(const tn_plan *const *plans, int n, tn_batch **out) {
   up(tasks.data(), sizeof(BatchTask) * tasks.size(), (void **)&b->d_tasks);
   up(circs.data(), sizeof(BatchCirc) * circs.size(), (void **)&b->d_circs);
   up(passes.data(), sizeof(PassDesc) * passes.size(), (void **)&b->d_passes);
+  b->n_fused_slots = order_slots_fused_first(all_slots);
   if (!all_slots.empty()) up(all_slots.data(), sizeof(MatSlot) * all_slots.size(), (void **)&b->d_slots);
   if (!all_fused.empty()) up(all_fused.data(), sizeof(FusedMember) * all_fused.size(), (void **)&b->d_fused);
   if (e != cudaSuccess) {
@@ -415,7 +417,7 @@ cudaError_t batch_run(const tn_batch *b, const double *params, float2 *states, v
   cudaError_t e = cudaMemsetAsync(ws, 0, b->ws_mats, s);
   if (e != cudaSuccess) return e;
   if (b->n_slots > 0) {  // every parameterised circuit's gate table, one kernel
-    e = launch_materialize(b->d_slots, b->n_slots, b->d_fused, params, b->n_params, 1, 0, run_mats, s);
+    e = launch_materialize(b->d_slots, b->n_slots, b->n_fused_slots, b->d_fused, params, b->n_params, 1, 0, run_mats, s);
     if (e != cudaSuccess) return e;
   }
   const size_t smem = ((size_t)sizeof(float2) << kBatchT) + ((size_t)1 << (kBatchT - kLowBits)) * sizeof(long long) +

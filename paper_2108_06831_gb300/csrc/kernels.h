@@ -10,8 +10,11 @@ namespace tnq {
 int num_sms();  // SM count of the current device (cached per device)
 
 // Matrix tables: write the complex64 entries of every slot for each batch element.
-cudaError_t launch_materialize(const MatSlot *d_slots, int n_slots, const FusedMember *d_fused, const double *params,
-                               int n_params, int batch, long long mstride, float2 *out, cudaStream_t s);
+cudaError_t launch_materialize(const MatSlot *d_slots, int n_slots, int n_fused_slots, const FusedMember *d_fused,
+                               const double *params, int n_params, int batch, long long mstride, float2 *out,
+                               cudaStream_t s);
+// Reorders a slot table for launch_materialize (fused blocks first); returns their count.
+int order_slots_fused_first(std::vector<MatSlot> &slots);
 
 // Kernel (a): all forward passes of a plan (state <- U_G .. U_1 |init>).
 cudaError_t launch_forward(const tn_plan *p, const float2 *mats, long long mstride, float2 *state, cudaStream_t s);

@@ -152,11 +152,23 @@ struct alignas(16) FusedMember {
 // ---------------------------------------------------------------------------------------
 TNQ_HD void cset(double *o, int i, double re, double im) { o[2 * i] = re; o[2 * i + 1] = im; }
 
-// sin and cos of one angle with one shared argument reduction on the device (FP64 is slow on this
-// GPU, and every gate table is built per call from the parameters).
+// sin and cos of one angle.  On the device, where FP64 arithmetic runs at a small fraction of the
+// FP32 rate and every gate table is built per call from the parameters: the angle is reduced to
+// [-pi, pi] in FP64, sin and cos of its FP32 rounding xf come from the FP32 routine, and the
+// rounding residual d = x - xf (exact in FP64) is put back to first order, sin x = sin xf +
+// d cos xf, cos x = cos xf - d sin xf (the dropped d^2 / 2 term is below 1e-14): the result is
+// as accurate as the FP32 routine, about 1e-7, comparable to the complex64 rounding the entries
+// are stored with.  On the host: the FP64 library functions.
 TNQ_HD void sincos2(double x, double *s, double *c) {
 #if defined(__CUDA_ARCH__)
-  sincos(x, s, c);
+  const double two_pi = 6.283185307179586476925287;
+  const double xr = x - two_pi * rint(x * 0.159154943091895335768884);
+  const float xf = (float)xr;
+  float sf, cf;
+  sincosf(xf, &sf, &cf);
+  const double d = xr - (double)xf;
+  *s = (double)sf + d * (double)cf;
+  *c = (double)cf - d * (double)sf;
 #else
   *s = std::sin(x);
   *c = std::cos(x);
@@ -388,6 +400,7 @@ struct tn_plan {
   std::vector<tnq::MatSlot> slots;  // forward + adjoint + derivative entries
   std::vector<tnq::FusedMember> fused;  // members of the forward plan's F2 gates
   int n_fused = 0;                      // F2 gates in the forward plan
+  int n_fused_slots = 0;                // F2 slots (listed first in d_slots)
   int mstride;                      // complex64 entries per batch element's matrix table
   bool param_dependent;
   PassPlan fwd, bwd;
