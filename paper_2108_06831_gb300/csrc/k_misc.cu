@@ -9,21 +9,67 @@
 namespace tnq {
 
 // Gate tensors are built once per call from the parameters (angles in FP64, entries stored as
-// complex64).  The slot array lists the fused blocks (KIND_F2) first: each fused block and batch
-// element takes one warp -- lane m evaluates member m's matrix embedded as a 4x4, then lanes
-// 0..15 form the product one entry each, member by member, and store it in the packed layout
-// (SHAPE_M4X); every other slot and batch element takes one thread (one gate's matrix).
+// complex64).  The slot array lists the fused blocks (KIND_F2) first.  Few fused blocks (small
+// batches): each block and batch element takes one warp -- lane m evaluates member m's matrix
+// embedded as a 4x4, then lanes 0..15 form the product one entry each, member by member.  Many
+// (kFusedPerThread or more): one thread each, members applied in turn to a 4x4 held by the thread
+// (all lanes busy; FP64 throughput is what bounds this on GB300).  Either way the product is
+// stored in the packed layout (SHAPE_M4X).  Every other slot and batch element takes one thread.
 constexpr int kMatWarps = 4;
+constexpr long long kFusedPerThread = 1024;  // fused blocks x batch from which each takes one thread
+
+// One regular slot (one gate's matrix) for one batch element; prow: its parameters (may be NULL).
+__device__ void materialize_one(const MatSlot &s, const double *prow, float2 *table) {
+  double ang[3] = {s.angle[0], s.angle[1], s.angle[2]};
+  for (int a = 0; a < 3; ++a)
+    for (int q = 0; q < 2; ++q)
+      if (s.pidx[a][q] >= 0) ang[a] += prow[s.pidx[a][q]];
+  double tmp[32];
+  float ent[32];
+  const int n = slot_entries(s, ang, tmp, ent);
+  float2 *dst = table + s.offset;
+  for (int i = 0; i < n; ++i) dst[i] = make_float2(ent[2 * i], ent[2 * i + 1]);
+}
 
 __global__ void __launch_bounds__(32 * kMatWarps) k_materialize(const MatSlot *__restrict__ slots, int n_slots,
                                                                int n_fused_slots,
                                                                const FusedMember *__restrict__ fused,
                                                                const double *__restrict__ params, int n_params,
-                                                               int batch, long long mstride, float2 *__restrict__ out) {
+                                                               int batch, long long mstride, float2 *__restrict__ out,
+                                                               int fused_per_thread) {
   __shared__ double emb[kMatWarps][kMaxFusedMembers][32];
   __shared__ double acc[kMatWarps][2][32];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long long gw = (long long)blockIdx.x * kMatWarps + w;  // global warp
+  if (fused_per_thread) {
+    // many fused blocks (large batches): one thread each, every lane busy in FP64
+    const long long n_ft = (long long)n_fused_slots * batch;
+    const long long n_fwt = (n_ft + 31) / 32;                    // warps of the fused blocks
+    if (gw < n_fwt) {
+      const long long t = gw * 32 + lane;
+      if (t >= n_ft) return;
+      const int b = (int)(t / n_fused_slots);
+      const MatSlot &s = slots[t % n_fused_slots];
+      const double *prow = params ? params + (long long)b * n_params : nullptr;
+      double M[32];
+      for (int i = 0; i < 32; ++i) M[i] = (i & 1) == 0 && ((i >> 1) % 5) == 0 ? 1.0 : 0.0;
+      for (int m = 0; m < s.fuse_count; ++m) fused_apply_member(fused[s.fuse_begin + m], prow, M);
+      float2 *dst = out + (long long)b * mstride + s.offset;
+      for (int k = 0; k < 16; ++k) {
+        const float re = (float)M[2 * k], im = (float)M[2 * k + 1];
+        dst[2 * k] = make_float2(re, re);
+        dst[2 * k + 1] = make_float2(-im, im);
+      }
+      return;
+    }
+    const int n_reg = n_slots - n_fused_slots;
+    const long long t = (gw - n_fwt) * 32 + lane;
+    if (t >= (long long)n_reg * batch) return;
+    const int b = (int)(t / n_reg);
+    materialize_one(slots[n_fused_slots + t % n_reg], params ? params + (long long)b * n_params : nullptr,
+                    out + (long long)b * mstride);
+    return;
+  }
   const long long n_fw = (long long)n_fused_slots * batch;      // warps of the fused blocks
   if (gw < n_fw) {
     const int b = (int)(gw / n_fused_slots);
@@ -63,25 +109,19 @@ __global__ void __launch_bounds__(32 * kMatWarps) k_materialize(const MatSlot *_
   const long long t = (gw - n_fw) * 32 + lane;
   if (t >= (long long)n_reg * batch) return;
   const int b = (int)(t / n_reg);
-  const MatSlot &s = slots[n_fused_slots + t % n_reg];
-  float2 *dst = out + (long long)b * mstride + s.offset;
-  double ang[3] = {s.angle[0], s.angle[1], s.angle[2]};
-  for (int a = 0; a < 3; ++a)
-    for (int q = 0; q < 2; ++q)
-      if (s.pidx[a][q] >= 0) ang[a] += params[(long long)b * n_params + s.pidx[a][q]];
-  double tmp[32];
-  float ent[32];
-  const int n = slot_entries(s, ang, tmp, ent);
-  for (int i = 0; i < n; ++i) dst[i] = make_float2(ent[2 * i], ent[2 * i + 1]);
+  materialize_one(slots[n_fused_slots + t % n_reg], params ? params + (long long)b * n_params : nullptr,
+                  out + (long long)b * mstride);
 }
 
 cudaError_t launch_materialize(const MatSlot *d_slots, int n_slots, int n_fused_slots, const FusedMember *d_fused,
                                const double *params, int n_params, int batch, long long mstride, float2 *out,
                                cudaStream_t s) {
-  const long long warps = (long long)n_fused_slots * batch + ((long long)(n_slots - n_fused_slots) * batch + 31) / 32;
+  const long long nf = (long long)n_fused_slots * batch, nr = (long long)(n_slots - n_fused_slots) * batch;
+  const int per_thread = nf >= kFusedPerThread ? 1 : 0;
+  const long long warps = (per_thread ? (nf + 31) / 32 : nf) + (nr + 31) / 32;
   if (warps == 0) return cudaSuccess;
   k_materialize<<<(unsigned)((warps + kMatWarps - 1) / kMatWarps), 32 * kMatWarps, 0, s>>>(
-      d_slots, n_slots, n_fused_slots, d_fused, params, n_params, batch, mstride, out);
+      d_slots, n_slots, n_fused_slots, d_fused, params, n_params, batch, mstride, out, per_thread);
   return cudaGetLastError();
 }
 

@@ -152,23 +152,11 @@ struct alignas(16) FusedMember {
 // ---------------------------------------------------------------------------------------
 TNQ_HD void cset(double *o, int i, double re, double im) { o[2 * i] = re; o[2 * i + 1] = im; }
 
-// sin and cos of one angle.  On the device, where FP64 arithmetic runs at a small fraction of the
-// FP32 rate and every gate table is built per call from the parameters: the angle is reduced to
-// [-pi, pi] in FP64, sin and cos of its FP32 rounding xf come from the FP32 routine, and the
-// rounding residual d = x - xf (exact in FP64) is put back to first order, sin x = sin xf +
-// d cos xf, cos x = cos xf - d sin xf (the dropped d^2 / 2 term is below 1e-14): the result is
-// as accurate as the FP32 routine, about 1e-7, comparable to the complex64 rounding the entries
-// are stored with.  On the host: the FP64 library functions.
+// sin and cos of one angle with one shared argument reduction on the device (FP64 is slow on this
+// GPU, and every gate table is built per call from the parameters).
 TNQ_HD void sincos2(double x, double *s, double *c) {
 #if defined(__CUDA_ARCH__)
-  const double two_pi = 6.283185307179586476925287;
-  const double xr = x - two_pi * rint(x * 0.159154943091895335768884);
-  const float xf = (float)xr;
-  float sf, cf;
-  sincosf(xf, &sf, &cf);
-  const double d = xr - (double)xf;
-  *s = (double)sf + d * (double)cf;
-  *c = (double)cf - d * (double)sf;
+  sincos(x, s, c);
 #else
   *s = std::sin(x);
   *c = std::cos(x);
@@ -304,6 +292,66 @@ TNQ_HD int slot_entries(const MatSlot &s, const double *ang, double *tmp /*32*/,
   return 0;
 }
 
+
+// M <- G M for one member of a fused block, M a 4x4 indexed 2 bit(a) + bit(b) (FP64 (re, im)
+// pairs): a one-qubit member mixes pairs of rows (half the work of a dense product), a diagonal
+// two-qubit member scales rows, any other two-qubit member is a dense product.
+TNQ_HD void fused_apply_member(const FusedMember &f, const double *param_row, double *M /*32*/) {
+  double ang[3] = {f.angle[0], f.angle[1], f.angle[2]};
+  for (int a = 0; a < 3; ++a)
+    for (int k = 0; k < 2; ++k)
+      if (f.pidx[a][k] >= 0 && param_row) ang[a] += param_row[f.pidx[a][k]];
+  double g[32];
+  const int dim = gate_matrix(f.kind, FORM_U, ang, f.mat, g);
+  if (dim == 2) {
+    const int step = f.role == ROLE_A ? 2 : 1;  // rows i and i + step differ in the member's qubit
+    for (int i = 0; i < 4; ++i) {
+      if (i & step) continue;
+      const int i1 = i + step;
+      for (int j = 0; j < 4; ++j) {
+        const double xr = M[2 * (4 * i + j)], xi = M[2 * (4 * i + j) + 1];
+        const double yr = M[2 * (4 * i1 + j)], yi = M[2 * (4 * i1 + j) + 1];
+        M[2 * (4 * i + j)] = g[0] * xr - g[1] * xi + g[2] * yr - g[3] * yi;
+        M[2 * (4 * i + j) + 1] = g[0] * xi + g[1] * xr + g[2] * yi + g[3] * yr;
+        M[2 * (4 * i1 + j)] = g[4] * xr - g[5] * xi + g[6] * yr - g[7] * yi;
+        M[2 * (4 * i1 + j) + 1] = g[4] * xi + g[5] * xr + g[6] * yi + g[7] * yr;
+      }
+    }
+    return;
+  }
+  // the member's own index is 2 bit(first) + bit(second); ROLE_BA swaps the two bits
+  auto perm = [&](int i) { return f.role == ROLE_AB ? i : ((i & 1) << 1) | (i >> 1); };
+  bool diag = true;
+  for (int i = 0; i < 4 && diag; ++i)
+    for (int j = 0; j < 4; ++j)
+      if (i != j && (g[2 * (4 * i + j)] != 0.0 || g[2 * (4 * i + j) + 1] != 0.0)) diag = false;
+  if (diag) {
+    for (int i = 0; i < 4; ++i) {
+      const int ii = perm(i);
+      const double dr = g[2 * (5 * ii)], di = g[2 * (5 * ii) + 1];
+      for (int j = 0; j < 4; ++j) {
+        const double xr = M[2 * (4 * i + j)], xi = M[2 * (4 * i + j) + 1];
+        M[2 * (4 * i + j)] = dr * xr - di * xi;
+        M[2 * (4 * i + j) + 1] = dr * xi + di * xr;
+      }
+    }
+    return;
+  }
+  double r[32];
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) {
+      double re = 0.0, im = 0.0;
+      for (int q = 0; q < 4; ++q) {
+        const double ur = g[2 * (4 * perm(i) + perm(q))], ui = g[2 * (4 * perm(i) + perm(q)) + 1];
+        const double xr = M[2 * (4 * q + j)], xi = M[2 * (4 * q + j) + 1];
+        re += ur * xr - ui * xi;
+        im += ur * xi + ui * xr;
+      }
+      r[2 * (4 * i + j)] = re;
+      r[2 * (4 * i + j) + 1] = im;
+    }
+  for (int i = 0; i < 32; ++i) M[i] = r[i];
+}
 
 // One member of a fused block as a 4x4 on (a, b), indexed 2 bit(a) + bit(b), FP64 (re, im) pairs.
 TNQ_HD void fused_embed(const FusedMember &f, const double *param_row, double *e /*32*/) {
