@@ -334,7 +334,9 @@ tn_status tn_plan_contraction(const tn_circuit *c, const tn_plan_opts *opts, tn_
     *out = p;
     return TN_OK;
   }
-  const bool fuse = !(o.flags & TN_PLAN_NO_FUSION);
+  // Precontracted blocks cost a per-call FP64 product when the circuit reads parameters; below
+  // kFuseMinQubitsParam qubits that costs more than the smaller state saves in the passes.
+  const bool fuse = !(o.flags & TN_PLAN_NO_FUSION) && (c->n_params == 0 || c->n >= kFuseMinQubitsParam);
   const tn_circuit fwd_circ = push_phases(fuse ? fuse_pairs(*c, p->fused) : *c, p->fused);
   for (const TnGate &g : fwd_circ.gates) p->n_fused += g.kind == KIND_F2 ? 1 : 0;
   tn_status st = build_pass_plan(fwd_circ, T, K, false, p->slots, p->fwd, err);

@@ -166,30 +166,13 @@ __global__ void __launch_bounds__(kBatchThreads, 3) k_batch_exec(const BatchTask
         sm[swz(li)] = make_float2(1.f, 0.f);
       }
     } else {
-      // written by other CTAs during the previous pass: read through L2, never a stale L1 line.
-      // A thread's loads go out four at a time before their shared-memory stores, so their
-      // latencies overlap instead of adding up.
-      constexpr int kLd = (1 << kBatchT) / 2 / kBatchThreads, kGrp = 4;
-#pragma unroll
-      for (int q0 = 0; q0 < kLd; q0 += kGrp) {
-        float4 v[kGrp];
-#pragma unroll
-        for (int q = 0; q < kGrp; ++q) {
-          const int c = threadIdx.x + (q0 + q) * kBatchThreads;
-          if (c < (tile >> 1)) {
-            const int i = c << 1;
-            v[q] = __ldcg(reinterpret_cast<const float4 *>(st + (long long)base + run_off[i >> L] + (i & lowmask)));
-          }
-        }
-#pragma unroll
-        for (int q = 0; q < kGrp; ++q) {
-          const int c = threadIdx.x + (q0 + q) * kBatchThreads;
-          if (c < (tile >> 1)) {
-            const int i = c << 1;
-            sm[swz(i)] = make_float2(v[q].x, v[q].y);
-            sm[swz(i + 1)] = make_float2(v[q].z, v[q].w);
-          }
-        }
+      // written by other CTAs during the previous pass: read through L2, never a stale L1 line
+      for (int c = threadIdx.x; c < (tile >> 1); c += blockDim.x) {
+        const int i = c << 1;
+        const long long g = (long long)base + run_off[i >> L] + (i & lowmask);
+        const float4 v = __ldcg(reinterpret_cast<const float4 *>(st + g));
+        sm[swz(i)] = make_float2(v.x, v.y);
+        sm[swz(i + 1)] = make_float2(v.z, v.w);
       }
     }
     __syncthreads();
