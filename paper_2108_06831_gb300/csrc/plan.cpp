@@ -160,6 +160,8 @@ double fuse_cost(const TnGate &g) {
   }
 }
 constexpr double kFusedCost = 8.0;
+// gates of one block: the phase-pushing rewrite may add two leading phase members later
+constexpr int kMaxBlockGates = kMaxFusedMembers - 2;
 constexpr double kFuseMargin = 0.5;  // fuse only when it saves more than this
 
 }  // namespace
@@ -232,7 +234,7 @@ tn_circuit fuse_pairs(const tn_circuit &c, std::vector<FusedMember> &fused) {
     if (gate_nqubits(g.kind) == 1) {
       const int q = g.q[0];
       int bi = open[(size_t)q];
-      if (bi >= 0 && (int)blocks[(size_t)bi].gates.size() >= kMaxFusedMembers) {
+      if (bi >= 0 && (int)blocks[(size_t)bi].gates.size() >= kMaxBlockGates) {
         close(q);
         bi = -1;
       }
@@ -247,14 +249,14 @@ tn_circuit fuse_pairs(const tn_circuit &c, std::vector<FusedMember> &fused) {
     }
     const int a = g.q[0], b = g.q[1];
     const int A = open[(size_t)a], B = open[(size_t)b];
-    if (A >= 0 && A == B && (int)blocks[(size_t)A].gates.size() < kMaxFusedMembers) {
+    if (A >= 0 && A == B && (int)blocks[(size_t)A].gates.size() < kMaxBlockGates) {
       add(A, gi);
       continue;
     }
     const bool a_free = A < 0 || blocks[(size_t)A].qb < 0;
     const bool b_free = B < 0 || blocks[(size_t)B].qb < 0;
     const size_t na = A >= 0 ? blocks[(size_t)A].gates.size() : 0, nb = B >= 0 ? blocks[(size_t)B].gates.size() : 0;
-    if (A != B && a_free && b_free && (int)(na + nb) < kMaxFusedMembers) {
+    if (A != B && a_free && b_free && (int)(na + nb) < kMaxBlockGates) {
       Block nbk;
       nbk.qa = a;
       nbk.qb = b;
@@ -372,7 +374,7 @@ tn_circuit push_phases(const tn_circuit &c, std::vector<FusedMember> &fused) {
         pp = Pending();
       }
       for (int k = 0; k < g.fuse_count; ++k) fused.push_back(fused[(size_t)(g.fuse_begin + k)]);
-      f.fuse_count = (int)fused.size() - f.fuse_begin;
+      f.fuse_count = (int)fused.size() - f.fuse_begin;  // at most kMaxFusedMembers (fuse_pairs leaves room)
       o.gates.push_back(f);
       continue;
     }
