@@ -124,7 +124,8 @@ typedef enum { TN_PREC_FP32 = 0, TN_PREC_3XTF32 = 1, TN_PREC_SPLIT_BF16 = 2 } tn
                            * call into one 2^k x 2^k unitary (FP64, from the parameters), and applied
                            * to the state viewed as [2^(N-k)] x [2^k] by the batched complex GEMM in
                            * opts->precision (FP32 on the CUDA cores, 3XTF32 or SPLIT_BF16 on the
-                           * tensor cores).  Needs k + 7 <= n_qubits and a power-of-two batch. */
+                           * tensor cores).  Needs k + 7 <= n_qubits (and n_qubits <= k + 23 on the
+                           * tensor cores) and a power-of-two batch. */
 #define TN_PLAN_NO_SPECIALIZE 2 /* run the interpreting gate-apply kernel instead of plan-specialised
                                  * kernels (those are generated as CUDA C++ and compiled with NVRTC
                                  * when the plan is built; compiled code is cached on disk) */

@@ -53,6 +53,10 @@ tn_status plan_blocks(const tn_circuit &c, int k, int batch, int precision, Bloc
     err = "uniform blocks need k + 7 <= n_qubits <= 34 (at least 128 rows per GEMM)";
     return TN_ERR_UNSUPPORTED;
   }
+  if (precision != TN_PREC_FP32 && N - k > 23) {
+    err = "uniform blocks on the tensor cores take at most k + 23 qubits (2^23 rows per GEMM)";
+    return TN_ERR_UNSUPPORTED;
+  }
   if (batch < 1 || (batch & (batch - 1)) != 0) {
     err = "uniform blocks take a power-of-two batch";
     return TN_ERR_UNSUPPORTED;

@@ -363,8 +363,13 @@ cudaError_t launch_cgemm_fp32(long long batch, long long M, long long N, long lo
   const OutMap ident;
   const OutMap &m = om ? *om : ident;
   const long long total = batch * M * N;
-  if (K <= 64 && (double)total * (double)K <= (double)kSmallWork) {
-    k_cgemm_small<<<(unsigned)std::min<long long>((total + 255) / 256, 1024), 256, 0, s>>>(M, N, K, total, A, B, C, m);
+  // small merges, and tall narrow ones (at most four output columns, where the tiled kernel's
+  // 8-column tiles would mostly compute padding) of any size: one thread per output element
+  // (on the Fig. 3.1 amplitude sweep: up to 2 columns 12.1 ms per step, up to 4 12.0, up to 8
+  // 13.1, none 22.4)
+  if (K <= 64 && ((double)total * (double)K <= (double)kSmallWork || N <= 4)) {
+    const long long blocks = std::min<long long>((total + 255) / 256, (long long)num_sms() * 16);
+    k_cgemm_small<<<(unsigned)blocks, 256, 0, s>>>(M, N, K, total, A, B, C, m);
     return cudaGetLastError();
   }
   if (K <= 8) return launch_k<8>(batch, M, N, K, A, B, C, P, m, s);
