@@ -434,6 +434,24 @@ std::string gen_pass(const tn_plan &p, int pi, const std::vector<int> &op_kind, 
   }
   snprintf(buf, sizeof buf, "    float2 *st = state + (b << %d);", N);
   E.line(buf);
+  if (pd.init_mode && pd.n_outer > 0) {
+    // a basis state is zero outside the one tile that holds it: store zeros, skip the phases
+    unsigned long long outer_mask = 0;
+    for (int j = 0; j < pd.n_outer; ++j) outer_mask |= 1ull << pd.outer_pos[j];
+    snprintf(buf, sizeof buf, "    if ((init_basis & %lluull) != base) {", outer_mask);
+    E.line(buf);
+    for (int k = 0; k < chunks; ++k) {
+      const int ik = 2 * k * NTHR;
+      long long depk = 0;
+      for (int j = 0; j < T; ++j)
+        if ((ik >> j) & 1) depk |= 1ll << pd.tile_pos[j];
+      snprintf(buf, sizeof buf,
+               "      *reinterpret_cast<float4 *>(st + base + dep_t + %lldll) = make_float4(0.f, 0.f, 0.f, 0.f);", depk);
+      E.line(buf);
+    }
+    E.line("      continue;");
+    E.line("    }");
+  }
   if (cmem) {
     snprintf(buf, sizeof buf, "    const float4 *M4 = tnq_cm%d - %d;", pi, pd.mat_begin / 2);
     E.line(buf);

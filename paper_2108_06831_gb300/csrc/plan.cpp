@@ -628,7 +628,8 @@ tn_status build_pass_plan(const tn_circuit &c, int T, int K, bool adjoint, std::
         }
         out.ops.push_back(op);
         out.op_gate.push_back(g);
-        out.flops += op_flops(gc.type, c.gates[g].kind) * (double)(1ull << N);
+        // the first pass computes only the tile that holds the basis state
+        out.flops += op_flops(gc.type, c.gates[g].kind) * (double)(1ull << (pd.init_mode ? nS : N));
         ++emitted;
       }
       if (emitted == 0) break;

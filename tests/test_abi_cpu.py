@@ -59,14 +59,16 @@ def test_host_only_plans():
         assert s["n_ops"] == len(c.gates) + 24 and s["n_fused"] == 0
         assert s["tile_qubits"] == T and s["reg_qubits"] == 4
         assert s["n_passes"] >= 2
-        # flops as executed: V costs 10 real flops per amplitude, a final phase 3, CZ none
-        assert s["flops"] == pytest.approx((10.0 * n_u3 + 3.0 * 24) * (1 << 24))
+        # flops as executed: V costs 10 real flops per amplitude, a final phase 3, CZ none; the
+        # first pass computes only the tile holding |x0> (the rest of a basis state stays zero)
+        full = (10.0 * n_u3 + 3.0 * 24) * (1 << 24)
+        assert 0.8 * full < s["flops"] < full
         # precontracted: each even-layer CZ pair with the U3s of its two qubits in that layer and
         # the next becomes one dense 4x4 (12 per two layers); the odd-layer CZs stay
         f = tn.Plan(ch, tile_qubits=T, host_only=True).stats()
         assert f["n_fused"] == 12 * 10
         assert f["n_ops"] == 120 + (n_cz - 120)
-        assert f["flops"] == pytest.approx(30.0 * 120 * (1 << 24))
+        assert 0.8 * 30.0 * 120 * (1 << 24) < f["flops"] < 30.0 * 120 * (1 << 24)
         assert f["n_phases"] < s["n_phases"]
     small = tn.Plan(tn.CircuitHandle(C.brickwork(10, 8, 1000)[0]), host_only=True).stats()
     assert small["tile_qubits"] == 10 and small["n_passes"] <= 2  # one tile; code budget may split it
