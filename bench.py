@@ -35,6 +35,9 @@ METRIC = "amplitudes/s, grads/s & % roofline; split-prec+batched vs plain FP32 a
 # (set_fp32_peak); the nominal rate from the device's SM count and maximum clock is reported beside it
 FP32_ALU_PEAK_TFLOPS = None
 FP32_ALU_PEAK_SRC = None
+# circuits of this many qubits and more run their own generated pass kernels inside a batch (the
+# library's rule for plans with generated kernels; the tuned batch builds such plans for them)
+SERVE_WIDE = 19
 
 
 def set_fp32_peak(tn, torch, dev):
@@ -521,10 +524,14 @@ def main():
     elif wl["kind"] == "serve":
         circs = C.serving_mix(wl["batch"], wl["seed"])
         handles = [tn.CircuitHandle(c) for c in circs]
-        plans = [tn.Plan(h, specialize=False) for h in handles]
         t_tune = time.perf_counter()
-        bat = tn.Batch.tuned(handles)  # tile sizes picked by measurement (untimed setup)
+        # tile sizes of the executor's circuits picked by measurement; circuits of SERVE_WIDE qubits
+        # and more get generated kernels (compiled in parallel) run on side streams (untimed setup)
+        bat = tn.Batch.tuned(handles)
         t_tune = time.perf_counter() - t_tune
+        # the sequential comparison: each circuit on its own, wide ones through their generated kernels
+        plans = [tn.Plan(h, specialize=c.n_qubits >= SERVE_WIDE) for h, c in zip(handles, circs)]
+        wide_passes = sum(p.stats()["n_passes"] for p, c in zip(plans, circs) if c.n_qubits >= SERVE_WIDE)
         tiles_by_n = {}
         for c, t in zip(circs, bat.tiles):
             tiles_by_n.setdefault(c.n_qubits, set()).add(t)
@@ -538,7 +545,7 @@ def main():
             # the brickwork halves' U3 angles as per-run parameters: plans at the tiles the autotuner
             # picked for the same circuits with fixed angles, gate tables built inside each run
             circs_p, params_p = C.serving_mix_params(wl["batch"], wl["seed"])
-            pplans = [tn.Plan(tn.CircuitHandle(c), tile_qubits=t, specialize=False)
+            pplans = [tn.Plan(tn.CircuitHandle(c), tile_qubits=t, specialize=c.n_qubits >= SERVE_WIDE)
                       for c, t in zip(circs_p, bat.tiles)]
             bat = tn.Batch(pplans)
             flat = np.zeros(max(bat.n_params, 1))
@@ -557,7 +564,8 @@ def main():
 
         def step():
             graph.replay()
-        launches_per_step = 2 if run_params is not None else 1  # (gate tables +) the persistent kernel
+        # (gate tables +) the persistent kernel + the wide circuits' pass kernels
+        launches_per_step = (2 if run_params is not None else 1) + wide_passes
         kernel_only = None
         ctr = None
         # the comparison: every circuit contracted on its own, one after another
@@ -980,7 +988,10 @@ def main():
             seq_step()
         sms = timed(seq_step, max(1, args.steps // 2))
         line["config"].update({"circuits": batch, "amplitudes_per_step": units_per_step,
-                               "launch": "one persistent kernel in a CUDA graph",
+                               "launch": (f"one CUDA graph: the persistent kernel for the circuits under {SERVE_WIDE} "
+                                          f"qubits, beside the generated pass kernels of the "
+                                          f"{sum(1 for c in circs if c.n_qubits >= SERVE_WIDE)} wider ones on 4 "
+                                          f"side streams"),
                                "tiles_by_qubits": {str(k): sorted(v) for k, v in sorted(tiles_by_n.items())},
                                "autotune_seconds": round(t_tune, 1)})
         if run_params is not None:
@@ -994,7 +1005,8 @@ def main():
         alg = sum(p.stats()["flops"] for p in plans)
         tfl = alg / (t_max / args.steps / 1000.0) / 1e12
         line["roofline"] = {"bound": "alu", "achieved": tfl, "peak": FP32_ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
-                            "frac": tfl / FP32_ALU_PEAK_TFLOPS, "traffic": None, "kernel": "k_batch_exec",
+                            "frac": tfl / FP32_ALU_PEAK_TFLOPS, "traffic": None,
+                            "kernel": "k_batch_exec + the wide circuits' tnq_p* (one graph)",
                             "peak_source": FP32_ALU_PEAK_SRC}
     if wl["kind"] == "sweep":
         # amplitudes/s of every (n, k) point, each timed on its own; the roofline is the largest

@@ -343,15 +343,23 @@ typedef struct tn_batch tn_batch; /* opaque, library-owned, holds device tables 
 
 /* Group plans (batch 1, any target, tile qubits in [6, 12]) for one launch.  The plans must
  * outlive the batch.  TN_ERR_UNSUPPORTED for plans of batch > 1.  Plans of circuits that read
- * parameters are allowed: their gate tables are built in the run (tn_batch_run_params). */
+ * parameters are allowed: their gate tables are built in the run (tn_batch_run_params).
+ * Plans of 19 qubits and more that carry generated kernels (built without TN_PLAN_NO_SPECIALIZE;
+ * any tile size) are not interpreted by the persistent kernel: a run launches their own pass
+ * kernels on the batch's four side streams, beside it.  The entries of one parameterised plan
+ * share a side stream (its per-call tables are rewritten before each pass); such a plan must not
+ * run on another stream while the batch runs. */
 tn_status tn_batch_build(const tn_plan *const *plans, int32_t n_plans, tn_batch **out);
 /* complex64 entries of the output buffer (all states, each 16-byte aligned) and workspace bytes. */
 tn_status tn_batch_sizes(const tn_batch *b, int64_t *state_elems, size_t *workspace_bytes);
 /* offsets[i] = first complex64 entry of circuit i's state in the output buffer. */
 tn_status tn_batch_state_offsets(const tn_batch *b, int64_t *offsets);
 /* Contract every circuit: states_dev receives all final states.  Enqueues one memset of the
- * workspace (its counters) and one kernel launch on s; capturable in a CUDA graph.  A wait that
- * runs out (about 2 s) is reported by tn_sync_status as TN_ERR_TIMEOUT. */
+ * workspace (its counters) and one kernel launch on s, and, for the batch's wide circuits of
+ * generated kernels, their pass launches on the side streams, which wait for s before they start
+ * and which s waits for after the launch (a fork and a join of events: capturable in a CUDA graph,
+ * where they become parallel branches).  A wait that runs out (about 2 s) is reported by
+ * tn_sync_status as TN_ERR_TIMEOUT. */
 tn_status tn_batch_run(const tn_batch *b, void *states_dev, void *workspace_dev, tn_stream_t s);
 /* As tn_batch_run, for batches with parameterised circuits (spec: many parameter sets in
  * one persistent launch; Sec. 2.2.3: the order is fixed ahead of the values).  params_dev
@@ -384,7 +392,10 @@ tn_status tn_batch_test_stall(tn_batch *b, int32_t circ, int32_t pass, int64_t w
  * fastest kept).  Blocking: allocates and frees its own scratch device memory, synchronises s.
  * *out receives a batch that owns its plans (tn_free_batch frees them); tiles_out (optional,
  * n_circuits entries) receives the chosen tile sizes.  A circuit of n <= 12 qubits may also run
- * as one tile (T = n).  Candidates here: tile sizes in [6, 12]; all zero = {8, 9, 10, 11, 12}. */
+ * as one tile (T = n).  Candidates here: tile sizes in [6, 12]; all zero = {8, 9, 10, 11, 12}.
+ * Circuits of 19 qubits and more are not tuned: they are planned with generated kernels at the
+ * default tile size (compiled on a pool of host threads) and run on the side streams, as in
+ * tn_batch_build; they take part in every timed launch. */
 struct tn_tune_opts {
   int32_t candidates[8]; /* tile sizes, 0-terminated; all zero = the tuner's default set */
   int32_t reps;          /* timed launches per candidate; 0 = 3 */

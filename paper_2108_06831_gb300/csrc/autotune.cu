@@ -9,11 +9,17 @@
 // decreasing work (amplitudes x gates), and for each class every candidate T is tried with
 // the other classes held at their current choice; the whole batch is launched and timed
 // with CUDA events on the caller's stream, and the fastest T is kept (one coordinate-descent
-// sweep).  Planning here is host work; the timed launches are the real executor.
+// sweep).  Planning here is host work; the timed launches are the real executor.  Circuits of
+// kBatchDirectMinQubits qubits and more get plan-specialised kernels at the default tile instead
+// (compiled on a pool of host threads, one circuit per thread), which the batch runs on its side
+// streams; they take part in every timed launch, so the small classes are tuned beside them.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <map>
+#include <string>
+#include <thread>
 #include <vector>
 
 #include "kernels.h"
@@ -69,19 +75,73 @@ tn_status batch_build_tuned(const tn_circuit *const *circuits, int n, const tn_t
     return p;
   };
 
-  // classes by qubit count, most work first
+  std::vector<int> T((size_t)n);
+  for (int i = 0; i < n; ++i) T[(size_t)i] = std::min(circuits[i]->n, 12);
+
+  // wide circuits: specialised plans at the default tile, built in parallel (each thread on the
+  // caller's device)
+  {
+    std::vector<int> wide;
+    for (int i = 0; i < n; ++i)
+      if (circuits[i]->n >= kBatchDirectMinQubits) wide.push_back(i);
+    std::vector<tn_plan *> made(wide.size(), nullptr);
+    std::vector<tn_status> sts(wide.size(), TN_OK);
+    std::vector<std::string> errs(wide.size());
+    int dev = 0;
+    cudaError_t ce = cudaGetDevice(&dev);
+    if (ce != cudaSuccess) return cuda_fail(ce, "autotune device");
+    std::atomic<size_t> next(0);
+    auto worker = [&]() {
+      if (cudaSetDevice(dev) != cudaSuccess) return;
+      for (size_t k = next++; k < wide.size(); k = next++) {
+        tn_plan_opts po;
+        std::memset(&po, 0, sizeof(po));
+        po.target = TN_TARGET_STATE;
+        po.batch = 1;
+        sts[k] = tn_plan_contraction(circuits[wide[k]], &po, &made[k]);
+        if (sts[k] != TN_OK) errs[k] = tn_last_error();
+      }
+    };
+    const unsigned hw = std::thread::hardware_concurrency();
+    const size_t nthreads = std::min<size_t>(wide.size(), std::max(1u, std::min(hw, 16u)));
+    std::vector<std::thread> pool;
+    for (size_t t = 0; t < nthreads; ++t) pool.emplace_back(worker);
+    for (auto &th : pool) th.join();
+    tn_status bad = TN_OK;
+    std::string bad_err;
+    for (size_t k = 0; k < wide.size(); ++k) {
+      if (made[k] == nullptr && sts[k] == TN_OK) {  // the worker could not select the device
+        sts[k] = TN_ERR_CUDA;
+        errs[k] = "autotune: selecting the device on a planning thread failed";
+      }
+      if (sts[k] != TN_OK && bad == TN_OK) {
+        bad = sts[k];
+        bad_err = errs[k];
+      }
+    }
+    if (bad != TN_OK) {
+      for (tn_plan *p : made)
+        if (p) tn_free_plan(p);
+      set_error("%s", bad_err.c_str());
+      return bad;
+    }
+    for (size_t k = 0; k < wide.size(); ++k) {
+      T[(size_t)wide[k]] = made[k]->T;
+      plans[{wide[k], made[k]->T}] = made[k];
+    }
+  }
+
+  // classes by qubit count (the executor's circuits), most work first
   std::map<int, std::vector<int>> by_n;
   std::map<int, double> work;
   for (int i = 0; i < n; ++i) {
+    if (circuits[i]->n >= kBatchDirectMinQubits && plans.count({i, T[(size_t)i]})) continue;
     by_n[circuits[i]->n].push_back(i);
     work[circuits[i]->n] += std::ldexp(1.0, circuits[i]->n) * (double)(circuits[i]->gates.size() + 1);
   }
   std::vector<int> order;
   for (auto &kv : by_n) order.push_back(kv.first);
   std::sort(order.begin(), order.end(), [&](int a, int b) { return work[a] > work[b]; });
-
-  std::vector<int> T((size_t)n);
-  for (int i = 0; i < n; ++i) T[(size_t)i] = std::min(circuits[i]->n, 12);
 
   DevBuf states, ws;
   cudaEvent_t e0 = nullptr, e1 = nullptr;

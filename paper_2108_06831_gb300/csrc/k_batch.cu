@@ -10,7 +10,14 @@
 // (it is nevertheless bounded: after ~2 s the executor records TN_ERR_TIMEOUT, raises a
 // global abort flag that every CTA checks, and returns).  Circuits that fit in one tile
 // run all of their passes inside one item without going back to HBM.
+//
+// Wide circuits whose plans carry generated pass kernels (kBatchDirectMinQubits qubits and more:
+// at least 128 tiles per pass) do not go through the interpreting executor: a run launches
+// their own pass kernels on a few side streams, forked from the caller's stream after the
+// gate tables are built and joined back after the persistent launch, so that they share the
+// GPU with the executor's small circuits (one graph when captured).
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <vector>
 
@@ -45,6 +52,7 @@ constexpr int kBatchThreads = 256;  // 2^(12 - 4): the largest tile (12 qubits) 
 constexpr int kBatchT = 12;
 constexpr size_t kBatchStageMax = 32 * 1024;  // shared memory for a pass's staged records
 constexpr unsigned long long kWaitNs = 2000000000ull;  // default bound of a dependency wait
+constexpr int kSideStreams = 4;  // side streams of the wide circuits (measured: 4 beat 1 and 8)
 
 __device__ __forceinline__ unsigned long long now_ns() {
   unsigned long long t;
@@ -157,6 +165,21 @@ __global__ void __launch_bounds__(kBatchThreads, 3) k_batch_exec(const BatchTask
     }
     float2 *st = states + circ.state_off;
     __syncthreads();
+    if (pd.init_mode && (circ.init & outer_mask) != base) {
+      // a basis state is zero outside the one tile that holds it: store zeros, skip the phases
+      if (threadIdx.x == 0) claimed = atomicAdd(next_item, 1ull);
+      for (int c = threadIdx.x; c < (tile >> 1); c += blockDim.x) {
+        const int i = c << 1;
+        const long long g = (long long)base + run_off[i >> L] + (i & lowmask);
+        *reinterpret_cast<float4 *>(st + g) = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(done + s_task, 1);
+      }
+      continue;
+    }
     if (pd.init_mode) {
       for (int i = threadIdx.x; i < tile; i += blockDim.x) sm[swz(i)] = make_float2(0.f, 0.f);
       __syncthreads();
@@ -257,6 +280,14 @@ struct tn_batch {
   std::vector<std::vector<int>> circ_tasks;       // tasks of each circuit, pass order
   unsigned long long wait_ns = 2000000000ull;     // dependency-wait bound passed to the kernel
   int stalled_task = -1;                          // task altered by tn_batch_test_stall, -1 if none
+  // circuits run by their own generated pass kernels on side streams (most work first)
+  std::vector<int> direct;
+  std::vector<int> direct_stream;                  // side stream of each
+  std::vector<const tn_plan *> plan_ptrs;          // every circuit's plan
+  std::vector<long long> mats_off;                 // parameterised circuits: offset in the per-run table
+  std::vector<cudaStream_t> side;
+  cudaEvent_t fork = nullptr;
+  std::vector<cudaEvent_t> join;
 };
 
 namespace tnq {
@@ -284,11 +315,15 @@ tn_status batch_build(const tn_plan *const *plans, int n, tn_batch **out) {
       set_error("plan %d: the batched executor takes plans of batch 1 (one parameter set per circuit)", i);
       return TN_ERR_UNSUPPORTED;
     }
-    if (p->K != 4 || p->T > kBatchT || p->T < kLowBits + 2) {
+    const bool direct = !p->jit_kernels.empty() && p->n >= kBatchDirectMinQubits;
+    if (!direct && (p->K != 4 || p->T > kBatchT || p->T < kLowBits + 2)) {
       delete b;
       set_error("plan %d: the batched executor needs 6 <= tile qubits <= 12 (circuit of %d qubits)", i, p->n);
       return TN_ERR_UNSUPPORTED;
     }
+    b->plan_ptrs.push_back(p);
+    b->mats_off.push_back(-1);
+    if (direct) b->direct.push_back(i);
     BatchCirc &c = circs[(size_t)i];
     std::memset(&c, 0, sizeof(c));
     c.state_off = off;
@@ -304,6 +339,7 @@ tn_status batch_build(const tn_plan *const *plans, int n, tn_batch **out) {
       // indices shifted to the circuit's place in the combined tables
       c.mats = nullptr;
       c.mats_off = run_mats;
+      b->mats_off[(size_t)i] = run_mats;
       const int fbase = (int)all_fused.size();
       for (const FusedMember &f : p->fused) {
         FusedMember g = f;
@@ -328,6 +364,7 @@ tn_status batch_build(const tn_plan *const *plans, int n, tn_batch **out) {
     b->offsets[(size_t)i] = off;
     off += 1ll << p->n;
     off = (off + 1) & ~1ll;  // keep every state 16-byte aligned
+    if (direct) continue;  // no work items: its own kernels run it
     const bool one_tile = p->fwd.passes.front().n_outer == 0;
     if (one_tile) {  // the whole state is one tile: every pass runs in the same item
       PassDesc m = p->fwd.passes.front();
@@ -344,6 +381,42 @@ tn_status batch_build(const tn_plan *const *plans, int n, tn_batch **out) {
     }
   }
   b->total_elems = off;
+  // side streams of the direct circuits: most work first, each to the least-loaded stream; the
+  // uses of one parameterised plan share a stream (its per-call constant tables are rewritten
+  // before each launch)
+  if (!b->direct.empty()) {
+    auto work = [&](int i) { return b->plan_ptrs[(size_t)i]->fwd.passes.size() * std::ldexp(1.0, b->plan_ptrs[(size_t)i]->n); };
+    std::stable_sort(b->direct.begin(), b->direct.end(), [&](int x, int y) { return work(x) > work(y); });
+    const int ns = std::min<int>(kSideStreams, (int)b->direct.size());
+    std::vector<double> load((size_t)ns, 0.0);
+    std::vector<std::pair<const tn_plan *, int>> owner;
+    for (int i : b->direct) {
+      const tn_plan *p = b->plan_ptrs[(size_t)i];
+      int k = -1;
+      if (p->param_dependent)
+        for (auto &o : owner)
+          if (o.first == p) k = o.second;
+      if (k < 0) {
+        k = 0;
+        for (int j = 1; j < ns; ++j)
+          if (load[(size_t)j] < load[(size_t)k]) k = j;
+        if (p->param_dependent) owner.push_back({p, k});
+      }
+      load[(size_t)k] += work(i);
+      b->direct_stream.push_back(k);
+    }
+    cudaError_t e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+    b->side.assign((size_t)ns, nullptr);
+    b->join.assign((size_t)ns, nullptr);
+    for (int k = 0; e == cudaSuccess && k < ns; ++k) {
+      e = cudaStreamCreateWithFlags(&b->side[(size_t)k], cudaStreamNonBlocking);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->join[(size_t)k], cudaEventDisableTiming);
+    }
+    if (e != cudaSuccess) {
+      batch_free(b);
+      return cuda_fail(e, "batch side streams");
+    }
+  }
   // staging budget: the largest pass's phase/op records and matrix entries, up to 32 KB
   size_t stage = 0;
   for (const PassDesc &pd : passes)
@@ -420,23 +493,44 @@ cudaError_t batch_run(const tn_batch *b, const double *params, float2 *states, v
     e = launch_materialize(b->d_slots, b->n_slots, b->n_fused_slots, b->d_fused, params, b->n_params, 1, 0, run_mats, s);
     if (e != cudaSuccess) return e;
   }
-  const size_t smem = ((size_t)sizeof(float2) << kBatchT) + ((size_t)1 << (kBatchT - kLowBits)) * sizeof(long long) +
-                      (size_t)b->stage_cap;
-  e = ensure_smem(reinterpret_cast<const void *>(k_batch_exec), smem);
-  if (e != cudaSuccess) return e;
-  int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_exec, kBatchThreads, smem);
-  if (e != cudaSuccess) return e;
-  if (per_sm < 1) per_sm = 1;
-  // never more CTAs than can be resident at once: a CTA may wait for items held by others
-  long long grid = (long long)num_sms() * per_sm;
-  if (grid > b->total_items) grid = b->total_items;
-  if (grid < 1) return cudaSuccess;
-  k_batch_exec<<<(unsigned)grid, kBatchThreads, smem, s>>>(b->d_tasks, b->n_tasks, b->d_circs, b->d_passes, states,
-                                                           done, next, abort_flag, b->total_items,
-                                                           static_cast<int *>(status_word_ptr()), b->stage_cap,
-                                                           b->wait_ns, run_mats);
-  return cudaGetLastError();
+  // wide circuits: their own pass kernels on the side streams (forked after the gate tables)
+  const int ns = (int)b->side.size();
+  if (ns > 0) {
+    e = cudaEventRecord(b->fork, s);
+    for (int k = 0; e == cudaSuccess && k < ns; ++k) e = cudaStreamWaitEvent(b->side[(size_t)k], b->fork, 0);
+    for (size_t j = 0; e == cudaSuccess && j < b->direct.size(); ++j) {
+      const int i = b->direct[j];
+      const tn_plan *p = b->plan_ptrs[(size_t)i];
+      const float2 *m = p->param_dependent ? run_mats + b->mats_off[(size_t)i] : reinterpret_cast<const float2 *>(p->d_fixed_mats);
+      e = launch_forward(p, m, p->mstride, states + b->offsets[(size_t)i], b->side[(size_t)b->direct_stream[j]]);
+    }
+    if (e != cudaSuccess) return e;
+  }
+  if (b->total_items > 0) {
+    const size_t smem = ((size_t)sizeof(float2) << kBatchT) +
+                        ((size_t)1 << (kBatchT - kLowBits)) * sizeof(long long) + (size_t)b->stage_cap;
+    e = ensure_smem(reinterpret_cast<const void *>(k_batch_exec), smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_exec, kBatchThreads, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    // never more CTAs than can be resident at once: a CTA may wait for items held by others
+    long long grid = (long long)num_sms() * per_sm;
+    if (grid > b->total_items) grid = b->total_items;
+    k_batch_exec<<<(unsigned)grid, kBatchThreads, smem, s>>>(b->d_tasks, b->n_tasks, b->d_circs, b->d_passes, states,
+                                                             done, next, abort_flag, b->total_items,
+                                                             static_cast<int *>(status_word_ptr()), b->stage_cap,
+                                                             b->wait_ns, run_mats);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  // join the side streams back into the caller's stream
+  for (int k = 0; e == cudaSuccess && k < ns; ++k) {
+    e = cudaEventRecord(b->join[(size_t)k], b->side[(size_t)k]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, b->join[(size_t)k], 0);
+  }
+  return e;
 }
 
 tn_status batch_sizes(const tn_batch *b, long long *elems, size_t *ws) {
@@ -501,6 +595,11 @@ void batch_free(tn_batch *b) {
   cudaFree(b->d_tasks);
   cudaFree(b->d_circs);
   cudaFree(b->d_passes);
+  for (cudaStream_t t : b->side)
+    if (t) cudaStreamDestroy(t);
+  for (cudaEvent_t ev : b->join)
+    if (ev) cudaEventDestroy(ev);
+  if (b->fork) cudaEventDestroy(b->fork);
   for (tn_plan *p : b->owned) tn_free_plan(p);
   delete b;
 }

@@ -63,7 +63,9 @@ cudaError_t launch_cgemm(int precision, long long batch, long long M, long long 
                          const float2 *B, float2 *C, void *ws, size_t ws_bytes, cudaStream_t s,
                          const OutMap *om = nullptr);
 
-// Persistent batched executor.
+// Persistent batched executor.  Circuits of at least kBatchDirectMinQubits qubits whose plans carry
+// generated pass kernels run those kernels on side streams instead (at least 128 tiles per pass).
+constexpr int kBatchDirectMinQubits = 19;
 tn_status batch_build(const tn_plan *const *plans, int n, tn_batch **out);
 // params: every parameterised circuit's parameters back to back (NULL when none has any).
 cudaError_t batch_run(const tn_batch *b, const double *params, float2 *states, void *ws, cudaStream_t s);

@@ -212,3 +212,59 @@ def test_serving_mix_subset_tuned_matches_oracle():
     for c, off, ref in zip(circs, b.offsets, refs):
         s = got[off:off + (1 << c.n_qubits)]
         assert np.linalg.norm(s - ref) / np.linalg.norm(ref) <= TOL, c.name
+
+
+def test_batch_wide_circuits_on_side_streams():
+    """Circuits of 19 qubits and more with plan-specialised kernels run those kernels on the batch's
+    side streams, beside the persistent launch of the small ones: six wide circuits on four streams
+    (fixed angles, a QFT, and one parameterised plan used twice with different parameters), every
+    state against the oracle, directly and as a replayed CUDA graph with new parameter values."""
+    from oracle.statevector import simulate_state
+    from paper_2108_06831_gb300 import tn
+    rng = np.random.default_rng(21)
+    wide_fixed = [C.brickwork(19, 5, 700)[0], C.brickwork(20, 4, 701)[0], C.qft(19, int(rng.integers(0, 1 << 19))),
+                  C.brickwork(21, 3, 702)[0]]
+    cp, pp = C.brickwork(19, 4, 703, parameterized=True)
+    small = [C.brickwork(10, 6, 704)[0], C.qft(14, 12345), C.brickwork(16, 5, 705)[0]]
+    hp = tn.CircuitHandle(cp)
+    p_wide = tn.Plan(hp)  # one parameterised plan, two entries of the batch
+    plans = [tn.Plan(tn.CircuitHandle(c)) for c in wide_fixed] + [p_wide, p_wide] + \
+            [tn.Plan(tn.CircuitHandle(c), specialize=False) for c in small]
+    assert all(p.stats()["specialized"] for p in plans[:6])
+    circs = wide_fixed + [cp, cp] + small
+    b = tn.Batch(plans)
+    params = [np.zeros(0)] * 4 + [pp, rng.uniform(-np.pi, np.pi, size=len(pp))] + [np.zeros(0)] * 3
+    flat = np.zeros(max(b.n_params, 1))
+    d_params = torch.empty(len(flat), dtype=torch.float64, device="cuda")
+
+    def load(ps):
+        for p, off in zip(ps, b.param_offsets):
+            flat[off:off + len(p)] = p
+        d_params.copy_(torch.as_tensor(flat))
+
+    states = torch.full((b.state_elems,), complex(float("nan"), 0), dtype=torch.complex64, device="cuda")
+    ws = torch.empty(b.workspace_bytes, dtype=torch.uint8, device="cuda")
+
+    def check(ps):
+        got = states.cpu().numpy()
+        for c, p, off in zip(circs, ps, b.offsets):
+            ref = simulate_state(c, p if len(p) else None)
+            s_ = got[off:off + (1 << c.n_qubits)]
+            assert np.linalg.norm(s_ - ref) / np.linalg.norm(ref) <= TOL, c.name
+    load(params)
+    tn.batch_run(b, states, ws, params=d_params)
+    torch.cuda.synchronize()
+    assert tn.sync_status() == tn.OK
+    check(params)
+    stream = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(stream):
+        with torch.cuda.graph(g, stream=stream):
+            tn.batch_run(b, states, ws, params=d_params)
+    params = params[:4] + [rng.uniform(-np.pi, np.pi, size=len(pp)) for _ in range(2)] + params[6:]
+    load(params)
+    states.fill_(float("nan"))
+    g.replay()
+    torch.cuda.synchronize()
+    assert tn.sync_status() == tn.OK
+    check(params)
