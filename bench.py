@@ -590,9 +590,28 @@ def main():
         units_per_step = float(batch)
         unit = "amplitudes/s"
 
-        def step():
+        def eager_step():
             for i in range(0, batch, chunk):
                 tn.contract_amplitudes(plan, None, xs[i:i + chunk], amps[i:i + chunk], aws)
+        # one call captured once as a CUDA graph (a capped plan's call is tens of thousands of small
+        # launches); a step copies each chunk of bitstrings into the captured buffer and replays it
+        xs_c = torch.empty(chunk, dtype=torch.int64, device=dev)
+        amps_c = torch.empty(chunk, dtype=torch.complex64, device=dev)
+        xs_c.copy_(xs[:chunk])
+        tn.contract_amplitudes(plan, None, xs_c, amps_c, aws)
+        torch.cuda.synchronize()
+        amps_graph = torch.cuda.CUDAGraph()
+        cap = torch.cuda.Stream(device=dev)
+        with torch.cuda.stream(cap):
+            with torch.cuda.graph(amps_graph, stream=cap):
+                tn.contract_amplitudes(plan, None, xs_c, amps_c, aws)
+        torch.cuda.synchronize()
+
+        def step():
+            for i in range(0, batch, chunk):
+                xs_c.copy_(xs[i:i + chunk])
+                amps_graph.replay()
+                amps[i:i + chunk].copy_(amps_c)
         # per pass of the network and slice: the closure kernel, one GEMM per launched merge, B's
         # split per tensor-core merge (and A's for split BF16); a sliced plan adds the FP64 slice
         # sum per slice and the final store per pass; a call runs chunk / 2^net_batch_log2 passes
@@ -937,6 +956,12 @@ def main():
                                "bitstrings_per_pass": 1 << nst["net_batch_log2"],
                                "tensor_core_merges_per_pass": nst["net_tensor_merges"]})
         line["config"]["folded_merges"] = nst["net_folded_merges"]
+        line["config"]["launch"] = "each call of 64 bitstrings replays one captured CUDA graph"
+        for _ in range(2):
+            eager_step()
+        eager_ms = statistics.mean(timed(eager_step, max(2, min(args.steps, 3))))
+        line["eager"] = {"value": units_per_step / (eager_ms / 1000.0), "unit": unit, "ms_per_step": eager_ms,
+                         "what": "the same calls issued one by one (no graph)"}
         # the dominant kernel: the dense merges (batch 64, M 32768, N = K = 64), HBM-bound;
         # the same GEMM shape is timed alone here with CUDA events (A read once as FP32 when
         # the split runs on chip; the epilogue of a network merge also permutes its output)
