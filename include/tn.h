@@ -281,8 +281,10 @@ tn_status tn_expectation_backward(const tn_plan *p, const tn_observable *H, cons
 
 /* Value and gradient in one sweep: out_dev[b] = <psi_b| H |psi_b> and grad_params_dev[b][k] =
  * d<H>_b / d theta_{b,k} (float64, device; both overwritten).  The same work as tn_expectation
- * followed by tn_expectation_backward with grad_out = 1, but the forward state is contracted once:
- * the reduction reads psi before the reverse sweep un-computes it in place. */
+ * followed by tn_expectation_backward with grad_out = 1, but the forward state is contracted once,
+ * and the energy is summed as Re <psi|lambda> while lambda = H psi is formed (its last pass),
+ * before the reverse sweep un-computes psi in place.  A circuit without parameters takes the
+ * plain reduction of tn_expectation. */
 tn_status tn_expectation_value_and_grad(const tn_plan *p, const tn_observable *H, const double *params_dev,
                                         double *out_dev, double *grad_params_dev, void *workspace_dev,
                                         tn_stream_t s);

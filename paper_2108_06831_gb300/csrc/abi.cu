@@ -822,10 +822,13 @@ tn_status tn_expectation_value_and_grad(const tn_plan *p, const tn_observable *H
   float2 *psi = reinterpret_cast<float2 *>(ws + p->ws_psi);
   float2 *lam = reinterpret_cast<float2 *>(ws + p->ws_lam);
   TN_CUDA(launch_forward(p, mats, mstride, psi, cs), "gate-apply kernel");
-  TN_CUDA(launch_expectation(H, p->batch, psi, reinterpret_cast<double *>(ws + p->ws_part), out_dev, cs),
-          "expectation kernel");
-  if (p->n_params == 0) return TN_OK;
-  TN_CUDA(launch_apply_hamiltonian(H, p->batch, psi, lam, cs), "H psi kernel");
+  double *part = reinterpret_cast<double *>(ws + p->ws_part);
+  if (p->n_params == 0) {
+    TN_CUDA(launch_expectation(H, p->batch, psi, part, out_dev, cs), "expectation kernel");
+    return TN_OK;
+  }
+  // lam = H psi, and the energy <psi|lam> from the last pass over lam (no separate reduction)
+  TN_CUDA(launch_apply_hamiltonian(H, p->batch, psi, lam, cs, part, out_dev), "H psi kernel");
   TN_CUDA(cudaMemsetAsync(grad_params_dev, 0, sizeof(double) * (size_t)p->batch * p->n_params, cs), "memset grad");
   TN_CUDA(launch_backward(p, mats, mstride, psi, lam, grad_params_dev, cs), "adjoint kernel");
   return TN_OK;

@@ -171,12 +171,17 @@ __global__ void k_expect_final(const double *__restrict__ part, int n_passes, in
 }
 
 // lam (+)= (sum of the pass's terms) psi, lam[x] = sum_t c_t i^ny (-1)^popc((x^xm)&zm) psi[x^xm].
+// With dot != NULL (the last pass) the CTA also sums Re conj(psi[x]) lam[x] over its amplitudes:
+// <psi|H|psi> from the finished lam, in the precision steps of k_expect_pass (the product and a
+// thread's sum over its amplitudes of one tile FP32, the rest FP64), into dot[b][blockIdx.x].
 __global__ void __launch_bounds__(kRedThreads) k_hamiltonian_pass(const RedPass *__restrict__ passes, int pass_idx,
                                                                   const DevTerm *__restrict__ terms,
                                                                   const float2 *__restrict__ psi,
-                                                                  float2 *__restrict__ lam, int N, int accumulate) {
+                                                                  float2 *__restrict__ lam, int N, int accumulate,
+                                                                  double *__restrict__ dot) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ RedPass rp;
+  __shared__ double scratch[kRedThreads / 32];
   for (int i = threadIdx.x; i < (int)(sizeof(RedPass) / 4); i += blockDim.x)
     reinterpret_cast<int *>(&rp)[i] = reinterpret_cast<const int *>(passes + pass_idx)[i];
   __syncthreads();
@@ -197,6 +202,7 @@ __global__ void __launch_bounds__(kRedThreads) k_hamiltonian_pass(const RedPass 
   const float2 *st = psi + ((long long)b << N);
   float2 *lt = lam + ((long long)b << N);
   const long long n_tiles = 1ll << rp.n_outer;
+  double acc = 0.0;
   for (long long t = blockIdx.x; t < n_tiles; t += gridDim.x) {
     const unsigned long long base = tile_base(rp, t);
     // parity of the Z mask on the outer bits; x ^ xm has the same outer bits as x
@@ -204,6 +210,7 @@ __global__ void __launch_bounds__(kRedThreads) k_hamiltonian_pass(const RedPass 
       sb[k] = (unsigned char)(__popcll(base & terms[rp.term_begin + k].zm) & 1);
     load_tile(sm, st, base, c);
     __syncthreads();
+    float tacc = 0.f;
     for (int i = threadIdx.x; i < c.tile; i += blockDim.x) {
       const unsigned long long x = base + (unsigned long long)c.run_off[i >> c.L] + (unsigned long long)(i & c.lowmask);
       float2 s = accumulate ? lt[x] : make_float2(0.f, 0.f);
@@ -216,8 +223,17 @@ __global__ void __launch_bounds__(kRedThreads) k_hamiltonian_pass(const RedPass 
         s.y = fmaf(sgn, w.y, s.y);
       }
       lt[x] = s;
+      if (dot) {
+        const float2 v = sm[swz(i)];
+        tacc = fmaf(v.x, s.x, fmaf(v.y, s.y, tacc));
+      }
     }
+    acc += (double)tacc;
     __syncthreads();
+  }
+  if (dot) {
+    const double tot = block_sum(acc, scratch);
+    if (threadIdx.x == 0) dot[(long long)b * kRedMaxCTAs + blockIdx.x] = tot;
   }
 }
 
@@ -276,18 +292,30 @@ cudaError_t launch_expectation(const tn_observable *o, int batch, const float2 *
 }
 
 cudaError_t launch_apply_hamiltonian(const tn_observable *o, int batch, const float2 *psi, float2 *lam,
-                                     cudaStream_t s) {
+                                     cudaStream_t s, double *part, double *out) {
   const int np = (int)o->passes.size();
-  if (np == 0) return cudaMemsetAsync(lam, 0, (sizeof(float2) << o->n) * batch, s);
+  if (np == 0) {
+    cudaError_t e = cudaMemsetAsync(lam, 0, (sizeof(float2) << o->n) * batch, s);
+    if (e == cudaSuccess && out) e = cudaMemsetAsync(out, 0, sizeof(double) * batch, s);
+    return e;
+  }
+  int gx_last = 1;
   for (int p = 0; p < np; ++p) {
     const size_t smem = red_smem(o->passes[p]);
     cudaError_t e = ensure_smem((const void *)k_hamiltonian_pass, smem);
     if (e != cudaSuccess) return e;
     const int gx = red_grid_x(o, p, batch, (const void *)k_hamiltonian_pass);
+    double *dot = (out && p == np - 1) ? part : nullptr;
     dim3 grid((unsigned)gx, (unsigned)batch);
-    k_hamiltonian_pass<<<grid, kRedThreads, smem, s>>>(o->d_passes, p, o->d_terms, psi, lam, o->n, p > 0 ? 1 : 0);
+    k_hamiltonian_pass<<<grid, kRedThreads, smem, s>>>(o->d_passes, p, o->d_terms, psi, lam, o->n, p > 0 ? 1 : 0,
+                                                       dot);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    gx_last = gx;
+  }
+  if (out) {  // every CTA of the last pass wrote its partial: no clearing needed
+    k_expect_final<<<batch, kRedThreads, 0, s>>>(part, 1, gx_last, out);
+    return cudaGetLastError();
   }
   return cudaSuccess;
 }

@@ -27,9 +27,10 @@ cudaError_t launch_backward(const tn_plan *p, const float2 *mats, long long mstr
 size_t observable_partials(const tn_observable *o, int batch);
 cudaError_t launch_expectation(const tn_observable *o, int batch, const float2 *state, double *part,
                                double *out, cudaStream_t s);
-// lam = H psi (complex64).
+// lam = H psi (complex64); with out != NULL also out[b] = <psi|H|psi> (FP64), summed from the
+// finished lam in the last pass (part: observable_partials(o, batch) doubles of scratch).
 cudaError_t launch_apply_hamiltonian(const tn_observable *o, int batch, const float2 *psi, float2 *lam,
-                                     cudaStream_t s);
+                                     cudaStream_t s, double *part = nullptr, double *out = nullptr);
 // amps[b][i] = state[b][x_i]
 cudaError_t launch_gather(const float2 *state, int N, int batch, const uint64_t *xs, long long nx, float2 *amps,
                           cudaStream_t s);

@@ -43,15 +43,17 @@ def test_hea_tfim_expectation_and_gradient(n, layers, tile):
         assert np.linalg.norm(G[b] - gref) / max(np.linalg.norm(gref), 1e-3) <= 1e-4
 
 
-@pytest.mark.parametrize("n,layers,tile", [(6, 3, 0), (13, 2, 8)])
-def test_value_and_grad_matches_separate_calls_and_oracle(n, layers, tile):
+@pytest.mark.parametrize("n,layers,tile,ham", [(6, 3, 0, "tfim"), (13, 2, 8, "tfim"), (11, 2, 8, "pauli")])
+def test_value_and_grad_matches_separate_calls_and_oracle(n, layers, tile, ham):
     """tn_expectation_value_and_grad contracts the forward state once; energies and gradients
-    equal the two-call path and the oracle (parameter shift)."""
+    equal the two-call path and the oracle (parameter shift).  Its energy is Re <psi|H psi> summed
+    from lambda = H psi, the two-call path's the direct term sum: both in FP32 per amplitude, so they
+    agree to FP32 rounding of the state's norm-sized sums, not bit for bit."""
     from oracle import gradients as GR
     from oracle import observables as OB
     tn = _tn()
     c = C.hea(n, layers)
-    H = C.tfim(n)
+    H = C.tfim(n) if ham == "tfim" else C.random_pauli_sum(n, 30, 90 + n)  # X, Y and Z factors
     batch = 2
     params = C.hea_params(c.n_params, batch, 70 + n)
     ctr = tn.Contractor(c, target=tn.TARGET_EXPECTATION, batch=batch, tile_qubits=tile)
@@ -62,7 +64,7 @@ def test_value_and_grad_matches_separate_calls_and_oracle(n, layers, tile):
     torch.cuda.synchronize()
     assert tn.sync_status() == tn.OK
     E, G = e1.cpu().numpy(), g1.cpu().numpy()
-    assert np.allclose(E, e0.cpu().numpy(), rtol=1e-12, atol=1e-12)
+    assert np.allclose(E, e0.cpu().numpy(), rtol=1e-5, atol=1e-5)
     assert np.allclose(G, g0.cpu().numpy(), rtol=1e-9, atol=1e-12)
     for b in range(batch):
         Eref = OB.expectation(c, H, params[b])
@@ -96,10 +98,14 @@ def test_cfg4_full_size_sampled():
     obs = tn.Observable(H)
     E = ctr.expectation(obs, _dev(params)).cpu().numpy()
     G = ctr.expectation_backward(obs, _dev(params)).cpu().numpy()
+    e2, g2 = ctr.expectation_value_and_grad(obs, _dev(params))  # the call the benchmark times
+    E2, G2 = e2.cpu().numpy(), g2.cpu().numpy()
+    assert np.allclose(G2, G, rtol=1e-9, atol=1e-12)
     rng = np.random.default_rng(1)
     for b in (0, 37):
         Eref = OB.expectation(c, H, params[b])
         assert abs(E[b] - Eref) <= 1e-4 * max(1.0, abs(Eref))
+        assert abs(E2[b] - Eref) <= 1e-4 * max(1.0, abs(Eref))
     for b in (37,):
         ks = rng.choice(c.n_params, size=3, replace=False)
         for k in ks:
