@@ -774,9 +774,13 @@ def main():
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
+    # the timed steps are the profiler's capture range (ncu --profile-from-start off records only
+    # these launches; without a profiler attached the two calls do nothing)
+    torch.cuda.profiler.start()
     with ClockSampler(local) as clk:
         ms = timed(step, args.steps)
     torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
     if world > 1:
         dist.barrier()
     # the arithmetic the step computes in: FP32 (complex64 states), or the tensor-core split forms
