@@ -1196,7 +1196,8 @@ OTHER_CONFIGS = [
     ("config 3: 6x6 grid depth 12, 4096 amplitudes, 3xTF32 merges", ["--workload", "amps36", "--prec", "1"]),
     ("config 3, plain FP32 merges", ["--workload", "amps36", "--prec", "0"]),
     ("config 4: 20-qubit HEA, TFIM energy + adjoint gradient, 64 parameter sets", ["--workload", "grad20"]),
-    ("config 5: 512-circuit serving mix, one persistent launch in a CUDA graph", ["--workload", "serving512"]),
+    ("config 5: 512-circuit serving mix, one CUDA graph (persistent launch + wide circuits on side streams)",
+     ["--workload", "serving512"]),
 ]
 
 
