@@ -54,6 +54,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_cgemm_fp32(long long M, long lo
                                                          float2 *__restrict__ C, float2 *__restrict__ P,
                                                          const __grid_constant__ StagedMap om) {
   static_assert((BM / TM) * (BN / TN) == kThreads, "one thread per TM x TN block");
+  pdl_wait();
+  pdl_trigger();
   // two K slices of both operands in flight (row-major, row stride BK + 1: a warp's reads across
   // rows fall in distinct banks); the C tile (row stride BN + 1) in the permuted epilogue
   constexpr int kLd = BK + 1;
@@ -178,6 +180,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_cgemm_fp32(long long M, long lo
 __global__ void __launch_bounds__(256) k_cgemm_small(long long M, long long N, long long K, long long total,
                                                      const float2 *__restrict__ A, const float2 *__restrict__ B,
                                                      float2 *__restrict__ C, const __grid_constant__ OutMap om) {
+  pdl_wait();
+  pdl_trigger();
   for (long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x; f < total;
        f += (long long)gridDim.x * blockDim.x) {
     const long long n = f % N, bm = f / N;  // bm = b M + m
@@ -201,6 +205,8 @@ constexpr long long kSmallWork = 1ll << 18;
 // output map: C[map(f)] = sum_s P[s][f], f the natural index (b M + m) N + n.
 __global__ void k_splitk_reduce(const float2 *__restrict__ P, int splits, long long total, float2 *__restrict__ C,
                                 const __grid_constant__ OutMap om) {
+  pdl_wait();
+  pdl_trigger();
   for (long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x; f < total;
        f += (long long)gridDim.x * blockDim.x) {
     float2 acc = P[f];
@@ -217,6 +223,8 @@ __global__ void k_splitk_reduce(const float2 *__restrict__ P, int splits, long l
 // splits, then a fixed tree (warp shuffles, then the four warp sums in order).
 __global__ void k_splitk_reduce_few(const float2 *__restrict__ P, int splits, long long total, float2 *__restrict__ C,
                                     const __grid_constant__ OutMap om) {
+  pdl_wait();
+  pdl_trigger();
   const long long f = blockIdx.x;
   float2 acc = make_float2(0.f, 0.f);
   for (int s = threadIdx.x; s < splits; s += blockDim.x) {
@@ -316,15 +324,15 @@ cudaError_t launch_shape(long long batch, long long M, long long N, long long K,
   std::memset(&sm, 0, sizeof(sm));
   sm.map = om;
   if (!om.identity && splits == 1) build_staged(sm, om, M, N, BM, BN);
-  k_cgemm_fp32<BM, BN, BK, TM, TN><<<grid, kThreads, 0, s>>>(M, N, K, k_len, A, B, C, splits > 1 ? P : nullptr, sm);
-  cudaError_t e = cudaGetLastError();
+  cudaError_t e = launch_pdl(k_cgemm_fp32<BM, BN, BK, TM, TN>, grid, dim3(kThreads), 0, s, M, N, K, k_len, A, B, C,
+                             splits > 1 ? P : (float2 *)nullptr, sm);
   if (e != cudaSuccess || splits == 1) return e;
   const long long total = batch * M * N;
   if (total <= 4096)
-    k_splitk_reduce_few<<<(unsigned)total, 128, 0, s>>>(P, splits, total, C, om);
-  else
-    k_splitk_reduce<<<(unsigned)std::min<long long>((total + 255) / 256, 4096), 256, 0, s>>>(P, splits, total, C, om);
-  return cudaGetLastError();
+    return launch_pdl(k_splitk_reduce_few, dim3((unsigned)total), dim3(128), 0, s, (const float2 *)P, splits, total, C,
+                      om);
+  return launch_pdl(k_splitk_reduce, dim3((unsigned)std::min<long long>((total + 255) / 256, 4096)), dim3(256), 0, s,
+                    (const float2 *)P, splits, total, C, om);
 }
 
 template <int BK>
@@ -369,8 +377,7 @@ cudaError_t launch_cgemm_fp32(long long batch, long long M, long long N, long lo
   // 13.1, none 22.4)
   if (K <= 64 && ((double)total * (double)K <= (double)kSmallWork || N <= 4)) {
     const long long blocks = std::min<long long>((total + 255) / 256, (long long)num_sms() * 16);
-    k_cgemm_small<<<(unsigned)blocks, 256, 0, s>>>(M, N, K, total, A, B, C, m);
-    return cudaGetLastError();
+    return launch_pdl(k_cgemm_small, dim3((unsigned)blocks), dim3(256), 0, s, M, N, K, total, A, B, C, m);
   }
   if (K <= 8) return launch_k<8>(batch, M, N, K, A, B, C, P, m, s);
   return launch_k<16>(batch, M, N, K, A, B, C, P, m, s);

@@ -219,6 +219,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_cgemm_tc(const __grid_constant_
                                                           int *status, const __grid_constant__ OutMap om) {
   using CF = Cfg<PREC>;
   static_assert(!SPLIT_A || PREC == PREC_TF32, "on-chip split is the TF32 form");
+  pdl_wait();  // before any memory access or TMEM allocation: the previous kernel has completed
+  pdl_trigger();
   constexpr int S = CF::kStages;
   constexpr int stage_bytes = CF::kParts * (kTileA + kTileB);
   // bytes the TMA delivers per stage: A once as FP32 when it is split here, else its parts
@@ -456,6 +458,8 @@ __global__ void __launch_bounds__(kStreamThreads, 1)
                       long long total_tiles, long long M, long long N2, float *__restrict__ C, int *status,
                       const __grid_constant__ OutMap om) {
   using CF = Cfg<PREC>;
+  pdl_wait();  // before any memory access or TMEM allocation: the previous kernel has completed
+  pdl_trigger();
   constexpr int S = CF::kStages;
   constexpr int stage_bytes = CF::kParts * (kTileA + kTileB);
   // A arrives as FP32: one 128-byte box per row and K tile for TF32, two for BF16 (64 elements)
@@ -742,6 +746,8 @@ __global__ void __launch_bounds__(kStreamThreads, 1)
 // A (real view [rows][cols]) -> parts
 template <int PREC>
 __global__ void k_split(const float *__restrict__ x, long long n, void *p0, void *p1, void *p2) {
+  pdl_wait();
+  pdl_trigger();
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     const float v = x[i];
     if constexpr (PREC == PREC_TF32) {
@@ -764,6 +770,8 @@ __global__ void k_split(const float *__restrict__ x, long long n, void *p0, void
 template <int PREC>
 __global__ void k_embed_split(const float2 *__restrict__ b, long long N, long long K, long long batch, void *p0,
                               void *p1, void *p2) {
+  pdl_wait();
+  pdl_trigger();
   const long long total = batch * N * K;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
        i += (long long)gridDim.x * blockDim.x) {
@@ -867,15 +875,13 @@ cudaError_t run_tc(long long batch, long long M, long long N, long long K, const
     ap[0] = const_cast<float2 *>(A);  // the GEMM reads A itself (FP32) and splits it on chip
   } else {
     const long long na = batch * M * 2 * K;
-    k_split<PREC><<<(unsigned)std::min<long long>((na + 255) / 256, 65535), 256, 0, s>>>(
-        reinterpret_cast<const float *>(A), na, ap[0], ap[1], ap[2]);
-    e = cudaGetLastError();
+    e = launch_pdl(k_split<PREC>, dim3((unsigned)std::min<long long>((na + 255) / 256, 65535)), dim3(256), 0, s,
+                   reinterpret_cast<const float *>(A), na, ap[0], ap[1], ap[2]);
     if (e != cudaSuccess) return e;
   }
   const long long nb = batch * N * K;
-  k_embed_split<PREC><<<(unsigned)std::min<long long>((nb + 255) / 256, 65535), 256, 0, s>>>(B, N, K, batch, bp[0],
-                                                                                           bp[1], bp[2]);
-  e = cudaGetLastError();
+  e = launch_pdl(k_embed_split<PREC>, dim3((unsigned)std::min<long long>((nb + 255) / 256, 65535)), dim3(256), 0, s,
+                 B, N, K, batch, bp[0], bp[1], bp[2]);
   if (e != cudaSuccess) return e;
   TmaMaps maps;
   std::memset(&maps, 0, sizeof(maps));
@@ -894,10 +900,9 @@ cudaError_t run_tc(long long batch, long long M, long long N, long long K, const
       const int tiles_n = (int)((2 * N) / BN), tiles_m = (int)(M / BM);
       const long long total = (long long)tiles_n * tiles_m * batch;
       const long long grid = std::min<long long>(total, num_sms());
-      k_cgemm_tc_stream<PREC><<<(unsigned)grid, kStreamThreads, smem, s>>>(
-          maps, k_tiles, tiles_n, tiles_m, total, M, 2 * N, reinterpret_cast<float *>(C),
-          static_cast<int *>(status_word_ptr()), om);
-      return cudaGetLastError();
+      return launch_pdl(k_cgemm_tc_stream<PREC>, dim3((unsigned)grid), dim3(kStreamThreads), smem, s, maps, k_tiles,
+                        tiles_n, tiles_m, total, M, 2 * N, reinterpret_cast<float *>(C),
+                        static_cast<int *>(status_word_ptr()), om);
     }
   }
   if constexpr (SPLIT_A && PREC == PREC_BF16) {
@@ -906,9 +911,8 @@ cudaError_t run_tc(long long batch, long long M, long long N, long long K, const
     e = ensure_smem(reinterpret_cast<const void *>(k_cgemm_tc<PREC, SPLIT_A>), smem);
     if (e != cudaSuccess) return e;
     dim3 grid((unsigned)((2 * N) / BN), (unsigned)(M / BM), (unsigned)batch);
-    k_cgemm_tc<PREC, SPLIT_A><<<grid, kThreads, smem, s>>>(maps, k_tiles, M, 2 * N, reinterpret_cast<float *>(C),
-                                                           static_cast<int *>(status_word_ptr()), om);
-    return cudaGetLastError();
+    return launch_pdl(k_cgemm_tc<PREC, SPLIT_A>, grid, dim3(kThreads), smem, s, maps, k_tiles, M, 2 * N,
+                      reinterpret_cast<float *>(C), static_cast<int *>(status_word_ptr()), om);
   }
 }
 

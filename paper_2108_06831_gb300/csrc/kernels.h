@@ -9,6 +9,30 @@ namespace tnq {
 
 int num_sms();  // SM count of the current device (cached per device)
 
+#ifdef __CUDACC__
+// Programmatic dependent launch (short kernels of the network path).  A kernel launched with
+// launch_pdl may be scheduled while the previous kernel on its stream is still running; it calls
+// pdl_wait() before it touches any memory (which returns once that kernel has completed and its
+// stores are visible), then pdl_trigger() to let the next such kernel be scheduled in turn.  In a
+// kernel launched the ordinary way both are no-ops.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+#endif
+
 // Matrix tables: write the complex64 entries of every slot for each batch element.
 cudaError_t launch_materialize(const MatSlot *d_slots, int n_slots, int n_fused_slots, const FusedMember *d_fused,
                                const double *params, int n_params, int batch, long long mstride, float2 *out,

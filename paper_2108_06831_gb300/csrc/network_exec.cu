@@ -31,6 +31,8 @@ struct OutDesc {  // one output closure on the device
 __global__ void k_build_outputs(const OutDesc *__restrict__ outs, int n_out, const uint64_t *__restrict__ xs,
                                 long long n_bits, long long B, int n_qubits, unsigned long long slice,
                                 float2 *__restrict__ ws) {
+  pdl_wait();
+  pdl_trigger();
   const long long total = (long long)n_out * B;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
     const int o = (int)(i / B);
@@ -53,6 +55,8 @@ __global__ void k_build_outputs(const OutDesc *__restrict__ outs, int n_out, con
 
 // Slice sum (FP64): acc[b] (+)= x[b] for the amplitudes of one slice.
 __global__ void k_slice_sum(double2 *__restrict__ acc, const float2 *__restrict__ x, long long n, int first) {
+  pdl_wait();
+  pdl_trigger();
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     const float2 v = x[i];
     if (first) {
@@ -65,6 +69,8 @@ __global__ void k_slice_sum(double2 *__restrict__ acc, const float2 *__restrict_
 }
 
 __global__ void k_slice_store(float2 *__restrict__ amps, const double2 *__restrict__ acc, long long n) {
+  pdl_wait();
+  pdl_trigger();
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     const double2 a = acc[i];
     amps[i] = make_float2((float)a.x, (float)a.y);
@@ -540,9 +546,9 @@ cudaError_t run_network(const NetPlan &net, const uint64_t *bitstrings, long lon
       // every slice: the closures' buffers are reused by later merges of the slice before
       if (net.n_outputs > 0) {
         const long long total = (long long)net.n_outputs * B;
-        k_build_outputs<<<(unsigned)std::min<long long>((total + 255) / 256, 65535), 256, 0, s>>>(
-            static_cast<const OutDesc *>(net.d_outputs), net.n_outputs, xs, nb, B, net.n, sl, w);
-        cudaError_t e = cudaGetLastError();
+        cudaError_t e = launch_pdl(k_build_outputs, dim3((unsigned)std::min<long long>((total + 255) / 256, 65535)),
+                                   dim3(256), 0, s, static_cast<const OutDesc *>(net.d_outputs), net.n_outputs, xs, nb,
+                                   B, net.n, sl, w);
         if (e != cudaSuccess) return e;
       }
       auto ptr = [&](int id) -> const float2 * {
@@ -558,15 +564,14 @@ cudaError_t run_network(const NetPlan &net, const uint64_t *bitstrings, long lon
         if (e != cudaSuccess) return e;
       }
       if (acc) {
-        k_slice_sum<<<grid_b, 256, 0, s>>>(acc, w + net.final_off, nb, sl == 0 ? 1 : 0);
-        cudaError_t e = cudaGetLastError();
+        cudaError_t e = launch_pdl(k_slice_sum, dim3(grid_b), dim3(256), 0, s, acc, (const float2 *)(w + net.final_off),
+                                   nb, sl == 0 ? 1 : 0);
         if (e != cudaSuccess) return e;
       }
     }
     cudaError_t e;
     if (acc) {
-      k_slice_store<<<grid_b, 256, 0, s>>>(amps + c0, acc, nb);
-      e = cudaGetLastError();
+      e = launch_pdl(k_slice_store, dim3(grid_b), dim3(256), 0, s, amps + c0, (const double2 *)acc, nb);
     } else {
       e = cudaMemcpyAsync(amps + c0, w + net.final_off, sizeof(float2) * (size_t)nb, cudaMemcpyDeviceToDevice, s);
     }
