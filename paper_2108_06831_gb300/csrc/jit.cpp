@@ -359,6 +359,9 @@ std::string gen_pass(const tn_plan &p, int pi, const std::vector<int> &op_kind, 
            NTHR, min_blocks, pi);
   E.line(buf);
   E.line("  extern __shared__ __align__(16) unsigned char smraw[];");
+  // launched as programmatic dependents: wait for the previous pass before any memory access
+  E.line("  asm volatile(\"griddepcontrol.wait;\" ::: \"memory\");");
+  E.line("  asm volatile(\"griddepcontrol.launch_dependents;\" ::: \"memory\");");
   const int nbuf = pd.init_mode ? 1 : 2;  // loaded passes double-buffer their tiles
   E.line("  float2 *const sm0 = reinterpret_cast<float2 *>(smraw);");
   snprintf(buf, sizeof buf, "  float2 *const sm1 = sm0 + %d;", (nbuf - 1) * TILE);
@@ -715,6 +718,9 @@ std::string gen_bwd_pass(const tn_plan &p, int pi, const std::vector<int> &op_ki
            NTHR, pi);
   E.line(buf);
   E.line("  extern __shared__ __align__(16) unsigned char smraw[];");
+  // launched as programmatic dependents: wait for the previous pass before any memory access
+  E.line("  asm volatile(\"griddepcontrol.wait;\" ::: \"memory\");");
+  E.line("  asm volatile(\"griddepcontrol.launch_dependents;\" ::: \"memory\");");
   E.line("  float2 *const p0 = reinterpret_cast<float2 *>(smraw);");
   // one psi and one lambda tile (no prefetch buffer): four CTAs per SM cover the load latency
   snprintf(buf, sizeof buf, "  float2 *const l0 = p0 + %d;", TILE);

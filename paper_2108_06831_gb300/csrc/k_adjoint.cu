@@ -246,8 +246,8 @@ cudaError_t launch_backward(const tn_plan *p, const float2 *mats, long long mstr
       const float2 *m = mats;
       int np = p->n_params;
       void *args[] = {(void *)&m, (void *)&mstride, (void *)&psi, (void *)&lam, (void *)&grad, (void *)&np};
-      e = cudaLaunchKernel((const void *)p->jit_bwd_kernels[i], dim3((unsigned)gx, (unsigned)p->batch), dim3(threads),
-                           args, smem, s);
+      e = launch_pdl_func((const void *)p->jit_bwd_kernels[i], dim3((unsigned)gx, (unsigned)p->batch), dim3(threads),
+                          args, smem, s);
       if (e != cudaSuccess) return e;
     }
     return cudaSuccess;

@@ -166,7 +166,8 @@ cudaError_t launch_fwd_k(const PassDesc &h, const PassDesc *d_pass, const PhaseD
 }
 }  // namespace
 
-cudaError_t launch_forward(const tn_plan *p, const float2 *mats, long long mstride, float2 *state, cudaStream_t s) {
+cudaError_t launch_forward(const tn_plan *p, const float2 *mats, long long mstride, float2 *state, cudaStream_t s,
+                           bool pdl) {
   if (!p->jit_kernels.empty()) {
     for (size_t i = 0; i < p->fwd.passes.size(); ++i) {
       const PassDesc &h = p->fwd.passes[i];
@@ -185,7 +186,8 @@ cudaError_t launch_forward(const tn_plan *p, const float2 *mats, long long mstri
         if (e != cudaSuccess) return e;
       }
       void *args[] = {(void *)&m, (void *)&mstride, (void *)&state, (void *)&work, (void *)&init};
-      e = cudaLaunchKernel((const void *)p->jit_kernels[i], dim3((unsigned)grid), dim3(threads), args, smem, s);
+      e = pdl ? launch_pdl_func((const void *)p->jit_kernels[i], dim3((unsigned)grid), dim3(threads), args, smem, s)
+              : cudaLaunchKernel((const void *)p->jit_kernels[i], dim3((unsigned)grid), dim3(threads), args, smem, s);
       if (e != cudaSuccess) return e;
     }
     return cudaSuccess;

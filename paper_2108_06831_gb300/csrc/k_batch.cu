@@ -502,7 +502,8 @@ cudaError_t batch_run(const tn_batch *b, const double *params, float2 *states, v
       const int i = b->direct[j];
       const tn_plan *p = b->plan_ptrs[(size_t)i];
       const float2 *m = p->param_dependent ? run_mats + b->mats_off[(size_t)i] : reinterpret_cast<const float2 *>(p->d_fixed_mats);
-      e = launch_forward(p, m, p->mstride, states + b->offsets[(size_t)i], b->side[(size_t)b->direct_stream[j]]);
+      e = launch_forward(p, m, p->mstride, states + b->offsets[(size_t)i], b->side[(size_t)b->direct_stream[j]],
+                         false);  // ordinary launches: the GPU is shared with the other streams
     }
     if (e != cudaSuccess) return e;
   }

@@ -31,6 +31,20 @@ cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t s
   cfg.numAttrs = 1;
   return cudaLaunchKernelEx(&cfg, kernel, args...);
 }
+// The same for a kernel known by address (generated kernels): args as for cudaLaunchKernel.
+inline cudaError_t launch_pdl_func(const void *func, dim3 grid, dim3 block, void **args, size_t smem, cudaStream_t s) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelExC(&cfg, func, args);
+}
 #endif
 
 // Matrix tables: write the complex64 entries of every slot for each batch element.
@@ -40,8 +54,11 @@ cudaError_t launch_materialize(const MatSlot *d_slots, int n_slots, int n_fused_
 // Reorders a slot table for launch_materialize (fused blocks first); returns their count.
 int order_slots_fused_first(std::vector<MatSlot> &slots);
 
-// Kernel (a): all forward passes of a plan (state <- U_G .. U_1 |init>).
-cudaError_t launch_forward(const tn_plan *p, const float2 *mats, long long mstride, float2 *state, cudaStream_t s);
+// Kernel (a): all forward passes of a plan (state <- U_G .. U_1 |init>).  Generated pass kernels
+// are launched as programmatic dependents of the previous pass (pdl) unless the caller shares the
+// GPU with other streams' work, where a pass waiting for its predecessor would hold SM resources.
+cudaError_t launch_forward(const tn_plan *p, const float2 *mats, long long mstride, float2 *state, cudaStream_t s,
+                           bool pdl = true);
 
 // Adjoint sweep: psi, lambda swept back through the gates; grad[b][k] accumulated (FP64).
 cudaError_t launch_backward(const tn_plan *p, const float2 *mats, long long mstride, float2 *psi, float2 *lam,
