@@ -166,6 +166,41 @@ __device__ __forceinline__ void reg_g2_dispatch(float2 (&a)[1 << K], int ra, int
   }
 }
 
+// SWAP of register bits RA and RB: exchange the amplitudes whose two bits differ.
+template <int K, int RA, int RB>
+__device__ __forceinline__ void reg_swap(float2 (&a)[1 << K]) {
+#pragma unroll
+  for (int j = 0; j < (1 << K); ++j)
+    if ((j & (1 << RA)) && !(j & (1 << RB))) {
+      const int j2 = (j & ~(1 << RA)) | (1 << RB);
+      const float2 t = a[j];
+      a[j] = a[j2];
+      a[j2] = t;
+    }
+}
+template <int K, int RA>
+__device__ __forceinline__ void reg_swap_b(float2 (&a)[1 << K], int rb) {
+  switch (rb) {
+    case 0: if constexpr (RA != 0) reg_swap<K, RA, 0>(a); break;
+    case 1: if constexpr (K > 1 && RA != 1) reg_swap<K, RA, 1>(a); break;
+    case 2: if constexpr (K > 2 && RA != 2) reg_swap<K, RA, 2>(a); break;
+    case 3: if constexpr (K > 3 && RA != 3) reg_swap<K, RA, 3>(a); break;
+    case 4: if constexpr (K > 4 && RA != 4) reg_swap<K, RA, 4>(a); break;
+  }
+}
+template <int K>
+__device__ __forceinline__ void reg_swap_dispatch(float2 (&a)[1 << K], int ra, int rb) {
+  if constexpr (K >= 2) {
+    switch (ra) {
+      case 0: reg_swap_b<K, 0>(a, rb); break;
+      case 1: reg_swap_b<K, 1>(a, rb); break;
+      case 2: if constexpr (K > 2) reg_swap_b<K, 2>(a, rb); break;
+      case 3: if constexpr (K > 3) reg_swap_b<K, 3>(a, rb); break;
+      case 4: if constexpr (K > 4) reg_swap_b<K, 4>(a, rb); break;
+    }
+  }
+}
+
 // diag(d0, d1) selected by mask m (1 -> d1).
 template <int K>
 __device__ __forceinline__ void reg_diag(float2 (&a)[1 << K], uint32_t m, float2 d0, float2 d1) {
@@ -186,8 +221,10 @@ __device__ __forceinline__ void reg_flush_sign(float2 (&a)[1 << K], uint32_t neg
 
 // Apply one op to the registers.  Sign flips of CZ ops accumulate in neg and are applied
 // lazily: they commute with every diagonal op and with every op whose register bits they do
-// not depend on; the planner sets OPF_FLUSH on the ops where that is not the case.
-template <int K>
+// not depend on; the planner sets OPF_FLUSH on the ops where that is not the case.  A SWAP is a
+// register exchange; SWAP_REGS = false applies it as the dense 4x4 permutation instead (one code
+// path for every two-qubit op, for kernels whose register budget the exchange code would exceed).
+template <int K, bool SWAP_REGS = true>
 __device__ __forceinline__ void apply_op(float2 (&a)[1 << K], const OpDesc &op, const BitCtx &c,
                                          const float2 *mats, uint32_t &neg) {
   switch (op.type) {
@@ -213,7 +250,8 @@ __device__ __forceinline__ void apply_op(float2 (&a)[1 << K], const OpDesc &op, 
         if (neg) reg_flush_sign<K>(a, neg);
         neg = 0;
       }
-      reg_g2_dispatch<K>(a, op.a_pos, op.b_pos, mats + op.mat, (op.flags & OPF_PACKED) != 0);
+      if (SWAP_REGS && (op.flags & OPF_SWAP)) reg_swap_dispatch<K>(a, op.a_pos, op.b_pos);
+      else reg_g2_dispatch<K>(a, op.a_pos, op.b_pos, mats + op.mat, (op.flags & OPF_PACKED) != 0);
       break;
     case OP_D1: {
       const float4 d = ld4(mats + op.mat);

@@ -223,7 +223,7 @@ __global__ void __launch_bounds__(kBatchThreads, 3) k_batch_exec(const BatchTask
         for (int o = ph.op_begin; o < ph.op_end; ++o) {
           OpDesc op;
           *reinterpret_cast<int4 *>(&op) = *reinterpret_cast<const int4 *>(ops + o);
-          apply_op<K>(a, op, ctx, mats, neg);
+          apply_op<K, false>(a, op, ctx, mats, neg);  // SWAP as a dense 4x4: 80 registers, 3 CTAs per SM
         }
         if (neg) reg_flush_sign<K>(a, neg);
 #pragma unroll

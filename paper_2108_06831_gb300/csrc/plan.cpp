@@ -65,7 +65,8 @@ GateCls classify(const TnGate &g) {
 // Real flops per amplitude of one op as executed (complex multiply = 6, add = 2; a real
 // coefficient times a complex value = 2): a general 2x2 costs 14, a matrix with a real first
 // column (V) 10, a real or real-diagonal/imaginary-off-diagonal one (RY, H, SY, RX, SX) 6;
-// a phase diag(1, e) touches half the amplitudes.
+// a phase diag(1, e) touches half the amplitudes; permutations (X, CNOT's target, SWAP) are
+// register exchanges.
 double op_flops(int type, int kind) {
   switch (type) {
     case OP_G1:
@@ -79,7 +80,7 @@ double op_flops(int type, int kind) {
         return 3.0;
       if (kind == TN_GATE_Z) return 0.0;
       return 6.0;
-    case OP_G2: return 30.0;
+    case OP_G2: return kind == TN_GATE_SWAP ? 0.0 : 30.0;  // a SWAP exchanges registers
     case OP_C1: return 7.0;
     case OP_DP: return 1.5;
     default: return 0.0;
@@ -590,6 +591,7 @@ tn_status build_pass_plan(const tn_circuit &c, int T, int K, bool adjoint, std::
         std::memset(&op, 0, sizeof(op));
         op.type = (uint8_t)gc.type;
         if (gc.shape == SHAPE_M4X) op.flags |= OPF_PACKED;
+        if (c.gates[g].kind == TN_GATE_SWAP) op.flags |= OPF_SWAP;
         src_of(gc.qa, op.a_kind, op.a_pos);
         if (gc.qb >= 0) src_of(gc.qb, op.b_kind, op.b_pos);
         op.mat = gc.shape >= 0 ? add_slot(g, adjoint ? FORM_ADJ : FORM_U, gc.shape) : 0;

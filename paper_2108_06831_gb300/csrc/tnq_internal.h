@@ -48,6 +48,7 @@ enum SrcKind : uint8_t { SRC_REG = 0, SRC_TILE = 1, SRC_GLOB = 2 };
 enum OpFlags : uint8_t {
   OPF_FLUSH = 1,   // apply the pending CZ signs first
   OPF_PACKED = 2,  // OP_G2 entries in the packed layout of SHAPE_M4X
+  OPF_SWAP = 4,    // OP_G2 of a SWAP: an exchange of registers, its entries are not read
 };
 
 struct alignas(16) OpDesc {
