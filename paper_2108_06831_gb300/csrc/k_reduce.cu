@@ -21,6 +21,7 @@
 namespace tnq {
 
 constexpr int kRedThreads = 256;
+constexpr int kRedGroup = 8;  // amplitudes a thread holds in registers at once (a tile gives it up to 16)
 constexpr int kRedMaxCTAs = 512;  // per pass and batch element
 
 namespace {
@@ -132,23 +133,50 @@ __global__ void __launch_bounds__(kRedThreads) k_expect_pass(const RedPass *__re
       sb[k] = (unsigned char)(__popcll(base & terms[rp.term_begin + k].zm) & 1);
     load_tile(sm, st, base, c);
     __syncthreads();
+    // the thread's amplitudes i = tid + j blockDim in registers and the terms in the outer loop, so
+    // each term's record is read once per tile; swz is linear, so a partner sits at swz(i) ^ swz(xl).
+    // Every amplitude still sums its terms in term order, and the thread its amplitudes in index
+    // order (the same bits as one amplitude at a time).
+    const int nj = c.tile < (int)blockDim.x ? 1 : c.tile / (int)blockDim.x;
+    const bool live0 = (int)threadIdx.x < c.tile;
     float tacc = 0.f;
-    for (int i = threadIdx.x; i < c.tile; i += blockDim.x) {
-      const float2 v = sm[swz(i)];
-      const float nrm = fmaf(v.x, v.x, v.y * v.y);
-      float s = 0.f;
+    for (int j0 = 0; j0 < nj && live0; j0 += kRedGroup) {
+      float2 v[kRedGroup];
+      float nrm[kRedGroup], sacc[kRedGroup];
+      int si[kRedGroup];
+#pragma unroll
+      for (int j = 0; j < kRedGroup; ++j) {
+        const int i = threadIdx.x + (j0 + j) * blockDim.x;
+        si[j] = swz(i);
+        v[j] = (j0 + j < nj) ? sm[si[j]] : make_float2(0.f, 0.f);
+        nrm[j] = fmaf(v[j].x, v[j].x, v[j].y * v[j].y);
+        sacc[j] = 0.f;
+      }
       for (int k = 0; k < nt; ++k) {
         const TermSm tm = st_terms[k];
-        const float sgn = ((__popc(i & tm.zl) ^ sb[k]) & 1) ? -tm.coef : tm.coef;
-        if (tm.xl == 0) {
-          s = fmaf(sgn, nrm, s);  // diagonal term (ny is even and i^ny = +-1)
+        const float c0 = sb[k] ? -tm.coef : tm.coef;
+        if (tm.xl == 0) {  // diagonal term (ny is even and i^ny = +-1)
+#pragma unroll
+          for (int j = 0; j < kRedGroup; ++j) {
+            const int i = threadIdx.x + (j0 + j) * blockDim.x;
+            sacc[j] = fmaf((__popc(i & tm.zl) & 1) ? -c0 : c0, nrm[j], sacc[j]);
+          }
           continue;
         }
-        const float2 w = sm[swz(i ^ tm.xl)];
-        const float2 z = make_float2(fmaf(w.x, v.x, w.y * v.y), fmaf(w.x, v.y, -w.y * v.x));  // conj(w) v
-        s = fmaf(sgn, times_i_pow(z, tm.ny).x, s);
+        const int sx = swz(tm.xl);
+#pragma unroll
+        for (int j = 0; j < kRedGroup; ++j) {
+          if (j0 + j >= nj) break;
+          const int i = threadIdx.x + (j0 + j) * blockDim.x;
+          const float sgn = (__popc(i & tm.zl) & 1) ? -c0 : c0;
+          const float2 w = sm[si[j] ^ sx];
+          const float2 z = make_float2(fmaf(w.x, v[j].x, w.y * v[j].y), fmaf(w.x, v[j].y, -w.y * v[j].x));  // conj(w) v
+          sacc[j] = fmaf(sgn, times_i_pow(z, tm.ny).x, sacc[j]);
+        }
       }
-      tacc += s;
+#pragma unroll
+      for (int j = 0; j < kRedGroup; ++j)
+        if (j0 + j < nj) tacc += sacc[j];
     }
     acc += (double)tacc;
     __syncthreads();
@@ -210,22 +238,45 @@ __global__ void __launch_bounds__(kRedThreads) k_hamiltonian_pass(const RedPass 
       sb[k] = (unsigned char)(__popcll(base & terms[rp.term_begin + k].zm) & 1);
     load_tile(sm, st, base, c);
     __syncthreads();
+    // as in k_expect_pass: the thread's amplitudes in registers, terms in the outer loop, every
+    // amplitude summing its terms in term order (the same bits as one amplitude at a time)
+    const int nj = c.tile < (int)blockDim.x ? 1 : c.tile / (int)blockDim.x;
+    const bool live0 = (int)threadIdx.x < c.tile;
     float tacc = 0.f;
-    for (int i = threadIdx.x; i < c.tile; i += blockDim.x) {
-      const unsigned long long x = base + (unsigned long long)c.run_off[i >> c.L] + (unsigned long long)(i & c.lowmask);
-      float2 s = accumulate ? lt[x] : make_float2(0.f, 0.f);
+    for (int j0 = 0; j0 < nj && live0; j0 += kRedGroup) {
+      float2 sacc[kRedGroup];
+      int si[kRedGroup];
+#pragma unroll
+      for (int j = 0; j < kRedGroup; ++j) {
+        const int i = threadIdx.x + (j0 + j) * blockDim.x;
+        si[j] = swz(i);
+        sacc[j] = make_float2(0.f, 0.f);
+        if (j0 + j < nj && accumulate)
+          sacc[j] = lt[base + (unsigned long long)c.run_off[i >> c.L] + (unsigned long long)(i & c.lowmask)];
+      }
       for (int k = 0; k < nt; ++k) {
         const TermSm tm = st_terms[k];
-        const int src = i ^ tm.xl;
-        const float sgn = ((__popc(src & tm.zl) ^ sb[k]) & 1) ? -tm.coef : tm.coef;
-        const float2 w = times_i_pow(sm[swz(src)], tm.ny);
-        s.x = fmaf(sgn, w.x, s.x);
-        s.y = fmaf(sgn, w.y, s.y);
+        const float c0 = sb[k] ? -tm.coef : tm.coef;
+        const int sx = swz(tm.xl);
+#pragma unroll
+        for (int j = 0; j < kRedGroup; ++j) {
+          if (j0 + j >= nj) break;
+          const int i = threadIdx.x + (j0 + j) * blockDim.x;
+          const float sgn = (__popc((i ^ tm.xl) & tm.zl) & 1) ? -c0 : c0;
+          const float2 w = times_i_pow(sm[si[j] ^ sx], tm.ny);
+          sacc[j].x = fmaf(sgn, w.x, sacc[j].x);
+          sacc[j].y = fmaf(sgn, w.y, sacc[j].y);
+        }
       }
-      lt[x] = s;
-      if (dot) {
-        const float2 v = sm[swz(i)];
-        tacc = fmaf(v.x, s.x, fmaf(v.y, s.y, tacc));
+#pragma unroll
+      for (int j = 0; j < kRedGroup; ++j) {
+        if (j0 + j >= nj) break;
+        const int i = threadIdx.x + (j0 + j) * blockDim.x;
+        lt[base + (unsigned long long)c.run_off[i >> c.L] + (unsigned long long)(i & c.lowmask)] = sacc[j];
+        if (dot) {
+          const float2 v = sm[si[j]];
+          tacc = fmaf(v.x, sacc[j].x, fmaf(v.y, sacc[j].y, tacc));
+        }
       }
     }
     acc += (double)tacc;
