@@ -78,6 +78,8 @@ def parse():
     ap.add_argument("--tile", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--order-trials", type=int, default=0,
+                    help="amps36: orders the contraction-path search tries (0: the planner's default)")
     ap.add_argument("--order-search", type=int, default=0,
                     help="network workloads: 1 = adaptive (cross-entropy) contraction-order search")
     ap.add_argument("--lanes", type=int, default=8,
@@ -580,7 +582,8 @@ def main():
         chunk = wl["chunk"]
         ctr = None
         plan = tn.Plan(tn.CircuitHandle(circ), target=tn.TARGET_AMPLITUDES, network_bitstrings=chunk,
-                       precision=args.prec, max_intermediate_log2=args.max_log2, order_search=args.order_search)
+                       precision=args.prec, max_intermediate_log2=args.max_log2, order_search=args.order_search,
+                       order_trials=args.order_trials)
         nst = plan.stats()
         aws = torch.empty(plan.workspace_bytes, dtype=torch.uint8, device=dev)
         xs_h = C.random_bitstrings(36, wl["batch"], wl["seed"] + 1)

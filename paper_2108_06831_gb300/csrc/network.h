@@ -51,6 +51,9 @@ constexpr double kFoldMaxWork = 2e8;   // complex multiply-adds over all folded 
 constexpr double kRidge = 32.0;
 constexpr double kLaunchBytes = 2e7;
 
+// Orders searched when the default search had to slice (plan_network's default is 256).
+constexpr int kSlicedTrials = 1024;
+
 // Slicing: at most 2^16 slices; the constant table of all slices at most 2^27 entries.
 constexpr int kMaxSliceBits = 16;
 constexpr long long kMaxTableEntries = 1ll << 27;
