@@ -254,3 +254,18 @@ def test_network_adaptive_search():
         assert a["net_cost"] <= greedy["net_cost"] and a["net_max_log2"] <= (cap or 28)
     with pytest.raises(tn.TnError):
         tn.Plan(tn.CircuitHandle(C.ghz(4)), order_search=2, **kw)
+
+
+def test_sliced_network_plans_search_wider():
+    """A network plan that had to slice is searched again with four times the orders and the cheaper
+    plan by the order cost is kept: under a 2^20 cap the default plan costs no more than the plan of
+    the 256-order search alone, and both fit the cap."""
+    from paper_2108_06831_gb300 import tn
+    ch = tn.CircuitHandle(C.grid(6, 6, 12, 3003))
+    kw = dict(target=tn.TARGET_AMPLITUDES, host_only=True, network_bitstrings=64, precision=tn.PREC_3XTF32,
+              max_intermediate_log2=20)
+    narrow = tn.Plan(ch, order_trials=256, **kw).stats()
+    default = tn.Plan(ch, **kw).stats()
+    assert narrow["net_sliced"] > 0
+    assert default["net_max_log2"] <= 20 and narrow["net_max_log2"] <= 20
+    assert default["net_cost"] <= narrow["net_cost"]
