@@ -757,6 +757,13 @@ def main():
         launches_per_step = None
         kernel_only = None
         bwd_alg_flops = (st["flops"] + st["bwd_flops"]) * batch
+        # algorithmic HBM bytes of the call: the forward passes (plan stats), the H psi passes (psi
+        # read and lambda written; lambda also read after the first), the adjoint passes (psi and
+        # lambda read and written: 32 B per amplitude)
+        obs_passes = tn.state_expectation_workspace_bytes(obs, 1) // (512 * 8)
+        amps_b = float(1 << wl["n"])
+        grad_alg_bytes = batch * (st["hbm_bytes"] + amps_b * (16.0 + 24.0 * (obs_passes - 1))
+                                  + amps_b * 32.0 * st["n_bwd_passes"])
 
     def timed(fn, k):
         times = []
@@ -1015,6 +1022,10 @@ def main():
                             "kernel": "tn_expectation_value_and_grad (tnq_p* forward + tnq_b* adjoint sweep)",
                             "algorithmic_flops_per_call": bwd_alg_flops,
                             "peak_source": FP32_ALU_PEAK_SRC}
+        gbs = grad_alg_bytes / (t_max / args.steps / 1000.0) / 1e9
+        line["roofline"]["also"] = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
+                                    "frac": gbs / hbm_peak, "algorithmic_bytes_per_call": grad_alg_bytes,
+                                    "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})"}
     if wl["kind"] == "serve":
         for _ in range(2):
             seq_step()
@@ -1040,6 +1051,12 @@ def main():
                             "frac": tfl / FP32_ALU_PEAK_TFLOPS, "traffic": None,
                             "kernel": "k_batch_exec + the wide circuits' tnq_p* (one graph)",
                             "peak_source": FP32_ALU_PEAK_SRC}
+        # the same step against HBM: every circuit's passes (8 B per amplitude for the first, 16 after)
+        sbytes = sum(p.stats()["hbm_bytes"] for p in plans)
+        gbs = sbytes / (t_max / args.steps / 1000.0) / 1e9
+        line["roofline"]["also"] = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
+                                    "frac": gbs / hbm_peak, "algorithmic_bytes_per_step": sbytes,
+                                    "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})"}
     if wl["kind"] == "sweep":
         # amplitudes/s of every (n, k) point, each timed on its own; the roofline is the largest
         # point's (n = 28, k = 14: 2 GiB state) gate work against the FP32 ALU peak
