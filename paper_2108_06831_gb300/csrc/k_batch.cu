@@ -467,12 +467,7 @@ tn_status batch_build(const tn_plan *const *plans, int n, tn_batch **out) {
   if (!all_slots.empty()) up(all_slots.data(), sizeof(MatSlot) * all_slots.size(), (void **)&b->d_slots);
   if (!all_fused.empty()) up(all_fused.data(), sizeof(FusedMember) * all_fused.size(), (void **)&b->d_fused);
   if (e != cudaSuccess) {
-    cudaFree(b->d_tasks);
-    cudaFree(b->d_circs);
-    cudaFree(b->d_passes);
-    cudaFree(b->d_slots);
-    cudaFree(b->d_fused);
-    delete b;
+    batch_free(b);  // the tables allocated so far, the side streams and their events
     return cuda_fail(e, "batched executor tables");
   }
   *out = b;
