@@ -151,6 +151,16 @@ def load_peaks():
         return 6800.0, "fallback"
 
 
+def load_bf16_peak():
+    """Dense BF16 tensor rate (TFLOP/s, burst) and where it came from: the measured figure, else the
+    fallback of an earlier GB300 measurement (1.9 PFLOP/s)."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"]), "MEASURED_PEAKS.json bf16_tflops"
+    except Exception:
+        return 1900.0, "fallback bf16 1900 TFLOP/s (no MEASURED_PEAKS.json)"
+
+
 # ----------------------------------------------------------------------------- clocks
 
 class ClockSampler:
@@ -841,17 +851,12 @@ def main():
                 tpk, tsrc, tk = alu_frac, FP32_ALU_PEAK_SRC, "alu"
                 tpeak, tach = FP32_ALU_PEAK_TFLOPS, tfl
             else:
-                bf16 = 1886.8
-                try:
-                    with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-                        bf16 = float(json.load(f)["bf16_tflops"])
-                except Exception:
-                    pass
+                bf16, bsrc = load_bf16_peak()
                 products = 3 if bprec == 1 else 6
                 tpeak = bf16 * (1.1 / 2.25) if bprec == 1 else bf16
                 tach = products * tfl
                 tpk, tk = tach / tpeak, "tensor"
-                tsrc = "MEASURED_PEAKS.json bf16_tflops" + (" x 1.1/2.25 (TF32 nominal ratio)" if bprec == 1 else "")
+                tsrc = bsrc + (" x 1.1/2.25 (TF32 nominal ratio)" if bprec == 1 else "")
             kname = ("k_cgemm_tc_stream (batched complex GEMM, tcgen05)" if bprec else "k_cgemm_fp32 (batched complex GEMM)")
             if tpk >= hbm_frac:
                 line["roofline"] = {"bound": tk, "achieved": tach, "peak": tpeak, "unit": "TFLOP/s", "frac": tpk,
@@ -874,6 +879,13 @@ def main():
                                 "traffic": None, "kernel": "tnq_p* (fused gate-apply pass kernels)",
                                 "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})",
                                 "also": {"tflops": tfl, "alu_frac": alu_frac}}
+        if wl["kind"] == "state" and not args.blocks:
+            # the same circuit applied one gate at a time, each gate a pass over the state (16 B per
+            # amplitude): the traffic the fused passes avoid
+            ub = 16.0 * (1 << wl["n"]) * batch * len(circ_f.gates)
+            line["roofline"]["unfused_gate_by_gate"] = {
+                "bytes_per_step": ub, "equivalent_gbs": ub / (t_max / args.steps / 1000.0) / 1e9,
+                "passes_avoided": len(circ_f.gates) - kernel_launches}
         if args.workload == "state24" and not args.tile and not args.no_specialize and not args.no_fuse:
             line["roofline"]["traffic"] = recorded_traffic(kernel_hash)
             line["roofline"]["kernel_source_hash"] = kernel_hash
@@ -1195,12 +1207,7 @@ def main():
     if wl["kind"] == "gemm":
         # tensor-pipe roofline of the whole call (operand split + GEMM), against the peak of the
         # arithmetic the tensor cores run: TF32 = measured bf16 peak x nominal 1.1/2.25
-        bf16_peak = 1886.8
-        try:
-            with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-                bf16_peak = float(json.load(f)["bf16_tflops"])
-        except Exception:
-            pass
+        bf16_peak, bf16_src = load_bf16_peak()
         per_step_s = t_max / args.steps / 1000.0
         alg = 8.0 * batch * wl["M"] * wl["N"] * wl["K"]
         alg_bytes = 8.0 * batch * (wl["M"] * wl["K"] + wl["N"] * wl["K"] + wl["M"] * wl["N"])
@@ -1221,8 +1228,7 @@ def main():
             comp = {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                     "frac": ach / peak, "traffic": None,
                     "kernel": "k_cgemm_tc / k_cgemm_tc_stream (+ operand split kernels)",
-                    "peak_source": "MEASURED_PEAKS.json bf16_tflops" + (" x 1.1/2.25 (TF32 nominal ratio)"
-                                                                       if wl["prec"] == 1 else "")}
+                    "peak_source": bf16_src + (" x 1.1/2.25 (TF32 nominal ratio)" if wl["prec"] == 1 else "")}
         hbm["kernel"] = comp["kernel"]
         # the binding roof is the one the kernel is closest to
         line["roofline"] = dict(comp if comp["frac"] >= hbm["frac"] else hbm)
