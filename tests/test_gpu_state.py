@@ -180,7 +180,7 @@ def test_fig31_largest_point_against_stored_oracle():
     nx = torch.linalg.vector_norm(x.to(torch.complex128)).item()
     assert abs(nx - 1.0) <= 1e-5
     got = x[torch.as_tensor(xs, device="cuda")].cpu().numpy()
-    # amplitudes of a 2^28-entry state are ~2^-14: judge them against the state's RMS scale
+    # amplitudes of a 2^28-entry state are ~2^-14: compare them against the state's RMS scale
     err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
     assert err <= 1e-5, err
 
