@@ -92,7 +92,17 @@ struct TermSm {
   int xl;   // tile-local flip mask
   int zl;   // tile-local Z/Y mask
   int ny;
+  // sign parity of the tile bits above the thread bits: bit J is the parity of ((J << 8) ^ f) & zl
+  // above bit 7, J = the 256-amplitude row of a tile index (f = xl for H psi, 0 for <P>), so the
+  // parity of (i ^ f) & zl for i = tid + 256 J is that bit xor a per-thread one
+  int hi;
 };
+// hi of a term: the parities for J = 0 .. 15 (tiles of at most 2^12 amplitudes)
+__device__ __forceinline__ int row_parities(int f, int zl) {
+  int h = 0;
+  for (int J = 0; J < 16; ++J) h |= (__popc(((J << 8) ^ f) & zl & ~0xFF) & 1) << J;
+  return h;
+}
 
 __device__ __forceinline__ int compress_bits(unsigned long long v, const RedPass &rp) {
   int r = 0;
@@ -120,7 +130,8 @@ __global__ void __launch_bounds__(kRedThreads) k_expect_pass(const RedPass *__re
   setup_tile(rp, run_off, c);
   for (int k = threadIdx.x; k < nt; k += blockDim.x) {
     const DevTerm &tm = terms[rp.term_begin + k];
-    st_terms[k] = TermSm{(float)tm.coef, tm.xl, compress_bits(tm.zm, rp), tm.ny};
+    const int zl = compress_bits(tm.zm, rp);
+    st_terms[k] = TermSm{(float)tm.coef, tm.xl, zl, tm.ny, row_parities(0, zl)};
   }
   __syncthreads();
   const int b = blockIdx.y;
@@ -155,20 +166,18 @@ __global__ void __launch_bounds__(kRedThreads) k_expect_pass(const RedPass *__re
       for (int k = 0; k < nt; ++k) {
         const TermSm tm = st_terms[k];
         const float c0 = sb[k] ? -tm.coef : tm.coef;
+        // parity of i & zl = bit J of tm.hi, flipped in every bit by this thread's part (bits 0..7)
+        const int par = (tm.hi >> j0) ^ -(__popc((int)threadIdx.x & tm.zl & 0xFF) & 1);
         if (tm.xl == 0) {  // diagonal term (ny is even and i^ny = +-1)
 #pragma unroll
-          for (int j = 0; j < kRedGroup; ++j) {
-            const int i = threadIdx.x + (j0 + j) * blockDim.x;
-            sacc[j] = fmaf((__popc(i & tm.zl) & 1) ? -c0 : c0, nrm[j], sacc[j]);
-          }
+          for (int j = 0; j < kRedGroup; ++j) sacc[j] = fmaf(((par >> j) & 1) ? -c0 : c0, nrm[j], sacc[j]);
           continue;
         }
         const int sx = swz(tm.xl);
 #pragma unroll
         for (int j = 0; j < kRedGroup; ++j) {
           if (j0 + j >= nj) break;
-          const int i = threadIdx.x + (j0 + j) * blockDim.x;
-          const float sgn = (__popc(i & tm.zl) & 1) ? -c0 : c0;
+          const float sgn = ((par >> j) & 1) ? -c0 : c0;
           const float2 w = sm[si[j] ^ sx];
           const float2 z = make_float2(fmaf(w.x, v[j].x, w.y * v[j].y), fmaf(w.x, v[j].y, -w.y * v[j].x));  // conj(w) v
           sacc[j] = fmaf(sgn, times_i_pow(z, tm.ny).x, sacc[j]);
@@ -223,7 +232,8 @@ __global__ void __launch_bounds__(kRedThreads) k_hamiltonian_pass(const RedPass 
   setup_tile(rp, run_off, c);
   for (int k = threadIdx.x; k < nt; k += blockDim.x) {
     const DevTerm &tm = terms[rp.term_begin + k];
-    st_terms[k] = TermSm{(float)tm.coef, tm.xl, compress_bits(tm.zm, rp), tm.ny};
+    const int zl = compress_bits(tm.zm, rp);
+    st_terms[k] = TermSm{(float)tm.coef, tm.xl, zl, tm.ny, row_parities(tm.xl, zl)};
   }
   __syncthreads();
   const int b = blockIdx.y;
@@ -258,11 +268,12 @@ __global__ void __launch_bounds__(kRedThreads) k_hamiltonian_pass(const RedPass 
         const TermSm tm = st_terms[k];
         const float c0 = sb[k] ? -tm.coef : tm.coef;
         const int sx = swz(tm.xl);
+        // parity of (i ^ xl) & zl = bit J of tm.hi, flipped in every bit by this thread's part (bits 0..7)
+        const int par = (tm.hi >> j0) ^ -(__popc(((int)threadIdx.x ^ tm.xl) & tm.zl & 0xFF) & 1);
 #pragma unroll
         for (int j = 0; j < kRedGroup; ++j) {
           if (j0 + j >= nj) break;
-          const int i = threadIdx.x + (j0 + j) * blockDim.x;
-          const float sgn = (__popc((i ^ tm.xl) & tm.zl) & 1) ? -c0 : c0;
+          const float sgn = ((par >> j) & 1) ? -c0 : c0;
           const float2 w = times_i_pow(sm[si[j] ^ sx], tm.ny);
           sacc[j].x = fmaf(sgn, w.x, sacc[j].x);
           sacc[j].y = fmaf(sgn, w.y, sacc[j].y);
@@ -294,7 +305,7 @@ size_t red_smem(const RedPass &rp) {
   const int L = T < kLowBits ? T : kLowBits;
   const size_t runs = ((size_t)1 << (T - L)) < 2 ? 2 : ((size_t)1 << (T - L));
   const size_t nt = (size_t)(rp.term_end - rp.term_begin);
-  return ((size_t)1 << T) * sizeof(float2) + runs * sizeof(long long) + nt * 16 + ((nt + 15) & ~(size_t)15);
+  return ((size_t)1 << T) * sizeof(float2) + runs * sizeof(long long) + nt * sizeof(TermSm) + ((nt + 15) & ~(size_t)15);
 }
 int red_grid_x(const tn_observable *o, int pass, int batch, const void *fn) {
   const RedPass &rp = o->passes[pass];
