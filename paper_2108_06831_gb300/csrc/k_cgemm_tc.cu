@@ -54,6 +54,7 @@ static_assert(BN / 2 == 1 << kColBits, "column table covers one tile");
 constexpr int kMain = 3;                      // leading-product accumulators, used round robin by K tile
 constexpr int kTmemCols = (kMain + 1) * BN;   // + one correction accumulator = all 512 columns
 constexpr unsigned long long kWaitNs = 2000000000ull;  // bound of every mbarrier wait
+constexpr int kRasterRows = 8;  // row tiles per group of the tile order (k_cgemm_tc)
 
 enum : int { PREC_TF32 = 1, PREC_BF16 = 2 };
 
@@ -236,7 +237,21 @@ __global__ void __launch_bounds__(kThreads, 1) k_cgemm_tc(const __grid_constant_
   __shared__ long long ctab[BN / 2];
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int n0 = blockIdx.x * BN, m0 = blockIdx.y * BM, bz = blockIdx.z;
+  // tile order: CTAs launch in linear order; consecutive CTAs walk kRasterRows row tiles before the
+  // next column tile, so the CTAs resident at once read few A and B panels and the panels they share
+  // stay in L2 (row-major order would re-read every B panel once per wave of CTAs)
+  int n0, m0;
+  {
+    const int tn = (int)gridDim.x, tm = (int)gridDim.y;
+    const int pid = (int)blockIdx.y * tn + (int)blockIdx.x;
+    const int group = pid / (kRasterRows * tn);
+    const int first = group * kRasterRows;
+    const int rows = tm - first < kRasterRows ? tm - first : kRasterRows;
+    const int in = pid - group * kRasterRows * tn;
+    m0 = (first + in % rows) * BM;
+    n0 = (in / rows) * BN;
+  }
+  const int bz = blockIdx.z;
   if (threadIdx.x < BN / 2) ctab[threadIdx.x] = om.identity ? 0 : map_bits(om, threadIdx.x, 0);
 
   if (threadIdx.x == 0) {
