@@ -346,8 +346,12 @@ std::string gen_pass(const tn_plan &p, int pi, const std::vector<int> &op_kind, 
   // constant cache, no shared-memory copy and no registers to hold them.  Otherwise staged in
   // shared memory per batch element.
   const bool cmem = jit_const_mats(p);
-  // resident CTAs per SM requested from the register allocator (TNQ_JIT_MIN_BLOCKS, default 2)
-  int min_blocks = 2;
+  // resident CTAs per SM requested from the register allocator (TNQ_JIT_MIN_BLOCKS overrides): three
+  // when the entries come from constant memory (a few spilled registers, but a third CTA covers
+  // another's barriers and tile loads: 1% faster alone, 7% on the serving mix, whose wide circuits share
+  // the SMs across streams); two when each batch element's entries are staged in shared memory (the
+  // 64-set adjoint configuration's forward passes ran 8% slower at three)
+  int min_blocks = cmem ? 3 : 2;
   if (const char *mb = getenv("TNQ_JIT_MIN_BLOCKS")) min_blocks = std::max(1, std::min(4, atoi(mb)));
   if (cmem) {
     snprintf(buf, sizeof buf, "__constant__ float4 tnq_cm%d[%d];", pi, std::max(1, mat_n / 2));
