@@ -332,7 +332,9 @@ def cgemm_batched(precision: int, batch: int, M: int, N: int, K: int, A, B, Cm, 
 
 
 class Batch:
-    """Many fixed-angle circuits contracted by one persistent launch (tn_batch_*)."""
+    """Many circuits (fixed angles, or parameters read per run) contracted by one persistent launch
+    (tn_batch_*); circuits of 19 qubits and more whose plans carry generated kernels run those on
+    the batch's side streams beside it."""
 
     def __init__(self, plans: Sequence[Plan]):
         arr = (_vp * len(plans))(*[p._h for p in plans])
