@@ -716,10 +716,13 @@ std::string gen_bwd_pass(const tn_plan &p, int pi, const std::vector<int> &op_ki
     snprintf(buf, sizeof buf, "__device__ const int tnq_bp%d[%d] = {", pi, SLOTS);
     E.line(std::string(buf) + tab + "};");
   }
+  // resident CTAs per SM requested from the register allocator (TNQ_JIT_BWD_MIN_BLOCKS overrides)
+  int bwd_blocks = 4;
+  if (const char *mb = getenv("TNQ_JIT_BWD_MIN_BLOCKS")) bwd_blocks = std::max(1, std::min(8, atoi(mb)));
   snprintf(buf, sizeof buf,
-           "extern \"C\" __global__ void __launch_bounds__(%d, 4) tnq_b%d(const float2 *__restrict__ mats_g, long long mstride, "
+           "extern \"C\" __global__ void __launch_bounds__(%d, %d) tnq_b%d(const float2 *__restrict__ mats_g, long long mstride, "
            "float2 *__restrict__ psi, float2 *__restrict__ lam, double *__restrict__ grad, int n_params) {",
-           NTHR, pi);
+           NTHR, bwd_blocks, pi);
   E.line(buf);
   E.line("  extern __shared__ __align__(16) unsigned char smraw[];");
   // launched as programmatic dependents: wait for the previous pass before any memory access
