@@ -269,3 +269,22 @@ def test_sliced_network_plans_search_wider():
     assert narrow["net_sliced"] > 0
     assert default["net_max_log2"] <= 20 and narrow["net_max_log2"] <= 20
     assert default["net_cost"] <= narrow["net_cost"]
+
+
+def test_generated_kernels_compile_without_a_device(tmp_path, monkeypatch):
+    """The plan-specialised kernels (forward passes with fused 4x4 blocks and constant tables, the
+    adjoint passes with derivative dots) are generated and compiled by NVRTC for sm_103a on the host,
+    without loading them: a code-generation error fails the plan here, before any GPU run."""
+    from paper_2108_06831_gb300 import tn
+    dump = tmp_path / "src"
+    monkeypatch.setenv("TNQ_JIT_COMPILE_CHECK", "1")
+    monkeypatch.setenv("TNQ_JIT_DUMP_DIR", str(dump))
+    monkeypatch.setenv("TNQ_CACHE_DIR", str(tmp_path / "cache"))
+    circ, _ = C.brickwork(16, 6, 5, parameterized=True)  # fused blocks (16 >= 14 qubits), first-pass skip
+    tn.Plan(tn.CircuitHandle(circ), host_only=True)
+    tn.Plan(tn.CircuitHandle(C.qft(15, 1234)), host_only=True)  # SWAPs as register exchanges
+    tn.Plan(tn.CircuitHandle(C.hea(14, 2)), target=tn.TARGET_EXPECTATION, batch=4, host_only=True)
+    srcs = [f.read_text() for f in dump.glob("*.cu")]
+    assert any("tnq_p" in t for t in srcs) and any("tnq_b" in t for t in srcs)
+    assert all("griddepcontrol.wait" in t for t in srcs)  # every pass waits for its predecessor
+    assert any("fma.rn.f32x2" in t for t in srcs)
